@@ -1,0 +1,187 @@
+/*
+ * passjoin.h -- C ABI of the GB300 Pass-Join edit-distance similarity join.
+ *
+ * Problem (Def. 1, Sec. 2 of the Pass-Join paper): given string sets R and S
+ * and an edit-distance threshold tau, find every pair <r, s> in R x S with
+ * ED(r, s) <= tau, where ED counts single-character insertions, deletions
+ * and substitutions.  R = S is the self join (Sec. 2); R != S is the join of
+ * Sec. 3.2.  Every call returns the exact pair set of that definition with
+ * the exact ED of each pair.
+ *
+ * Method (all of it runs in this library's CUDA kernels on one GPU):
+ *   - strings are grouped by length and each string of length >= tau + 1 is
+ *     cut into tau + 1 even segments (Sec. 3.1), kept in a segment index keyed
+ *     by (string length l, segment number i, segment content) (Sec. 3.2);
+ *   - every probing string selects its multi-match-aware substrings for each
+ *     admissible length l (Sec. 4.2, Alg. 2, Lemma 2) and looks them up;
+ *   - every hit is checked by extension-based verification (Sec. 5.2, Alg. 3)
+ *     built on length-aware banded DP with expected-edit-distance early
+ *     termination (Sec. 5.1, Lemma 4).
+ *
+ * Conventions shared by every entry point:
+ *   - Return value: PJ_OK (0) or a negative PJ_E* code.  pj_strerror() names a
+ *     code; pj_last_error() gives the calling thread's last detailed message.
+ *   - Strings are byte strings of length 0..65535.  A string set is the
+ *     concatenation of its strings (bytes) plus n + 1 non-decreasing offsets;
+ *     string k is bytes[offsets[k] .. offsets[k+1]).  offsets[0] need not be 0.
+ *   - pj_strings.on_device = 0: bytes and offsets are host pointers;
+ *     on_device = 1: device pointers on the library's device.  The caller owns
+ *     them; they are read during the call only and may be freed afterwards.
+ *   - 0 <= tau <= PJ_TAU_LIMIT.  Ids are 0-based input positions.
+ *   - Results are library-allocated (host memory unless
+ *     pj_options.results_on_device = 1), sorted by (a, b), released with
+ *     pj_result_free().
+ *   - All device work of a call is ordered on pj_options.stream; a call
+ *     returns after its results are complete.
+ */
+#ifndef PASSJOIN_H
+#define PASSJOIN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PJ_TAU_LIMIT 32     /* largest threshold the kernels accept */
+#define PJ_MAX_STRING_LEN 65535
+
+enum {
+  PJ_OK = 0,
+  PJ_EINVAL = -1,     /* bad argument: NULL, tau out of range, offsets decreasing, string too long */
+  PJ_ENOMEM = -2,     /* a device or host allocation failed */
+  PJ_ECUDA = -3,      /* a CUDA runtime call or kernel failed (see pj_last_error) */
+  PJ_ETIMEDOUT = -4,  /* a bounded wait expired (serving) */
+  PJ_ECANCELED = -5   /* the request was cancelled (serving) */
+};
+
+/* verify_mode values (pj_options.verify_mode) */
+enum {
+  PJ_VERIFY_AUTO = 0,       /* library's choice (currently: extension) */
+  PJ_VERIFY_EXTENSION = 1   /* extension-based verification (Sec. 5.2, Alg. 3) */
+};
+
+/* A set of n strings; see the conventions above. */
+typedef struct {
+  const uint8_t* bytes;
+  const uint64_t* offsets; /* n + 1 entries */
+  uint32_t n;
+  int on_device;
+} pj_strings;
+
+/* One similar pair.  Self join: a < b are input ids of the one set.
+ * pj_join: a indexes R, b indexes S.  pj_query: a indexes the query batch,
+ * b indexes the indexed set.  ed = ED(a, b) exactly, 0 <= ed <= tau. */
+typedef struct {
+  uint32_t a;
+  uint32_t b;
+  uint32_t ed;
+} pj_pair;
+
+/* Work counters of one call (all exact counts). */
+typedef struct {
+  uint64_t lookups;     /* selected substrings looked up in the segment index */
+  uint64_t candidates;  /* (probe, indexed string, segment, position) matches verified */
+  uint64_t accepted;    /* matches accepted by extension verification */
+  uint64_t dp_cells;    /* DP cells evaluated by the verification kernels */
+  uint64_t fallback_pairs; /* pairs verified directly because a string has length <= tau */
+} pj_stats;
+
+typedef struct {
+  pj_pair* pairs;   /* count entries; host memory, or device memory if on_device */
+  uint64_t count;
+  int on_device;
+  pj_stats stats;
+  void* priv;       /* library-owned; do not touch */
+} pj_result;
+
+/* Device memory provider.  alloc returns device memory of at least `bytes`
+ * bytes usable on `stream` (NULL on failure); free releases it. */
+typedef void* (*pj_alloc_fn)(void* ctx, size_t bytes, void* stream);
+typedef void (*pj_free_fn)(void* ctx, void* ptr, void* stream);
+
+typedef struct {
+  void* stream;           /* cudaStream_t for all device work; NULL = default stream */
+  pj_alloc_fn alloc;      /* NULL = cudaMallocAsync on the stream */
+  pj_free_fn free;        /* must be set iff alloc is set */
+  void* alloc_ctx;
+  int verify_mode;        /* PJ_VERIFY_* */
+  int results_on_device;  /* 1: pj_result.pairs stays in device memory */
+} pj_options;
+
+typedef struct pj_index pj_index; /* opaque, library-owned */
+
+/* Fill *opt with defaults (default stream, cudaMallocAsync, auto verify,
+ * host results). */
+void pj_options_init(pj_options* opt);
+
+/*
+ * pj_build_index -- build the resident segment index of S for every
+ * threshold 0..tau_max (Sec. 3.1 even partition, Sec. 3.2 index
+ * L_l^i keyed by length, segment number and segment content).
+ *   S       : the strings to index (host or device; see conventions).
+ *   tau_max : 0..PJ_TAU_LIMIT.
+ *   opt     : stream and allocator used for the index's whole life (copied).
+ *             NULL = defaults.
+ *   out     : receives the index; release with pj_index_free().
+ * Errors: PJ_EINVAL (NULL S/out, tau_max out of range, decreasing offsets,
+ * a string longer than PJ_MAX_STRING_LEN), PJ_ENOMEM, PJ_ECUDA.  On error
+ * *out is NULL.
+ */
+int pj_build_index(const pj_strings* S, int tau_max, const pj_options* opt, pj_index** out);
+
+/*
+ * pj_self_join -- Def. 1 with R = S over the indexed set (Alg. 1): every
+ * unordered pair of distinct ids a < b with ED <= tau.  Equal strings with
+ * different ids are reported with ed = 0.
+ *   idx : from pj_build_index; tau : 0..tau_max of idx.
+ *   out : receives the result (stream, allocator and results_on_device of
+ *         the index's options).
+ * Errors: PJ_EINVAL (NULL, tau out of range), PJ_ENOMEM, PJ_ECUDA.
+ */
+int pj_self_join(pj_index* idx, int tau, pj_result* out);
+
+/*
+ * pj_join -- Def. 1 for two sets (Sec. 3.2: index S, probe every r of R over
+ * the lengths [|r| - tau, |r| + tau]).  Builds a temporary index of S for
+ * this tau only.
+ *   R, S : string sets (host or device); tau : 0..PJ_TAU_LIMIT;
+ *   opt  : NULL = defaults.  out: pairs (a in R, b in S).
+ * Errors as pj_build_index / pj_self_join.
+ */
+int pj_join(const pj_strings* R, const pj_strings* S, int tau, const pj_options* opt,
+            pj_result* out);
+
+/*
+ * pj_query -- probe a batch of query strings against a resident index
+ * (Sec. 3.2 join with R = the batch): pairs (a = query position, b = indexed
+ * id) with ED <= tau.  Uses the index's stream and allocator; concurrent
+ * calls on one index from several host threads are serialised by the
+ * library.
+ *   idx : from pj_build_index; batch : query strings (host or device);
+ *   tau : 0..tau_max of idx.
+ * Errors: PJ_EINVAL, PJ_ENOMEM, PJ_ECUDA.
+ */
+int pj_query(pj_index* idx, const pj_strings* batch, int tau, pj_result* out);
+
+/* Number of strings / largest tau of an index (0 for NULL). */
+uint32_t pj_index_size(const pj_index* idx);
+int pj_index_tau_max(const pj_index* idx);
+/* Device bytes held by the index (store + every threshold's tables). */
+uint64_t pj_index_device_bytes(const pj_index* idx);
+
+/* Release a result / an index.  NULL and already-released results are
+ * ignored.  A result must be released before the index it came from. */
+void pj_result_free(pj_result* res);
+void pj_index_free(pj_index* idx);
+
+/* Static name of an error code; message of the calling thread's last error. */
+const char* pj_strerror(int code);
+const char* pj_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PASSJOIN_H */

@@ -1,0 +1,138 @@
+// Shared host/device plumbing of the Pass-Join CUDA library: error
+// propagation, the caller-supplied (or stream-ordered) device allocator, RAII
+// device buffers and a few warp helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <utility>
+
+#include "passjoin.h"
+
+namespace pj {
+
+// ----------------------------------------------------------------- errors --
+
+struct Error {
+  int code;
+  std::string msg;
+};
+
+[[noreturn]] void fail(int code, const std::string& msg);
+void check_cuda(cudaError_t e, const char* what, const char* file, int line);
+#define PJ_CUDA(call) ::pj::check_cuda((call), #call, __FILE__, __LINE__)
+#define PJ_LAUNCHED(name) ::pj::check_cuda(cudaGetLastError(), name, __FILE__, __LINE__)
+
+// -------------------------------------------------------------- allocator --
+
+// Device memory and the stream every piece of work of one call is ordered on.
+struct Ctx {
+  cudaStream_t stream = nullptr;
+  pj_alloc_fn alloc = nullptr;
+  pj_free_fn free_fn = nullptr;
+  void* alloc_ctx = nullptr;
+
+  void* get(size_t bytes) const;
+  void put(void* p) const;
+  void sync() const { PJ_CUDA(cudaStreamSynchronize(stream)); }
+};
+
+Ctx make_ctx(const pj_options* opt);
+
+// Phase trace on stderr, enabled by the environment variable PJ_TRACE=1: each
+// call synchronises the stream and prints the time since the previous mark.
+void trace_mark(const Ctx& c, const char* phase);
+// Same trace, without synchronising (marks host-side progress only).
+void trace_note(const char* what);
+
+// Device array of T obtained from a Ctx; freed (stream-ordered) on scope exit.
+template <class T>
+struct DBuf {
+  const Ctx* ctx = nullptr;
+  T* p = nullptr;
+  size_t n = 0;
+
+  DBuf() = default;
+  DBuf(const Ctx& c, size_t count) { reset(c, count); }
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  DBuf(DBuf&& o) noexcept { *this = std::move(o); }
+  DBuf& operator=(DBuf&& o) noexcept {
+    if (this != &o) {
+      release();
+      ctx = o.ctx;
+      p = o.p;
+      n = o.n;
+      o.p = nullptr;
+      o.n = 0;
+    }
+    return *this;
+  }
+  ~DBuf() { release(); }
+
+  void reset(const Ctx& c, size_t count) {
+    release();
+    ctx = &c;
+    n = count;
+    p = static_cast<T*>(c.get((count ? count : 1) * sizeof(T)));
+  }
+  void release() {
+    if (p && ctx) ctx->put(p);
+    p = nullptr;
+    n = 0;
+  }
+  T* get() const { return p; }
+  size_t bytes() const { return n * sizeof(T); }
+};
+
+// ------------------------------------------------------------ small utils --
+
+inline unsigned ceil_div(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
+inline int bits_for(uint64_t v) {  // bits needed to hold values < v (at least 1)
+  int b = 1;
+  while (b < 64 && (uint64_t(1) << b) < v) ++b;
+  return b;
+}
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Inclusive warp scan (all 32 lanes participate).
+template <class T>
+__device__ __forceinline__ T warp_incl_scan(T v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T t = __shfl_up_sync(FULL, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return v;
+}
+
+// Number of lanes whose (non-decreasing) inclusive prefix value is <= f,
+// i.e. the lane that owns flat item f.  Every lane must call it.
+__device__ __forceinline__ int warp_owner(int incl, int f) {
+  int pos = 0;
+#pragma unroll
+  for (int step = 16; step > 0; step >>= 1) {
+    int v = __shfl_sync(FULL, incl, pos + step - 1);
+    if (v <= f) pos += step;
+  }
+  return pos;
+}
+
+}  // namespace pj

@@ -1,0 +1,480 @@
+// Packed string store and segment index (the build half of the hot path).
+//
+//   A1  lengths + validation, stable counting order by length (radix sort of
+//       (length, id)), offsets by prefix sum, warp-per-string gather of the
+//       bytes into sid order, length buckets (Sec. 3.2 groups S_l; Alg. 1
+//       line 2's sort by length).
+//   A2  even partition of every string of length >= tau+1 into tau+1
+//       segments and one (key, sid) record per segment (Sec. 3.1).
+//   A3  records sorted by key -> runs = inverted lists L_l^i(w) (Sec. 3.2),
+//       run heads by flag + prefix sum, open-addressing table key -> run.
+#include <cstdio>
+#include <algorithm>
+#include <chrono>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+
+#include "pj_internal.cuh"
+#include "pj_prims.cuh"
+
+namespace pj {
+
+// ------------------------------------------------------------ plumbing ----
+
+static thread_local std::string g_last_error;
+
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+const std::string& last_error() { return g_last_error; }
+
+void fail(int code, const std::string& msg) { throw Error{code, msg}; }
+
+void check_cuda(cudaError_t e, const char* what, const char* file, int line) {
+  if (e == cudaSuccess) return;
+  char buf[512];
+  snprintf(buf, sizeof(buf), "%s failed at %s:%d: %s (%s)", what, file, line, cudaGetErrorName(e),
+           cudaGetErrorString(e));
+  fail(e == cudaErrorMemoryAllocation ? PJ_ENOMEM : PJ_ECUDA, buf);
+}
+
+void* Ctx::get(size_t bytes) const {
+  void* p = nullptr;
+  if (alloc) {
+    p = alloc(alloc_ctx, bytes, (void*)stream);
+    if (!p) fail(PJ_ENOMEM, "device allocator returned NULL for " + std::to_string(bytes) + " bytes");
+  } else {
+    cudaError_t e = cudaMallocAsync(&p, bytes, stream);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      fail(PJ_ENOMEM, "cudaMallocAsync of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+    }
+  }
+  return p;
+}
+
+void Ctx::put(void* p) const {
+  if (!p) return;
+  if (alloc) {
+    free_fn(alloc_ctx, p, (void*)stream);
+  } else {
+    cudaFreeAsync(p, stream);
+  }
+}
+
+Ctx make_ctx(const pj_options* opt) {
+  Ctx c;
+  if (opt) {
+    c.stream = (cudaStream_t)opt->stream;
+    c.alloc = opt->alloc;
+    c.free_fn = opt->free;
+    c.alloc_ctx = opt->alloc_ctx;
+    if ((c.alloc == nullptr) != (c.free_fn == nullptr)) fail(PJ_EINVAL, "pj_options: alloc and free must be set together");
+  }
+  return c;
+}
+
+static bool trace_enabled() {
+  static const bool on = [] {
+    const char* v = getenv("PJ_TRACE");
+    return v && v[0] && v[0] != '0';
+  }();
+  return on;
+}
+
+void trace_mark(const Ctx& c, const char* phase) {
+  if (!trace_enabled()) return;
+  static thread_local std::chrono::steady_clock::time_point last = std::chrono::steady_clock::now();
+  cudaError_t e = cudaStreamSynchronize(c.stream);
+  const auto now = std::chrono::steady_clock::now();
+  const double ms = std::chrono::duration<double, std::milli>(now - last).count();
+  fprintf(stderr, "[pj] %-28s %9.3f ms  %s\n", phase, ms, e == cudaSuccess ? "" : cudaGetErrorString(e));
+  fflush(stderr);
+  last = now;
+}
+
+void trace_note(const char* what) {
+  if (!trace_enabled()) return;
+  fprintf(stderr, "[pj]   . %s\n", what);
+  fflush(stderr);
+}
+
+// ---------------------------------------------------------------- A1 ------
+
+namespace {
+
+__global__ void k_lengths(const uint64_t* __restrict__ off, uint32_t n, uint32_t* __restrict__ len,
+                          uint32_t* __restrict__ ids, int* __restrict__ err, unsigned* __restrict__ lmax) {
+  const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned l = 0;
+  if (k < n) {
+    const uint64_t a = off[k], b = off[k + 1];
+    if (b < a || b - a > PJ_MAX_STRING_LEN) {
+      atomicOr(err, 1);
+    } else {
+      l = (unsigned)(b - a);
+    }
+    len[k] = l;
+    ids[k] = k;
+  }
+  // one atomic per warp
+  unsigned m = l;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(FULL, m, o));
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(lmax, m);
+}
+
+// One warp per string: copy its bytes from input order to sid order.
+__global__ void k_gather(const uint8_t* __restrict__ in_bytes, const uint64_t* __restrict__ in_off,
+                         const uint32_t* __restrict__ perm, const uint64_t* __restrict__ soff,
+                         uint8_t* __restrict__ sbytes, uint32_t n) {
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  for (uint32_t sid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; sid < n; sid += warps) {
+    const uint64_t src = in_off[perm[sid]];
+    const uint64_t dst = soff[sid];
+    const uint32_t L = (uint32_t)(soff[sid + 1] - dst);
+    for (uint32_t k = lane; k < L; k += 32) sbytes[dst + k] = in_bytes[src + k];
+  }
+}
+
+// bbeg[l] = first sid whose length is >= l, for l = 0 .. lmax + 1.
+__global__ void k_buckets(const uint32_t* __restrict__ slen, uint32_t n, uint32_t* __restrict__ bbeg, int lmax) {
+  const uint32_t sid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sid > n) return;
+  const int cur = sid < n ? (int)slen[sid] : lmax + 1;
+  const int prev = sid > 0 ? (int)slen[sid - 1] : -1;
+  for (int l = prev + 1; l <= cur; ++l) bbeg[l] = sid;
+}
+
+// ---------------------------------------------------------------- A2 ------
+
+__global__ void k_seg_records(const uint8_t* __restrict__ sbytes, const uint64_t* __restrict__ soff,
+                              const uint32_t* __restrict__ slen, uint32_t first, uint64_t n_records, int tau,
+                              unsigned long long* __restrict__ keys, uint32_t* __restrict__ vals) {
+  const uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_records) return;
+  const uint32_t sid = first + (uint32_t)(r / (tau + 1));
+  const int i = (int)(r % (tau + 1)) + 1;
+  const int l = (int)slen[sid];
+  int P, li;
+  even_segment(l, tau, i, P, li);
+  keys[r] = seg_key(sbytes + soff[sid] + P, li, l, i);
+  vals[r] = sid;
+}
+
+// ---------------------------------------------------------------- A3 ------
+
+__global__ void k_head_flags(const unsigned long long* __restrict__ keys, uint64_t n, uint32_t* __restrict__ flags) {
+  const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) flags[k] = (k == 0 || keys[k] != keys[k - 1]) ? 1u : 0u;
+}
+
+__global__ void k_heads(const uint32_t* __restrict__ flags, const uint32_t* __restrict__ uidx, uint64_t n,
+                        uint32_t* __restrict__ heads) {
+  const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n && flags[k]) heads[uidx[k]] = (uint32_t)k;
+  if (k == 0) heads[uidx[n - 1] + flags[n - 1]] = (uint32_t)n;
+}
+
+__global__ void k_table_insert(const unsigned long long* __restrict__ keys, const uint32_t* __restrict__ heads,
+                               uint64_t n_unique, Slot* __restrict__ table, unsigned long long mask,
+                               int* __restrict__ err) {
+  const uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= n_unique) return;
+  const uint32_t b = heads[u], e = heads[u + 1];
+  const unsigned long long key = keys[b];
+  unsigned long long h = (key >> 7) & mask;
+  for (unsigned long long probe = 0; probe <= mask; ++probe) {
+    const unsigned long long prev = atomicCAS(&table[h].key, 0ull, key);
+    if (prev == 0ull) {
+      table[h].begin = b;
+      table[h].count = e - b;
+      return;
+    }
+    h = (h + 1) & mask;
+  }
+  atomicOr(err, 2);  // table full (cannot happen at load factor <= 1/2)
+}
+
+}  // namespace
+
+// Stage a string set on the device (bytes rebased to offset 0).
+static void stage_strings(const Ctx& c, const pj_strings& S, DBuf<uint8_t>& bytes, DBuf<uint64_t>& off,
+                          const uint8_t** dbytes, const uint64_t** doff, uint64_t* total) {
+  const uint32_t n = S.n;
+  if (!S.offsets || (!S.bytes && n > 0)) fail(PJ_EINVAL, "pj_strings: NULL bytes or offsets");
+  if (S.on_device) {
+    uint64_t o[2];
+    PJ_CUDA(cudaMemcpyAsync(&o[0], S.offsets, sizeof(uint64_t), cudaMemcpyDeviceToHost, c.stream));
+    PJ_CUDA(cudaMemcpyAsync(&o[1], S.offsets + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, c.stream));
+    c.sync();
+    if (o[1] < o[0]) fail(PJ_EINVAL, "pj_strings: offsets decrease");
+    *dbytes = S.bytes;
+    *doff = S.offsets;
+    *total = o[1] - o[0];
+    return;
+  }
+  const uint64_t o0 = S.offsets[0];
+  for (uint32_t k = 0; k < n; ++k)
+    if (S.offsets[k + 1] < S.offsets[k]) fail(PJ_EINVAL, "pj_strings: offsets decrease at " + std::to_string(k));
+  const uint64_t tot = S.offsets[n] - o0;
+  off.reset(c, (size_t)n + 1);
+  std::vector<uint64_t> h(n + 1);
+  for (uint32_t k = 0; k <= n; ++k) h[k] = S.offsets[k] - o0;
+  PJ_CUDA(cudaMemcpyAsync(off.p, h.data(), (n + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice, c.stream));
+  bytes.reset(c, tot ? tot : 1);
+  if (tot) PJ_CUDA(cudaMemcpyAsync(bytes.p, S.bytes + o0, tot, cudaMemcpyHostToDevice, c.stream));
+  c.sync();  // h goes out of scope
+  *dbytes = bytes.p;
+  *doff = off.p;
+  *total = tot;
+}
+
+void build_store(pj_index& idx, const pj_strings& S) {
+  const Ctx& c = idx.ctx;
+  const uint32_t n = S.n;
+  idx.n = n;
+  DBuf<uint8_t> in_bytes_buf;
+  DBuf<uint64_t> in_off_buf;
+  const uint8_t* in_bytes = nullptr;
+  const uint64_t* in_off = nullptr;
+  uint64_t total = 0;
+  trace_mark(c, "build: start");
+  stage_strings(c, S, in_bytes_buf, in_off_buf, &in_bytes, &in_off, &total);
+  idx.total_bytes = total;
+  trace_mark(c, "build: stage input");
+
+  DBuf<int> err(c, 1);
+  DBuf<unsigned> lmax(c, 1);
+  PJ_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), c.stream));
+  PJ_CUDA(cudaMemsetAsync(lmax.p, 0, sizeof(unsigned), c.stream));
+  idx.slen.reset(c, n);
+  idx.perm.reset(c, n);
+  if (n) {
+    k_lengths<<<ceil_div(n, 256), 256, 0, c.stream>>>(in_off, n, idx.slen.p, idx.perm.p, err.p, lmax.p);
+    PJ_LAUNCHED("k_lengths");
+  }
+  int h_err = 0;
+  unsigned h_lmax = 0;
+  PJ_CUDA(cudaMemcpyAsync(&h_err, err.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  PJ_CUDA(cudaMemcpyAsync(&h_lmax, lmax.p, sizeof(unsigned), cudaMemcpyDeviceToHost, c.stream));
+  c.sync();
+  if (h_err) fail(PJ_EINVAL, "pj_strings: offsets decrease or a string is longer than 65535 bytes");
+  idx.lmax = (int)h_lmax;
+
+  // stable order by length (ties keep input order)
+  radix_sort_pairs<uint32_t>(c, idx.slen.p, idx.perm.p, n, bits_for((uint64_t)idx.lmax + 1));
+  trace_mark(c, "build: lengths + sort");
+
+  DBuf<uint64_t> len64(c, (size_t)n + 1);
+  PJ_CUDA(cudaMemsetAsync(len64.p + n, 0, sizeof(uint64_t), c.stream));
+  widen_u32(c, idx.slen.p, len64.p, n);
+  idx.soff.reset(c, (size_t)n + 1);
+  exclusive_scan<uint64_t>(c, len64.p, idx.soff.p, (size_t)n + 1);
+
+  idx.sbytes.reset(c, total ? total : 1);
+  if (n) {
+    const unsigned blocks = std::min<unsigned>(ceil_div((size_t)n * 32, 256), 152u * 16u);
+    k_gather<<<blocks, 256, 0, c.stream>>>(in_bytes, in_off, idx.perm.p, idx.soff.p, idx.sbytes.p, n);
+    PJ_LAUNCHED("k_gather");
+  }
+  idx.bbeg.reset(c, (size_t)idx.lmax + 2);
+  k_buckets<<<ceil_div((size_t)n + 1, 256), 256, 0, c.stream>>>(idx.slen.p, n, idx.bbeg.p, idx.lmax);
+  PJ_LAUNCHED("k_buckets");
+  trace_mark(c, "build: gather + buckets");
+  idx.h_bbeg.resize((size_t)idx.lmax + 2);
+  PJ_CUDA(cudaMemcpyAsync(idx.h_bbeg.data(), idx.bbeg.p, idx.h_bbeg.size() * sizeof(uint32_t),
+                          cudaMemcpyDeviceToHost, c.stream));
+  c.sync();
+}
+
+void check_partition(const Ctx& c, const Partition& part);
+
+void build_partition(pj_index& idx, int tau, Partition& part) {
+  const Ctx& c = idx.ctx;
+  part.tau = tau;
+  const int lcut = tau + 1 <= idx.lmax + 1 ? tau + 1 : idx.lmax + 1;
+  part.first = idx.h_bbeg[lcut];
+  const uint64_t nrec = (uint64_t)(idx.n - part.first) * (uint64_t)(tau + 1);
+  part.n_records = nrec;
+  if (nrec > 0xFFFFFFF0ull) fail(PJ_EINVAL, "segment index: more than 2^32 records");
+  part.postings.reset(c, nrec);
+  if (nrec == 0) {
+    part.n_unique = 0;
+    part.table.reset(c, 1);
+    PJ_CUDA(cudaMemsetAsync(part.table.p, 0, sizeof(Slot), c.stream));
+    return;
+  }
+  DBuf<unsigned long long> keys(c, nrec);
+  k_seg_records<<<ceil_div(nrec, 256), 256, 0, c.stream>>>(idx.sbytes.p, idx.soff.p, idx.slen.p, part.first, nrec,
+                                                           tau, keys.p, part.postings.p);
+  PJ_LAUNCHED("k_seg_records");
+  trace_mark(c, "partition: records");
+  radix_sort_pairs<unsigned long long>(c, keys.p, part.postings.p, nrec, 64);
+  trace_mark(c, "partition: sort");
+
+  DBuf<uint32_t> flags(c, nrec), uidx(c, nrec);
+  k_head_flags<<<ceil_div(nrec, 256), 256, 0, c.stream>>>(keys.p, nrec, flags.p);
+  PJ_LAUNCHED("k_head_flags");
+  exclusive_scan<uint32_t>(c, flags.p, uidx.p, nrec);
+  uint32_t last[2] = {0, 0};
+  PJ_CUDA(cudaMemcpyAsync(&last[0], uidx.p + nrec - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.stream));
+  PJ_CUDA(cudaMemcpyAsync(&last[1], flags.p + nrec - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.stream));
+  c.sync();
+  const uint64_t n_unique = (uint64_t)last[0] + last[1];
+  part.n_unique = n_unique;
+  DBuf<uint32_t> heads(c, n_unique + 1);
+  k_heads<<<ceil_div(nrec, 256), 256, 0, c.stream>>>(flags.p, uidx.p, nrec, heads.p);
+  PJ_LAUNCHED("k_heads");
+  uint64_t cap = 1024;
+  while (cap < 2 * n_unique) cap <<= 1;
+  part.table.reset(c, cap);
+  PJ_CUDA(cudaMemsetAsync(part.table.p, 0, cap * sizeof(Slot), c.stream));
+  DBuf<int> err(c, 1);
+  PJ_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), c.stream));
+  k_table_insert<<<ceil_div(n_unique, 256), 256, 0, c.stream>>>(keys.p, heads.p, n_unique, part.table.p, cap - 1,
+                                                                err.p);
+  PJ_LAUNCHED("k_table_insert");
+  int h_err = 0;
+  PJ_CUDA(cudaMemcpyAsync(&h_err, err.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  c.sync();
+  if (h_err) fail(PJ_ECUDA, "segment table insertion failed");
+  trace_mark(c, "partition: table");
+  if (getenv("PJ_CHECK_INDEX")) check_partition(c, part);
+}
+
+// Host-side audit of one partition (environment PJ_CHECK_INDEX=1): the runs
+// tile the postings exactly, every posting is a valid sid, and the table
+// keeps at least half of its slots empty.
+void check_partition(const Ctx& c, const Partition& part) {
+  std::vector<Slot> t(part.table.n);
+  std::vector<uint32_t> post(part.n_records);
+  PJ_CUDA(cudaMemcpyAsync(t.data(), part.table.p, t.size() * sizeof(Slot), cudaMemcpyDeviceToHost, c.stream));
+  if (!post.empty())
+    PJ_CUDA(cudaMemcpyAsync(post.data(), part.postings.p, post.size() * 4, cudaMemcpyDeviceToHost, c.stream));
+  c.sync();
+  uint64_t empty = 0, used = 0, covered = 0;
+  std::vector<uint8_t> seen(part.n_records, 0);
+  for (const Slot& s : t) {
+    if (s.key == 0) {
+      ++empty;
+      continue;
+    }
+    ++used;
+    if ((uint64_t)s.begin + s.count > part.n_records || s.count == 0) fail(PJ_ECUDA, "index audit: bad run");
+    for (uint32_t k = s.begin; k < s.begin + s.count; ++k) {
+      if (seen[k]) fail(PJ_ECUDA, "index audit: overlapping runs");
+      seen[k] = 1;
+      ++covered;
+    }
+  }
+  fprintf(stderr, "[pj] audit tau=%d: slots=%zu used=%llu empty=%llu runs=%llu covered=%llu of %llu\n", part.tau,
+          t.size(), (unsigned long long)used, (unsigned long long)empty, (unsigned long long)part.n_unique,
+          (unsigned long long)covered, (unsigned long long)part.n_records);
+  if (used != part.n_unique || covered != part.n_records || empty < t.size() / 2)
+    fail(PJ_ECUDA, "index audit failed");
+}
+
+void upload_probe_set(const Ctx& c, const pj_strings& R, ProbeSet& out) {
+  const uint8_t* dbytes = nullptr;
+  const uint64_t* doff = nullptr;
+  uint64_t total = 0;
+  DBuf<uint8_t> bb;
+  DBuf<uint64_t> ob;
+  stage_strings(c, R, bb, ob, &dbytes, &doff, &total);
+  out.n = R.n;
+  // keep the device copy (host input) or reference the caller's (device input)
+  out.len.reset(c, R.n);
+  DBuf<uint32_t> ids(c, R.n);
+  DBuf<int> err(c, 1);
+  DBuf<unsigned> lmax(c, 1);
+  PJ_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), c.stream));
+  PJ_CUDA(cudaMemsetAsync(lmax.p, 0, sizeof(unsigned), c.stream));
+  if (R.n) {
+    k_lengths<<<ceil_div(R.n, 256), 256, 0, c.stream>>>(doff, R.n, out.len.p, ids.p, err.p, lmax.p);
+    PJ_LAUNCHED("k_lengths");
+  }
+  int h_err = 0;
+  unsigned h_lmax = 0;
+  PJ_CUDA(cudaMemcpyAsync(&h_err, err.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  PJ_CUDA(cudaMemcpyAsync(&h_lmax, lmax.p, sizeof(unsigned), cudaMemcpyDeviceToHost, c.stream));
+  c.sync();
+  if (h_err) fail(PJ_EINVAL, "pj_strings: offsets decrease or a string is longer than 65535 bytes");
+  out.lmax = (int)h_lmax;
+  out.bytes = dbytes;
+  out.off = doff;
+  out.own_bytes = std::move(bb);
+  out.own_off = std::move(ob);
+}
+
+}  // namespace pj
+
+// ------------------------------------------------------------------ C ABI --
+
+uint64_t pj_index::device_bytes() const {
+  uint64_t b = sbytes.bytes() + soff.bytes() + slen.bytes() + perm.bytes() + bbeg.bytes();
+  for (const auto& p : parts) b += p.table.bytes() + p.postings.bytes();
+  return b;
+}
+
+extern "C" {
+
+void pj_options_init(pj_options* opt) {
+  if (!opt) return;
+  memset(opt, 0, sizeof(*opt));
+  opt->verify_mode = PJ_VERIFY_AUTO;
+}
+
+int pj_build_index(const pj_strings* S, int tau_max, const pj_options* opt, pj_index** out) {
+  if (out) *out = nullptr;
+  pj_index* idx = nullptr;
+  try {
+    if (!S || !out) pj::fail(PJ_EINVAL, "pj_build_index: NULL argument");
+    if (tau_max < 0 || tau_max > PJ_TAU_LIMIT) pj::fail(PJ_EINVAL, "pj_build_index: tau_max out of range");
+    idx = new pj_index();
+    idx->ctx = pj::make_ctx(opt);
+    idx->results_on_device = opt ? opt->results_on_device != 0 : false;
+    PJ_CUDA(cudaGetDevice(&idx->device));
+    pj::build_store(*idx, *S);
+    idx->parts.resize(tau_max + 1);
+    for (int t = 0; t <= tau_max; ++t) pj::build_partition(*idx, t, idx->parts[t]);
+    idx->ctx.sync();
+    *out = idx;
+    return PJ_OK;
+  } catch (const pj::Error& e) {
+    pj::set_last_error(e.msg);
+    delete idx;
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    pj::set_last_error("host allocation failed");
+    delete idx;
+    return PJ_ENOMEM;
+  }
+}
+
+uint32_t pj_index_size(const pj_index* idx) { return idx ? idx->n : 0; }
+int pj_index_tau_max(const pj_index* idx) { return idx ? (int)idx->parts.size() - 1 : 0; }
+uint64_t pj_index_device_bytes(const pj_index* idx) { return idx ? idx->device_bytes() : 0; }
+
+void pj_index_free(pj_index* idx) {
+  if (!idx) return;
+  cudaStream_t s = idx->ctx.stream;
+  delete idx;  // buffers are released stream-ordered
+  cudaStreamSynchronize(s);
+}
+
+const char* pj_strerror(int code) {
+  switch (code) {
+    case PJ_OK: return "PJ_OK";
+    case PJ_EINVAL: return "PJ_EINVAL: invalid argument";
+    case PJ_ENOMEM: return "PJ_ENOMEM: out of memory";
+    case PJ_ECUDA: return "PJ_ECUDA: CUDA error";
+    case PJ_ETIMEDOUT: return "PJ_ETIMEDOUT: wait timed out";
+    case PJ_ECANCELED: return "PJ_ECANCELED: request cancelled";
+    default: return "unknown pj error";
+  }
+}
+
+const char* pj_last_error(void) { return pj::last_error().c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,136 @@
+// Internal data layout of the GB300 Pass-Join index.
+//
+// Strings live in HBM in "sorted-id" (sid) order: ascending length, ties by
+// input id.  Strings of one length l therefore occupy the contiguous sid
+// range [bbeg[l], bbeg[l+1]), which is the paper's group S_l (Sec. 3.2), and
+// "visited before" in the self join (Alg. 1: by length, then a fixed order)
+// becomes plain sid order.
+//
+// For each threshold tau the index holds the tau+1 even segments (Sec. 3.1)
+// of every string of length >= tau+1 as records (key, sid), where the key is
+// a 64-bit hash of (l, i, segment bytes).  Records sorted by key give the
+// inverted lists L_l^i(w) as contiguous runs of the postings array (sids in
+// ascending order inside a run); an open-addressing table maps a key to its
+// run.  Hash collisions only merge runs: every candidate's segment is
+// byte-compared before verification, so results stay exact.
+#pragma once
+
+#include <mutex>
+#include <vector>
+
+#include "pj_common.cuh"
+
+namespace pj {
+
+struct __align__(16) Slot {
+  unsigned long long key;  // 0 = empty
+  uint32_t begin;          // first posting of the run
+  uint32_t count;          // run length
+};
+
+// Even partition (Sec. 3.1) of a length-l string into tau+1 segments: the
+// first tau+1-k have floor(l/(tau+1)) characters, the last k one more, with
+// k = l - floor(l/(tau+1))*(tau+1).  Segment i is 1-based; P = 0-based start.
+__host__ __device__ __forceinline__ void even_segment(int l, int tau, int i, int& P, int& li) {
+  const int parts = tau + 1;
+  const int base = l / parts;
+  const int k = l - base * parts;
+  const int first_long = parts - k + 1;  // segments i >= first_long are longer
+  li = base + (i >= first_long ? 1 : 0);
+  P = (i - 1) * base + (i > first_long ? i - first_long : 0);
+}
+
+// 64-bit key of segment number i of a length-l string with the given bytes:
+// FNV-1a over the bytes, then (l, i, len) folded in and the MurmurHash3
+// 64-bit finaliser applied.  Never 0 (0 marks an empty table slot).
+__host__ __device__ __forceinline__ unsigned long long seg_key(const uint8_t* p, int len, int l, int i) {
+  unsigned long long h = 0xcbf29ce484222325ull;
+  for (int k = 0; k < len; ++k) {
+    h ^= p[k];
+    h *= 0x100000001b3ull;
+  }
+  h ^= ((unsigned long long)l << 40) ^ ((unsigned long long)i << 20) ^ (unsigned long long)len;
+  h ^= h >> 33;
+  h *= 0xff51afd7ed558ccdull;
+  h ^= h >> 33;
+  h *= 0xc4ceb9fe1a85ec53ull;
+  h ^= h >> 33;
+  return h ? h : 1ull;
+}
+
+// Longest linear-probe sequence a lookup follows.  At load factor <= 1/2 a
+// run of this many occupied slots does not occur in a correct table, so a
+// lookup that reaches it reports an inconsistent index instead of scanning.
+constexpr int TABLE_MAX_PROBES = 4096;
+
+// 1: found (begin, count); 0: not present; -1: probe limit reached.
+__device__ __forceinline__ int table_find(const Slot* __restrict__ t, unsigned long long mask,
+                                          unsigned long long key, uint32_t& begin, uint32_t& count) {
+  unsigned long long h = (key >> 7) & mask;
+  for (int probe = 0; probe < TABLE_MAX_PROBES; ++probe) {
+    const uint4 raw = __ldg(reinterpret_cast<const uint4*>(t + h));
+    const unsigned long long k = ((unsigned long long)raw.y << 32) | raw.x;
+    if (k == key) {
+      begin = raw.z;
+      count = raw.w;
+      return 1;
+    }
+    if (k == 0) return 0;
+    h = (h + 1) & mask;
+  }
+  return -1;
+}
+
+// One threshold's segment index.
+struct Partition {
+  int tau = -1;
+  uint32_t first = 0;        // first sid with length >= tau + 1
+  uint64_t n_records = 0;    // (n - first) * (tau + 1)
+  uint64_t n_unique = 0;     // distinct keys
+  DBuf<Slot> table;          // power-of-two capacity
+  DBuf<uint32_t> postings;   // sids, runs in key order, ascending inside a run
+};
+
+}  // namespace pj
+
+// Opaque index handle of the C ABI.
+struct pj_index {
+  pj::Ctx ctx;
+  int device = 0;
+  std::mutex mu;             // serialises calls that use the index
+  bool results_on_device = false;
+  uint32_t n = 0;
+  int lmax = 0;              // longest string
+  uint64_t total_bytes = 0;
+  pj::DBuf<uint8_t> sbytes;  // strings in sid order
+  pj::DBuf<uint64_t> soff;   // n + 1 offsets
+  pj::DBuf<uint32_t> slen;   // lengths by sid
+  pj::DBuf<uint32_t> perm;   // sid -> input id
+  pj::DBuf<uint32_t> bbeg;   // lmax + 2 bucket starts by length
+  std::vector<uint32_t> h_bbeg;
+  std::vector<pj::Partition> parts;  // index = tau
+  uint64_t device_bytes() const;
+};
+
+namespace pj {
+
+// Builds the sorted store of S into idx (host or device input).
+void build_store(pj_index& idx, const pj_strings& S);
+// Builds the segment index of idx for one threshold.
+void build_partition(pj_index& idx, int tau, Partition& part);
+
+// Device copy of a probe set (R or a query batch) in input order.
+struct ProbeSet {
+  DBuf<uint8_t> own_bytes;   // device copy when the input was on the host
+  DBuf<uint64_t> own_off;
+  const uint8_t* bytes = nullptr;  // string k = bytes[off[k] .. off[k+1])
+  const uint64_t* off = nullptr;
+  DBuf<uint32_t> len;
+  uint32_t n = 0;
+  int lmax = 0;
+};
+void upload_probe_set(const Ctx& c, const pj_strings& R, ProbeSet& out);
+
+void set_last_error(const std::string& msg);
+
+}  // namespace pj

@@ -1,0 +1,618 @@
+// Probe and verification half of the hot path, and the join entry points.
+//
+//   A4  multi-match-aware substring selection + index lookup (Sec. 4.2,
+//       Alg. 2, Lemma 2): k_probe_hits, one thread per (probing string,
+//       indexed length l, segment i) group; each thread looks up the
+//       selected substrings s[p, l_i] of its window and writes one Hit per
+//       non-empty posting run.  Blocks aggregate their hits through shared
+//       memory, so the kernel has no warp-level collectives.
+//   A6  extension-based verification (Sec. 5.2, Alg. 3): k_verify_hits, a
+//       load-balanced expansion of the hits' runs into candidates
+//       (q, r, i, p), one candidate per thread: segment bytes compared, then
+//       d_l = VERIFYSTRINGPAIR(s_l, r_l, i-1) and, if it passes,
+//       d_r = VERIFYSTRINGPAIR(s_r, r_r, tau+1-i), each the length-aware band
+//       of Sec. 5.1 held in registers with the Lemma 4 early exit.
+//   A8  pairs whose indexed (shorter-in-order) string has length <= tau have
+//       no even partition (footnote to Sec. 3.1): k_fallback verifies them
+//       directly, one thread per short string.
+//   A5/A7  accepted matches (pair key, d_l + d_r) are radix-sorted by key,
+//       each run of equal keys keeps its least ed (the exact ED of the pair),
+//       and runs are compacted by prefix sum into sorted (a, b, ed) records.
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+
+#include "pj_internal.cuh"
+#include "pj_prims.cuh"
+#include "pj_probe.cuh"
+
+namespace pj {
+
+struct Counters {
+  unsigned long long accepted;
+  unsigned long long lookups;
+  unsigned long long candidates;
+  unsigned long long cells;
+  unsigned long long fallback;
+  unsigned long long hits;
+  unsigned long long err;  // bit 0: run or posting outside the index; bit 1: probe limit
+  unsigned long long pad;
+};
+
+struct AccOut {
+  unsigned long long* key;
+  uint32_t* ed;
+  unsigned long long cap;
+};
+
+constexpr int BLOCK = 256;
+
+// Block-wide exclusive prefix sum of one value per thread, shared memory
+// only.  Every thread of the block must call it.  Returns the exclusive
+// prefix; *total receives the block sum.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* sm, uint32_t* total) {
+  const int tid = threadIdx.x;
+  sm[tid] = v;
+  __syncthreads();
+  for (int off = 1; off < BLOCK; off <<= 1) {
+    const uint32_t x = tid >= off ? sm[tid - off] : 0u;
+    __syncthreads();
+    sm[tid] += x;
+    __syncthreads();
+  }
+  const uint32_t incl = sm[tid];
+  *total = sm[BLOCK - 1];
+  __syncthreads();
+  return incl - v;
+}
+
+// ---------------------------------------------------------------- A4 ------
+
+template <bool SELF>
+__global__ void __launch_bounds__(BLOCK) k_probe_hits(const ProbeView v, unsigned long long n_groups, Hit* hits,
+                                                      unsigned long long cap, Counters* ctr) {
+  __shared__ uint32_t sm[BLOCK];
+  __shared__ unsigned long long s_base;
+  __shared__ unsigned long long s_lookups;
+  __shared__ int s_err;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    s_lookups = 0;
+    s_err = 0;
+  }
+  __syncthreads();
+  const int G = groups_per_probe(v.tau, SELF);
+  for (unsigned long long tile = blockIdx.x; tile * BLOCK < n_groups; tile += gridDim.x) {
+    const unsigned long long t = tile * BLOCK + tid;
+    bool valid = false;
+    int l = 0, i = 0, P = 0, li = 0, lo = 0, hi = -1, ls = 0;
+    uint32_t q = 0;
+    const uint8_t* s = nullptr;
+    if (t < n_groups) {
+      q = v.pbegin + (uint32_t)(t / G);
+      ls = (int)v.plen[q];
+      s = v.pbytes + v.poff[q];
+      valid = group_window(v, SELF, q, ls, (int)(t % G), l, i, P, li, lo, hi);
+    }
+    // round 1: count the non-empty runs of this group's window
+    uint32_t nh = 0;
+    int err = 0;
+    if (valid) {
+      for (int p = lo; p <= hi; ++p) {
+        uint32_t b;
+        if (lookup(v, SELF, s, ls, q, l, i, p, li, b, err)) ++nh;
+      }
+      atomicAdd(&s_lookups, (unsigned long long)(hi - lo + 1));
+    }
+    if (err) atomicOr(&s_err, err);
+    uint32_t total;
+    const uint32_t excl = block_excl_scan(nh, sm, &total);
+    if (tid == 0) s_base = total ? atomicAdd(&ctr->hits, (unsigned long long)total) : 0ull;
+    __syncthreads();
+    // round 2: write the hits
+    if (nh) {
+      unsigned long long pos = s_base + excl;
+      int err2 = 0;
+      for (int p = lo; p <= hi; ++p) {
+        uint32_t b;
+        const uint32_t c = lookup(v, SELF, s, ls, q, l, i, p, li, b, err2);
+        if (c) {
+          if (pos < cap) hits[pos] = Hit{q, b, c, (uint32_t)p | ((uint32_t)i << 16)};
+          ++pos;
+        }
+      }
+    }
+    __syncthreads();  // s_base is reused by the next tile
+  }
+  if (tid == 0) {
+    atomicAdd(&ctr->lookups, s_lookups);
+    if (s_err) atomicOr(&ctr->err, (unsigned long long)s_err);
+  }
+}
+
+__global__ void k_hit_counts(const Hit* __restrict__ hits, unsigned long long n, unsigned long long* __restrict__ cnt) {
+  const unsigned long long k = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) cnt[k] = hits[k].count;
+}
+
+// ---------------------------------------------------------------- A6 ------
+
+constexpr int V_ITEMS = 4;
+constexpr int V_CHUNK = BLOCK * V_ITEMS;
+
+template <int MAXW, bool SELF>
+__global__ void __launch_bounds__(BLOCK) k_verify_hits(const ProbeView v, const Hit* __restrict__ hits,
+                                                       const unsigned long long* __restrict__ cand_off,
+                                                       unsigned long long n_hits, unsigned long long n_cand,
+                                                       AccOut out, Counters* ctr) {
+  __shared__ unsigned long long s_off[V_CHUNK + 1];
+  __shared__ unsigned long long s_h0;
+  __shared__ unsigned long long s_accbase;
+  __shared__ uint32_t s_nacc;
+  __shared__ unsigned long long s_cells;
+  __shared__ int s_err;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    s_cells = 0;
+    s_err = 0;
+  }
+  __syncthreads();
+  unsigned long long cells = 0;
+  int err = 0;
+  for (unsigned long long chunk = blockIdx.x; chunk * V_CHUNK < n_cand; chunk += gridDim.x) {
+    const unsigned long long c_lo = chunk * V_CHUNK;
+    const unsigned long long c_hi = min(n_cand, c_lo + V_CHUNK);
+    if (tid == 0) {  // last hit whose first candidate is <= c_lo
+      unsigned long long lo = 0, hi = n_hits;
+      while (hi - lo > 1) {
+        const unsigned long long mid = (lo + hi) >> 1;
+        if (cand_off[mid] <= c_lo) lo = mid; else hi = mid;
+      }
+      s_h0 = lo;
+      s_nacc = 0;
+    }
+    __syncthreads();
+    const unsigned long long h0 = s_h0;
+    const int nload = (int)min((unsigned long long)(V_CHUNK + 1), n_hits - h0);
+    for (int k = tid; k < nload; k += BLOCK) s_off[k] = cand_off[h0 + k];
+    __syncthreads();
+    bool ok[V_ITEMS];
+    unsigned long long key[V_ITEMS];
+    int ed[V_ITEMS];
+    uint32_t mine = 0;
+#pragma unroll
+    for (int j = 0; j < V_ITEMS; ++j) {
+      ok[j] = false;
+      key[j] = 0;
+      ed[j] = 0;
+      const unsigned long long c = c_lo + tid + (unsigned long long)j * BLOCK;
+      if (c < c_hi) {
+        int lo = 0, hi = nload;  // last k with s_off[k] <= c
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (s_off[mid] <= c) lo = mid; else hi = mid;
+        }
+        const Hit h = hits[h0 + lo];
+        ok[j] = verify_candidate<MAXW>(v, SELF, h, (uint32_t)(c - s_off[lo]), key[j], ed[j], cells, err);
+        mine += ok[j] ? 1u : 0u;
+      }
+    }
+    const uint32_t my_pos = mine ? atomicAdd(&s_nacc, mine) : 0u;
+    __syncthreads();
+    if (tid == 0) s_accbase = s_nacc ? atomicAdd(&ctr->accepted, (unsigned long long)s_nacc) : 0ull;
+    __syncthreads();
+    unsigned long long pos = s_accbase + my_pos;
+#pragma unroll
+    for (int j = 0; j < V_ITEMS; ++j) {
+      if (ok[j]) {
+        if (pos < out.cap) {
+          out.key[pos] = key[j];
+          out.ed[pos] = (uint32_t)ed[j];
+        }
+        ++pos;
+      }
+    }
+    __syncthreads();  // shared state is rewritten by the next chunk
+  }
+  atomicAdd(&s_cells, cells);
+  if (err) atomicOr(&s_err, err);
+  __syncthreads();
+  if (tid == 0) {
+    atomicAdd(&ctr->cells, s_cells);
+    if (s_err) atomicOr(&ctr->err, (unsigned long long)s_err);
+  }
+}
+
+// ---------------------------------------------------------------- A8 ------
+
+// Pairs whose indexed string is too short to partition (length <= tau).
+// SELF: every short sid x against the sids y > x with |y| <= |x| + tau.
+// Otherwise: every probe x against the indexed strings of length <= tau
+// within the length filter.  One thread per x.
+template <int MAXW, bool SELF>
+__global__ void __launch_bounds__(BLOCK) k_fallback(const ProbeView v, uint32_t xcount, AccOut out, Counters* ctr) {
+  const int tau = v.tau;
+  unsigned long long cells = 0, pairs = 0;
+  for (uint32_t x = blockIdx.x * BLOCK + threadIdx.x; x < xcount; x += gridDim.x * BLOCK) {
+    const uint8_t* xs = v.pbytes + v.poff[x];
+    const int lx = (int)v.plen[x];
+    uint32_t y0, y1;
+    if (SELF) {
+      y0 = x + 1;
+      y1 = v.ibbeg[min(lx + tau, v.ilmax) + 1];
+    } else {
+      const int llo = max(0, lx - tau);
+      const int lhi = min(min(tau, lx + tau), v.ilmax);
+      y0 = llo <= lhi ? v.ibbeg[llo] : 0u;
+      y1 = llo <= lhi ? v.ibbeg[lhi + 1] : 0u;
+    }
+    const uint32_t qid = v.pid ? v.pid[x] : x;
+    for (uint32_t y = y0; y < y1; ++y) {
+      ++pairs;
+      const int d = vsp<MAXW>(xs, lx, v.ibytes + v.ioff[y], (int)v.ilen[y], tau, cells);
+      if (d <= tau) {
+        const uint32_t rid = v.iperm[y];
+        const uint32_t ka = SELF ? min(qid, rid) : qid;
+        const uint32_t kb = SELF ? max(qid, rid) : rid;
+        const unsigned long long pos = atomicAdd(&ctr->accepted, 1ull);
+        if (pos < out.cap) {
+          out.key[pos] = ((unsigned long long)ka << v.key_shift) | kb;
+          out.ed[pos] = (uint32_t)d;
+        }
+      }
+    }
+  }
+  if (cells) atomicAdd(&ctr->cells, cells);
+  if (pairs) atomicAdd(&ctr->fallback, pairs);
+}
+
+// ------------------------------------------------------------ A5 + A7 -----
+
+__global__ void k_run_heads(const unsigned long long* __restrict__ keys, uint64_t n, uint32_t* __restrict__ flags) {
+  const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) flags[k] = (k == 0 || keys[k] != keys[k - 1]) ? 1u : 0u;
+}
+
+__global__ void k_emit_pairs(const unsigned long long* __restrict__ keys, const uint32_t* __restrict__ eds,
+                             const uint32_t* __restrict__ flags, const uint32_t* __restrict__ pos, uint64_t n,
+                             int key_shift, pj_pair* __restrict__ out) {
+  const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n || !flags[k]) return;
+  const unsigned long long key = keys[k];
+  uint32_t ed = eds[k];
+  for (uint64_t j = k + 1; j < n && keys[j] == key; ++j) ed = min(ed, eds[j]);
+  pj_pair pr;
+  pr.a = (uint32_t)(key >> key_shift);
+  pr.b = (uint32_t)(key & ((1ull << key_shift) - 1));
+  pr.ed = ed;
+  out[pos[k]] = pr;
+}
+
+// ------------------------------------------------------------- launch -----
+
+static int sm_count() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    PJ_CUDA(cudaGetDevice(&dev));
+    PJ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  return sms;
+}
+
+template <class K>
+static unsigned persistent_grid(K kernel, unsigned long long work_blocks) {
+  int bps = 0;
+  PJ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kernel, BLOCK, 0));
+  const unsigned long long full = (unsigned long long)std::max(1, bps) * sm_count();
+  return (unsigned)std::max<unsigned long long>(1, std::min(full, work_blocks));
+}
+
+template <int MAXW, bool SELF>
+static void launch_verify(const Ctx& c, const ProbeView& v, const Hit* hits, const unsigned long long* off,
+                          unsigned long long n_hits, unsigned long long n_cand, AccOut out, Counters* ctr) {
+  const unsigned grid = persistent_grid(k_verify_hits<MAXW, SELF>, (n_cand + V_CHUNK - 1) / V_CHUNK);
+  k_verify_hits<MAXW, SELF><<<grid, BLOCK, 0, c.stream>>>(v, hits, off, n_hits, n_cand, out, ctr);
+  PJ_LAUNCHED("k_verify_hits");
+}
+
+template <int MAXW, bool SELF>
+static void launch_fallback(const Ctx& c, const ProbeView& v, uint32_t xcount, AccOut out, Counters* ctr) {
+  const unsigned grid = persistent_grid(k_fallback<MAXW, SELF>, (xcount + BLOCK - 1) / BLOCK);
+  k_fallback<MAXW, SELF><<<grid, BLOCK, 0, c.stream>>>(v, xcount, out, ctr);
+  PJ_LAUNCHED("k_fallback");
+}
+
+#define PJ_BY_TAU(tau, CALL)          \
+  do {                                \
+    const int t_ = (tau);             \
+    if (t_ <= 1) { CALL(2); }         \
+    else if (t_ <= 2) { CALL(3); }    \
+    else if (t_ <= 4) { CALL(5); }    \
+    else if (t_ <= 8) { CALL(9); }    \
+    else if (t_ <= 16) { CALL(17); }  \
+    else { CALL(33); }                \
+  } while (0)
+
+struct ResultPriv {
+  Ctx ctx;
+};
+
+// Probe + verify for all probing strings, in chunks of probing strings whose
+// groups fit the hit buffer; then the short-string fallback.  Returns the
+// number of accepted matches (the buffer holds min(that, out.cap)).
+template <bool SELF>
+static void probe_and_verify(const Ctx& c, const ProbeView& v0, uint32_t fb_count, AccOut out, Counters* ctr,
+                             Counters& h) {
+  const int G = groups_per_probe(v0.tau, SELF);
+  const unsigned long long group_budget = 64ull << 20;  // groups per chunk
+  const uint32_t chunk_items = (uint32_t)std::max<unsigned long long>(1, group_budget / G);
+  unsigned long long hit_cap = 1ull << 22;
+  DBuf<Hit> hits(c, hit_cap);
+  DBuf<unsigned long long> cnt, off;
+  for (uint32_t done = 0; done < v0.pcount;) {
+    ProbeView v = v0;
+    v.pbegin = v0.pbegin + done;
+    v.pcount = std::min(chunk_items, v0.pcount - done);
+    const unsigned long long n_groups = (unsigned long long)v.pcount * G;
+    unsigned long long n_hits = 0;
+    for (int attempt = 0;; ++attempt) {
+      PJ_CUDA(cudaMemsetAsync(&ctr->hits, 0, sizeof(unsigned long long), c.stream));
+      const unsigned grid = persistent_grid(k_probe_hits<SELF>, (n_groups + BLOCK - 1) / BLOCK);
+      k_probe_hits<SELF><<<grid, BLOCK, 0, c.stream>>>(v, n_groups, hits.p, hit_cap, ctr);
+      PJ_LAUNCHED("k_probe_hits");
+      PJ_CUDA(cudaMemcpyAsync(&n_hits, &ctr->hits, sizeof(n_hits), cudaMemcpyDeviceToHost, c.stream));
+      c.sync();
+      if (n_hits <= hit_cap) break;
+      if (attempt >= 1) fail(PJ_ECUDA, "hit buffer overflowed twice");
+      hit_cap = n_hits;
+      hits.reset(c, hit_cap);
+    }
+    trace_mark(c, "join: probe (hits)");
+    if (n_hits == 0) {
+      done += v.pcount;
+      continue;
+    }
+    cnt.reset(c, n_hits + 1);
+    off.reset(c, n_hits + 1);
+    PJ_CUDA(cudaMemsetAsync(cnt.p + n_hits, 0, sizeof(unsigned long long), c.stream));
+    k_hit_counts<<<ceil_div(n_hits, 256), 256, 0, c.stream>>>(hits.p, n_hits, cnt.p);
+    PJ_LAUNCHED("k_hit_counts");
+    exclusive_scan<unsigned long long>(c, cnt.p, off.p, n_hits + 1);
+    unsigned long long n_cand = 0;
+    PJ_CUDA(cudaMemcpyAsync(&n_cand, off.p + n_hits, sizeof(n_cand), cudaMemcpyDeviceToHost, c.stream));
+    c.sync();
+    h.candidates += n_cand;
+    if (n_cand) {
+#define PJ_CALL(W) launch_verify<W, SELF>(c, v, hits.p, off.p, n_hits, n_cand, out, ctr)
+      PJ_BY_TAU(v.tau, PJ_CALL);
+#undef PJ_CALL
+    }
+    trace_mark(c, "join: verify");
+    done += v.pcount;
+  }
+  if (fb_count) {
+    ProbeView v = v0;
+#define PJ_CALL(W) launch_fallback<W, SELF>(c, v, fb_count, out, ctr)
+    PJ_BY_TAU(v.tau, PJ_CALL);
+#undef PJ_CALL
+  }
+  const unsigned long long cand = h.candidates;
+  PJ_CUDA(cudaMemcpyAsync(&h, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, c.stream));
+  c.sync();
+  h.candidates = cand;
+  if (h.err)
+    fail(PJ_ECUDA, std::string("segment index consistency check failed (") +
+                       ((h.err & 1) ? "posting outside the index" : "probe limit reached") + ")");
+}
+
+// Runs the join, retries once with an exact-size buffer if the accepted
+// matches overflowed, then dedupes and compacts into *out.
+static void run_join(const Ctx& c, const ProbeView& v, bool self, uint32_t fb_count, int a_bits,
+                     bool results_on_device, pj_result* out) {
+  uint64_t cap = 1u << 20;
+  Counters h{};
+  DBuf<unsigned long long> acc_key;
+  DBuf<uint32_t> acc_ed;
+  DBuf<Counters> ctr(c, 1);
+  for (int attempt = 0;; ++attempt) {
+    acc_key.reset(c, cap);
+    acc_ed.reset(c, cap);
+    PJ_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(Counters), c.stream));
+    h = Counters{};
+    AccOut o{acc_key.p, acc_ed.p, cap};
+    if (self) probe_and_verify<true>(c, v, fb_count, o, ctr.p, h);
+    else probe_and_verify<false>(c, v, fb_count, o, ctr.p, h);
+    if (h.accepted <= cap) break;
+    if (attempt >= 1) fail(PJ_ECUDA, "accepted-match buffer overflowed twice");
+    cap = h.accepted;
+  }
+  const uint64_t nacc = h.accepted;
+  uint64_t count = 0;
+  DBuf<pj_pair> pairs;
+  if (nacc > 0) {
+    radix_sort_pairs<unsigned long long>(c, acc_key.p, acc_ed.p, nacc, v.key_shift + a_bits);
+    trace_mark(c, "join: sort accepted");
+    DBuf<uint32_t> flags(c, nacc), pos(c, nacc);
+    k_run_heads<<<ceil_div(nacc, 256), 256, 0, c.stream>>>(acc_key.p, nacc, flags.p);
+    PJ_LAUNCHED("k_run_heads");
+    exclusive_scan<uint32_t>(c, flags.p, pos.p, nacc);
+    uint32_t last[2] = {0, 0};
+    PJ_CUDA(cudaMemcpyAsync(&last[0], pos.p + nacc - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.stream));
+    PJ_CUDA(cudaMemcpyAsync(&last[1], flags.p + nacc - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.stream));
+    c.sync();
+    count = (uint64_t)last[0] + last[1];
+    pairs.reset(c, count);
+    k_emit_pairs<<<ceil_div(nacc, 256), 256, 0, c.stream>>>(acc_key.p, acc_ed.p, flags.p, pos.p, nacc, v.key_shift,
+                                                             pairs.p);
+    PJ_LAUNCHED("k_emit_pairs");
+  }
+  trace_mark(c, "join: dedupe + compact");
+  out->count = count;
+  out->stats.lookups = h.lookups;
+  out->stats.candidates = h.candidates;
+  out->stats.accepted = h.accepted;
+  out->stats.dp_cells = h.cells;
+  out->stats.fallback_pairs = h.fallback;
+  out->priv = new ResultPriv{c};
+  if (results_on_device) {
+    out->on_device = 1;
+    if (count == 0) pairs.reset(c, 1);
+    out->pairs = pairs.p;
+    pairs.p = nullptr;  // ownership moves to the result
+    c.sync();
+  } else {
+    out->on_device = 0;
+    out->pairs = static_cast<pj_pair*>(malloc(std::max<uint64_t>(count, 1) * sizeof(pj_pair)));
+    if (!out->pairs) fail(PJ_ENOMEM, "host result allocation failed");
+    if (count)
+      PJ_CUDA(cudaMemcpyAsync(out->pairs, pairs.p, count * sizeof(pj_pair), cudaMemcpyDeviceToHost, c.stream));
+    c.sync();
+  }
+}
+
+static ProbeView index_side(const pj_index& idx, const Partition& part) {
+  ProbeView v{};
+  v.ibytes = idx.sbytes.p;
+  v.ioff = idx.soff.p;
+  v.ilen = idx.slen.p;
+  v.ibbeg = idx.bbeg.p;
+  v.ilmax = idx.lmax;
+  v.iperm = idx.perm.p;
+  v.n_index = idx.n;
+  v.table = part.table.p;
+  v.mask = part.table.n - 1;
+  v.postings = part.postings.p;
+  v.n_postings = part.n_records;
+  v.tau = part.tau;
+  return v;
+}
+
+static void self_join_impl(pj_index& idx, int tau, pj_result* out, bool on_device) {
+  const Partition& part = idx.parts[tau];
+  ProbeView v = index_side(idx, part);
+  v.pbytes = idx.sbytes.p;
+  v.poff = idx.soff.p;
+  v.plen = idx.slen.p;
+  v.pbegin = part.first;
+  v.pcount = idx.n - part.first;
+  v.pid = idx.perm.p;
+  v.key_shift = bits_for(idx.n);
+  run_join(idx.ctx, v, true, part.first, bits_for(idx.n), on_device, out);
+}
+
+static void probe_join_impl(const Ctx& c, const pj_index& idx, const Partition& part, const ProbeSet& R,
+                            pj_result* out, bool on_device) {
+  ProbeView v = index_side(idx, part);
+  v.pbytes = R.bytes;
+  v.poff = R.off;
+  v.plen = R.len.p;
+  v.pbegin = 0;
+  v.pcount = R.n;
+  v.pid = nullptr;
+  v.key_shift = bits_for(idx.n);
+  const bool has_short = part.first > 0;  // indexed strings too short to partition
+  run_join(c, v, false, has_short ? R.n : 0, bits_for(R.n), on_device, out);
+}
+
+}  // namespace pj
+
+// ------------------------------------------------------------------ C ABI --
+
+static void clear_result(pj_result* out) {
+  if (out) memset(out, 0, sizeof(*out));
+}
+
+extern "C" {
+
+int pj_self_join(pj_index* idx, int tau, pj_result* out) {
+  clear_result(out);
+  try {
+    if (!idx || !out) pj::fail(PJ_EINVAL, "pj_self_join: NULL argument");
+    if (tau < 0 || tau >= (int)idx->parts.size()) pj::fail(PJ_EINVAL, "pj_self_join: tau outside 0..tau_max");
+    std::lock_guard<std::mutex> g(idx->mu);
+    pj::self_join_impl(*idx, tau, out, idx->results_on_device);
+    return PJ_OK;
+  } catch (const pj::Error& e) {
+    pj::set_last_error(e.msg);
+    pj_result_free(out);
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    pj::set_last_error("host allocation failed");
+    pj_result_free(out);
+    return PJ_ENOMEM;
+  }
+}
+
+int pj_join(const pj_strings* R, const pj_strings* S, int tau, const pj_options* opt, pj_result* out) {
+  clear_result(out);
+  pj_index* tmp = nullptr;
+  try {
+    if (!R || !S || !out) pj::fail(PJ_EINVAL, "pj_join: NULL argument");
+    if (tau < 0 || tau > PJ_TAU_LIMIT) pj::fail(PJ_EINVAL, "pj_join: tau out of range");
+    tmp = new pj_index();
+    tmp->ctx = pj::make_ctx(opt);
+    tmp->results_on_device = opt ? opt->results_on_device != 0 : false;
+    PJ_CUDA(cudaGetDevice(&tmp->device));
+    pj::build_store(*tmp, *S);
+    tmp->parts.resize(tau + 1);
+    pj::build_partition(*tmp, tau, tmp->parts[tau]);
+    pj::ProbeSet P;
+    pj::upload_probe_set(tmp->ctx, *R, P);
+    pj::probe_join_impl(tmp->ctx, *tmp, tmp->parts[tau], P, out, tmp->results_on_device);
+    tmp->ctx.sync();
+    delete tmp;
+    return PJ_OK;
+  } catch (const pj::Error& e) {
+    pj::set_last_error(e.msg);
+    pj_result_free(out);
+    delete tmp;
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    pj::set_last_error("host allocation failed");
+    pj_result_free(out);
+    delete tmp;
+    return PJ_ENOMEM;
+  }
+}
+
+int pj_query(pj_index* idx, const pj_strings* batch, int tau, pj_result* out) {
+  clear_result(out);
+  try {
+    if (!idx || !batch || !out) pj::fail(PJ_EINVAL, "pj_query: NULL argument");
+    if (tau < 0 || tau >= (int)idx->parts.size()) pj::fail(PJ_EINVAL, "pj_query: tau outside 0..tau_max");
+    std::lock_guard<std::mutex> g(idx->mu);
+    pj::ProbeSet P;
+    pj::upload_probe_set(idx->ctx, *batch, P);
+    pj::probe_join_impl(idx->ctx, *idx, idx->parts[tau], P, out, idx->results_on_device);
+    return PJ_OK;
+  } catch (const pj::Error& e) {
+    pj::set_last_error(e.msg);
+    pj_result_free(out);
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    pj::set_last_error("host allocation failed");
+    pj_result_free(out);
+    return PJ_ENOMEM;
+  }
+}
+
+void pj_result_free(pj_result* res) {
+  if (!res) return;
+  auto* priv = static_cast<pj::ResultPriv*>(res->priv);
+  if (res->pairs) {
+    if (res->on_device) {
+      if (priv) {
+        priv->ctx.put(res->pairs);
+        cudaStreamSynchronize(priv->ctx.stream);
+      }
+    } else {
+      free(res->pairs);
+    }
+  }
+  delete priv;
+  memset(res, 0, sizeof(*res));
+}
+
+}  // extern "C"

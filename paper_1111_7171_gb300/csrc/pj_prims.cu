@@ -1,0 +1,204 @@
+// Exclusive scan and stable LSD radix sort, written for this library.
+//
+// Scan: tiles of 4096 values per 1024-thread block (4 per thread), block
+// totals scanned recursively, then added back.
+//
+// Radix sort: 8-bit digits, one pass per digit.  Each pass runs a histogram
+// kernel (per-tile digit counts, stored digit-major so that one exclusive
+// scan over them yields every (digit, tile) output offset) and a scatter
+// kernel.  Inside a tile each warp owns 512 consecutive items, handled 32 at
+// a time; lanes holding the same digit find each other with match.any, so the
+// rank of an item among equal digits follows input order and the sort is
+// stable.
+#include "pj_prims.cuh"
+
+namespace pj {
+
+namespace {
+
+constexpr int SCAN_THREADS = 1024;
+constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+template <class T>
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(const T* __restrict__ in, T* __restrict__ out,
+                                                             T* __restrict__ tile_sums, size_t n) {
+  __shared__ T warp_tot[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const size_t base = (size_t)blockIdx.x * SCAN_TILE + (size_t)tid * SCAN_ITEMS;
+  T v[SCAN_ITEMS];
+  T sum = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    v[k] = (base + k < n) ? in[base + k] : T(0);
+    sum += v[k];
+  }
+  T incl = warp_incl_scan(sum);
+  if (lane == 31) warp_tot[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    T w = warp_tot[lane];
+    T wi = warp_incl_scan(w);
+    warp_tot[lane] = wi - w;  // exclusive offset of each warp
+    if (lane == 31 && tile_sums) tile_sums[blockIdx.x] = wi;
+  }
+  __syncthreads();
+  T run = incl - sum + warp_tot[warp];
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    if (base + k < n) out[base + k] = run;
+    run += v[k];
+  }
+}
+
+template <class T>
+__global__ void k_scan_add(T* __restrict__ out, const T* __restrict__ tile_off, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] += tile_off[i / SCAN_TILE];
+}
+
+__global__ void k_widen(const uint32_t* __restrict__ in, uint64_t* __restrict__ out, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = in[i];
+}
+
+constexpr int RS_THREADS = 256;
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_ROUNDS = 16;  // items per lane
+constexpr int RS_WARP_ITEMS = 32 * RS_ROUNDS;
+constexpr int RS_TILE = RS_WARPS * RS_WARP_ITEMS;  // 4096
+
+template <class K>
+__global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const K* __restrict__ keys, size_t n, int shift,
+                                                        uint32_t* __restrict__ hist, unsigned ntiles) {
+  __shared__ uint32_t h[256];
+  const int tid = threadIdx.x;
+  h[tid] = 0;
+  __syncthreads();
+  const size_t base = (size_t)blockIdx.x * RS_TILE;
+#pragma unroll 4
+  for (int k = 0; k < RS_TILE / RS_THREADS; ++k) {
+    const size_t i = base + (size_t)k * RS_THREADS + tid;
+    if (i < n) atomicAdd(&h[(unsigned)(keys[i] >> shift) & 0xFFu], 1u);
+  }
+  __syncthreads();
+  hist[(size_t)tid * ntiles + blockIdx.x] = h[tid];
+}
+
+template <class K>
+__global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                                           K* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                           size_t n, int shift, const uint32_t* __restrict__ offs,
+                                                           unsigned ntiles) {
+  __shared__ uint32_t wcnt[RS_WARPS][256];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int d = tid; d < RS_WARPS * 256; d += RS_THREADS) (&wcnt[0][0])[d] = 0;
+  __syncthreads();
+  const size_t wbase = (size_t)blockIdx.x * RS_TILE + (size_t)warp * RS_WARP_ITEMS;
+  K key[RS_ROUNDS];
+  uint32_t val[RS_ROUNDS];
+  uint32_t rank[RS_ROUNDS];
+  const unsigned lt = lanemask_lt();
+#pragma unroll
+  for (int r = 0; r < RS_ROUNDS; ++r) {
+    const size_t i = wbase + (size_t)r * 32 + lane;
+    const bool valid = i < n;
+    key[r] = valid ? kin[i] : K(0);
+    val[r] = valid ? vin[i] : 0u;
+    const unsigned d = valid ? ((unsigned)(key[r] >> shift) & 0xFFu) : 256u + lane;
+    const unsigned peers = __match_any_sync(FULL, d);
+    const int leader = __ffs(peers) - 1;
+    uint32_t cnt = 0;
+    if (valid && lane == leader) cnt = wcnt[warp][d];
+    cnt = __shfl_sync(FULL, cnt, leader);
+    rank[r] = cnt + __popc(peers & lt);
+    __syncwarp();
+    if (valid && lane == leader) wcnt[warp][d] = cnt + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  {
+    const int d = tid;  // one thread per digit
+    uint32_t run = offs[(size_t)d * ntiles + blockIdx.x];
+#pragma unroll
+    for (int w = 0; w < RS_WARPS; ++w) {
+      const uint32_t t = wcnt[w][d];
+      wcnt[w][d] = run;
+      run += t;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < RS_ROUNDS; ++r) {
+    const size_t i = wbase + (size_t)r * 32 + lane;
+    if (i < n) {
+      const unsigned d = (unsigned)(key[r] >> shift) & 0xFFu;
+      const uint32_t pos = wcnt[warp][d] + rank[r];
+      kout[pos] = key[r];
+      vout[pos] = val[r];
+    }
+  }
+}
+
+}  // namespace
+
+template <class T>
+void exclusive_scan(const Ctx& c, const T* in, T* out, size_t n) {
+  if (n == 0) return;
+  const unsigned tiles = ceil_div(n, SCAN_TILE);
+  if (tiles == 1) {
+    k_scan_tiles<T><<<1, SCAN_THREADS, 0, c.stream>>>(in, out, nullptr, n);
+    PJ_LAUNCHED("k_scan_tiles");
+    return;
+  }
+  DBuf<T> sums(c, tiles), sums_off(c, tiles);
+  k_scan_tiles<T><<<tiles, SCAN_THREADS, 0, c.stream>>>(in, out, sums.p, n);
+  PJ_LAUNCHED("k_scan_tiles");
+  exclusive_scan<T>(c, sums.p, sums_off.p, tiles);
+  k_scan_add<T><<<ceil_div(n, 256), 256, 0, c.stream>>>(out, sums_off.p, n);
+  PJ_LAUNCHED("k_scan_add");
+}
+
+template <class K>
+void radix_sort_pairs(const Ctx& c, K* keys, uint32_t* vals, size_t n, int nbits) {
+  if (n <= 1 || nbits <= 0) return;
+  if (n > 0xFFFFFFFFull) fail(PJ_EINVAL, "radix sort: more than 2^32 items");
+  const unsigned ntiles = ceil_div(n, RS_TILE);
+  DBuf<K> k2(c, n);
+  DBuf<uint32_t> v2(c, n);
+  DBuf<uint32_t> hist(c, (size_t)256 * ntiles), offs(c, (size_t)256 * ntiles);
+  K* ka = keys;
+  uint32_t* va = vals;
+  K* kb = k2.p;
+  uint32_t* vb = v2.p;
+  const int passes = (nbits + 7) / 8;
+  for (int p = 0; p < passes; ++p) {
+    const int shift = 8 * p;
+    k_rs_hist<K><<<ntiles, RS_THREADS, 0, c.stream>>>(ka, n, shift, hist.p, ntiles);
+    PJ_LAUNCHED("k_rs_hist");
+    exclusive_scan<uint32_t>(c, hist.p, offs.p, (size_t)256 * ntiles);
+    k_rs_scatter<K><<<ntiles, RS_THREADS, 0, c.stream>>>(ka, va, kb, vb, n, shift, offs.p, ntiles);
+    PJ_LAUNCHED("k_rs_scatter");
+    K* tk = ka; ka = kb; kb = tk;
+    uint32_t* tv = va; va = vb; vb = tv;
+  }
+  if (ka != keys) {
+    PJ_CUDA(cudaMemcpyAsync(keys, ka, n * sizeof(K), cudaMemcpyDeviceToDevice, c.stream));
+    PJ_CUDA(cudaMemcpyAsync(vals, va, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, c.stream));
+  }
+}
+
+void widen_u32(const Ctx& c, const uint32_t* in, uint64_t* out, size_t n) {
+  if (n == 0) return;
+  k_widen<<<ceil_div(n, 256), 256, 0, c.stream>>>(in, out, n);
+  PJ_LAUNCHED("k_widen");
+}
+
+template void exclusive_scan<uint32_t>(const Ctx&, const uint32_t*, uint32_t*, size_t);
+template void exclusive_scan<uint64_t>(const Ctx&, const uint64_t*, uint64_t*, size_t);
+template void exclusive_scan<unsigned long long>(const Ctx&, const unsigned long long*, unsigned long long*, size_t);
+template void radix_sort_pairs<uint32_t>(const Ctx&, uint32_t*, uint32_t*, size_t, int);
+template void radix_sort_pairs<uint64_t>(const Ctx&, uint64_t*, uint32_t*, size_t, int);
+template void radix_sort_pairs<unsigned long long>(const Ctx&, unsigned long long*, uint32_t*, size_t, int);
+
+}  // namespace pj

@@ -1,0 +1,157 @@
+// Per-thread steps of selection, probing and verification (Sec. 4.2, Alg. 2,
+// Sec. 5.2, Alg. 3), shared by the kernels and by host-side checks.
+//
+// Work is split into two collective-free phases:
+//   * a "group" is one (probing string q, indexed length l, segment i); its
+//     multi-match window gives at most tau + 1 positions p, each one lookup;
+//     a lookup whose (filtered) posting run is non-empty becomes a Hit;
+//   * a "candidate" is one posting of a Hit's run, i.e. one match
+//     (q, r, i, p), verified by extension-based verification.
+#pragma once
+
+#include "pj_internal.cuh"
+#include "pj_verify.cuh"
+
+namespace pj {
+
+// A lookup with a non-empty posting run.  pi = p | (i << 16).
+struct Hit {
+  uint32_t q;
+  uint32_t begin;
+  uint32_t count;
+  uint32_t pi;
+};
+
+struct ProbeView {
+  // probing strings: id q has bytes pbytes[poff[q] .. poff[q] + plen[q])
+  const uint8_t* pbytes;
+  const uint64_t* poff;
+  const uint32_t* plen;
+  uint32_t pbegin, pcount;  // probe ids pbegin .. pbegin + pcount - 1
+  const uint32_t* pid;      // probe id -> reported id (NULL: identity)
+  // indexed strings, sid order
+  const uint8_t* ibytes;
+  const uint64_t* ioff;
+  const uint32_t* ilen;
+  const uint32_t* ibbeg;  // first sid of each length, ilmax + 2 entries
+  int ilmax;
+  const uint32_t* iperm;  // sid -> reported id
+  uint32_t n_index;
+  const Slot* table;
+  unsigned long long mask;
+  const uint32_t* postings;
+  unsigned long long n_postings;
+  int tau;
+  int key_shift;  // pair key = a << key_shift | b
+};
+
+// Groups per probing string: lengths |s|-tau..|s| (self join, Alg. 1 line 4)
+// or |s|-tau..|s|+tau (R != S, Sec. 3.2), times tau + 1 segments.
+__host__ __device__ __forceinline__ int groups_per_probe(int tau, bool self) {
+  return (tau + 1) * (self ? tau + 1 : 2 * tau + 1);
+}
+
+// Group g of probing string q (length ls): indexed length l, segment i, its
+// even-partition start P and length li, and the multi-match window
+// [lo, hi] of start positions in q (Sec. 4.2):
+//   lo = max(P - (i-1), P + D - (tau+1-i)),  hi = min(P + (i-1), P + D + (tau+1-i)),
+// clipped to [0, ls - li], with D = ls - l.  False when the group selects
+// nothing (no such length indexed, no string of it visited before q, or an
+// empty window).
+__host__ __device__ __forceinline__ bool group_window(const ProbeView& v, bool self, uint32_t q, int ls, int g,
+                                                      int& l, int& i, int& P, int& li, int& lo, int& hi) {
+  const int tau = v.tau, parts = tau + 1;
+  l = ls - tau + g / parts;
+  i = 1 + g % parts;
+  if (l < parts || l > v.ilmax) return false;
+  const uint32_t b0 = v.ibbeg[l];
+  uint32_t b1 = v.ibbeg[l + 1];
+  if (self && l == ls && b1 > q) b1 = q;  // only strings visited before q
+  if (b1 <= b0) return false;
+  even_segment(l, tau, i, P, li);
+  const int D = ls - l;
+  lo = max(0, max(P - (i - 1), P + D - (parts - i)));
+  hi = min(ls - li, min(P + (i - 1), P + D + (parts - i)));
+  return hi >= lo;
+}
+
+__host__ __device__ __forceinline__ int table_find_any(const Slot* t, unsigned long long mask, unsigned long long key,
+                                                       uint32_t& begin, uint32_t& count) {
+#ifdef __CUDA_ARCH__
+  return table_find(t, mask, key, begin, count);
+#else
+  unsigned long long h = (key >> 7) & mask;
+  for (int probe = 0; probe < TABLE_MAX_PROBES; ++probe) {
+    if (t[h].key == key) {
+      begin = t[h].begin;
+      count = t[h].count;
+      return 1;
+    }
+    if (t[h].key == 0) return 0;
+    h = (h + 1) & mask;
+  }
+  return -1;
+#endif
+}
+
+// Lookup of s[p, li] in L_l^i.  Returns the number of postings to verify
+// (for the self join with l == |s|, only sids below q: runs ascend) and sets
+// begin.  err |= 1 for a run outside the postings, 2 for the probe limit.
+__host__ __device__ __forceinline__ uint32_t lookup(const ProbeView& v, bool self, const uint8_t* s, int ls,
+                                                    uint32_t q, int l, int i, int p, int li, uint32_t& begin,
+                                                    int& err) {
+  uint32_t cnt = 0;
+  begin = 0;
+  const int found = table_find_any(v.table, v.mask, seg_key(s + p, li, l, i), begin, cnt);
+  if (found < 0) {
+    err |= 2;
+    return 0;
+  }
+  if (found == 0) return 0;
+  if ((unsigned long long)begin + cnt > v.n_postings) {
+    err |= 1;
+    return 0;
+  }
+  if (self && l == ls) {
+    uint32_t x0 = 0, x1 = cnt;
+    while (x0 < x1) {
+      const uint32_t mid = (x0 + x1) >> 1;
+      if (v.postings[begin + mid] < q) x0 = mid + 1; else x1 = mid;
+    }
+    cnt = x0;
+  }
+  return cnt;
+}
+
+// Verify candidate `off` of hit h.  Returns true with the pair key and
+// ed = d_l + d_r when extension verification accepts it.
+template <int MAXW>
+__host__ __device__ __forceinline__ bool verify_candidate(const ProbeView& v, bool self, const Hit& h, uint32_t off,
+                                                          unsigned long long& key, int& ed,
+                                                          unsigned long long& cells, int& err) {
+  const uint32_t r = v.postings[h.begin + off];
+  if (r >= v.n_index) {
+    err |= 1;
+    return false;
+  }
+  const uint32_t q = h.q;
+  if (self && r == q) return false;  // a colliding run may hold the probe itself
+  const int p = (int)(h.pi & 0xFFFFu);
+  const int i = (int)(h.pi >> 16);
+  const int ls = (int)v.plen[q];
+  const int lr = (int)v.ilen[r];
+  if (i < 1 || i > v.tau + 1 || lr < v.tau + 1) return false;  // not a partitioned string
+  int P, li;
+  even_segment(lr, v.tau, i, P, li);
+  if (p + li > ls) return false;
+  if (!verify_ext<MAXW>(v.pbytes + v.poff[q], ls, v.ibytes + v.ioff[r], lr, i, p, li, P, v.tau, ed, cells))
+    return false;
+  const uint32_t qid = v.pid ? v.pid[q] : q;
+  const uint32_t rid = v.iperm[r];
+  const uint32_t ka = self ? min(qid, rid) : qid;
+  const uint32_t kb = self ? max(qid, rid) : rid;
+  key = ((unsigned long long)ka << v.key_shift) | kb;
+  return true;
+}
+
+}  // namespace pj

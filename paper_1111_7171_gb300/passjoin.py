@@ -1,0 +1,349 @@
+"""Thin Python binding of libpassjoin (the C ABI in include/passjoin.h).
+
+Argument marshalling only: every step of the join runs in the library's CUDA
+kernels.  PyTorch supplies device memory (the library's allocator callbacks
+draw from torch's caching allocator) and the stream (torch's current stream
+unless one is given).  There is no CPU fallback: if the library or a GPU is
+missing, every call raises.
+
+Strings can be given as
+  * a list of ``bytes``;
+  * ``(bytes_u8, offsets_u64)`` numpy arrays (host), or
+  * ``(bytes_u8, offsets)`` torch CUDA tensors (uint8 and int64/uint64), which
+    the library reads in place.
+
+Results are numpy structured arrays with fields (a, b, ed) sorted by (a, b);
+``DeviceResult`` keeps them in device memory.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libpassjoin.so")
+
+PJ_OK, PJ_EINVAL, PJ_ENOMEM, PJ_ECUDA, PJ_ETIMEDOUT, PJ_ECANCELED = 0, -1, -2, -3, -4, -5
+PJ_TAU_LIMIT = 32
+PAIR_DTYPE = np.dtype([("a", np.uint32), ("b", np.uint32), ("ed", np.uint32)])
+
+
+class PJError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str):
+        super().__init__(f"{where}: {detail} (code {code})")
+        self.code = code
+
+
+class pj_strings(ctypes.Structure):
+    _fields_ = [("bytes", ctypes.c_void_p), ("offsets", ctypes.c_void_p), ("n", ctypes.c_uint32),
+                ("on_device", ctypes.c_int)]
+
+
+class pj_stats(ctypes.Structure):
+    _fields_ = [("lookups", ctypes.c_uint64), ("candidates", ctypes.c_uint64), ("accepted", ctypes.c_uint64),
+                ("dp_cells", ctypes.c_uint64), ("fallback_pairs", ctypes.c_uint64)]
+
+
+class pj_result(ctypes.Structure):
+    _fields_ = [("pairs", ctypes.c_void_p), ("count", ctypes.c_uint64), ("on_device", ctypes.c_int),
+                ("stats", pj_stats), ("priv", ctypes.c_void_p)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class pj_options(ctypes.Structure):
+    _fields_ = [("stream", ctypes.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
+                ("verify_mode", ctypes.c_int), ("results_on_device", ctypes.c_int)]
+
+
+_lib = None
+_lib_lock = threading.Lock()
+
+
+def library():
+    """Load libpassjoin.so (raises if it has not been built)."""
+    global _lib
+    with _lib_lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libpassjoin.so is not built ({LIB_PATH}); run "
+                                   "`python -c 'import __graft_entry__ as g; g.build()'`")
+            L = ctypes.CDLL(LIB_PATH)
+            P = ctypes.POINTER
+            L.pj_options_init.argtypes = [P(pj_options)]
+            L.pj_options_init.restype = None
+            L.pj_build_index.argtypes = [P(pj_strings), ctypes.c_int, P(pj_options), P(ctypes.c_void_p)]
+            L.pj_build_index.restype = ctypes.c_int
+            L.pj_self_join.argtypes = [ctypes.c_void_p, ctypes.c_int, P(pj_result)]
+            L.pj_self_join.restype = ctypes.c_int
+            L.pj_join.argtypes = [P(pj_strings), P(pj_strings), ctypes.c_int, P(pj_options), P(pj_result)]
+            L.pj_join.restype = ctypes.c_int
+            L.pj_query.argtypes = [ctypes.c_void_p, P(pj_strings), ctypes.c_int, P(pj_result)]
+            L.pj_query.restype = ctypes.c_int
+            L.pj_result_free.argtypes = [P(pj_result)]
+            L.pj_result_free.restype = None
+            L.pj_index_free.argtypes = [ctypes.c_void_p]
+            L.pj_index_free.restype = None
+            L.pj_index_size.argtypes = [ctypes.c_void_p]
+            L.pj_index_size.restype = ctypes.c_uint32
+            L.pj_index_tau_max.argtypes = [ctypes.c_void_p]
+            L.pj_index_tau_max.restype = ctypes.c_int
+            L.pj_index_device_bytes.argtypes = [ctypes.c_void_p]
+            L.pj_index_device_bytes.restype = ctypes.c_uint64
+            L.pj_strerror.argtypes = [ctypes.c_int]
+            L.pj_strerror.restype = ctypes.c_char_p
+            L.pj_last_error.argtypes = []
+            L.pj_last_error.restype = ctypes.c_char_p
+            _lib = L
+    return _lib
+
+
+def _check(code: int, where: str):
+    if code != PJ_OK:
+        L = library()
+        raise PJError(code, where, f"{L.pj_strerror(code).decode()}: {L.pj_last_error().decode()}")
+
+
+# ------------------------------------------------------------- allocator --
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("libpassjoin needs a CUDA GPU; torch.cuda.is_available() is False")
+    return torch
+
+
+_LOG_ALLOC = bool(os.environ.get("PJ_LOG_ALLOC"))
+
+
+@ALLOC_FN
+def _torch_alloc(ctx, nbytes, stream):
+    try:
+        import torch
+        ptr = torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(), stream or 0)
+        if _LOG_ALLOC:
+            print(f"[alloc] {ptr:#x} {int(nbytes)} stream={stream}", flush=True)
+        return ptr
+    except Exception:  # reported to the caller as PJ_ENOMEM
+        return None
+
+
+@FREE_FN
+def _torch_free(ctx, ptr, stream):
+    import torch
+    if _LOG_ALLOC:
+        print(f"[free]  {ptr:#x}", flush=True)
+    torch.cuda.caching_allocator_delete(ptr)
+
+
+def make_options(stream=None, results_on_device: bool = False, torch_allocator: bool = True) -> pj_options:
+    torch = _torch()
+    opt = pj_options()
+    library().pj_options_init(ctypes.byref(opt))
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    opt.stream = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream) or 0))
+    if torch_allocator:
+        opt.alloc = _torch_alloc
+        opt.free = _torch_free
+    opt.results_on_device = 1 if results_on_device else 0
+    return opt
+
+
+# --------------------------------------------------------------- strings --
+
+class Strings:
+    """Marshalled pj_strings plus the buffers that back it."""
+
+    def __init__(self, data):
+        self._keep = []
+        s = pj_strings()
+        if isinstance(data, (list, tuple)) and (len(data) == 0 or isinstance(data[0], (bytes, bytearray))) \
+                and not (isinstance(data, tuple) and len(data) == 2 and hasattr(data[0], "dtype")):
+            lens = np.fromiter((len(x) for x in data), dtype=np.uint64, count=len(data))
+            off = np.zeros(len(data) + 1, dtype=np.uint64)
+            np.cumsum(lens, out=off[1:])
+            buf = np.frombuffer(b"".join(data), dtype=np.uint8) if len(data) else np.zeros(0, np.uint8)
+            self._host(s, buf, off)
+        elif isinstance(data, tuple) and len(data) == 2:
+            b, o = data
+            if hasattr(b, "is_cuda") and b.is_cuda:
+                if o.numel() != 0 and not o.is_cuda:
+                    raise ValueError("device bytes need device offsets")
+                b = b.contiguous()
+                o = o.contiguous()
+                self._keep += [b, o]
+                s.bytes = ctypes.c_void_p(b.data_ptr() if b.numel() else 0)
+                s.offsets = ctypes.c_void_p(o.data_ptr())
+                s.n = o.numel() - 1
+                s.on_device = 1
+            else:
+                self._host(s, np.asarray(b, dtype=np.uint8), np.asarray(o, dtype=np.uint64))
+        else:
+            raise TypeError("strings must be a list of bytes or a (bytes, offsets) pair")
+        self.c = s
+        self.n = int(s.n)
+
+    def _host(self, s, buf, off):
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        if buf.size == 0:
+            buf = np.zeros(1, np.uint8)
+        off = np.ascontiguousarray(off, dtype=np.uint64)
+        self._keep += [buf, off]
+        s.bytes = ctypes.c_void_p(buf.ctypes.data)
+        s.offsets = ctypes.c_void_p(off.ctypes.data)
+        s.n = len(off) - 1
+        s.on_device = 0
+
+
+# ---------------------------------------------------------------- results --
+
+class JoinResult:
+    """Host result: ``pairs`` (structured a, b, ed) and ``stats`` (dict)."""
+
+    def __init__(self, pairs: np.ndarray, stats: dict):
+        self.pairs = pairs
+        self.stats = stats
+
+    def __len__(self):
+        return len(self.pairs)
+
+
+class _DeviceBytes:
+    """__cuda_array_interface__ view of a raw device byte range."""
+
+    def __init__(self, ptr: int, nbytes: int):
+        self.__cuda_array_interface__ = {"shape": (nbytes,), "typestr": "|u1", "data": (ptr, False),
+                                         "version": 3, "strides": None}
+
+
+class DeviceResult:
+    """Result left in device memory; ``count``, ``stats``, ``to_host()``, ``free()``."""
+
+    def __init__(self, res: pj_result):
+        self._res = res
+        self.count = int(res.count)
+        self.stats = _stats(res.stats)
+        self.ptr = int(res.pairs or 0)
+
+    def tensor(self):
+        """The pairs as a uint8 torch CUDA tensor view (count * 12 bytes)."""
+        torch = _torch()
+        return torch.as_tensor(_DeviceBytes(self.ptr, self.count * PAIR_DTYPE.itemsize), device="cuda")
+
+    def to_host(self) -> np.ndarray:
+        if self.count == 0:
+            return np.zeros(0, dtype=PAIR_DTYPE)
+        return self.tensor().cpu().numpy().view(PAIR_DTYPE).copy()
+
+    def free(self):
+        if self._res is not None:
+            library().pj_result_free(ctypes.byref(self._res))
+            self._res = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def _stats(st: pj_stats) -> dict:
+    return dict(lookups=int(st.lookups), candidates=int(st.candidates), accepted=int(st.accepted),
+                dp_cells=int(st.dp_cells), fallback_pairs=int(st.fallback_pairs))
+
+
+def _take(res: pj_result):
+    if res.on_device:
+        return DeviceResult(res)
+    n = int(res.count)
+    if n:
+        raw = (ctypes.c_uint8 * (n * PAIR_DTYPE.itemsize)).from_address(res.pairs)
+        pairs = np.frombuffer(raw, dtype=PAIR_DTYPE).copy()
+    else:
+        pairs = np.zeros(0, dtype=PAIR_DTYPE)
+    stats = _stats(res.stats)
+    library().pj_result_free(ctypes.byref(res))
+    return JoinResult(pairs, stats)
+
+
+# ----------------------------------------------------------------- index --
+
+class Index:
+    """A resident segment index (pj_index*)."""
+
+    def __init__(self, handle, options, strings_keepalive):
+        self._h = handle
+        self._opt = options
+        self._keep = strings_keepalive
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise RuntimeError("index already freed")
+        return self._h
+
+    @property
+    def n(self) -> int:
+        return int(library().pj_index_size(self.handle))
+
+    @property
+    def tau_max(self) -> int:
+        return int(library().pj_index_tau_max(self.handle))
+
+    @property
+    def device_bytes(self) -> int:
+        return int(library().pj_index_device_bytes(self.handle))
+
+    def free(self):
+        if self._h:
+            library().pj_index_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------ entry points --
+
+def pj_build_index(strings, tau_max: int, stream=None, results_on_device: bool = False) -> Index:
+    """pj_build_index: resident segment index for thresholds 0..tau_max."""
+    opt = make_options(stream, results_on_device)
+    S = Strings(strings)
+    h = ctypes.c_void_p()
+    _check(library().pj_build_index(ctypes.byref(S.c), int(tau_max), ctypes.byref(opt), ctypes.byref(h)),
+           "pj_build_index")
+    return Index(h, opt, None)
+
+
+def pj_self_join(index: Index, tau: int):
+    """pj_self_join: all pairs a < b of the indexed set with ED <= tau."""
+    res = pj_result()
+    _check(library().pj_self_join(index.handle, int(tau), ctypes.byref(res)), "pj_self_join")
+    return _take(res)
+
+
+def pj_join(R, S, tau: int, stream=None, results_on_device: bool = False):
+    """pj_join: all (a in R, b in S) with ED <= tau."""
+    opt = make_options(stream, results_on_device)
+    r, s = Strings(R), Strings(S)
+    res = pj_result()
+    _check(library().pj_join(ctypes.byref(r.c), ctypes.byref(s.c), int(tau), ctypes.byref(opt), ctypes.byref(res)),
+           "pj_join")
+    return _take(res)
+
+
+def pj_query(index: Index, batch, tau: int):
+    """pj_query: (query position, indexed id) pairs with ED <= tau."""
+    b = Strings(batch)
+    res = pj_result()
+    _check(library().pj_query(index.handle, ctypes.byref(b.c), int(tau), ctypes.byref(res)), "pj_query")
+    return _take(res)

@@ -1,0 +1,228 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Integer work, so the bar is bit-exact: the sorted (a, b, ed) arrays must be
+equal.  Sizes here span many tiles, warps and posting runs and include ragged
+tails; full-size workloads are checked on sampled outputs that the oracle
+computes one by one (tests/test_gpu_fullsize.py).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from oracle import method as M
+from paper_1111_7171_gb300 import passjoin as pj
+from paper_1111_7171_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    yield
+
+
+def gpu_self(strings, tau, tau_max=None):
+    idx = pj.pj_build_index(strings, tau if tau_max is None else tau_max)
+    try:
+        return pj.pj_self_join(idx, tau)
+    finally:
+        idx.free()
+
+
+def cpu_self(strings, tau, banded=False):
+    b, o = synth.pack(strings)
+    return oracle.self_join(b, o, tau, banded=banded)
+
+
+def assert_same(got, want, what=""):
+    got = np.asarray(got)
+    if len(got) != len(want) or not np.array_equal(got, want):
+        gs = set(map(tuple, got.tolist()))
+        ws = set(map(tuple, want.tolist()))
+        raise AssertionError(f"{what}: {len(got)} vs {len(want)} pairs; "
+                             f"extra {sorted(gs - ws)[:5]} missing {sorted(ws - gs)[:5]}")
+
+
+# --------------------------------------------------------------- workloads --
+
+@pytest.mark.parametrize("tau", [0, 1, 2, 3])
+def test_short2k_full(tau):
+    strings = synth.generate("short2k", 2)
+    assert_same(gpu_self(strings, tau).pairs, cpu_self(strings, tau), f"short2k tau={tau}")
+
+
+@pytest.mark.parametrize("tau", [1, 2, 3, 4])
+def test_short_subsample(tau):
+    strings = synth.generate("short", tau, n=6000)
+    assert_same(gpu_self(strings, tau).pairs, cpu_self(strings, tau), f"short n=6000 tau={tau}")
+
+
+@pytest.mark.parametrize("tau", [2, 4, 6, 8])
+def test_medium_subsample(tau):
+    strings = synth.generate("medium", tau, n=5000)
+    assert_same(gpu_self(strings, tau).pairs, cpu_self(strings, tau, banded=True), f"medium tau={tau}")
+
+
+@pytest.mark.parametrize("tau", [8, 16, 32])
+def test_long_subsample(tau):
+    strings = synth.generate("long", tau, n=1200)
+    assert_same(gpu_self(strings, tau).pairs, cpu_self(strings, tau, banded=True), f"long tau={tau}")
+
+
+def test_index_reuse_across_tau():
+    """One index built for tau_max answers every smaller tau exactly."""
+    strings = synth.generate("short", 4, n=3000)
+    idx = pj.pj_build_index(strings, 4)
+    try:
+        for tau in range(0, 5):
+            assert_same(pj.pj_self_join(idx, tau).pairs, cpu_self(strings, tau), f"tau={tau}")
+    finally:
+        idx.free()
+
+
+def test_candidate_and_accept_counts_match_algorithm():
+    """The kernels examine exactly the (s, r, i, p) matches of Alg. 1 with
+    multi-match selection (visiting by length, then id) and accept exactly
+    the ones extension verification accepts."""
+    strings = synth.generate("short", 3, n=700)
+    st = {}
+    M.pass_join_self(strings, 3, order="id", stats=st)
+    res = gpu_self(strings, 3)
+    assert res.stats["candidates"] == st["tuples"]
+    assert res.stats["accepted"] == st["accepted"]
+
+
+# --------------------------------------------------------- R x S and query --
+
+def _rs_sets(seed, tau):
+    S = synth.generate("short", tau, n=2500, seed=seed)
+    S += [b"", b"a", b"ab", b"abc"[:tau], b"zz"]
+    R = synth.generate("short", tau, n=800, seed=seed + 1)
+    rng = np.random.default_rng(seed)
+    for k in rng.integers(0, len(S), size=300).tolist():
+        s = bytearray(S[k])
+        for _ in range(int(rng.integers(0, tau + 1))):
+            if s and rng.random() < 0.4:
+                del s[int(rng.integers(0, len(s)))]
+            else:
+                s.insert(int(rng.integers(0, len(s) + 1)), ord("a") + int(rng.integers(0, 26)))
+        R.append(bytes(s))
+    R += [b"", b"b", b"abcd"]
+    return R, S
+
+
+@pytest.mark.parametrize("tau", [1, 2, 4])
+def test_join_rs(tau):
+    R, S = _rs_sets(40 + tau, tau)
+    rb, ro = synth.pack(R)
+    sb, so = synth.pack(S)
+    assert_same(pj.pj_join(R, S, tau).pairs, oracle.join(rb, ro, sb, so, tau), f"join tau={tau}")
+
+
+def test_query_against_resident_index():
+    R, S = _rs_sets(77, 4)
+    sb, so = synth.pack(S)
+    idx = pj.pj_build_index(S, 4)
+    try:
+        for tau in (1, 2, 3, 4):
+            batch = R[tau * 100:(tau + 1) * 150]
+            qb, qo = synth.pack(batch)
+            assert_same(pj.pj_query(idx, batch, tau).pairs, oracle.join(qb, qo, sb, so, tau), f"query tau={tau}")
+    finally:
+        idx.free()
+
+
+def test_device_inputs_match_host_inputs():
+    strings = synth.generate("medium", 4, n=2000)
+    b, o = synth.pack(strings)
+    db = torch.from_numpy(b).cuda()
+    do = torch.from_numpy(o.astype(np.int64)).cuda()
+    idx = pj.pj_build_index((db, do), 4)
+    try:
+        assert_same(pj.pj_self_join(idx, 4).pairs, cpu_self(strings, 4, banded=True), "device input")
+    finally:
+        idx.free()
+
+
+def test_results_on_device():
+    strings = synth.generate("short", 2, n=3000)
+    idx = pj.pj_build_index(strings, 2, results_on_device=True)
+    try:
+        r = pj.pj_self_join(idx, 2)
+        assert isinstance(r, pj.DeviceResult)
+        host = r.to_host()
+        r.free()
+        assert_same(host, cpu_self(strings, 2), "device results")
+    finally:
+        idx.free()
+
+
+# ------------------------------------------------------------- edge cases --
+
+def test_empty_and_single():
+    for strings in ([], [b""], [b"abc"], [b"", b""], [b"a", b""]):
+        for tau in (0, 1, 3):
+            assert_same(gpu_self(strings, tau).pairs, cpu_self(strings, tau), f"{strings} tau={tau}")
+
+
+def test_all_identical_one_posting_run():
+    strings = [b"abcdefgh"] * 700 + [b"abcdefgX", b"Xbcdefgh"]
+    for tau in (0, 1, 2):
+        assert_same(gpu_self(strings, tau).pairs, cpu_self(strings, tau), f"identical tau={tau}")
+
+
+def test_one_symbol_alphabet():
+    rng = np.random.default_rng(3)
+    strings = [b"a" * int(k) for k in rng.integers(0, 30, size=400)]
+    for tau in (1, 3, 5):
+        assert_same(gpu_self(strings, tau).pairs, cpu_self(strings, tau), f"unary tau={tau}")
+
+
+def test_lengths_around_tau_plus_one():
+    rng = np.random.default_rng(5)
+    strings = []
+    for _ in range(900):
+        L = int(rng.integers(0, 9))
+        strings.append(bytes(rng.choice(list(b"abc"), size=L).tolist()))
+    for tau in (2, 3, 4, 6):
+        assert_same(gpu_self(strings, tau).pairs, cpu_self(strings, tau), f"short lengths tau={tau}")
+
+
+def test_long_strings_beyond_staging():
+    rng = np.random.default_rng(9)
+    base = bytes(rng.integers(97, 101, size=5000).tolist())
+    strings = [base]
+    for k in range(6):
+        s = bytearray(base)
+        for _ in range(k):
+            s[int(rng.integers(0, len(s)))] = ord("z")
+        strings.append(bytes(s))
+    strings += [bytes(rng.integers(97, 101, size=int(L)).tolist()) for L in rng.integers(4990, 5010, size=20)]
+    for tau in (3, 8):
+        assert_same(gpu_self(strings, tau).pairs, cpu_self(strings, tau, banded=True), f"5000-byte tau={tau}")
+
+
+def test_invalid_arguments():
+    idx = pj.pj_build_index([b"abc", b"abd"], 2)
+    try:
+        with pytest.raises(pj.PJError) as e:
+            pj.pj_self_join(idx, 3)
+        assert e.value.code == pj.PJ_EINVAL
+        with pytest.raises(pj.PJError):
+            pj.pj_self_join(idx, -1)
+    finally:
+        idx.free()
+    with pytest.raises(pj.PJError) as e:
+        pj.pj_build_index([b"abc"], pj.PJ_TAU_LIMIT + 1)
+    assert e.value.code == pj.PJ_EINVAL
+    with pytest.raises(pj.PJError) as e:
+        pj.pj_build_index((np.frombuffer(b"abcdef", np.uint8), np.array([0, 4, 2, 6], np.uint64)), 1)
+    assert e.value.code == pj.PJ_EINVAL
+    with pytest.raises(pj.PJError) as e:
+        pj.pj_join([b"a"], [b"b"], pj.PJ_TAU_LIMIT + 1)
+    assert e.value.code == pj.PJ_EINVAL

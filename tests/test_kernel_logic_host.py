@@ -1,0 +1,98 @@
+"""The probe/verify kernels' per-thread logic, run on the CPU.
+
+tests/host_logic/probe_emu.cu includes the same __host__ __device__ functions
+the kernels call (group windows, lookups, extension verification) and runs
+them through the kernels' two phases on the host.  Its pair sets must equal
+the oracle's, and its candidate / accepted counts must equal those of the
+paper's algorithm (oracle.method, visiting by length then id).  CPU only.
+"""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import method as M
+from paper_1111_7171_gb300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "tests", "host_logic", "probe_emu.cu")
+CSRC = os.path.join(ROOT, "paper_1111_7171_gb300", "csrc")
+
+
+@pytest.fixture(scope="module")
+def emu(tmp_path_factory):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    exe = tmp_path_factory.mktemp("emu") / "probe_emu"
+    subprocess.run([nvcc, "-std=c++17", "-O2", "-I", CSRC, "-I", os.path.join(ROOT, "include"), "-o", str(exe), SRC],
+                   check=True)
+    return str(exe)
+
+
+def run_emu(exe, tmp, strings, tau, queries=None):
+    b, o = synth.pack(strings)
+    (tmp / "b").write_bytes(b.tobytes())
+    (tmp / "o").write_bytes(o.tobytes())
+    args = [exe, str(tmp / "b"), str(tmp / "o"), str(tau)]
+    if queries is not None:
+        qb, qo = synth.pack(queries)
+        (tmp / "qb").write_bytes(qb.tobytes())
+        (tmp / "qo").write_bytes(qo.tobytes())
+        args += [str(tmp / "qb"), str(tmp / "qo")]
+    out = subprocess.run(args, capture_output=True, text=True, check=True).stdout.split("\n")
+    st = list(map(int, out[0].split()[1:]))
+    pairs = np.array([tuple(map(int, line.split())) for line in out[1:] if line.strip()],
+                     dtype=np.int64).reshape(-1, 3)
+    return st, pairs
+
+
+def oracle_self(strings, tau):
+    b, o = synth.pack(strings)
+    r = oracle.self_join(b, o, tau)
+    return np.stack([r["a"], r["b"], r["ed"]], axis=1).astype(np.int64) if len(r) else np.zeros((0, 3), np.int64)
+
+
+@pytest.mark.parametrize("name,tau,n", [("short2k", 2, 2000), ("short", 1, 3000), ("short", 2, 3000),
+                                        ("short", 4, 2000), ("medium", 4, 800), ("medium", 8, 600),
+                                        ("long", 16, 150)])
+def test_self_join_logic(emu, tmp_path, name, tau, n):
+    strings = synth.generate(name, tau, n=n)
+    st, pairs = run_emu(emu, tmp_path, strings, tau)
+    assert st[4] == 0
+    want = oracle_self(strings, tau) if name != "long" else None
+    if want is None:
+        b, o = synth.pack(strings)
+        r = oracle.self_join(b, o, tau, banded=True)
+        want = np.stack([r["a"], r["b"], r["ed"]], axis=1).astype(np.int64) if len(r) else np.zeros((0, 3), np.int64)
+    assert np.array_equal(pairs, want)
+
+
+def test_counts_equal_the_algorithm(emu, tmp_path):
+    strings = synth.generate("short", 3, n=500)
+    st, _ = run_emu(emu, tmp_path, strings, 3)
+    ref = {}
+    M.pass_join_self(strings, 3, order="id", stats=ref)
+    assert st[1] == ref["tuples"] and st[2] == ref["accepted"]
+
+
+def test_short_and_empty_strings(emu, tmp_path):
+    rng = np.random.default_rng(2)
+    strings = [bytes(rng.choice(list(b"ab"), size=int(L)).tolist()) for L in rng.integers(0, 7, size=300)]
+    for tau in (0, 1, 2, 3):
+        st, pairs = run_emu(emu, tmp_path, strings, tau)
+        assert np.array_equal(pairs, oracle_self(strings, tau)), tau
+
+
+def test_rs_join_logic(emu, tmp_path):
+    S = synth.generate("short", 3, n=1500) + [b"", b"ab", b"abc"]
+    R = synth.generate("short", 3, n=400, seed=5) + [s[1:] for s in S[:200]] + [s + b"x" for s in S[200:300]] + [b""]
+    st, pairs = run_emu(emu, tmp_path, S, 3, queries=R)
+    rb, ro = synth.pack(R)
+    sb, so = synth.pack(S)
+    r = oracle.join(rb, ro, sb, so, 3)
+    want = np.stack([r["a"], r["b"], r["ed"]], axis=1).astype(np.int64)
+    assert np.array_equal(pairs, want)
