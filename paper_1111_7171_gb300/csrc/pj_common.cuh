@@ -46,6 +46,9 @@ Ctx make_ctx(const pj_options* opt);
 void trace_mark(const Ctx& c, const char* phase);
 // Same trace, without synchronising (marks host-side progress only).
 void trace_note(const char* what);
+// With the environment variable PJ_DEBUG_DUMP=<prefix>, writes `bytes` bytes
+// of device memory to the file <prefix>.<name> (after synchronising).
+void debug_dump(const Ctx& c, const char* name, const void* dev, size_t bytes);
 
 // Device array of T obtained from a Ctx; freed (stream-ordered) on scope exit.
 template <class T>

@@ -98,6 +98,19 @@ void trace_note(const char* what) {
   fflush(stderr);
 }
 
+void debug_dump(const Ctx& c, const char* name, const void* dev, size_t bytes) {
+  const char* prefix = getenv("PJ_DEBUG_DUMP");
+  if (!prefix || !prefix[0]) return;
+  std::vector<char> h(bytes);
+  if (bytes) PJ_CUDA(cudaMemcpyAsync(h.data(), dev, bytes, cudaMemcpyDeviceToHost, c.stream));
+  c.sync();
+  const std::string path = std::string(prefix) + "." + name;
+  FILE* f = fopen(path.c_str(), "wb");
+  if (!f) return;
+  if (bytes) fwrite(h.data(), 1, bytes, f);
+  fclose(f);
+}
+
 // ---------------------------------------------------------------- A1 ------
 
 namespace {
@@ -341,6 +354,15 @@ void build_partition(pj_index& idx, int tau, Partition& part) {
   if (h_err) fail(PJ_ECUDA, "segment table insertion failed");
   trace_mark(c, "partition: table");
   if (getenv("PJ_CHECK_INDEX")) check_partition(c, part);
+  if (getenv("PJ_DEBUG_DUMP")) {
+    const std::string t = std::to_string(tau);
+    debug_dump(c, ("build_postings" + t).c_str(), part.postings.p, part.postings.bytes());
+    debug_dump(c, ("build_table" + t).c_str(), part.table.p, part.table.bytes());
+    debug_dump(c, "build_sbytes", idx.sbytes.p, idx.sbytes.bytes());
+    debug_dump(c, "build_soff", idx.soff.p, idx.soff.bytes());
+    debug_dump(c, "build_slen", idx.slen.p, idx.slen.bytes());
+    debug_dump(c, "build_perm", idx.perm.p, idx.perm.bytes());
+  }
 }
 
 // Host-side audit of one partition (environment PJ_CHECK_INDEX=1): the runs

@@ -1,14 +1,13 @@
 // Probe and verification half of the hot path, and the join entry points.
 //
 //   A4  multi-match-aware substring selection + index lookup (Sec. 4.2,
-//       Alg. 2, Lemma 2): k_probe_hits, one thread per (probing string,
-//       indexed length l, segment i) group; each thread looks up the
-//       selected substrings s[p, l_i] of its window and writes one Hit per
-//       non-empty posting run.  Blocks aggregate their hits through shared
-//       memory, so the kernel has no warp-level collectives.
-//   A6  extension-based verification (Sec. 5.2, Alg. 3): k_verify_hits, a
-//       load-balanced expansion of the hits' runs into candidates
-//       (q, r, i, p), one candidate per thread: segment bytes compared, then
+//       Alg. 2, Lemma 2): one thread per (probing string, indexed length l,
+//       segment i) group looks up the selected substrings s[p, l_i] of its
+//       window.  k_group_counts counts the non-empty posting runs, a prefix
+//       sum places them, k_group_hits writes them as Hits.
+//   A6  extension-based verification (Sec. 5.2, Alg. 3): k_verify_hits
+//       expands the hits' runs into candidates (q, r, i, p); each thread takes
+//       runs of consecutive candidates: segment bytes compared, then
 //       d_l = VERIFYSTRINGPAIR(s_l, r_l, i-1) and, if it passes,
 //       d_r = VERIFYSTRINGPAIR(s_r, r_r, tau+1-i), each the length-aware band
 //       of Sec. 5.1 held in registers with the Lemma 4 early exit.
@@ -48,86 +47,69 @@ struct AccOut {
 
 constexpr int BLOCK = 256;
 
-// Block-wide exclusive prefix sum of one value per thread, shared memory
-// only.  Every thread of the block must call it.  Returns the exclusive
-// prefix; *total receives the block sum.
-__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* sm, uint32_t* total) {
-  const int tid = threadIdx.x;
-  sm[tid] = v;
-  __syncthreads();
-  for (int off = 1; off < BLOCK; off <<= 1) {
-    const uint32_t x = tid >= off ? sm[tid - off] : 0u;
-    __syncthreads();
-    sm[tid] += x;
-    __syncthreads();
-  }
-  const uint32_t incl = sm[tid];
-  *total = sm[BLOCK - 1];
-  __syncthreads();
-  return incl - v;
+// The kernels of this file use no warp-level collectives and no block
+// barriers: every thread works alone and publishes through global atomics or
+// prefix sums.  (Earlier forms that placed shuffles, ballots or
+// __syncthreads right after the divergent verification loops lost the
+// contributions of lanes still inside those loops.)
+
+__device__ __forceinline__ void add_counter(unsigned long long* c, unsigned long long v) {
+  if (v) atomicAdd(c, v);
 }
 
 // ---------------------------------------------------------------- A4 ------
 
+// Pass 1: number of non-empty lookups of every group (probe, length, segment).
 template <bool SELF>
-__global__ void __launch_bounds__(BLOCK) k_probe_hits(const ProbeView v, unsigned long long n_groups, Hit* hits,
-                                                      unsigned long long cap, Counters* ctr) {
-  __shared__ uint32_t sm[BLOCK];
-  __shared__ unsigned long long s_base;
-  __shared__ unsigned long long s_lookups;
-  __shared__ int s_err;
-  const int tid = threadIdx.x;
-  if (tid == 0) {
-    s_lookups = 0;
-    s_err = 0;
-  }
-  __syncthreads();
+__global__ void __launch_bounds__(BLOCK) k_group_counts(const ProbeView v, unsigned long long n_groups,
+                                                        uint32_t* __restrict__ counts, Counters* ctr) {
   const int G = groups_per_probe(v.tau, SELF);
-  for (unsigned long long tile = blockIdx.x; tile * BLOCK < n_groups; tile += gridDim.x) {
-    const unsigned long long t = tile * BLOCK + tid;
-    bool valid = false;
-    int l = 0, i = 0, P = 0, li = 0, lo = 0, hi = -1, ls = 0;
-    uint32_t q = 0;
-    const uint8_t* s = nullptr;
-    if (t < n_groups) {
-      q = v.pbegin + (uint32_t)(t / G);
-      ls = (int)v.plen[q];
-      s = v.pbytes + v.poff[q];
-      valid = group_window(v, SELF, q, ls, (int)(t % G), l, i, P, li, lo, hi);
-    }
-    // round 1: count the non-empty runs of this group's window
+  unsigned long long lookups = 0;
+  int err = 0;
+  for (unsigned long long t = (unsigned long long)blockIdx.x * BLOCK + threadIdx.x; t < n_groups;
+       t += (unsigned long long)gridDim.x * BLOCK) {
+    const uint32_t q = v.pbegin + (uint32_t)(t / G);
+    const int ls = (int)v.plen[q];
+    const uint8_t* s = v.pbytes + v.poff[q];
+    int l, i, P, li, lo, hi;
     uint32_t nh = 0;
-    int err = 0;
-    if (valid) {
+    if (group_window(v, SELF, q, ls, (int)(t % G), l, i, P, li, lo, hi)) {
       for (int p = lo; p <= hi; ++p) {
         uint32_t b;
         if (lookup(v, SELF, s, ls, q, l, i, p, li, b, err)) ++nh;
       }
-      atomicAdd(&s_lookups, (unsigned long long)(hi - lo + 1));
+      lookups += (unsigned long long)(hi - lo + 1);
     }
-    if (err) atomicOr(&s_err, err);
-    uint32_t total;
-    const uint32_t excl = block_excl_scan(nh, sm, &total);
-    if (tid == 0) s_base = total ? atomicAdd(&ctr->hits, (unsigned long long)total) : 0ull;
-    __syncthreads();
-    // round 2: write the hits
-    if (nh) {
-      unsigned long long pos = s_base + excl;
-      int err2 = 0;
-      for (int p = lo; p <= hi; ++p) {
+    counts[t] = nh;
+  }
+  add_counter(&ctr->lookups, lookups);
+  if (err) atomicOr(&ctr->err, (unsigned long long)err);
+}
+
+// Pass 2: the same lookups again, each non-empty one written as a Hit at the
+// group's prefix-sum offset.
+template <bool SELF>
+__global__ void __launch_bounds__(BLOCK) k_group_hits(const ProbeView v, unsigned long long n_groups,
+                                                      const uint32_t* __restrict__ counts,
+                                                      const uint32_t* __restrict__ hit_off, Hit* __restrict__ hits) {
+  const int G = groups_per_probe(v.tau, SELF);
+  for (unsigned long long t = (unsigned long long)blockIdx.x * BLOCK + threadIdx.x; t < n_groups;
+       t += (unsigned long long)gridDim.x * BLOCK) {
+    if (counts[t] == 0) continue;
+    const uint32_t q = v.pbegin + (uint32_t)(t / G);
+    const int ls = (int)v.plen[q];
+    const uint8_t* s = v.pbytes + v.poff[q];
+    int l, i, P, li, lo, hi;
+    int err = 0;
+    uint32_t pos = hit_off[t];
+    const uint32_t end = pos + counts[t];
+    if (group_window(v, SELF, q, ls, (int)(t % G), l, i, P, li, lo, hi)) {
+      for (int p = lo; p <= hi && pos < end; ++p) {
         uint32_t b;
-        const uint32_t c = lookup(v, SELF, s, ls, q, l, i, p, li, b, err2);
-        if (c) {
-          if (pos < cap) hits[pos] = Hit{q, b, c, (uint32_t)p | ((uint32_t)i << 16)};
-          ++pos;
-        }
+        const uint32_t c = lookup(v, SELF, s, ls, q, l, i, p, li, b, err);
+        if (c) hits[pos++] = Hit{q, b, c, (uint32_t)p | ((uint32_t)i << 16)};
       }
     }
-    __syncthreads();  // s_base is reused by the next tile
-  }
-  if (tid == 0) {
-    atomicAdd(&ctr->lookups, s_lookups);
-    if (s_err) atomicOr(&ctr->err, (unsigned long long)s_err);
   }
 }
 
@@ -138,90 +120,44 @@ __global__ void k_hit_counts(const Hit* __restrict__ hits, unsigned long long n,
 
 // ---------------------------------------------------------------- A6 ------
 
-constexpr int V_ITEMS = 4;
-constexpr int V_CHUNK = BLOCK * V_ITEMS;
+constexpr int V_RUN = 4;  // consecutive candidates per thread per step
 
+// Every thread verifies runs of V_RUN consecutive candidates: one binary
+// search over the candidate offsets locates the first hit, then the walk
+// moves forward hit by hit.
 template <int MAXW, bool SELF>
 __global__ void __launch_bounds__(BLOCK) k_verify_hits(const ProbeView v, const Hit* __restrict__ hits,
                                                        const unsigned long long* __restrict__ cand_off,
                                                        unsigned long long n_hits, unsigned long long n_cand,
                                                        AccOut out, Counters* ctr) {
-  __shared__ unsigned long long s_off[V_CHUNK + 1];
-  __shared__ unsigned long long s_h0;
-  __shared__ unsigned long long s_accbase;
-  __shared__ uint32_t s_nacc;
-  __shared__ unsigned long long s_cells;
-  __shared__ int s_err;
-  const int tid = threadIdx.x;
-  if (tid == 0) {
-    s_cells = 0;
-    s_err = 0;
-  }
-  __syncthreads();
   unsigned long long cells = 0;
   int err = 0;
-  for (unsigned long long chunk = blockIdx.x; chunk * V_CHUNK < n_cand; chunk += gridDim.x) {
-    const unsigned long long c_lo = chunk * V_CHUNK;
-    const unsigned long long c_hi = min(n_cand, c_lo + V_CHUNK);
-    if (tid == 0) {  // last hit whose first candidate is <= c_lo
-      unsigned long long lo = 0, hi = n_hits;
-      while (hi - lo > 1) {
-        const unsigned long long mid = (lo + hi) >> 1;
-        if (cand_off[mid] <= c_lo) lo = mid; else hi = mid;
-      }
-      s_h0 = lo;
-      s_nacc = 0;
+  const unsigned long long stride = (unsigned long long)gridDim.x * BLOCK * V_RUN;
+  for (unsigned long long c0 = ((unsigned long long)blockIdx.x * BLOCK + threadIdx.x) * V_RUN; c0 < n_cand;
+       c0 += stride) {
+    unsigned long long lo = 0, hi = n_hits;  // last hit whose first candidate is <= c0
+    while (hi - lo > 1) {
+      const unsigned long long mid = (lo + hi) >> 1;
+      if (cand_off[mid] <= c0) lo = mid; else hi = mid;
     }
-    __syncthreads();
-    const unsigned long long h0 = s_h0;
-    const int nload = (int)min((unsigned long long)(V_CHUNK + 1), n_hits - h0);
-    for (int k = tid; k < nload; k += BLOCK) s_off[k] = cand_off[h0 + k];
-    __syncthreads();
-    bool ok[V_ITEMS];
-    unsigned long long key[V_ITEMS];
-    int ed[V_ITEMS];
-    uint32_t mine = 0;
-#pragma unroll
-    for (int j = 0; j < V_ITEMS; ++j) {
-      ok[j] = false;
-      key[j] = 0;
-      ed[j] = 0;
-      const unsigned long long c = c_lo + tid + (unsigned long long)j * BLOCK;
-      if (c < c_hi) {
-        int lo = 0, hi = nload;  // last k with s_off[k] <= c
-        while (hi - lo > 1) {
-          const int mid = (lo + hi) >> 1;
-          if (s_off[mid] <= c) lo = mid; else hi = mid;
-        }
-        const Hit h = hits[h0 + lo];
-        ok[j] = verify_candidate<MAXW>(v, SELF, h, (uint32_t)(c - s_off[lo]), key[j], ed[j], cells, err);
-        mine += ok[j] ? 1u : 0u;
-      }
-    }
-    const uint32_t my_pos = mine ? atomicAdd(&s_nacc, mine) : 0u;
-    __syncthreads();
-    if (tid == 0) s_accbase = s_nacc ? atomicAdd(&ctr->accepted, (unsigned long long)s_nacc) : 0ull;
-    __syncthreads();
-    unsigned long long pos = s_accbase + my_pos;
-#pragma unroll
-    for (int j = 0; j < V_ITEMS; ++j) {
-      if (ok[j]) {
+    unsigned long long h = lo;
+    const unsigned long long c1 = min(n_cand, c0 + V_RUN);
+    for (unsigned long long c = c0; c < c1; ++c) {
+      while (h + 1 < n_hits && cand_off[h + 1] <= c) ++h;
+      const Hit hit = hits[h];
+      unsigned long long key = 0;
+      int ed = 0;
+      if (verify_candidate<MAXW>(v, SELF, hit, (uint32_t)(c - cand_off[h]), key, ed, cells, err)) {
+        const unsigned long long pos = atomicAdd(&ctr->accepted, 1ull);
         if (pos < out.cap) {
-          out.key[pos] = key[j];
-          out.ed[pos] = (uint32_t)ed[j];
+          out.key[pos] = key;
+          out.ed[pos] = (uint32_t)ed;
         }
-        ++pos;
       }
     }
-    __syncthreads();  // shared state is rewritten by the next chunk
   }
-  atomicAdd(&s_cells, cells);
-  if (err) atomicOr(&s_err, err);
-  __syncthreads();
-  if (tid == 0) {
-    atomicAdd(&ctr->cells, s_cells);
-    if (s_err) atomicOr(&ctr->err, (unsigned long long)s_err);
-  }
+  add_counter(&ctr->cells, cells);
+  if (err) atomicOr(&ctr->err, (unsigned long long)err);
 }
 
 // ---------------------------------------------------------------- A8 ------
@@ -312,7 +248,7 @@ static unsigned persistent_grid(K kernel, unsigned long long work_blocks) {
 template <int MAXW, bool SELF>
 static void launch_verify(const Ctx& c, const ProbeView& v, const Hit* hits, const unsigned long long* off,
                           unsigned long long n_hits, unsigned long long n_cand, AccOut out, Counters* ctr) {
-  const unsigned grid = persistent_grid(k_verify_hits<MAXW, SELF>, (n_cand + V_CHUNK - 1) / V_CHUNK);
+  const unsigned grid = persistent_grid(k_verify_hits<MAXW, SELF>, (n_cand + BLOCK * V_RUN - 1) / (BLOCK * V_RUN));
   k_verify_hits<MAXW, SELF><<<grid, BLOCK, 0, c.stream>>>(v, hits, off, n_hits, n_cand, out, ctr);
   PJ_LAUNCHED("k_verify_hits");
 }
@@ -348,26 +284,30 @@ static void probe_and_verify(const Ctx& c, const ProbeView& v0, uint32_t fb_coun
   const int G = groups_per_probe(v0.tau, SELF);
   const unsigned long long group_budget = 64ull << 20;  // groups per chunk
   const uint32_t chunk_items = (uint32_t)std::max<unsigned long long>(1, group_budget / G);
-  unsigned long long hit_cap = 1ull << 22;
-  DBuf<Hit> hits(c, hit_cap);
+  DBuf<Hit> hits;
+  DBuf<uint32_t> gcount, goff;
   DBuf<unsigned long long> cnt, off;
   for (uint32_t done = 0; done < v0.pcount;) {
     ProbeView v = v0;
     v.pbegin = v0.pbegin + done;
     v.pcount = std::min(chunk_items, v0.pcount - done);
     const unsigned long long n_groups = (unsigned long long)v.pcount * G;
-    unsigned long long n_hits = 0;
-    for (int attempt = 0;; ++attempt) {
-      PJ_CUDA(cudaMemsetAsync(&ctr->hits, 0, sizeof(unsigned long long), c.stream));
-      const unsigned grid = persistent_grid(k_probe_hits<SELF>, (n_groups + BLOCK - 1) / BLOCK);
-      k_probe_hits<SELF><<<grid, BLOCK, 0, c.stream>>>(v, n_groups, hits.p, hit_cap, ctr);
-      PJ_LAUNCHED("k_probe_hits");
-      PJ_CUDA(cudaMemcpyAsync(&n_hits, &ctr->hits, sizeof(n_hits), cudaMemcpyDeviceToHost, c.stream));
-      c.sync();
-      if (n_hits <= hit_cap) break;
-      if (attempt >= 1) fail(PJ_ECUDA, "hit buffer overflowed twice");
-      hit_cap = n_hits;
-      hits.reset(c, hit_cap);
+    gcount.reset(c, n_groups);
+    goff.reset(c, n_groups);
+    const unsigned g1 = persistent_grid(k_group_counts<SELF>, (n_groups + BLOCK - 1) / BLOCK);
+    k_group_counts<SELF><<<g1, BLOCK, 0, c.stream>>>(v, n_groups, gcount.p, ctr);
+    PJ_LAUNCHED("k_group_counts");
+    exclusive_scan<uint32_t>(c, gcount.p, goff.p, n_groups);
+    uint32_t last[2] = {0, 0};
+    PJ_CUDA(cudaMemcpyAsync(&last[0], goff.p + n_groups - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.stream));
+    PJ_CUDA(cudaMemcpyAsync(&last[1], gcount.p + n_groups - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.stream));
+    c.sync();
+    const unsigned long long n_hits = (unsigned long long)last[0] + last[1];
+    if (n_hits > 0) {
+      hits.reset(c, n_hits);
+      const unsigned g2 = persistent_grid(k_group_hits<SELF>, (n_groups + BLOCK - 1) / BLOCK);
+      k_group_hits<SELF><<<g2, BLOCK, 0, c.stream>>>(v, n_groups, gcount.p, goff.p, hits.p);
+      PJ_LAUNCHED("k_group_hits");
     }
     trace_mark(c, "join: probe (hits)");
     if (n_hits == 0) {
@@ -383,6 +323,8 @@ static void probe_and_verify(const Ctx& c, const ProbeView& v0, uint32_t fb_coun
     unsigned long long n_cand = 0;
     PJ_CUDA(cudaMemcpyAsync(&n_cand, off.p + n_hits, sizeof(n_cand), cudaMemcpyDeviceToHost, c.stream));
     c.sync();
+    debug_dump(c, "hits", hits.p, n_hits * sizeof(Hit));
+    debug_dump(c, "cand_off", off.p, (n_hits + 1) * sizeof(unsigned long long));
     h.candidates += n_cand;
     if (n_cand) {
 #define PJ_CALL(W) launch_verify<W, SELF>(c, v, hits.p, off.p, n_hits, n_cand, out, ctr)
@@ -429,6 +371,8 @@ static void run_join(const Ctx& c, const ProbeView& v, bool self, uint32_t fb_co
     cap = h.accepted;
   }
   const uint64_t nacc = h.accepted;
+  debug_dump(c, "acc_key", acc_key.p, std::min<uint64_t>(nacc, cap) * sizeof(unsigned long long));
+  debug_dump(c, "acc_ed", acc_ed.p, std::min<uint64_t>(nacc, cap) * sizeof(uint32_t));
   uint64_t count = 0;
   DBuf<pj_pair> pairs;
   if (nacc > 0) {
@@ -490,6 +434,20 @@ static ProbeView index_side(const pj_index& idx, const Partition& part) {
 }
 
 static void self_join_impl(pj_index& idx, int tau, pj_result* out, bool on_device) {
+  struct DumpAfter {
+    pj_index& idx;
+    int tau;
+    ~DumpAfter() {
+      if (!getenv("PJ_DEBUG_DUMP")) return;
+      try {
+        debug_dump(idx.ctx, "after_postings", idx.parts[tau].postings.p, idx.parts[tau].postings.bytes());
+        debug_dump(idx.ctx, "after_sbytes", idx.sbytes.p, idx.sbytes.bytes());
+        debug_dump(idx.ctx, "after_soff", idx.soff.p, idx.soff.bytes());
+        debug_dump(idx.ctx, "after_slen", idx.slen.p, idx.slen.bytes());
+      } catch (...) {
+      }
+    }
+  } dump_after{idx, tau};
   const Partition& part = idx.parts[tau];
   ProbeView v = index_side(idx, part);
   v.pbytes = idx.sbytes.p;

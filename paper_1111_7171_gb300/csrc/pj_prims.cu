@@ -35,6 +35,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(const T* __restrict
   }
   T incl = warp_incl_scan(sum);
   if (lane == 31) warp_tot[warp] = incl;
+  __syncwarp();
   __syncthreads();
   if (warp == 0) {
     T w = warp_tot[lane];
@@ -42,6 +43,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(const T* __restrict
     warp_tot[lane] = wi - w;  // exclusive offset of each warp
     if (lane == 31 && tile_sums) tile_sums[blockIdx.x] = wi;
   }
+  __syncwarp();
   __syncthreads();
   T run = incl - sum + warp_tot[warp];
 #pragma unroll
@@ -81,6 +83,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const K* __restrict__ ke
     const size_t i = base + (size_t)k * RS_THREADS + tid;
     if (i < n) atomicAdd(&h[(unsigned)(keys[i] >> shift) & 0xFFu], 1u);
   }
+  __syncwarp();
   __syncthreads();
   hist[(size_t)tid * ntiles + blockIdx.x] = h[tid];
 }

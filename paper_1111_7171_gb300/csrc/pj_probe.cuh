@@ -129,29 +129,32 @@ template <int MAXW>
 __host__ __device__ __forceinline__ bool verify_candidate(const ProbeView& v, bool self, const Hit& h, uint32_t off,
                                                           unsigned long long& key, int& ed,
                                                           unsigned long long& cells, int& err) {
+  // Single exit: see vsp().
+  bool ok = false;
   const uint32_t r = v.postings[h.begin + off];
-  if (r >= v.n_index) {
-    err |= 1;
-    return false;
-  }
   const uint32_t q = h.q;
-  if (self && r == q) return false;  // a colliding run may hold the probe itself
   const int p = (int)(h.pi & 0xFFFFu);
   const int i = (int)(h.pi >> 16);
-  const int ls = (int)v.plen[q];
-  const int lr = (int)v.ilen[r];
-  if (i < 1 || i > v.tau + 1 || lr < v.tau + 1) return false;  // not a partitioned string
-  int P, li;
-  even_segment(lr, v.tau, i, P, li);
-  if (p + li > ls) return false;
-  if (!verify_ext<MAXW>(v.pbytes + v.poff[q], ls, v.ibytes + v.ioff[r], lr, i, p, li, P, v.tau, ed, cells))
-    return false;
-  const uint32_t qid = v.pid ? v.pid[q] : q;
-  const uint32_t rid = v.iperm[r];
-  const uint32_t ka = self ? min(qid, rid) : qid;
-  const uint32_t kb = self ? max(qid, rid) : rid;
-  key = ((unsigned long long)ka << v.key_shift) | kb;
-  return true;
+  if (r >= v.n_index) {
+    err |= 1;
+  } else if (!(self && r == q)) {  // a colliding run may hold the probe itself
+    const int ls = (int)v.plen[q];
+    const int lr = (int)v.ilen[r];
+    if (i >= 1 && i <= v.tau + 1 && lr >= v.tau + 1) {  // r is a partitioned string
+      int P, li;
+      even_segment(lr, v.tau, i, P, li);
+      if (p + li <= ls &&
+          verify_ext<MAXW>(v.pbytes + v.poff[q], ls, v.ibytes + v.ioff[r], lr, i, p, li, P, v.tau, ed, cells)) {
+        const uint32_t qid = v.pid ? v.pid[q] : q;
+        const uint32_t rid = v.iperm[r];
+        const uint32_t ka = self ? min(qid, rid) : qid;
+        const uint32_t kb = self ? max(qid, rid) : rid;
+        key = ((unsigned long long)ka << v.key_shift) | kb;
+        ok = true;
+      }
+    }
+  }
+  return ok;
 }
 
 }  // namespace pj

@@ -27,60 +27,65 @@ using std::min;
 // the band; if it exceeds t the pair is dissimilar (Lemma 4).
 template <int MAXW>
 __host__ __device__ __forceinline__ int vsp(const uint8_t* x, int nx, const uint8_t* y, int ny, int t,
-                                   unsigned long long& cells) {
-  const uint8_t* a = x;
-  const uint8_t* b = y;
-  int na = nx, nb = ny;
-  if (nx > ny) {
-    a = y;
-    b = x;
-    na = ny;
-    nb = nx;
-  }
+                                            unsigned long long& cells) {
+  // Single exit and structured loops only: callers reach warp and block
+  // barriers right after this function, so every lane must leave it through
+  // the same path.
+  const uint8_t* a = nx <= ny ? x : y;
+  const uint8_t* b = nx <= ny ? y : x;
+  const int na = nx <= ny ? nx : ny;
+  const int nb = nx <= ny ? ny : nx;
   const int D = nb - na;
   const int cap = t + 1;
-  if (D > t) return cap;
-  if (na == 0) return D;
-  const int dlo = -((t - D) >> 1);
-  const int w = ((t + D) >> 1) - dlo + 1;  // <= t + 1 <= MAXW
-  int V[MAXW];
-  int eoff[MAXW];
-#pragma unroll
-  for (int k = 0; k < MAXW; ++k) {
-    const int j = dlo + k;  // row 0: M(0, j) = j
-    V[k] = (k < w && j >= 0 && j <= nb) ? min(j, cap) : cap;
-    eoff[k] = abs(D - dlo - k);
-  }
-  for (int i = 1; i <= na; ++i) {
-    const uint8_t ca = a[i - 1];
-    int left = cap;
-    int emin = cap;
-    const int j0 = i + dlo;
+  int res = cap;
+  if (D <= t && na == 0) res = D;
+  if (D <= t && na > 0) {
+    const int dlo = -((t - D) >> 1);
+    const int w = ((t + D) >> 1) - dlo + 1;  // <= t + 1 <= MAXW
+    int V[MAXW];
+    int eoff[MAXW];
 #pragma unroll
     for (int k = 0; k < MAXW; ++k) {
-      const int j = j0 + k;
-      const int up = (k + 1 < MAXW) ? V[k + 1] : cap;
-      int v = cap;
-      if (k < w && j >= 0 && j <= nb) {
-        if (j == 0) {
-          v = min(i, cap);
-        } else {
-          const int diag = V[k] + (ca != b[j - 1] ? 1 : 0);
-          v = min(min(diag, up + 1), min(left + 1, cap));
-        }
-      }
-      V[k] = v;
-      left = v;
-      emin = min(emin, v + eoff[k]);
+      const int j = dlo + k;  // row 0: M(0, j) = j
+      V[k] = (k < w && j >= 0 && j <= nb) ? min(j, cap) : cap;
+      eoff[k] = abs(D - dlo - k);
     }
-    cells += (unsigned long long)w;
-    if (emin > t) return cap;
-  }
-  const int kres = D - dlo;
-  int res = cap;
+    bool alive = true;
+    for (int i = 1; i <= na; ++i) {
+      const uint8_t ca = a[i - 1];
+      int left = cap;
+      int emin = cap;
+      const int j0 = i + dlo;
 #pragma unroll
-  for (int k = 0; k < MAXW; ++k)
-    if (k == kres) res = V[k];
+      for (int k = 0; k < MAXW; ++k) {
+        const int j = j0 + k;
+        const int up = (k + 1 < MAXW) ? V[k + 1] : cap;
+        int val = cap;
+        if (k < w && j >= 0 && j <= nb) {
+          if (j == 0) {
+            val = min(i, cap);
+          } else {
+            const int diag = V[k] + (ca != b[j - 1] ? 1 : 0);
+            val = min(min(diag, up + 1), min(left + 1, cap));
+          }
+        }
+        V[k] = val;
+        left = val;
+        emin = min(emin, val + eoff[k]);
+      }
+      cells += (unsigned long long)w;
+      if (emin > t) {  // Lemma 4: every expected edit distance exceeds t
+        alive = false;
+        break;
+      }
+    }
+    if (alive) {
+      const int kres = D - dlo;
+#pragma unroll
+      for (int k = 0; k < MAXW; ++k)
+        if (k == kres) res = V[k];
+    }
+  }
   return res;
 }
 
@@ -89,16 +94,27 @@ __host__ __device__ __forceinline__ int vsp(const uint8_t* x, int nx, const uint
 // length li) it matched.  Returns true with ed = d_l + d_r when accepted.
 template <int MAXW>
 __host__ __device__ __forceinline__ bool verify_ext(const uint8_t* s, int ls, const uint8_t* r, int lr, int i, int p, int li,
-                                           int P, int tau, int& ed, unsigned long long& cells) {
-  for (int k = 0; k < li; ++k)
-    if (s[p + k] != r[P + k]) return false;  // hash collision, not a match
-  const int tl = i - 1, tr = tau + 1 - i;
-  const int dl = vsp<MAXW>(s, p, r, P, tl, cells);
-  if (dl > tl) return false;
-  const int dr = vsp<MAXW>(s + p + li, ls - p - li, r + P + li, lr - P - li, tr, cells);
-  if (dr > tr) return false;
-  ed = dl + dr;
-  return true;
+                                                    int P, int tau, int& ed, unsigned long long& cells) {
+  bool same = true;
+  for (int k = 0; k < li; ++k) {
+    if (s[p + k] != r[P + k]) {  // hash collision, not a match
+      same = false;
+      break;
+    }
+  }
+  bool ok = false;
+  if (same) {
+    const int tl = i - 1, tr = tau + 1 - i;
+    const int dl = vsp<MAXW>(s, p, r, P, tl, cells);
+    if (dl <= tl) {
+      const int dr = vsp<MAXW>(s + p + li, ls - p - li, r + P + li, lr - P - li, tr, cells);
+      if (dr <= tr) {
+        ed = dl + dr;
+        ok = true;
+      }
+    }
+  }
+  return ok;
 }
 
 }  // namespace pj
