@@ -1,0 +1,367 @@
+"""Benchmark: Pass-Join self join on one GB300 (or N replicas).
+
+One step = the whole hot path on one batch: pj_build_index (packed store,
+length buckets, even-partition segment index) + pj_self_join (multi-match
+selection and lookup, extension verification, dedupe and compaction) over
+the `short` workload: 1,000,000 strings over 27 symbols with Zipf(1.1)
+characters, lengths N(15, 4) clipped to [5, 40], 30% in near-duplicate
+clusters, at tau = 4.
+
+Metric: verified candidate pairs per second (candidates = (probe, indexed
+string, segment, position) matches that extension verification examines),
+with the self-join time per step beside it.
+
+`value` times the step with the strings already in HBM and the result left
+in device memory; `e2e` times the same step through the C ABI with host
+buffers (host->device copy of the strings and device->host copy of the pairs
+inside the timed region).  The L2 (129 MB) is flushed between timed steps by
+writing a 256 MB buffer, because the workload's 15 MB store would otherwise
+stay cached across steps.
+
+`--impl reference` times the CPU oracle (length filter + full DP, OpenMP on
+the host cores) on a bounded sample of the same workload instead.
+
+Under torchrun with N > 1 each rank runs the same job on its own GPU
+(replicas; the path needs no collective) and rank 0 reports the sum of the
+work over the max of the times.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "self-join verified candidate pairs/s (short workload, 1M strings)"
+UNIT = "pairs/s"
+L2_FLUSH_BYTES = 256 << 20
+INT_LANES_PER_SM = 128      # 32-bit integer lanes per SM (4 sub-partitions x 32)
+OPS_PER_CELL = 8            # integer ops of one length-aware DP cell
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--workload", default="short")
+    ap.add_argument("--tau", type=int, default=4)
+    ap.add_argument("--n", type=int, default=None, help="override the workload size (testing only)")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU-baseline sample time")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks --
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self._t = threading.Thread(target=self._read, daemon=True)
+        self._t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self._t:
+            self._t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- helpers --
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(strings, tau, target_s, seed=123):
+    """The oracle (length filter + full Wagner-Fischer DP on every pair) on a
+    bounded sample: every string of the set against Q sampled probe strings.
+    Rate = DP-verified pairs per second; also the extrapolated self-join time."""
+    import oracle
+    from paper_1111_7171_gb300 import synth
+    buf, off = synth.pack(strings)
+    n = len(strings)
+    rng = np.random.default_rng(seed)
+    lens = np.diff(off).astype(np.int64)
+    hist = np.bincount(lens, minlength=lens.max() + 2 + tau)
+    cum = np.concatenate([[0], np.cumsum(hist)])
+
+    def pairs_for(idx):
+        tot = 0
+        for k in idx.tolist():
+            L = int(lens[k])
+            lo, hi = max(0, L - tau), L + tau
+            tot += int(cum[min(hi + 1, len(cum) - 1)] - cum[lo])
+        return tot
+
+    q = 16
+    while True:
+        idx = rng.choice(n, size=q, replace=False)
+        qb, qo = synth.pack([strings[k] for k in idx.tolist()])
+        t0 = time.perf_counter()
+        oracle.similar_to(qb, qo, buf, off, tau, banded=False)
+        dt = time.perf_counter() - t0
+        if dt >= target_s * 0.5 or q >= n:
+            break
+        q = min(n, int(q * max(2.0, min(16.0, target_s / max(dt, 1e-3)))))
+    pairs = pairs_for(idx)
+    full_pairs = int(sum(int(cum[min(int(L) + tau + 1, len(cum) - 1)] - cum[max(0, int(L) - tau)]) for L in lens)) // 2
+    rate = pairs / dt
+    return {"value": rate, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{q} probe strings x all {n} strings (length filter, then full DP on {pairs} pairs) "
+                      f"in {dt:.1f} s; self join extrapolated to {full_pairs / rate:.0f} s",
+            "seconds": dt, "pairs": pairs, "self_join_s_extrapolated": full_pairs / rate}
+
+
+# -------------------------------------------------------------- reference --
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1111_7171_gb300 import synth
+    strings = synth.generate(args.workload, args.tau, n=args.n)
+    per_step = []
+    base = None
+    for k in range(args.warmup + args.steps):
+        res = cpu_baseline(strings, args.tau, args.cpu_seconds / 2, seed=1000 + k)
+        if k >= args.warmup:
+            per_step.append(res)
+            base = res
+    secs = sum(r["seconds"] for r in per_step)
+    pairs = sum(r["pairs"] for r in per_step)
+    value = pairs / secs
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic", "config": workload_config(args, len(strings)),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": base["cores"], "kind": "oracle",
+                             "sample": base["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(args, n):
+    return {"workload": f"{args.workload}: {n} strings, tau={args.tau} (self join)", "n_strings": n,
+            "tau": args.tau, "l2": "flushed between timed steps (256 MB write)",
+            "parallelism": f"replicas x{args.gpus}" if args.gpus > 1 else "1 GPU"}
+
+
+# ----------------------------------------------------------------- native --
+
+def run_native(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1111_7171_gb300 import passjoin as pj
+    from paper_1111_7171_gb300 import synth
+
+    world, rank, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1111_7171_gb300 import build as pj_build
+    pj_build.build()
+
+    strings = synth.generate(args.workload, args.tau, n=args.n)
+    buf, off = synth.pack(strings)
+    n = len(strings)
+    d_bytes = torch.from_numpy(buf).to(dev)
+    d_off = torch.from_numpy(off.astype(np.int64)).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+
+    def device_step():
+        idx = pj.pj_build_index((d_bytes, d_off), args.tau, results_on_device=True, lazy_partitions=True)
+        r = pj.pj_self_join(idx, args.tau)
+        out = (r.count, r.stats, idx.build_ms)
+        r.free()
+        idx.free()
+        return out
+
+    def host_step():
+        idx = pj.pj_build_index((buf, off), args.tau, lazy_partitions=True)
+        r = pj.pj_self_join(idx, args.tau)
+        idx.free()
+        return len(r.pairs), r.stats
+
+    for _ in range(args.warmup):
+        device_step()
+    barrier()
+
+    # ---- timed device-resident steps
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = pj.pj_kernel_launches()
+    step_ms, stats_all, build_ms, counts = [], [], [], []
+    barrier()
+    for _ in range(args.steps):
+        flush.zero_()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        cnt, st, bms = device_step()
+        ev1.record(stream)
+        ev1.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+        stats_all.append(st)
+        build_ms.append(bms)
+        counts.append(cnt)
+    barrier()
+    launches = pj.pj_kernel_launches() - launches0
+    clk = clocks.stop()
+
+    # ---- end-to-end through the C ABI with host buffers
+    host_step()
+    barrier()
+    e2e_ms = []
+    e2e_pairs = 0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        e2e_pairs, _ = host_step()
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    barrier()
+
+    cand = sum(s["candidates"] for s in stats_all)
+    total_s = sum(step_ms) / 1e3
+    e2e_s = sum(e2e_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([cand, total_s, e2e_s], dtype=torch.float64, device=dev)
+        c_sum = t.clone()
+        dist.all_reduce(c_sum, op=dist.ReduceOp.SUM)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        cand_all, total_s, e2e_s = float(c_sum[0]), float(t[1]), float(t[2])
+    else:
+        cand_all = float(cand)
+
+    if rank == 0:
+        st = stats_all[-1]
+        peaks, peak_src = measured_peaks()
+        sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+        sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+        alu_peak_gcells = sm_count * INT_LANES_PER_SM * sm_mhz * 1e6 / OPS_PER_CELL / 1e9
+        verify_ms = statistics.mean(s["verify_ms"] for s in stats_all)
+        probe_ms = statistics.mean(s["probe_ms"] for s in stats_all)
+        cells = statistics.mean(s["dp_cells"] for s in stats_all)
+        achieved = cells / (verify_ms / 1e3) / 1e9
+        roofline = {"bound": "alu", "kernel": "k_verify_hits", "achieved": achieved, "peak": alu_peak_gcells,
+                    "unit": "Gcell/s", "frac": achieved / alu_peak_gcells, "traffic": None,
+                    "peak_source": f"{sm_count} SMs x {INT_LANES_PER_SM} int32 lanes x {sm_mhz:.0f} MHz "
+                                   f"({peak_src} SM clock) / {OPS_PER_CELL} ops per DP cell"}
+        cpu = None
+        if not args.no_cpu_baseline:
+            cpu = cpu_baseline(strings, args.tau, args.cpu_seconds)
+            cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        ms_per_step = 1e3 * total_s / args.steps
+        line = {
+            "metric": METRIC, "value": cand_all / total_s, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": workload_config(args, n),
+            "self_join_ms": ms_per_step,
+            "pairs": int(counts[-1]),
+            "work": {"candidates": int(st["candidates"]), "lookups": int(st["lookups"]), "hits": int(st["hits"]),
+                     "accepted": int(st["accepted"]), "dp_cells": int(st["dp_cells"])},
+            "phase_ms": {"store_build": statistics.mean(build_ms),
+                         "partition": statistics.mean(s["partition_ms"] for s in stats_all),
+                         "probe": probe_ms, "verify": verify_ms,
+                         "fallback": statistics.mean(s["fallback_ms"] for s in stats_all),
+                         "dedupe": statistics.mean(s["dedupe_ms"] for s in stats_all)},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": cand_all / e2e_s, "unit": UNIT, "ms_per_step": 1e3 * e2e_s / args.steps,
+                    "h2d_bytes_per_step": int(buf.nbytes + off.nbytes),
+                    "d2h_bytes_per_step": int(e2e_pairs * 12)},
+            "gpu_launches": int(launches),
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -79,13 +79,20 @@ typedef struct {
   uint32_t ed;
 } pj_pair;
 
-/* Work counters of one call (all exact counts). */
+/* Work counters of one call (all exact counts) and its device times. */
 typedef struct {
   uint64_t lookups;     /* selected substrings looked up in the segment index */
   uint64_t candidates;  /* (probe, indexed string, segment, position) matches verified */
   uint64_t accepted;    /* matches accepted by extension verification */
   uint64_t dp_cells;    /* DP cells evaluated by the verification kernels */
   uint64_t fallback_pairs; /* pairs verified directly because a string has length <= tau */
+  uint64_t hits;        /* lookups whose posting run was non-empty */
+  float probe_ms;       /* device time of selection + lookup (CUDA events on the call's stream) */
+  float verify_ms;      /* device time of extension verification */
+  float fallback_ms;    /* device time of the short-string verification */
+  float dedupe_ms;      /* device time of sort, min-reduce and compaction */
+  float partition_ms;   /* device time spent building a lazily built threshold index, else 0 */
+  uint32_t reserved;
 } pj_stats;
 
 typedef struct {
@@ -108,6 +115,9 @@ typedef struct {
   void* alloc_ctx;
   int verify_mode;        /* PJ_VERIFY_* */
   int results_on_device;  /* 1: pj_result.pairs stays in device memory */
+  int lazy_partitions;    /* 1: pj_build_index builds only the store; each threshold's
+                             segment index is built by the first call that needs it */
+  int reserved;
 } pj_options;
 
 typedef struct pj_index pj_index; /* opaque, library-owned */
@@ -170,6 +180,13 @@ uint32_t pj_index_size(const pj_index* idx);
 int pj_index_tau_max(const pj_index* idx);
 /* Device bytes held by the index (store + every threshold's tables). */
 uint64_t pj_index_device_bytes(const pj_index* idx);
+
+/* Device time of pj_build_index (store and eagerly built thresholds), ms. */
+float pj_index_build_ms(const pj_index* idx);
+
+/* Number of CUDA kernels this library has launched since it was loaded
+ * (all threads, all calls). */
+uint64_t pj_kernel_launches(void);
 
 /* Release a result / an index.  NULL and already-released results are
  * ignored.  A result must be released before the index it came from. */

@@ -22,8 +22,14 @@ struct Error {
 
 [[noreturn]] void fail(int code, const std::string& msg);
 void check_cuda(cudaError_t e, const char* what, const char* file, int line);
+void count_launch();
 #define PJ_CUDA(call) ::pj::check_cuda((call), #call, __FILE__, __LINE__)
-#define PJ_LAUNCHED(name) ::pj::check_cuda(cudaGetLastError(), name, __FILE__, __LINE__)
+// After every kernel launch: count it and surface launch errors.
+#define PJ_LAUNCHED(name)                                                  \
+  do {                                                                     \
+    ::pj::count_launch();                                                  \
+    ::pj::check_cuda(cudaGetLastError(), name, __FILE__, __LINE__);        \
+  } while (0)
 
 // -------------------------------------------------------------- allocator --
 
@@ -40,6 +46,31 @@ struct Ctx {
 };
 
 Ctx make_ctx(const pj_options* opt);
+
+// Device time between start() and stop(), measured with CUDA events on one
+// stream.  ms() synchronises on the stop event.
+struct EventTimer {
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaStream_t s = nullptr;
+  explicit EventTimer(cudaStream_t stream) : s(stream) {
+    PJ_CUDA(cudaEventCreate(&a));
+    PJ_CUDA(cudaEventCreate(&b));
+  }
+  ~EventTimer() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+  EventTimer(const EventTimer&) = delete;
+  EventTimer& operator=(const EventTimer&) = delete;
+  void start() { PJ_CUDA(cudaEventRecord(a, s)); }
+  void stop() { PJ_CUDA(cudaEventRecord(b, s)); }
+  float ms() {
+    PJ_CUDA(cudaEventSynchronize(b));
+    float t = 0.f;
+    PJ_CUDA(cudaEventElapsedTime(&t, a, b));
+    return t;
+  }
+};
 
 // Phase trace on stderr, enabled by the environment variable PJ_TRACE=1: each
 // call synchronises the stream and prints the time since the previous mark.

@@ -10,6 +10,7 @@
 //       run heads by flag + prefix sum, open-addressing table key -> run.
 #include <cstdio>
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cstdlib>
 #include <cstring>
@@ -28,6 +29,9 @@ void set_last_error(const std::string& msg) { g_last_error = msg; }
 const std::string& last_error() { return g_last_error; }
 
 void fail(int code, const std::string& msg) { throw Error{code, msg}; }
+
+static std::atomic<unsigned long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void check_cuda(cudaError_t e, const char* what, const char* file, int line) {
   if (e == cudaSuccess) return;
@@ -397,6 +401,19 @@ void check_partition(const Ctx& c, const Partition& part) {
     fail(PJ_ECUDA, "index audit failed");
 }
 
+Partition& ensure_partition(pj_index& idx, int tau, float* ms) {
+  Partition& part = idx.parts[tau];
+  if (ms) *ms = 0.f;
+  if (part.tau == tau) return part;
+  EventTimer t(idx.ctx.stream);
+  t.start();
+  build_partition(idx, tau, part);
+  t.stop();
+  const float dt = t.ms();
+  if (ms) *ms = dt;
+  return part;
+}
+
 void upload_probe_set(const Ctx& c, const pj_strings& R, ProbeSet& out) {
   const uint8_t* dbytes = nullptr;
   const uint64_t* doff = nullptr;
@@ -456,10 +473,16 @@ int pj_build_index(const pj_strings* S, int tau_max, const pj_options* opt, pj_i
     idx = new pj_index();
     idx->ctx = pj::make_ctx(opt);
     idx->results_on_device = opt ? opt->results_on_device != 0 : false;
+    idx->lazy = opt ? opt->lazy_partitions != 0 : false;
     PJ_CUDA(cudaGetDevice(&idx->device));
+    pj::EventTimer timer(idx->ctx.stream);
+    timer.start();
     pj::build_store(*idx, *S);
     idx->parts.resize(tau_max + 1);
-    for (int t = 0; t <= tau_max; ++t) pj::build_partition(*idx, t, idx->parts[t]);
+    if (!idx->lazy)
+      for (int t = 0; t <= tau_max; ++t) pj::build_partition(*idx, t, idx->parts[t]);
+    timer.stop();
+    idx->build_ms = timer.ms();
     idx->ctx.sync();
     *out = idx;
     return PJ_OK;
@@ -475,6 +498,8 @@ int pj_build_index(const pj_strings* S, int tau_max, const pj_options* opt, pj_i
 }
 
 uint32_t pj_index_size(const pj_index* idx) { return idx ? idx->n : 0; }
+float pj_index_build_ms(const pj_index* idx) { return idx ? idx->build_ms : 0.f; }
+uint64_t pj_kernel_launches(void) { return pj::g_launches.load(); }
 int pj_index_tau_max(const pj_index* idx) { return idx ? (int)idx->parts.size() - 1 : 0; }
 uint64_t pj_index_device_bytes(const pj_index* idx) { return idx ? idx->device_bytes() : 0; }
 

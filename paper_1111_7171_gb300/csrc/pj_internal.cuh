@@ -99,6 +99,8 @@ struct pj_index {
   int device = 0;
   std::mutex mu;             // serialises calls that use the index
   bool results_on_device = false;
+  bool lazy = false;         // thresholds are built on first use
+  float build_ms = 0.f;
   uint32_t n = 0;
   int lmax = 0;              // longest string
   uint64_t total_bytes = 0;
@@ -118,6 +120,9 @@ namespace pj {
 void build_store(pj_index& idx, const pj_strings& S);
 // Builds the segment index of idx for one threshold.
 void build_partition(pj_index& idx, int tau, Partition& part);
+// Returns idx.parts[tau], building it first if the index is lazy and it is
+// not built yet (*ms receives the device time spent, else 0).
+Partition& ensure_partition(pj_index& idx, int tau, float* ms);
 
 // Device copy of a probe set (R or a query batch) in input order.
 struct ProbeSet {

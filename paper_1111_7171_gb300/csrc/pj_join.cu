@@ -275,12 +275,17 @@ struct ResultPriv {
   Ctx ctx;
 };
 
+struct Timings {
+  float probe = 0.f, verify = 0.f, fallback = 0.f, dedupe = 0.f;
+};
+
 // Probe + verify for all probing strings, in chunks of probing strings whose
 // groups fit the hit buffer; then the short-string fallback.  Returns the
 // number of accepted matches (the buffer holds min(that, out.cap)).
 template <bool SELF>
 static void probe_and_verify(const Ctx& c, const ProbeView& v0, uint32_t fb_count, AccOut out, Counters* ctr,
-                             Counters& h) {
+                             Counters& h, Timings& tm) {
+  EventTimer tp(c.stream), tv(c.stream), tf(c.stream);
   const int G = groups_per_probe(v0.tau, SELF);
   const unsigned long long group_budget = 64ull << 20;  // groups per chunk
   const uint32_t chunk_items = (uint32_t)std::max<unsigned long long>(1, group_budget / G);
@@ -294,6 +299,7 @@ static void probe_and_verify(const Ctx& c, const ProbeView& v0, uint32_t fb_coun
     const unsigned long long n_groups = (unsigned long long)v.pcount * G;
     gcount.reset(c, n_groups);
     goff.reset(c, n_groups);
+    tp.start();
     const unsigned g1 = persistent_grid(k_group_counts<SELF>, (n_groups + BLOCK - 1) / BLOCK);
     k_group_counts<SELF><<<g1, BLOCK, 0, c.stream>>>(v, n_groups, gcount.p, ctr);
     PJ_LAUNCHED("k_group_counts");
@@ -311,6 +317,8 @@ static void probe_and_verify(const Ctx& c, const ProbeView& v0, uint32_t fb_coun
     }
     trace_mark(c, "join: probe (hits)");
     if (n_hits == 0) {
+      tp.stop();
+      tm.probe += tp.ms();
       done += v.pcount;
       continue;
     }
@@ -322,28 +330,37 @@ static void probe_and_verify(const Ctx& c, const ProbeView& v0, uint32_t fb_coun
     exclusive_scan<unsigned long long>(c, cnt.p, off.p, n_hits + 1);
     unsigned long long n_cand = 0;
     PJ_CUDA(cudaMemcpyAsync(&n_cand, off.p + n_hits, sizeof(n_cand), cudaMemcpyDeviceToHost, c.stream));
-    c.sync();
+    tp.stop();
+    tm.probe += tp.ms();
     debug_dump(c, "hits", hits.p, n_hits * sizeof(Hit));
     debug_dump(c, "cand_off", off.p, (n_hits + 1) * sizeof(unsigned long long));
     h.candidates += n_cand;
+    h.hits += n_hits;
     if (n_cand) {
+      tv.start();
 #define PJ_CALL(W) launch_verify<W, SELF>(c, v, hits.p, off.p, n_hits, n_cand, out, ctr)
       PJ_BY_TAU(v.tau, PJ_CALL);
 #undef PJ_CALL
+      tv.stop();
+      tm.verify += tv.ms();
     }
     trace_mark(c, "join: verify");
     done += v.pcount;
   }
   if (fb_count) {
     ProbeView v = v0;
+    tf.start();
 #define PJ_CALL(W) launch_fallback<W, SELF>(c, v, fb_count, out, ctr)
     PJ_BY_TAU(v.tau, PJ_CALL);
 #undef PJ_CALL
+    tf.stop();
+    tm.fallback += tf.ms();
   }
-  const unsigned long long cand = h.candidates;
+  const unsigned long long cand = h.candidates, nh = h.hits;
   PJ_CUDA(cudaMemcpyAsync(&h, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, c.stream));
   c.sync();
   h.candidates = cand;
+  h.hits = nh;
   if (h.err)
     fail(PJ_ECUDA, std::string("segment index consistency check failed (") +
                        ((h.err & 1) ? "posting outside the index" : "probe limit reached") + ")");
@@ -355,6 +372,7 @@ static void run_join(const Ctx& c, const ProbeView& v, bool self, uint32_t fb_co
                      bool results_on_device, pj_result* out) {
   uint64_t cap = 1u << 20;
   Counters h{};
+  Timings tm;
   DBuf<unsigned long long> acc_key;
   DBuf<uint32_t> acc_ed;
   DBuf<Counters> ctr(c, 1);
@@ -363,14 +381,17 @@ static void run_join(const Ctx& c, const ProbeView& v, bool self, uint32_t fb_co
     acc_ed.reset(c, cap);
     PJ_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(Counters), c.stream));
     h = Counters{};
+    tm = Timings{};
     AccOut o{acc_key.p, acc_ed.p, cap};
-    if (self) probe_and_verify<true>(c, v, fb_count, o, ctr.p, h);
-    else probe_and_verify<false>(c, v, fb_count, o, ctr.p, h);
+    if (self) probe_and_verify<true>(c, v, fb_count, o, ctr.p, h, tm);
+    else probe_and_verify<false>(c, v, fb_count, o, ctr.p, h, tm);
     if (h.accepted <= cap) break;
     if (attempt >= 1) fail(PJ_ECUDA, "accepted-match buffer overflowed twice");
     cap = h.accepted;
   }
   const uint64_t nacc = h.accepted;
+  EventTimer td(c.stream);
+  td.start();
   debug_dump(c, "acc_key", acc_key.p, std::min<uint64_t>(nacc, cap) * sizeof(unsigned long long));
   debug_dump(c, "acc_ed", acc_ed.p, std::min<uint64_t>(nacc, cap) * sizeof(uint32_t));
   uint64_t count = 0;
@@ -392,6 +413,8 @@ static void run_join(const Ctx& c, const ProbeView& v, bool self, uint32_t fb_co
                                                              pairs.p);
     PJ_LAUNCHED("k_emit_pairs");
   }
+  td.stop();
+  tm.dedupe = td.ms();
   trace_mark(c, "join: dedupe + compact");
   out->count = count;
   out->stats.lookups = h.lookups;
@@ -399,6 +422,11 @@ static void run_join(const Ctx& c, const ProbeView& v, bool self, uint32_t fb_co
   out->stats.accepted = h.accepted;
   out->stats.dp_cells = h.cells;
   out->stats.fallback_pairs = h.fallback;
+  out->stats.hits = h.hits;
+  out->stats.probe_ms = tm.probe;
+  out->stats.verify_ms = tm.verify;
+  out->stats.fallback_ms = tm.fallback;
+  out->stats.dedupe_ms = tm.dedupe;
   out->priv = new ResultPriv{c};
   if (results_on_device) {
     out->on_device = 1;
@@ -434,6 +462,8 @@ static ProbeView index_side(const pj_index& idx, const Partition& part) {
 }
 
 static void self_join_impl(pj_index& idx, int tau, pj_result* out, bool on_device) {
+  float part_ms = 0.f;
+  ensure_partition(idx, tau, &part_ms);
   struct DumpAfter {
     pj_index& idx;
     int tau;
@@ -458,6 +488,7 @@ static void self_join_impl(pj_index& idx, int tau, pj_result* out, bool on_devic
   v.pid = idx.perm.p;
   v.key_shift = bits_for(idx.n);
   run_join(idx.ctx, v, true, part.first, bits_for(idx.n), on_device, out);
+  out->stats.partition_ms = part_ms;
 }
 
 static void probe_join_impl(const Ctx& c, const pj_index& idx, const Partition& part, const ProbeSet& R,
@@ -541,9 +572,12 @@ int pj_query(pj_index* idx, const pj_strings* batch, int tau, pj_result* out) {
     if (!idx || !batch || !out) pj::fail(PJ_EINVAL, "pj_query: NULL argument");
     if (tau < 0 || tau >= (int)idx->parts.size()) pj::fail(PJ_EINVAL, "pj_query: tau outside 0..tau_max");
     std::lock_guard<std::mutex> g(idx->mu);
+    float part_ms = 0.f;
+    pj::Partition& part = pj::ensure_partition(*idx, tau, &part_ms);
     pj::ProbeSet P;
     pj::upload_probe_set(idx->ctx, *batch, P);
-    pj::probe_join_impl(idx->ctx, *idx, idx->parts[tau], P, out, idx->results_on_device);
+    pj::probe_join_impl(idx->ctx, *idx, part, P, out, idx->results_on_device);
+    out->stats.partition_ms = part_ms;
     return PJ_OK;
   } catch (const pj::Error& e) {
     pj::set_last_error(e.msg);

@@ -44,7 +44,9 @@ class pj_strings(ctypes.Structure):
 
 class pj_stats(ctypes.Structure):
     _fields_ = [("lookups", ctypes.c_uint64), ("candidates", ctypes.c_uint64), ("accepted", ctypes.c_uint64),
-                ("dp_cells", ctypes.c_uint64), ("fallback_pairs", ctypes.c_uint64)]
+                ("dp_cells", ctypes.c_uint64), ("fallback_pairs", ctypes.c_uint64), ("hits", ctypes.c_uint64),
+                ("probe_ms", ctypes.c_float), ("verify_ms", ctypes.c_float), ("fallback_ms", ctypes.c_float),
+                ("dedupe_ms", ctypes.c_float), ("partition_ms", ctypes.c_float), ("reserved", ctypes.c_uint32)]
 
 
 class pj_result(ctypes.Structure):
@@ -58,7 +60,8 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void
 
 class pj_options(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
-                ("verify_mode", ctypes.c_int), ("results_on_device", ctypes.c_int)]
+                ("verify_mode", ctypes.c_int), ("results_on_device", ctypes.c_int), ("lazy_partitions", ctypes.c_int),
+                ("reserved", ctypes.c_int)]
 
 
 _lib = None
@@ -95,6 +98,10 @@ def library():
             L.pj_index_tau_max.restype = ctypes.c_int
             L.pj_index_device_bytes.argtypes = [ctypes.c_void_p]
             L.pj_index_device_bytes.restype = ctypes.c_uint64
+            L.pj_index_build_ms.argtypes = [ctypes.c_void_p]
+            L.pj_index_build_ms.restype = ctypes.c_float
+            L.pj_kernel_launches.argtypes = []
+            L.pj_kernel_launches.restype = ctypes.c_uint64
             L.pj_strerror.argtypes = [ctypes.c_int]
             L.pj_strerror.restype = ctypes.c_char_p
             L.pj_last_error.argtypes = []
@@ -141,7 +148,8 @@ def _torch_free(ctx, ptr, stream):
     torch.cuda.caching_allocator_delete(ptr)
 
 
-def make_options(stream=None, results_on_device: bool = False, torch_allocator: bool = True) -> pj_options:
+def make_options(stream=None, results_on_device: bool = False, torch_allocator: bool = True,
+                 lazy_partitions: bool = False) -> pj_options:
     torch = _torch()
     opt = pj_options()
     library().pj_options_init(ctypes.byref(opt))
@@ -152,6 +160,7 @@ def make_options(stream=None, results_on_device: bool = False, torch_allocator: 
         opt.alloc = _torch_alloc
         opt.free = _torch_free
     opt.results_on_device = 1 if results_on_device else 0
+    opt.lazy_partitions = 1 if lazy_partitions else 0
     return opt
 
 
@@ -255,7 +264,9 @@ class DeviceResult:
 
 def _stats(st: pj_stats) -> dict:
     return dict(lookups=int(st.lookups), candidates=int(st.candidates), accepted=int(st.accepted),
-                dp_cells=int(st.dp_cells), fallback_pairs=int(st.fallback_pairs))
+                dp_cells=int(st.dp_cells), fallback_pairs=int(st.fallback_pairs), hits=int(st.hits),
+                probe_ms=float(st.probe_ms), verify_ms=float(st.verify_ms), fallback_ms=float(st.fallback_ms),
+                dedupe_ms=float(st.dedupe_ms), partition_ms=float(st.partition_ms))
 
 
 def _take(res: pj_result):
@@ -300,6 +311,10 @@ class Index:
     def device_bytes(self) -> int:
         return int(library().pj_index_device_bytes(self.handle))
 
+    @property
+    def build_ms(self) -> float:
+        return float(library().pj_index_build_ms(self.handle))
+
     def free(self):
         if self._h:
             library().pj_index_free(self._h)
@@ -314,9 +329,15 @@ class Index:
 
 # ------------------------------------------------------------ entry points --
 
-def pj_build_index(strings, tau_max: int, stream=None, results_on_device: bool = False) -> Index:
+def pj_kernel_launches() -> int:
+    """pj_kernel_launches: kernels launched by the library since it was loaded."""
+    return int(library().pj_kernel_launches())
+
+
+def pj_build_index(strings, tau_max: int, stream=None, results_on_device: bool = False,
+                   lazy_partitions: bool = False) -> Index:
     """pj_build_index: resident segment index for thresholds 0..tau_max."""
-    opt = make_options(stream, results_on_device)
+    opt = make_options(stream, results_on_device, lazy_partitions=lazy_partitions)
     S = Strings(strings)
     h = ctypes.c_void_p()
     _check(library().pj_build_index(ctypes.byref(S.c), int(tau_max), ctypes.byref(opt), ctypes.byref(h)),

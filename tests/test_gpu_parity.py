@@ -226,3 +226,29 @@ def test_invalid_arguments():
     with pytest.raises(pj.PJError) as e:
         pj.pj_join([b"a"], [b"b"], pj.PJ_TAU_LIMIT + 1)
     assert e.value.code == pj.PJ_EINVAL
+
+
+def test_lazy_partitions_match_eager():
+    strings = synth.generate("short", 3, n=3000)
+    want = cpu_self(strings, 3)
+    idx = pj.pj_build_index(strings, 4, lazy_partitions=True)
+    try:
+        r = pj.pj_self_join(idx, 3)
+        assert r.stats["partition_ms"] > 0
+        assert_same(r.pairs, want, "lazy tau=3")
+        r2 = pj.pj_self_join(idx, 3)  # built once
+        assert r2.stats["partition_ms"] == 0
+        assert_same(r2.pairs, want, "lazy again")
+    finally:
+        idx.free()
+
+
+def test_stats_timings_and_launch_counter():
+    strings = synth.generate("medium", 4, n=2000)
+    before = pj.pj_kernel_launches()
+    idx = pj.pj_build_index(strings, 4)
+    r = pj.pj_self_join(idx, 4)
+    idx.free()
+    assert pj.pj_kernel_launches() - before >= 10
+    assert r.stats["verify_ms"] > 0 and r.stats["probe_ms"] > 0 and r.stats["dedupe_ms"] > 0
+    assert r.stats["hits"] > 0 and r.stats["candidates"] >= r.stats["hits"]
