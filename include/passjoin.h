@@ -175,6 +175,39 @@ int pj_join(const pj_strings* R, const pj_strings* S, int tau, const pj_options*
  */
 int pj_query(pj_index* idx, const pj_strings* batch, int tau, pj_result* out);
 
+/*
+ * pj_query_noalloc -- pj_query for callers that cannot allocate memory on the
+ * call path: a serving thread that must not block in cudaMalloc/cudaFree
+ * (they can synchronise the device), or an embedder that reserved its GPU
+ * memory up front.  It allocates nothing: no device or host allocation and
+ * no allocating library call.  The paper has no counterpart; this is a
+ * serving convenience of this library.
+ *   idx       : from pj_build_index; the threshold's index must already be
+ *               built (always true unless lazy_partitions was set).
+ *   batch     : query strings in DEVICE memory (on_device = 1), at most
+ *               PJ_NOALLOC_MAX_QUERIES of them.
+ *   tau       : 0..tau_max of idx.
+ *   out_pairs : caller-owned device buffer of out_cap pj_pair entries; on
+ *               success it holds *out_count pairs sorted by (a, b), exactly
+ *               what pj_query returns for the same input.
+ *   out_count : host pointer; receives the number of pairs (also when the
+ *               buffer is too small, so the caller can retry).
+ * All temporaries live in one device array of PJ_NOALLOC_SCRATCH_BYTES bytes
+ * inside the library; every GPU that loads the library holds it until the
+ * process exits.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  Every call shares the array and leaves its contents behind;
+ * calls are serialised on the host, but calls whose GPU work overlaps (other
+ * processes, or work still running on another stream) race on it.
+ * Errors: PJ_EINVAL (NULL, tau out of range, host batch, batch too large,
+ * index for tau not built, output buffer too small), PJ_ENOMEM (more
+ * accepted matches than the scratch holds), PJ_ECUDA.
+ */
+#define PJ_NOALLOC_SCRATCH_BYTES (64u << 20)
+#define PJ_NOALLOC_MAX_QUERIES 65536
+int pj_query_noalloc(pj_index* idx, const pj_strings* batch, int tau, pj_pair* out_pairs, uint64_t out_cap,
+                     uint64_t* out_count);
+
 /* Number of strings / largest tau of an index (0 for NULL). */
 uint32_t pj_index_size(const pj_index* idx);
 int pj_index_tau_max(const pj_index* idx);

@@ -98,6 +98,9 @@ def library():
             L.pj_index_tau_max.restype = ctypes.c_int
             L.pj_index_device_bytes.argtypes = [ctypes.c_void_p]
             L.pj_index_device_bytes.restype = ctypes.c_uint64
+            L.pj_query_noalloc.argtypes = [ctypes.c_void_p, P(pj_strings), ctypes.c_int, ctypes.c_void_p,
+                                           ctypes.c_uint64, P(ctypes.c_uint64)]
+            L.pj_query_noalloc.restype = ctypes.c_int
             L.pj_index_build_ms.argtypes = [ctypes.c_void_p]
             L.pj_index_build_ms.restype = ctypes.c_float
             L.pj_kernel_launches.argtypes = []
@@ -368,3 +371,15 @@ def pj_query(index: Index, batch, tau: int):
     res = pj_result()
     _check(library().pj_query(index.handle, ctypes.byref(b.c), int(tau), ctypes.byref(res)), "pj_query")
     return _take(res)
+
+
+def pj_query_noalloc(index: Index, batch, tau: int, out_pairs, out_cap: int) -> int:
+    """pj_query_noalloc: probe a device-resident batch into a caller-owned
+    device buffer (``out_pairs``: a CUDA tensor or a device address holding
+    ``out_cap`` pj_pair entries) without allocating.  Returns the pair count."""
+    b = Strings(batch)
+    ptr = out_pairs.data_ptr() if hasattr(out_pairs, "data_ptr") else int(out_pairs)
+    n = ctypes.c_uint64(0)
+    _check(library().pj_query_noalloc(index.handle, ctypes.byref(b.c), int(tau), ctypes.c_void_p(ptr),
+                                      int(out_cap), ctypes.byref(n)), "pj_query_noalloc")
+    return int(n.value)
