@@ -128,12 +128,12 @@ constexpr int V_RUN = 4;  // consecutive candidates per thread per step
 template <int MAXW, bool SELF>
 __global__ void __launch_bounds__(BLOCK) k_verify_hits(const ProbeView v, const Hit* __restrict__ hits,
                                                        const unsigned long long* __restrict__ cand_off,
-                                                       unsigned long long n_hits, unsigned long long n_cand,
-                                                       AccOut out, Counters* ctr) {
+                                                       unsigned long long n_hits, unsigned long long c_begin,
+                                                       unsigned long long n_cand, AccOut out, Counters* ctr) {
   unsigned long long cells = 0;
   int err = 0;
   const unsigned long long stride = (unsigned long long)gridDim.x * BLOCK * V_RUN;
-  for (unsigned long long c0 = ((unsigned long long)blockIdx.x * BLOCK + threadIdx.x) * V_RUN; c0 < n_cand;
+  for (unsigned long long c0 = c_begin + ((unsigned long long)blockIdx.x * BLOCK + threadIdx.x) * V_RUN; c0 < n_cand;
        c0 += stride) {
     unsigned long long lo = 0, hi = n_hits;  // last hit whose first candidate is <= c0
     while (hi - lo > 1) {
@@ -247,9 +247,11 @@ static unsigned persistent_grid(K kernel, unsigned long long work_blocks) {
 
 template <int MAXW, bool SELF>
 static void launch_verify(const Ctx& c, const ProbeView& v, const Hit* hits, const unsigned long long* off,
-                          unsigned long long n_hits, unsigned long long n_cand, AccOut out, Counters* ctr) {
-  const unsigned grid = persistent_grid(k_verify_hits<MAXW, SELF>, (n_cand + BLOCK * V_RUN - 1) / (BLOCK * V_RUN));
-  k_verify_hits<MAXW, SELF><<<grid, BLOCK, 0, c.stream>>>(v, hits, off, n_hits, n_cand, out, ctr);
+                          unsigned long long n_hits, unsigned long long c_begin, unsigned long long c_end,
+                          AccOut out, Counters* ctr) {
+  const unsigned grid =
+      persistent_grid(k_verify_hits<MAXW, SELF>, (c_end - c_begin + BLOCK * V_RUN - 1) / (BLOCK * V_RUN));
+  k_verify_hits<MAXW, SELF><<<grid, BLOCK, 0, c.stream>>>(v, hits, off, n_hits, c_begin, c_end, out, ctr);
   PJ_LAUNCHED("k_verify_hits");
 }
 
@@ -275,23 +277,88 @@ struct ResultPriv {
   Ctx ctx;
 };
 
+// Sizing knobs, overridable through the environment (used by tests to drive
+// the chunked and growing paths at small sizes):
+//   PJ_GROUP_BUDGET      groups probed per chunk          (default 64 Mi)
+//   PJ_LAUNCH_CANDS      candidates per verification launch (default 1 Gi)
+//   PJ_ACCEPT_INITIAL    initial accepted-match capacity  (default 4 Mi)
+static unsigned long long env_knob(const char* name, unsigned long long dflt) {
+  const char* e = getenv(name);
+  if (!e || !e[0]) return dflt;
+  const unsigned long long v = strtoull(e, nullptr, 10);
+  return v ? v : dflt;
+}
+
 struct Timings {
   float probe = 0.f, verify = 0.f, fallback = 0.f, dedupe = 0.f;
+};
+
+// Accepted-match buffer that grows between launches: after a launch that
+// overflowed it, the buffer is enlarged (keeping the entries accepted before
+// that launch), the counter is wound back and the launch runs again.
+struct AcceptBuf {
+  const Ctx& c;
+  Counters* ctr;
+  DBuf<unsigned long long> key;
+  DBuf<uint32_t> ed;
+  unsigned long long cap = 0;
+  AcceptBuf(const Ctx& ctx, Counters* counters, unsigned long long initial) : c(ctx), ctr(counters) {
+    key.reset(c, initial);
+    ed.reset(c, initial);
+    cap = initial;
+  }
+  AccOut out() const { return AccOut{key.p, ed.p, cap}; }
+  unsigned long long read_count() const {
+    unsigned long long n = 0;
+    PJ_CUDA(cudaMemcpyAsync(&n, &ctr->accepted, sizeof(n), cudaMemcpyDeviceToHost, c.stream));
+    c.sync();
+    return n;
+  }
+  // Runs `launch` (which appends to out()); retries once after growing to
+  // `want(after)` entries if the buffer overflowed.
+  template <class Launch, class Want>
+  void run(Launch launch, Want want) {
+    Counters saved{};  // all counters, so that a re-run launch is counted once
+    PJ_CUDA(cudaMemcpyAsync(&saved, ctr, sizeof(saved), cudaMemcpyDeviceToHost, c.stream));
+    c.sync();
+    const unsigned long long before = saved.accepted;
+    launch(out());
+    const unsigned long long after = read_count();
+    if (after <= cap) return;
+    grow(std::max<unsigned long long>(after, want(after)), before);
+    PJ_CUDA(cudaMemcpyAsync(ctr, &saved, sizeof(saved), cudaMemcpyHostToDevice, c.stream));
+    c.sync();  // `saved` lives on this stack frame
+    launch(out());
+    if (read_count() > cap) fail(PJ_ECUDA, "accepted-match buffer overflowed after growing");
+  }
+  void grow(unsigned long long new_cap, unsigned long long keep) {
+    DBuf<unsigned long long> k2(c, new_cap);
+    DBuf<uint32_t> e2(c, new_cap);
+    if (keep) {
+      PJ_CUDA(cudaMemcpyAsync(k2.p, key.p, keep * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, c.stream));
+      PJ_CUDA(cudaMemcpyAsync(e2.p, ed.p, keep * sizeof(uint32_t), cudaMemcpyDeviceToDevice, c.stream));
+    }
+    key = std::move(k2);
+    ed = std::move(e2);
+    cap = new_cap;
+  }
 };
 
 // Probe + verify for all probing strings, in chunks of probing strings whose
 // groups fit the hit buffer; then the short-string fallback.  Returns the
 // number of accepted matches (the buffer holds min(that, out.cap)).
 template <bool SELF>
-static void probe_and_verify(const Ctx& c, const ProbeView& v0, uint32_t fb_count, AccOut out, Counters* ctr,
+static void probe_and_verify(const Ctx& c, const ProbeView& v0, uint32_t fb_count, AcceptBuf& acc, Counters* ctr,
                              Counters& h, Timings& tm) {
   EventTimer tp(c.stream), tv(c.stream), tf(c.stream);
   const int G = groups_per_probe(v0.tau, SELF);
-  const unsigned long long group_budget = 64ull << 20;  // groups per chunk
+  const unsigned long long group_budget = env_knob("PJ_GROUP_BUDGET", 64ull << 20);
+  const unsigned long long launch_cands = env_knob("PJ_LAUNCH_CANDS", 1ull << 30);
   const uint32_t chunk_items = (uint32_t)std::max<unsigned long long>(1, group_budget / G);
   DBuf<Hit> hits;
   DBuf<uint32_t> gcount, goff;
   DBuf<unsigned long long> cnt, off;
+  unsigned long long total_cand = 0, verified = 0;
   for (uint32_t done = 0; done < v0.pcount;) {
     ProbeView v = v0;
     v.pbegin = v0.pbegin + done;
@@ -336,13 +403,25 @@ static void probe_and_verify(const Ctx& c, const ProbeView& v0, uint32_t fb_coun
     debug_dump(c, "cand_off", off.p, (n_hits + 1) * sizeof(unsigned long long));
     h.candidates += n_cand;
     h.hits += n_hits;
-    if (n_cand) {
+    total_cand += n_cand;
+    const double remaining_groups = (double)(v0.pcount - done - v.pcount) / std::max(1u, v.pcount) + 1.0;
+    for (unsigned long long cb = 0; cb < n_cand; cb += launch_cands) {
+      const unsigned long long ce = std::min(n_cand, cb + launch_cands);
       tv.start();
-#define PJ_CALL(W) launch_verify<W, SELF>(c, v, hits.p, off.p, n_hits, n_cand, out, ctr)
-      PJ_BY_TAU(v.tau, PJ_CALL);
+      acc.run(
+          [&](AccOut o) {
+#define PJ_CALL(W) launch_verify<W, SELF>(c, v, hits.p, off.p, n_hits, cb, ce, o, ctr)
+            PJ_BY_TAU(v.tau, PJ_CALL);
 #undef PJ_CALL
+          },
+          [&](unsigned long long after) {  // project the whole join from the rate so far
+            const double rate = (double)after / (double)(verified + (ce - cb));
+            const double left = (double)(n_cand - ce) + (remaining_groups - 1.0) * (double)n_cand;
+            return (unsigned long long)(1.25 * (after + rate * left)) + (1ull << 20);
+          });
       tv.stop();
       tm.verify += tv.ms();
+      verified += ce - cb;
     }
     trace_mark(c, "join: verify");
     done += v.pcount;
@@ -350,9 +429,13 @@ static void probe_and_verify(const Ctx& c, const ProbeView& v0, uint32_t fb_coun
   if (fb_count) {
     ProbeView v = v0;
     tf.start();
-#define PJ_CALL(W) launch_fallback<W, SELF>(c, v, fb_count, out, ctr)
-    PJ_BY_TAU(v.tau, PJ_CALL);
+    acc.run(
+        [&](AccOut o) {
+#define PJ_CALL(W) launch_fallback<W, SELF>(c, v, fb_count, o, ctr)
+          PJ_BY_TAU(v.tau, PJ_CALL);
 #undef PJ_CALL
+        },
+        [&](unsigned long long after) { return 2 * after; });
     tf.stop();
     tm.fallback += tf.ms();
   }
@@ -370,25 +453,16 @@ static void probe_and_verify(const Ctx& c, const ProbeView& v0, uint32_t fb_coun
 // matches overflowed, then dedupes and compacts into *out.
 static void run_join(const Ctx& c, const ProbeView& v, bool self, uint32_t fb_count, int a_bits,
                      bool results_on_device, pj_result* out) {
-  uint64_t cap = 1u << 20;
   Counters h{};
   Timings tm;
-  DBuf<unsigned long long> acc_key;
-  DBuf<uint32_t> acc_ed;
   DBuf<Counters> ctr(c, 1);
-  for (int attempt = 0;; ++attempt) {
-    acc_key.reset(c, cap);
-    acc_ed.reset(c, cap);
-    PJ_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(Counters), c.stream));
-    h = Counters{};
-    tm = Timings{};
-    AccOut o{acc_key.p, acc_ed.p, cap};
-    if (self) probe_and_verify<true>(c, v, fb_count, o, ctr.p, h, tm);
-    else probe_and_verify<false>(c, v, fb_count, o, ctr.p, h, tm);
-    if (h.accepted <= cap) break;
-    if (attempt >= 1) fail(PJ_ECUDA, "accepted-match buffer overflowed twice");
-    cap = h.accepted;
-  }
+  PJ_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(Counters), c.stream));
+  AcceptBuf acc(c, ctr.p, env_knob("PJ_ACCEPT_INITIAL", 4ull << 20));
+  if (self) probe_and_verify<true>(c, v, fb_count, acc, ctr.p, h, tm);
+  else probe_and_verify<false>(c, v, fb_count, acc, ctr.p, h, tm);
+  DBuf<unsigned long long>& acc_key = acc.key;
+  DBuf<uint32_t>& acc_ed = acc.ed;
+  const uint64_t cap = acc.cap;
   const uint64_t nacc = h.accepted;
   EventTimer td(c.stream);
   td.start();

@@ -252,3 +252,19 @@ def test_stats_timings_and_launch_counter():
     assert pj.pj_kernel_launches() - before >= 10
     assert r.stats["verify_ms"] > 0 and r.stats["probe_ms"] > 0 and r.stats["dedupe_ms"] > 0
     assert r.stats["hits"] > 0 and r.stats["candidates"] >= r.stats["hits"]
+
+
+def test_chunked_probe_multi_launch_and_buffer_growth(monkeypatch):
+    """Small probe chunks, small verification launches and a tiny initial
+    accepted-match buffer must give the same exact result."""
+    strings = synth.generate("short", 3, n=5000)
+    want = cpu_self(strings, 3)
+    monkeypatch.setenv("PJ_GROUP_BUDGET", "3000")
+    monkeypatch.setenv("PJ_LAUNCH_CANDS", "5000")
+    monkeypatch.setenv("PJ_ACCEPT_INITIAL", "7")
+    r = gpu_self(strings, 3)
+    assert_same(r.pairs, want, "chunked")
+    R, S = _rs_sets(5, 2)
+    rb, ro = synth.pack(R)
+    sb, so = synth.pack(S)
+    assert_same(pj.pj_join(R, S, 2).pairs, oracle.join(rb, ro, sb, so, 2), "chunked join")
