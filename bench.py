@@ -42,7 +42,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-METRIC = "self-join verified candidate pairs/s (short workload, 1M strings)"
+METRIC = "self-join verified candidate pairs/s"
 UNIT = "pairs/s"
 L2_FLUSH_BYTES = 256 << 20
 INT_LANES_PER_SM = 128      # 32-bit integer lanes per SM (4 sub-partitions x 32)

@@ -120,11 +120,14 @@ __global__ void k_hit_counts(const Hit* __restrict__ hits, unsigned long long n,
 
 // ---------------------------------------------------------------- A6 ------
 
-constexpr int V_RUN = 4;  // consecutive candidates per thread per step
+constexpr int V_RUN = 4;  // candidates per lane per step
 
-// Every thread verifies runs of V_RUN consecutive candidates: one binary
-// search over the candidate offsets locates the first hit, then the walk
-// moves forward hit by hit.
+// Lane l of a warp verifies candidates base + l + 32 k (k < V_RUN): the 32
+// lanes take consecutive candidates, which mostly belong to one posting run
+// and so share the probing string, the segment, the position and the
+// indexed length -- the verification loops then have equal trip counts up to
+// early termination.  Each lane finds its first hit by binary search over the
+// candidate offsets and walks forward from there; lanes never communicate.
 template <int MAXW, bool SELF>
 __global__ void __launch_bounds__(BLOCK) k_verify_hits(const ProbeView v, const Hit* __restrict__ hits,
                                                        const unsigned long long* __restrict__ cand_off,
@@ -132,17 +135,20 @@ __global__ void __launch_bounds__(BLOCK) k_verify_hits(const ProbeView v, const 
                                                        unsigned long long n_cand, AccOut out, Counters* ctr) {
   unsigned long long cells = 0;
   int err = 0;
-  const unsigned long long stride = (unsigned long long)gridDim.x * BLOCK * V_RUN;
-  for (unsigned long long c0 = c_begin + ((unsigned long long)blockIdx.x * BLOCK + threadIdx.x) * V_RUN; c0 < n_cand;
-       c0 += stride) {
-    unsigned long long lo = 0, hi = n_hits;  // last hit whose first candidate is <= c0
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned long long warp = ((unsigned long long)blockIdx.x * BLOCK + threadIdx.x) >> 5;
+  const unsigned long long n_warps = ((unsigned long long)gridDim.x * BLOCK) >> 5;
+  const unsigned long long span = 32ull * V_RUN;
+  for (unsigned long long base = c_begin + warp * span; base < n_cand; base += n_warps * span) {
+    unsigned long long c = base + lane;
+    if (c >= n_cand) continue;
+    unsigned long long lo = 0, hi = n_hits;  // last hit whose first candidate is <= c
     while (hi - lo > 1) {
       const unsigned long long mid = (lo + hi) >> 1;
-      if (cand_off[mid] <= c0) lo = mid; else hi = mid;
+      if (cand_off[mid] <= c) lo = mid; else hi = mid;
     }
     unsigned long long h = lo;
-    const unsigned long long c1 = min(n_cand, c0 + V_RUN);
-    for (unsigned long long c = c0; c < c1; ++c) {
+    for (int k = 0; k < V_RUN && c < n_cand; ++k, c += 32) {
       while (h + 1 < n_hits && cand_off[h + 1] <= c) ++h;
       const Hit hit = hits[h];
       unsigned long long key = 0;
@@ -251,6 +257,7 @@ static void launch_verify(const Ctx& c, const ProbeView& v, const Hit* hits, con
                           AccOut out, Counters* ctr) {
   const unsigned grid =
       persistent_grid(k_verify_hits<MAXW, SELF>, (c_end - c_begin + BLOCK * V_RUN - 1) / (BLOCK * V_RUN));
+  // lanes past c_end in the last warp span are skipped inside the kernel
   k_verify_hits<MAXW, SELF><<<grid, BLOCK, 0, c.stream>>>(v, hits, off, n_hits, c_begin, c_end, out, ctr);
   PJ_LAUNCHED("k_verify_hits");
 }

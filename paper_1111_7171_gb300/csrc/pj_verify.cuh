@@ -18,72 +18,111 @@ using std::max;
 using std::min;
 #endif
 
-// VERIFYSTRINGPAIR (Alg. 3): min(t + 1, ED(x, y)).  Rows run over the shorter
-// string a, columns over the longer b, D = |b| - |a|.  Row i keeps only the
-// cells j in [i - floor((t - D)/2), i + floor((t + D)/2)] (Sec. 5.1): at
-// most t + 1 <= MAXW registers, indexed by diagonal d = j - i.  Values are
-// saturated at t + 1 (exact for the capped result).  After each row the
-// expected edit distance E(i, j) = M(i, j) + |D - (j - i)| is minimised over
-// the band; if it exceeds t the pair is dissimilar (Lemma 4).
+// VERIFYSTRINGPAIR (Alg. 3): min(t + 1, ED(x, y)).
+//
+// Rows run over the shorter string a, columns over the longer b, D = |b| -
+// |a| <= t.  Row i holds the diagonals d = j - i from dlo = -floor((t-D)/2)
+// upward: the length-aware band of Sec. 5.1 is d <= floor((t+D)/2), and the
+// W registers (W >= t + 1) may cover a few more diagonals above it.  Any
+// value computed over a superset of the band is the cost of a real
+// alignment, and the band holds every alignment of cost <= t, so the capped
+// result is unchanged.  Values saturate at t + 1 (exact for the capped
+// result); cells left of column 0 stay at t + 1, which makes M(i, 0) = i
+// fall out of the recurrence, and cells right of column |b| never feed a
+// cell inside the matrix.  So the inner loop has no bounds checks.
+//
+// After each row the expected edit distance E(i, j) = M(i, j) + |D - (j - i)|
+// is minimised over the row; if every E exceeds t the pair is dissimilar
+// (Lemma 4).  cells counts the length-aware band cells of the rows evaluated.
+//
+// Single exit and structured loops only: callers may reach synchronisation
+// points right after this function.
+template <int W>
+__host__ __device__ __forceinline__ int vsp_band(const uint8_t* a, int na, const uint8_t* b, int nb, int t,
+                                                 unsigned long long& cells) {
+  const int D = nb - na;
+  const int cap = t + 1;
+  const int dlo = -((t - D) >> 1);
+  const int w = ((t + D) >> 1) - dlo + 1;  // length-aware band width, <= t + 1 <= W
+  int V[W];
+  int eoff[W];
+  uint8_t B[W];  // B[k] = b[i + dlo + k - 1] for the current row i (0 outside b)
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    const int j = dlo + k;  // row 0: M(0, j) = j
+    V[k] = j < 0 ? cap : min(j, cap);
+    eoff[k] = abs(D - dlo - k);
+    const int jb = dlo + k;  // b index for row 1
+    B[k] = (jb >= 0 && jb < nb) ? b[jb] : (uint8_t)0;
+  }
+  bool alive = true;
+  for (int i = 1; i <= na; ++i) {
+    const uint8_t ca = a[i - 1];
+    int left = cap;
+    int emin = cap;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      const int up = (k + 1 < W) ? V[k + 1] : cap;
+      const int diag = V[k] + (ca != B[k] ? 1 : 0);
+      const int val = min(min(diag, up + 1), min(left + 1, cap));
+      V[k] = val;
+      left = val;
+      emin = min(emin, val + eoff[k]);
+    }
+    cells += (unsigned long long)w;
+    if (emin > t) {  // Lemma 4: every expected edit distance of the row exceeds t
+      alive = false;
+      break;
+    }
+    const int jn = i + dlo + W - 1;  // next row's last column character
+#pragma unroll
+    for (int k = 0; k + 1 < W; ++k) B[k] = B[k + 1];
+    B[W - 1] = (jn >= 0 && jn < nb) ? b[jn] : (uint8_t)0;
+  }
+  int res = cap;
+  if (alive) {
+    const int kres = D - dlo;
+#pragma unroll
+    for (int k = 0; k < W; ++k)
+      if (k == kres) res = V[k];
+  }
+  return res;
+}
+
 template <int MAXW>
 __host__ __device__ __forceinline__ int vsp(const uint8_t* x, int nx, const uint8_t* y, int ny, int t,
                                             unsigned long long& cells) {
-  // Single exit and structured loops only: callers reach warp and block
-  // barriers right after this function, so every lane must leave it through
-  // the same path.
   const uint8_t* a = nx <= ny ? x : y;
   const uint8_t* b = nx <= ny ? y : x;
   const int na = nx <= ny ? nx : ny;
   const int nb = nx <= ny ? ny : nx;
   const int D = nb - na;
-  const int cap = t + 1;
-  int res = cap;
-  if (D <= t && na == 0) res = D;
-  if (D <= t && na > 0) {
-    const int dlo = -((t - D) >> 1);
-    const int w = ((t + D) >> 1) - dlo + 1;  // <= t + 1 <= MAXW
-    int V[MAXW];
-    int eoff[MAXW];
-#pragma unroll
-    for (int k = 0; k < MAXW; ++k) {
-      const int j = dlo + k;  // row 0: M(0, j) = j
-      V[k] = (k < w && j >= 0 && j <= nb) ? min(j, cap) : cap;
-      eoff[k] = abs(D - dlo - k);
-    }
-    bool alive = true;
-    for (int i = 1; i <= na; ++i) {
-      const uint8_t ca = a[i - 1];
-      int left = cap;
-      int emin = cap;
-      const int j0 = i + dlo;
-#pragma unroll
-      for (int k = 0; k < MAXW; ++k) {
-        const int j = j0 + k;
-        const int up = (k + 1 < MAXW) ? V[k + 1] : cap;
-        int val = cap;
-        if (k < w && j >= 0 && j <= nb) {
-          if (j == 0) {
-            val = min(i, cap);
-          } else {
-            const int diag = V[k] + (ca != b[j - 1] ? 1 : 0);
-            val = min(min(diag, up + 1), min(left + 1, cap));
-          }
+  int res = t + 1;
+  if (D <= t) {
+    if (na == 0) {
+      res = D;
+    } else if (t == 0) {  // exact match of equal lengths
+      bool eq = true;
+      for (int k = 0; k < na; ++k) {
+        if (a[k] != b[k]) {
+          eq = false;
+          break;
         }
-        V[k] = val;
-        left = val;
-        emin = min(emin, val + eoff[k]);
       }
-      cells += (unsigned long long)w;
-      if (emin > t) {  // Lemma 4: every expected edit distance exceeds t
-        alive = false;
-        break;
-      }
-    }
-    if (alive) {
-      const int kres = D - dlo;
-#pragma unroll
-      for (int k = 0; k < MAXW; ++k)
-        if (k == kres) res = V[k];
+      cells += (unsigned long long)na;
+      res = eq ? 0 : 1;
+    } else if (t + 1 <= 2 || MAXW <= 2) {
+      res = vsp_band<(MAXW < 2 ? MAXW : 2)>(a, na, b, nb, t, cells);
+    } else if (t + 1 <= 3 || MAXW <= 3) {
+      res = vsp_band<(MAXW < 3 ? MAXW : 3)>(a, na, b, nb, t, cells);
+    } else if (t + 1 <= 5 || MAXW <= 5) {
+      res = vsp_band<(MAXW < 5 ? MAXW : 5)>(a, na, b, nb, t, cells);
+    } else if (t + 1 <= 9 || MAXW <= 9) {
+      res = vsp_band<(MAXW < 9 ? MAXW : 9)>(a, na, b, nb, t, cells);
+    } else if (t + 1 <= 17 || MAXW <= 17) {
+      res = vsp_band<(MAXW < 17 ? MAXW : 17)>(a, na, b, nb, t, cells);
+    } else {
+      res = vsp_band<MAXW>(a, na, b, nb, t, cells);
     }
   }
   return res;

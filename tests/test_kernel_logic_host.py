@@ -96,3 +96,16 @@ def test_rs_join_logic(emu, tmp_path):
     r = oracle.join(rb, ro, sb, so, 3)
     want = np.stack([r["a"], r["b"], r["ed"]], axis=1).astype(np.int64)
     assert np.array_equal(pairs, want)
+
+
+def test_vsp_widths_match_plain_dp(tmp_path):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    exe = tmp_path / "vsp_check"
+    subprocess.run([nvcc, "-std=c++17", "-O2", "-I", CSRC, "-o", str(exe),
+                    os.path.join(ROOT, "tests", "host_logic", "vsp_check.cu")], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    bad = {tok.split("=")[1]: None for tok in out if tok.startswith("W=")}
+    assert len(bad) == 5
+    assert all(tok == "bad=0" for tok in out if tok.startswith("bad="))
