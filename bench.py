@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--n", type=int, default=None, help="override the workload size (testing only)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU-baseline sample time")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-requests", type=int, default=400)
     return ap.parse_args()
 
 
@@ -176,6 +178,104 @@ def cpu_baseline(strings, tau, target_s, seed=123):
             "sample": f"{q} probe strings x all {n} strings (length filter, then full DP on {pairs} pairs) "
                       f"in {dt:.1f} s; self join extrapolated to {full_pairs / rate:.0f} s",
             "seconds": dt, "pairs": pairs, "self_join_s_extrapolated": full_pairs / rate}
+
+
+# --------------------------------------------------------------- serving --
+
+def percentile(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    k = min(len(xs) - 1, max(0, int(round(q / 100.0 * (len(xs) - 1)))))
+    return xs[k]
+
+
+def serving_bench(strings, n_requests, seed=4000):
+    """Resident index of the workload (tau_max = 4) and a stream of query
+    batches (sizes log-uniform 1..4096, tau uniform 1..4, half short-like and
+    half medium-like queries, half of them edited copies of indexed strings).
+
+    plain  : one pj_query per request, in arrival order, one at a time.
+    served : the continuous-batching server (3 slots).
+    Peak throughput: every request submitted at time 0.  Latency: Poisson
+    arrivals at 70% of the served peak request rate; latency = completion -
+    arrival (p50 / p99).  Both forms return identical pairs (tests)."""
+    import torch
+    from paper_1111_7171_gb300 import passjoin as pj
+    from paper_1111_7171_gb300 import synth
+
+    reqs = synth.query_stream(strings, n_requests, seed=seed, tau_max=4, max_batch=4096)
+    n_queries = sum(len(q) for q, _ in reqs)
+    idx = pj.pj_build_index(strings, 4)
+    try:
+        for qs, t in reqs[:3]:  # warm-up
+            pj.pj_query(idx, qs, t)
+        torch.cuda.synchronize()
+        # plain, back to back
+        t0 = time.perf_counter()
+        for qs, t in reqs:
+            pj.pj_query(idx, qs, t)
+        plain_s = time.perf_counter() - t0
+        # served, all at once
+        srv = pj.Server(idx, slots=3)
+        try:
+            for qs, t in reqs[:3]:
+                srv.wait(srv.submit(qs, t))
+            t0 = time.perf_counter()
+            tickets = [srv.submit(qs, t) for qs, t in reqs]
+            for tk in tickets:
+                srv.wait(tk)
+            served_s = time.perf_counter() - t0
+            st = srv.stats()
+        finally:
+            srv.stop()
+        peak_rps = n_requests / served_s
+        rate = 0.7 * peak_rps
+        rng = np.random.default_rng(seed + 1)
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_requests))
+        # served at the Poisson rate
+        srv = pj.Server(idx, slots=3)
+        lat_served = []
+        try:
+            start = time.perf_counter()
+            tickets = []
+            for (qs, t), at in zip(reqs, arrivals):
+                d = start + at - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                tickets.append(srv.submit(qs, t))
+            for tk in tickets:
+                _, tm = srv.wait(tk)
+                lat_served.append(tm["queue_ms"] + tm["service_ms"])
+            served_wall = time.perf_counter() - start
+            st2 = srv.stats()
+        finally:
+            srv.stop()
+        # plain at the same arrivals
+        lat_plain = []
+        start = time.perf_counter()
+        for (qs, t), at in zip(reqs, arrivals):
+            d = start + at - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            pj.pj_query(idx, qs, t)
+            lat_plain.append(1e3 * (time.perf_counter() - start - at))
+        plain_wall = time.perf_counter() - start
+    finally:
+        idx.free()
+    return {
+        "requests": n_requests, "queries": n_queries, "index": f"{len(strings)} strings, tau_max 4",
+        "peak_queries_per_s": {"served": n_queries / served_s, "plain": n_queries / plain_s},
+        "speedup_served_vs_plain": plain_s / served_s,
+        "poisson": {"rate_requests_per_s": rate,
+                    "served": {"p50_ms": percentile(lat_served, 50), "p99_ms": percentile(lat_served, 99),
+                               "queries_per_s": n_queries / served_wall},
+                    "plain": {"p50_ms": percentile(lat_plain, 50), "p99_ms": percentile(lat_plain, 99),
+                              "queries_per_s": n_queries / plain_wall}},
+        "batches": {"peak_run": st["batches"], "poisson_run": st2["batches"],
+                    "max_requests_per_batch": max(st["max_batch_requests"], st2["max_batch_requests"]),
+                    "max_in_flight": max(st["max_in_flight"], st2["max_in_flight"])},
+    }
 
 
 # -------------------------------------------------------------- reference --
@@ -322,6 +422,9 @@ def run_native(args):
                     "unit": "Gcell/s", "frac": achieved / alu_peak_gcells, "traffic": None,
                     "peak_source": f"{sm_count} SMs x {INT_LANES_PER_SM} int32 lanes x {sm_mhz:.0f} MHz "
                                    f"({peak_src} SM clock) / {OPS_PER_CELL} ops per DP cell"}
+        serving = None
+        if not args.no_serve and args.workload == "short":
+            serving = serving_bench(strings, args.serve_requests)
         cpu = None
         if not args.no_cpu_baseline:
             cpu = cpu_baseline(strings, args.tau, args.cpu_seconds)
@@ -348,6 +451,7 @@ def run_native(args):
                     "d2h_bytes_per_step": int(e2e_pairs * 12)},
             "gpu_launches": int(launches),
             "clocks": clk,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -176,6 +176,72 @@ int pj_join(const pj_strings* R, const pj_strings* S, int tau, const pj_options*
 int pj_query(pj_index* idx, const pj_strings* batch, int tau, pj_result* out);
 
 /*
+ * pj_query_multi -- one batched probe of many queries that carry their own
+ * thresholds (Sec. 3.2 join with R = the batch; each query q uses
+ * threshold taus[q] and that threshold's segment index): all queries go
+ * through one sequence of probe and verification launches.  Pairs are
+ * (a = query position in the batch, b = indexed id, ed) sorted by (a, b);
+ * for every query they equal pj_query of that query alone at its threshold.
+ *   taus : host array of batch->n thresholds, each 0..tau_max of idx.
+ * Errors as pj_query.
+ */
+int pj_query_multi(pj_index* idx, const pj_strings* batch, const uint8_t* taus, pj_result* out);
+
+/* ---------------------------------------------------------------- serving --
+ * A continuous-batching query server over a resident index (the R != S join
+ * of Sec. 3.2 per request).  Requests are queued by pj_server_submit; each
+ * of `slots` worker threads owns a CUDA stream, and whenever a slot is free
+ * it admits every pending request that fits its caps -- max_batch_queries,
+ * max_batch_bytes, and (free device memory - device_reserve) /
+ * bytes_per_query queries -- and runs them together as one pj_query_multi
+ * batch.  Requests arriving while other batches run are taken by the next
+ * free slot, so batches overlap on the device.  Each request's result is
+ * exactly what pj_query returns for it alone.  The index must outlive the
+ * server; the server builds every threshold's segment index at start and
+ * then only reads the index. */
+typedef struct pj_server pj_server;
+
+typedef struct {
+  int slots;                   /* concurrent batches (1..16, default 3) */
+  uint32_t max_batch_queries;  /* queries per batch (default 65536) */
+  uint64_t max_batch_bytes;    /* query bytes per batch (default 16 MiB) */
+  uint64_t bytes_per_query;    /* device-memory estimate per query for admission (default 64 KiB) */
+  uint64_t device_reserve;     /* device memory kept free (default 2 GiB) */
+} pj_server_options;
+
+/* Time a request spent queued and being served (host clock), and how many
+ * requests shared its batch. */
+typedef struct {
+  float queue_ms;
+  float service_ms;
+  uint32_t batch_requests;
+} pj_request_times;
+
+typedef struct {
+  uint64_t requests, batches, queries, max_batch_requests;
+  uint32_t max_in_flight;
+  uint64_t pending;
+} pj_server_counters;
+
+void pj_server_options_init(pj_server_options* opt);
+/* Start the server (opt NULL = defaults).  Errors: PJ_EINVAL, PJ_ENOMEM, PJ_ECUDA. */
+int pj_server_start(pj_index* idx, const pj_server_options* opt, pj_server** out);
+/* Queue one request: host strings (copied before returning) and its tau in
+ * 0..tau_max.  *ticket identifies it.  Errors: PJ_EINVAL, PJ_ECANCELED (stopping). */
+int pj_server_submit(pj_server* srv, const pj_strings* batch, int tau, uint64_t* ticket);
+/* Wait up to timeout_ms (< 0: no limit) for a request.  PJ_OK: *out holds its
+ * pairs (a = position in the request's batch, b = indexed id), release with
+ * pj_result_free; times (may be NULL) receives its timings.  PJ_ETIMEDOUT:
+ * not finished, the ticket stays valid.  PJ_ECANCELED: cancelled.  Any other
+ * error is the batch's error.  A ticket can be collected once. */
+int pj_server_wait(pj_server* srv, uint64_t ticket, int timeout_ms, pj_result* out, pj_request_times* times);
+/* Cancel a queued or running request (its result is dropped). */
+int pj_server_cancel(pj_server* srv, uint64_t ticket);
+int pj_server_stats(pj_server* srv, pj_server_counters* out);
+/* Finish running batches, cancel queued requests, join the slots, free. */
+void pj_server_stop(pj_server* srv);
+
+/*
  * pj_query_noalloc -- pj_query for callers that cannot allocate memory on the
  * call path: a serving thread that must not block in cudaMalloc/cudaFree
  * (they can synchronise the device), or an embedder that reserved its GPU

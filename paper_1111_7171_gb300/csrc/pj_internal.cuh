@@ -136,6 +136,12 @@ struct ProbeSet {
 };
 void upload_probe_set(const Ctx& c, const pj_strings& R, ProbeSet& out);
 
+// R != S probe of a resident index where probe q has threshold h_tau[q]
+// (host array).  Every threshold present must be built.  Work is ordered on
+// c's stream and uses c's allocator; the index is only read.
+void query_multi_impl(const Ctx& c, pj_index& idx, const ProbeSet& R, const uint8_t* h_tau, pj_result* out,
+                      bool on_device);
+
 void set_last_error(const std::string& msg);
 
 }  // namespace pj

@@ -59,24 +59,50 @@ __device__ __forceinline__ void add_counter(unsigned long long* c, unsigned long
 
 // ---------------------------------------------------------------- A4 ------
 
+// Group t of a chunk: its probe q, its index g within q's groups, and the
+// view (threshold) the group belongs to.  MULTI: thresholds differ per probe
+// and q is found by binary search over the per-probe group offsets.
+template <bool SELF, bool MULTI>
+__device__ __forceinline__ void group_of(const ProbeView& v, unsigned long long t, uint32_t& q, int& g,
+                                         ProbeView& vt) {
+  if (MULTI) {
+    const unsigned long long tg = v.qgoff[v.pbegin] + t;
+    uint32_t lo = v.pbegin, hi = v.pbegin + v.pcount;  // last q with qgoff[q] <= tg
+    while (hi - lo > 1) {
+      const uint32_t mid = lo + ((hi - lo) >> 1);
+      if (v.qgoff[mid] <= tg) lo = mid; else hi = mid;
+    }
+    q = lo;
+    g = (int)(tg - v.qgoff[q]);
+    vt = view_for_tau(v, v.ptau[q]);
+  } else {
+    const int G = groups_per_probe(v.tau, SELF);
+    q = v.pbegin + (uint32_t)(t / G);
+    g = (int)(t % G);
+    vt = v;
+  }
+}
+
 // Pass 1: number of non-empty lookups of every group (probe, length, segment).
-template <bool SELF>
+template <bool SELF, bool MULTI>
 __global__ void __launch_bounds__(BLOCK) k_group_counts(const ProbeView v, unsigned long long n_groups,
                                                         uint32_t* __restrict__ counts, Counters* ctr) {
-  const int G = groups_per_probe(v.tau, SELF);
   unsigned long long lookups = 0;
   int err = 0;
   for (unsigned long long t = (unsigned long long)blockIdx.x * BLOCK + threadIdx.x; t < n_groups;
        t += (unsigned long long)gridDim.x * BLOCK) {
-    const uint32_t q = v.pbegin + (uint32_t)(t / G);
-    const int ls = (int)v.plen[q];
-    const uint8_t* s = v.pbytes + v.poff[q];
+    uint32_t q;
+    int g;
+    ProbeView vt;
+    group_of<SELF, MULTI>(v, t, q, g, vt);
+    const int ls = (int)vt.plen[q];
+    const uint8_t* s = vt.pbytes + vt.poff[q];
     int l, i, P, li, lo, hi;
     uint32_t nh = 0;
-    if (group_window(v, SELF, q, ls, (int)(t % G), l, i, P, li, lo, hi)) {
+    if (group_window(vt, SELF, q, ls, g, l, i, P, li, lo, hi)) {
       for (int p = lo; p <= hi; ++p) {
         uint32_t b;
-        if (lookup(v, SELF, s, ls, q, l, i, p, li, b, err)) ++nh;
+        if (lookup(vt, SELF, s, ls, q, l, i, p, li, b, err)) ++nh;
       }
       lookups += (unsigned long long)(hi - lo + 1);
     }
@@ -88,26 +114,29 @@ __global__ void __launch_bounds__(BLOCK) k_group_counts(const ProbeView v, unsig
 
 // Pass 2: the same lookups again, each non-empty one written as a Hit at the
 // group's prefix-sum offset.
-template <bool SELF>
+template <bool SELF, bool MULTI>
 __global__ void __launch_bounds__(BLOCK) k_group_hits(const ProbeView v, unsigned long long n_groups,
                                                       const uint32_t* __restrict__ counts,
                                                       const uint32_t* __restrict__ hit_off, Hit* __restrict__ hits) {
-  const int G = groups_per_probe(v.tau, SELF);
   for (unsigned long long t = (unsigned long long)blockIdx.x * BLOCK + threadIdx.x; t < n_groups;
        t += (unsigned long long)gridDim.x * BLOCK) {
     if (counts[t] == 0) continue;
-    const uint32_t q = v.pbegin + (uint32_t)(t / G);
-    const int ls = (int)v.plen[q];
-    const uint8_t* s = v.pbytes + v.poff[q];
+    uint32_t q;
+    int g;
+    ProbeView vt;
+    group_of<SELF, MULTI>(v, t, q, g, vt);
+    const int ls = (int)vt.plen[q];
+    const uint8_t* s = vt.pbytes + vt.poff[q];
     int l, i, P, li, lo, hi;
     int err = 0;
     uint32_t pos = hit_off[t];
     const uint32_t end = pos + counts[t];
-    if (group_window(v, SELF, q, ls, (int)(t % G), l, i, P, li, lo, hi)) {
+    const uint32_t tau_tag = MULTI ? ((uint32_t)vt.tau << 24) : 0u;
+    if (group_window(vt, SELF, q, ls, g, l, i, P, li, lo, hi)) {
       for (int p = lo; p <= hi && pos < end; ++p) {
         uint32_t b;
-        const uint32_t c = lookup(v, SELF, s, ls, q, l, i, p, li, b, err);
-        if (c) hits[pos++] = Hit{q, b, c, (uint32_t)p | ((uint32_t)i << 16)};
+        const uint32_t c = lookup(vt, SELF, s, ls, q, l, i, p, li, b, err);
+        if (c) hits[pos++] = Hit{q, b, c, (uint32_t)p | ((uint32_t)i << 16) | tau_tag};
       }
     }
   }
@@ -128,7 +157,7 @@ constexpr int V_RUN = 4;  // candidates per lane per step
 // indexed length -- the verification loops then have equal trip counts up to
 // early termination.  Each lane finds its first hit by binary search over the
 // candidate offsets and walks forward from there; lanes never communicate.
-template <int MAXW, bool SELF>
+template <int MAXW, bool SELF, bool MULTI>
 __global__ void __launch_bounds__(BLOCK) k_verify_hits(const ProbeView v, const Hit* __restrict__ hits,
                                                        const unsigned long long* __restrict__ cand_off,
                                                        unsigned long long n_hits, unsigned long long c_begin,
@@ -153,7 +182,8 @@ __global__ void __launch_bounds__(BLOCK) k_verify_hits(const ProbeView v, const 
       const Hit hit = hits[h];
       unsigned long long key = 0;
       int ed = 0;
-      if (verify_candidate<MAXW>(v, SELF, hit, (uint32_t)(c - cand_off[h]), key, ed, cells, err)) {
+      const ProbeView vt = MULTI ? view_for_tau(v, (int)(hit.pi >> 24)) : v;
+      if (verify_candidate<MAXW>(vt, SELF, hit, (uint32_t)(c - cand_off[h]), key, ed, cells, err)) {
         const unsigned long long pos = atomicAdd(&ctr->accepted, 1ull);
         if (pos < out.cap) {
           out.key[pos] = key;
@@ -172,11 +202,11 @@ __global__ void __launch_bounds__(BLOCK) k_verify_hits(const ProbeView v, const 
 // SELF: every short sid x against the sids y > x with |y| <= |x| + tau.
 // Otherwise: every probe x against the indexed strings of length <= tau
 // within the length filter.  One thread per x.
-template <int MAXW, bool SELF>
+template <int MAXW, bool SELF, bool MULTI>
 __global__ void __launch_bounds__(BLOCK) k_fallback(const ProbeView v, uint32_t xcount, AccOut out, Counters* ctr) {
-  const int tau = v.tau;
   unsigned long long cells = 0, pairs = 0;
   for (uint32_t x = blockIdx.x * BLOCK + threadIdx.x; x < xcount; x += gridDim.x * BLOCK) {
+    const int tau = MULTI ? (int)v.ptau[x] : v.tau;
     const uint8_t* xs = v.pbytes + v.poff[x];
     const int lx = (int)v.plen[x];
     uint32_t y0, y1;
@@ -251,21 +281,21 @@ static unsigned persistent_grid(K kernel, unsigned long long work_blocks) {
   return (unsigned)std::max<unsigned long long>(1, std::min(full, work_blocks));
 }
 
-template <int MAXW, bool SELF>
+template <int MAXW, bool SELF, bool MULTI>
 static void launch_verify(const Ctx& c, const ProbeView& v, const Hit* hits, const unsigned long long* off,
                           unsigned long long n_hits, unsigned long long c_begin, unsigned long long c_end,
                           AccOut out, Counters* ctr) {
   const unsigned grid =
-      persistent_grid(k_verify_hits<MAXW, SELF>, (c_end - c_begin + BLOCK * V_RUN - 1) / (BLOCK * V_RUN));
+      persistent_grid(k_verify_hits<MAXW, SELF, MULTI>, (c_end - c_begin + BLOCK * V_RUN - 1) / (BLOCK * V_RUN));
   // lanes past c_end in the last warp span are skipped inside the kernel
-  k_verify_hits<MAXW, SELF><<<grid, BLOCK, 0, c.stream>>>(v, hits, off, n_hits, c_begin, c_end, out, ctr);
+  k_verify_hits<MAXW, SELF, MULTI><<<grid, BLOCK, 0, c.stream>>>(v, hits, off, n_hits, c_begin, c_end, out, ctr);
   PJ_LAUNCHED("k_verify_hits");
 }
 
-template <int MAXW, bool SELF>
+template <int MAXW, bool SELF, bool MULTI>
 static void launch_fallback(const Ctx& c, const ProbeView& v, uint32_t xcount, AccOut out, Counters* ctr) {
-  const unsigned grid = persistent_grid(k_fallback<MAXW, SELF>, (xcount + BLOCK - 1) / BLOCK);
-  k_fallback<MAXW, SELF><<<grid, BLOCK, 0, c.stream>>>(v, xcount, out, ctr);
+  const unsigned grid = persistent_grid(k_fallback<MAXW, SELF, MULTI>, (xcount + BLOCK - 1) / BLOCK);
+  k_fallback<MAXW, SELF, MULTI><<<grid, BLOCK, 0, c.stream>>>(v, xcount, out, ctr);
   PJ_LAUNCHED("k_fallback");
 }
 
@@ -354,11 +384,11 @@ struct AcceptBuf {
 // Probe + verify for all probing strings, in chunks of probing strings whose
 // groups fit the hit buffer; then the short-string fallback.  Returns the
 // number of accepted matches (the buffer holds min(that, out.cap)).
-template <bool SELF>
+template <bool SELF, bool MULTI>
 static void probe_and_verify(const Ctx& c, const ProbeView& v0, uint32_t fb_count, AcceptBuf& acc, Counters* ctr,
-                             Counters& h, Timings& tm) {
+                             Counters& h, Timings& tm, const unsigned long long* h_qgoff) {
   EventTimer tp(c.stream), tv(c.stream), tf(c.stream);
-  const int G = groups_per_probe(v0.tau, SELF);
+  const int G = MULTI ? 1 : groups_per_probe(v0.tau, SELF);
   const unsigned long long group_budget = env_knob("PJ_GROUP_BUDGET", 64ull << 20);
   const unsigned long long launch_cands = env_knob("PJ_LAUNCH_CANDS", 1ull << 30);
   const uint32_t chunk_items = (uint32_t)std::max<unsigned long long>(1, group_budget / G);
@@ -370,12 +400,22 @@ static void probe_and_verify(const Ctx& c, const ProbeView& v0, uint32_t fb_coun
     ProbeView v = v0;
     v.pbegin = v0.pbegin + done;
     v.pcount = std::min(chunk_items, v0.pcount - done);
-    const unsigned long long n_groups = (unsigned long long)v.pcount * G;
+    unsigned long long n_groups = (unsigned long long)v.pcount * G;
+    if (MULTI) {  // probes whose groups fit the budget (at least one)
+      uint32_t q1 = v.pbegin + 1;
+      while (q1 < v0.pbegin + v0.pcount && h_qgoff[q1 + 1] - h_qgoff[v.pbegin] <= group_budget) ++q1;
+      v.pcount = q1 - v.pbegin;
+      n_groups = h_qgoff[q1] - h_qgoff[v.pbegin];
+      if (n_groups == 0) {
+        done += v.pcount;
+        continue;
+      }
+    }
     gcount.reset(c, n_groups);
     goff.reset(c, n_groups);
     tp.start();
-    const unsigned g1 = persistent_grid(k_group_counts<SELF>, (n_groups + BLOCK - 1) / BLOCK);
-    k_group_counts<SELF><<<g1, BLOCK, 0, c.stream>>>(v, n_groups, gcount.p, ctr);
+    const unsigned g1 = persistent_grid(k_group_counts<SELF, MULTI>, (n_groups + BLOCK - 1) / BLOCK);
+    k_group_counts<SELF, MULTI><<<g1, BLOCK, 0, c.stream>>>(v, n_groups, gcount.p, ctr);
     PJ_LAUNCHED("k_group_counts");
     exclusive_scan<uint32_t>(c, gcount.p, goff.p, n_groups);
     uint32_t last[2] = {0, 0};
@@ -385,8 +425,8 @@ static void probe_and_verify(const Ctx& c, const ProbeView& v0, uint32_t fb_coun
     const unsigned long long n_hits = (unsigned long long)last[0] + last[1];
     if (n_hits > 0) {
       hits.reset(c, n_hits);
-      const unsigned g2 = persistent_grid(k_group_hits<SELF>, (n_groups + BLOCK - 1) / BLOCK);
-      k_group_hits<SELF><<<g2, BLOCK, 0, c.stream>>>(v, n_groups, gcount.p, goff.p, hits.p);
+      const unsigned g2 = persistent_grid(k_group_hits<SELF, MULTI>, (n_groups + BLOCK - 1) / BLOCK);
+      k_group_hits<SELF, MULTI><<<g2, BLOCK, 0, c.stream>>>(v, n_groups, gcount.p, goff.p, hits.p);
       PJ_LAUNCHED("k_group_hits");
     }
     trace_mark(c, "join: probe (hits)");
@@ -411,13 +451,13 @@ static void probe_and_verify(const Ctx& c, const ProbeView& v0, uint32_t fb_coun
     h.candidates += n_cand;
     h.hits += n_hits;
     total_cand += n_cand;
-    const double remaining_groups = (double)(v0.pcount - done - v.pcount) / std::max(1u, v.pcount) + 1.0;
+    const double remaining_groups = (double)(v0.pcount - done - v.pcount) / std::max(1u, v.pcount) + 1.0;  // chunks left
     for (unsigned long long cb = 0; cb < n_cand; cb += launch_cands) {
       const unsigned long long ce = std::min(n_cand, cb + launch_cands);
       tv.start();
       acc.run(
           [&](AccOut o) {
-#define PJ_CALL(W) launch_verify<W, SELF>(c, v, hits.p, off.p, n_hits, cb, ce, o, ctr)
+#define PJ_CALL(W) launch_verify<W, SELF, MULTI>(c, v, hits.p, off.p, n_hits, cb, ce, o, ctr)
             PJ_BY_TAU(v.tau, PJ_CALL);
 #undef PJ_CALL
           },
@@ -438,7 +478,7 @@ static void probe_and_verify(const Ctx& c, const ProbeView& v0, uint32_t fb_coun
     tf.start();
     acc.run(
         [&](AccOut o) {
-#define PJ_CALL(W) launch_fallback<W, SELF>(c, v, fb_count, o, ctr)
+#define PJ_CALL(W) launch_fallback<W, SELF, MULTI>(c, v, fb_count, o, ctr)
           PJ_BY_TAU(v.tau, PJ_CALL);
 #undef PJ_CALL
         },
@@ -459,14 +499,15 @@ static void probe_and_verify(const Ctx& c, const ProbeView& v0, uint32_t fb_coun
 // Runs the join, retries once with an exact-size buffer if the accepted
 // matches overflowed, then dedupes and compacts into *out.
 static void run_join(const Ctx& c, const ProbeView& v, bool self, uint32_t fb_count, int a_bits,
-                     bool results_on_device, pj_result* out) {
+                     bool results_on_device, pj_result* out, const unsigned long long* h_qgoff = nullptr) {
   Counters h{};
   Timings tm;
   DBuf<Counters> ctr(c, 1);
   PJ_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(Counters), c.stream));
   AcceptBuf acc(c, ctr.p, env_knob("PJ_ACCEPT_INITIAL", 4ull << 20));
-  if (self) probe_and_verify<true>(c, v, fb_count, acc, ctr.p, h, tm);
-  else probe_and_verify<false>(c, v, fb_count, acc, ctr.p, h, tm);
+  if (self) probe_and_verify<true, false>(c, v, fb_count, acc, ctr.p, h, tm, nullptr);
+  else if (v.ptau) probe_and_verify<false, true>(c, v, fb_count, acc, ctr.p, h, tm, h_qgoff);
+  else probe_and_verify<false, false>(c, v, fb_count, acc, ctr.p, h, tm, nullptr);
   DBuf<unsigned long long>& acc_key = acc.key;
   DBuf<uint32_t>& acc_ed = acc.ed;
   const uint64_t cap = acc.cap;
@@ -586,6 +627,52 @@ static void probe_join_impl(const Ctx& c, const pj_index& idx, const Partition& 
   run_join(c, v, false, has_short ? R.n : 0, bits_for(R.n), on_device, out);
 }
 
+void query_multi_impl(const Ctx& c, pj_index& idx, const ProbeSet& R, const uint8_t* h_tau, pj_result* out,
+                      bool on_device) {
+  const int tau_max = (int)idx.parts.size() - 1;
+  int tmax = 0;
+  bool present[PJ_TAU_LIMIT + 1] = {};
+  std::vector<unsigned long long> qgoff((size_t)R.n + 1, 0);
+  for (uint32_t q = 0; q < R.n; ++q) {
+    const int t = h_tau[q];
+    if (t > tau_max) fail(PJ_EINVAL, "query threshold " + std::to_string(t) + " above the index's tau_max");
+    if (idx.parts[t].tau != t) fail(PJ_EINVAL, "index for tau " + std::to_string(t) + " not built");
+    present[t] = true;
+    tmax = std::max(tmax, t);
+    qgoff[q + 1] = qgoff[q] + (unsigned long long)groups_per_probe(t, false);
+  }
+  std::vector<PartView> hp((size_t)tau_max + 1);
+  bool has_short = false;
+  for (int t = 0; t <= tau_max; ++t) {
+    PartView pv{};
+    if (present[t]) {
+      const Partition& part = idx.parts[t];
+      pv = PartView{part.table.p, part.table.n - 1, part.postings.p, part.n_records, part.first, t};
+      has_short |= part.first > 0;
+    }
+    hp[t] = pv;
+  }
+  DBuf<uint8_t> d_tau(c, std::max<uint32_t>(R.n, 1));
+  DBuf<unsigned long long> d_qgoff(c, (size_t)R.n + 1);
+  DBuf<PartView> d_parts(c, hp.size());
+  if (R.n) PJ_CUDA(cudaMemcpyAsync(d_tau.p, h_tau, R.n, cudaMemcpyHostToDevice, c.stream));
+  PJ_CUDA(cudaMemcpyAsync(d_qgoff.p, qgoff.data(), qgoff.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice,
+                          c.stream));
+  PJ_CUDA(cudaMemcpyAsync(d_parts.p, hp.data(), hp.size() * sizeof(PartView), cudaMemcpyHostToDevice, c.stream));
+  ProbeView v = index_side(idx, idx.parts[tmax]);
+  v.pbytes = R.bytes;
+  v.poff = R.off;
+  v.plen = R.len.p;
+  v.pbegin = 0;
+  v.pcount = R.n;
+  v.pid = nullptr;
+  v.key_shift = bits_for(idx.n);
+  v.ptau = d_tau.p;
+  v.qgoff = d_qgoff.p;
+  v.parts = d_parts.p;
+  run_join(c, v, false, has_short ? R.n : 0, bits_for(R.n), on_device, out, qgoff.data());
+}
+
 }  // namespace pj
 
 // ------------------------------------------------------------------ C ABI --
@@ -659,6 +746,33 @@ int pj_query(pj_index* idx, const pj_strings* batch, int tau, pj_result* out) {
     pj::upload_probe_set(idx->ctx, *batch, P);
     pj::probe_join_impl(idx->ctx, *idx, part, P, out, idx->results_on_device);
     out->stats.partition_ms = part_ms;
+    return PJ_OK;
+  } catch (const pj::Error& e) {
+    pj::set_last_error(e.msg);
+    pj_result_free(out);
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    pj::set_last_error("host allocation failed");
+    pj_result_free(out);
+    return PJ_ENOMEM;
+  }
+}
+
+int pj_query_multi(pj_index* idx, const pj_strings* batch, const uint8_t* taus, pj_result* out) {
+  clear_result(out);
+  try {
+    if (!idx || !batch || !out || (!taus && batch->n)) pj::fail(PJ_EINVAL, "pj_query_multi: NULL argument");
+    std::lock_guard<std::mutex> g(idx->mu);
+    bool seen[PJ_TAU_LIMIT + 1] = {};
+    for (uint32_t q = 0; q < batch->n; ++q) {
+      if ((int)taus[q] >= (int)idx->parts.size()) pj::fail(PJ_EINVAL, "pj_query_multi: tau outside 0..tau_max");
+      seen[taus[q]] = true;
+    }
+    for (int t = 0; t < (int)idx->parts.size(); ++t)
+      if (seen[t]) pj::ensure_partition(*idx, t, nullptr);
+    pj::ProbeSet P;
+    pj::upload_probe_set(idx->ctx, *batch, P);
+    pj::query_multi_impl(idx->ctx, *idx, P, taus, out, idx->results_on_device);
     return PJ_OK;
   } catch (const pj::Error& e) {
     pj::set_last_error(e.msg);

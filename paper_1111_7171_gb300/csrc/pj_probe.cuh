@@ -14,12 +14,23 @@
 
 namespace pj {
 
-// A lookup with a non-empty posting run.  pi = p | (i << 16).
+// A lookup with a non-empty posting run.  pi = p | (i << 16) | (tau << 24);
+// the tau byte is used by multi-threshold batches only.
 struct Hit {
   uint32_t q;
   uint32_t begin;
   uint32_t count;
   uint32_t pi;
+};
+
+// One threshold's segment index, as seen by the kernels.
+struct PartView {
+  const Slot* table;
+  unsigned long long mask;
+  const uint32_t* postings;
+  unsigned long long n_postings;
+  uint32_t first;  // first sid of length >= tau + 1
+  int tau;
 };
 
 struct ProbeView {
@@ -43,7 +54,24 @@ struct ProbeView {
   unsigned long long n_postings;
   int tau;
   int key_shift;  // pair key = a << key_shift | b
+  // multi-threshold batches (R != S only): probe q has threshold ptau[q],
+  // its groups are qgoff[q] .. qgoff[q+1]-1, parts[tau] is tau's index
+  const uint8_t* ptau;
+  const unsigned long long* qgoff;
+  const PartView* parts;
 };
+
+// The view of threshold tau inside a multi-threshold batch.
+__host__ __device__ __forceinline__ ProbeView view_for_tau(const ProbeView& v, int tau) {
+  ProbeView t = v;
+  const PartView& pv = v.parts[tau];
+  t.table = pv.table;
+  t.mask = pv.mask;
+  t.postings = pv.postings;
+  t.n_postings = pv.n_postings;
+  t.tau = tau;
+  return t;
+}
 
 // Groups per probing string: lengths |s|-tau..|s| (self join, Alg. 1 line 4)
 // or |s|-tau..|s|+tau (R != S, Sec. 3.2), times tau + 1 segments.
@@ -134,7 +162,7 @@ __host__ __device__ __forceinline__ bool verify_candidate(const ProbeView& v, bo
   const uint32_t r = v.postings[h.begin + off];
   const uint32_t q = h.q;
   const int p = (int)(h.pi & 0xFFFFu);
-  const int i = (int)(h.pi >> 16);
+  const int i = (int)((h.pi >> 16) & 0xFFu);
   if (r >= v.n_index) {
     err |= 1;
   } else if (!(self && r == q)) {  // a colliding run may hold the probe itself

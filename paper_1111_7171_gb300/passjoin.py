@@ -64,6 +64,21 @@ class pj_options(ctypes.Structure):
                 ("reserved", ctypes.c_int)]
 
 
+class pj_server_options(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int), ("max_batch_queries", ctypes.c_uint32), ("max_batch_bytes", ctypes.c_uint64),
+                ("bytes_per_query", ctypes.c_uint64), ("device_reserve", ctypes.c_uint64)]
+
+
+class pj_request_times(ctypes.Structure):
+    _fields_ = [("queue_ms", ctypes.c_float), ("service_ms", ctypes.c_float), ("batch_requests", ctypes.c_uint32)]
+
+
+class pj_server_counters(ctypes.Structure):
+    _fields_ = [("requests", ctypes.c_uint64), ("batches", ctypes.c_uint64), ("queries", ctypes.c_uint64),
+                ("max_batch_requests", ctypes.c_uint64), ("max_in_flight", ctypes.c_uint32),
+                ("pending", ctypes.c_uint64)]
+
+
 _lib = None
 _lib_lock = threading.Lock()
 
@@ -98,6 +113,23 @@ def library():
             L.pj_index_tau_max.restype = ctypes.c_int
             L.pj_index_device_bytes.argtypes = [ctypes.c_void_p]
             L.pj_index_device_bytes.restype = ctypes.c_uint64
+            L.pj_query_multi.argtypes = [ctypes.c_void_p, P(pj_strings), ctypes.c_void_p, P(pj_result)]
+            L.pj_query_multi.restype = ctypes.c_int
+            L.pj_server_options_init.argtypes = [P(pj_server_options)]
+            L.pj_server_options_init.restype = None
+            L.pj_server_start.argtypes = [ctypes.c_void_p, P(pj_server_options), P(ctypes.c_void_p)]
+            L.pj_server_start.restype = ctypes.c_int
+            L.pj_server_submit.argtypes = [ctypes.c_void_p, P(pj_strings), ctypes.c_int, P(ctypes.c_uint64)]
+            L.pj_server_submit.restype = ctypes.c_int
+            L.pj_server_wait.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, P(pj_result),
+                                         P(pj_request_times)]
+            L.pj_server_wait.restype = ctypes.c_int
+            L.pj_server_cancel.argtypes = [ctypes.c_void_p, ctypes.c_uint64]
+            L.pj_server_cancel.restype = ctypes.c_int
+            L.pj_server_stats.argtypes = [ctypes.c_void_p, P(pj_server_counters)]
+            L.pj_server_stats.restype = ctypes.c_int
+            L.pj_server_stop.argtypes = [ctypes.c_void_p]
+            L.pj_server_stop.restype = None
             L.pj_query_noalloc.argtypes = [ctypes.c_void_p, P(pj_strings), ctypes.c_int, ctypes.c_void_p,
                                            ctypes.c_uint64, P(ctypes.c_uint64)]
             L.pj_query_noalloc.restype = ctypes.c_int
@@ -383,3 +415,68 @@ def pj_query_noalloc(index: Index, batch, tau: int, out_pairs, out_cap: int) -> 
     _check(library().pj_query_noalloc(index.handle, ctypes.byref(b.c), int(tau), ctypes.c_void_p(ptr),
                                       int(out_cap), ctypes.byref(n)), "pj_query_noalloc")
     return int(n.value)
+
+
+def pj_query_multi(index: Index, batch, taus):
+    """pj_query_multi: one batched probe where query q uses threshold taus[q]."""
+    b = Strings(batch)
+    t = np.ascontiguousarray(np.asarray(taus, dtype=np.uint8))
+    if len(t) != b.n:
+        raise ValueError("one threshold per query")
+    res = pj_result()
+    _check(library().pj_query_multi(index.handle, ctypes.byref(b.c), ctypes.c_void_p(t.ctypes.data if len(t) else 0),
+                                    ctypes.byref(res)), "pj_query_multi")
+    return _take(res)
+
+
+class Server:
+    """pj_server_*: continuous-batching query server over a resident index."""
+
+    def __init__(self, index: Index, slots: int = 3, max_batch_queries: int = 1 << 16,
+                 max_batch_bytes: int = 16 << 20, bytes_per_query: int = 64 << 10, device_reserve: int = 2 << 30):
+        _torch()
+        L = library()
+        o = pj_server_options()
+        L.pj_server_options_init(ctypes.byref(o))
+        o.slots, o.max_batch_queries, o.max_batch_bytes = slots, max_batch_queries, max_batch_bytes
+        o.bytes_per_query, o.device_reserve = bytes_per_query, device_reserve
+        h = ctypes.c_void_p()
+        _check(L.pj_server_start(index.handle, ctypes.byref(o), ctypes.byref(h)), "pj_server_start")
+        self._h = h
+        self._index = index
+
+    def submit(self, strings, tau: int) -> int:
+        s = Strings(strings)
+        t = ctypes.c_uint64(0)
+        _check(library().pj_server_submit(self._h, ctypes.byref(s.c), int(tau), ctypes.byref(t)), "pj_server_submit")
+        return int(t.value)
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        """Returns (JoinResult, times dict); raises PJError (code PJ_ETIMEDOUT,
+        PJ_ECANCELED, ...) otherwise."""
+        res = pj_result()
+        tm = pj_request_times()
+        _check(library().pj_server_wait(self._h, int(ticket), int(timeout_ms), ctypes.byref(res), ctypes.byref(tm)),
+               "pj_server_wait")
+        times = dict(queue_ms=float(tm.queue_ms), service_ms=float(tm.service_ms),
+                     batch_requests=int(tm.batch_requests))
+        return _take(res), times
+
+    def cancel(self, ticket: int):
+        _check(library().pj_server_cancel(self._h, int(ticket)), "pj_server_cancel")
+
+    def stats(self) -> dict:
+        c = pj_server_counters()
+        _check(library().pj_server_stats(self._h, ctypes.byref(c)), "pj_server_stats")
+        return {f: int(getattr(c, f)) for f, _ in pj_server_counters._fields_}
+
+    def stop(self):
+        if self._h:
+            library().pj_server_stop(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.stop()
+        except Exception:
+            pass
