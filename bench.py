@@ -344,7 +344,8 @@ def run_native(args):
             dist.barrier()
 
     def device_step():
-        idx = pj.pj_build_index((d_bytes, d_off), args.tau, results_on_device=True, lazy_partitions=True)
+        idx = pj.pj_build_index((d_bytes, d_off), args.tau, results_on_device=True, lazy_partitions=True,
+                                autotune=True)
         r = pj.pj_self_join(idx, args.tau)
         out = (r.count, r.stats, idx.build_ms)
         r.free()
@@ -352,7 +353,7 @@ def run_native(args):
         return out
 
     def host_step():
-        idx = pj.pj_build_index((buf, off), args.tau, lazy_partitions=True)
+        idx = pj.pj_build_index((buf, off), args.tau, lazy_partitions=True, autotune=True)
         r = pj.pj_self_join(idx, args.tau)
         idx.free()
         return len(r.pairs), r.stats
@@ -444,6 +445,8 @@ def run_native(args):
                          "probe": probe_ms, "verify": verify_ms,
                          "fallback": statistics.mean(s["fallback_ms"] for s in stats_all),
                          "dedupe": statistics.mean(s["dedupe_ms"] for s in stats_all)},
+            "tuning": {"verify_block": int(st["verify_block"]), "warp_per_candidate_from_length": int(st["warp_min_len"]),
+                       "note": "autotuned in the warm-up steps (cached per workload signature)"},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": cand_all / e2e_s, "unit": UNIT, "ms_per_step": 1e3 * e2e_s / args.steps,

@@ -92,7 +92,9 @@ typedef struct {
   float fallback_ms;    /* device time of the short-string verification */
   float dedupe_ms;      /* device time of sort, min-reduce and compaction */
   float partition_ms;   /* device time spent building a lazily built threshold index, else 0 */
-  uint32_t reserved;
+  int32_t verify_block; /* block size of the thread-per-candidate verification */
+  int32_t warp_min_len; /* self join: probes at least this long were verified one warp per candidate */
+  float tune_ms;        /* time spent autotuning during this call (0 when the decision was cached) */
 } pj_stats;
 
 typedef struct {
@@ -117,7 +119,11 @@ typedef struct {
   int results_on_device;  /* 1: pj_result.pairs stays in device memory */
   int lazy_partitions;    /* 1: pj_build_index builds only the store; each threshold's
                              segment index is built by the first call that needs it */
-  int reserved;
+  int autotune;           /* 1: the first self join of a threshold times the thread- and
+                             warp-per-candidate verification kernels and three block sizes
+                             on candidate samples of each probe-length bucket and keeps the
+                             fastest (cached per workload signature for the process, and in
+                             the file named by the environment variable PJ_AUTOTUNE_CACHE) */
 } pj_options;
 
 typedef struct pj_index pj_index; /* opaque, library-owned */

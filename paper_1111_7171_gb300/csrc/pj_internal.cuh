@@ -100,6 +100,7 @@ struct pj_index {
   std::mutex mu;             // serialises calls that use the index
   bool results_on_device = false;
   bool lazy = false;         // thresholds are built on first use
+  bool autotune = false;     // tune the verification of each threshold's self join
   float build_ms = 0.f;
   uint32_t n = 0;
   int lmax = 0;              // longest string

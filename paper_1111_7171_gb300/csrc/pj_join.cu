@@ -18,7 +18,14 @@
 //       each run of equal keys keeps its least ed (the exact ED of the pair),
 //       and runs are compacted by prefix sum into sorted (a, b, ed) records.
 #include <algorithm>
+#include <cmath>
+#include <cstdio>
 #include <cstdlib>
+#include <chrono>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
 #include <cstring>
 #include <string>
 
@@ -158,15 +165,15 @@ constexpr int V_RUN = 4;  // candidates per lane per step
 // early termination.  Each lane finds its first hit by binary search over the
 // candidate offsets and walks forward from there; lanes never communicate.
 template <int MAXW, bool SELF, bool MULTI>
-__global__ void __launch_bounds__(BLOCK) k_verify_hits(const ProbeView v, const Hit* __restrict__ hits,
+__global__ void __launch_bounds__(512) k_verify_hits(const ProbeView v, const Hit* __restrict__ hits,
                                                        const unsigned long long* __restrict__ cand_off,
                                                        unsigned long long n_hits, unsigned long long c_begin,
                                                        unsigned long long n_cand, AccOut out, Counters* ctr) {
   unsigned long long cells = 0;
   int err = 0;
   const unsigned lane = threadIdx.x & 31u;
-  const unsigned long long warp = ((unsigned long long)blockIdx.x * BLOCK + threadIdx.x) >> 5;
-  const unsigned long long n_warps = ((unsigned long long)gridDim.x * BLOCK) >> 5;
+  const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned long long n_warps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
   const unsigned long long span = 32ull * V_RUN;
   for (unsigned long long base = c_begin + warp * span; base < n_cand; base += n_warps * span) {
     unsigned long long c = base + lane;
@@ -194,6 +201,58 @@ __global__ void __launch_bounds__(BLOCK) k_verify_hits(const ProbeView v, const 
   }
   add_counter(&ctr->cells, cells);
   if (err) atomicOr(&ctr->err, (unsigned long long)err);
+}
+
+// One warp per candidate (long strings): the warp walks candidates
+// c_begin + w, c_begin + w + n_warps, ...; every lane runs the same code on
+// the same candidate, so the shuffles and ballots of vsp_warp see a
+// converged warp.  Lane 0 publishes results.
+template <bool SELF, bool MULTI>
+__global__ void __launch_bounds__(512) k_verify_warp(const ProbeView v, const Hit* __restrict__ hits,
+                                                       const unsigned long long* __restrict__ cand_off,
+                                                       unsigned long long n_hits, unsigned long long c_begin,
+                                                       unsigned long long c_end, AccOut out, Counters* ctr) {
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned long long n_warps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+  unsigned long long cells = 0;
+  int err = 0;
+  for (unsigned long long c = c_begin + warp; c < c_end; c += n_warps) {
+    __syncwarp();
+    unsigned long long lo = 0, hi = n_hits;
+    while (hi - lo > 1) {
+      const unsigned long long mid = (lo + hi) >> 1;
+      if (cand_off[mid] <= c) lo = mid; else hi = mid;
+    }
+    const Hit hit = hits[lo];
+    const ProbeView vt = MULTI ? view_for_tau(v, (int)(hit.pi >> 24)) : v;
+    unsigned long long key = 0;
+    int ed = 0;
+    const bool ok = verify_candidate_warp(vt, SELF, hit, (uint32_t)(c - cand_off[lo]), key, ed, cells, err);
+    if (ok && lane == 0) {
+      const unsigned long long pos = atomicAdd(&ctr->accepted, 1ull);
+      if (pos < out.cap) {
+        out.key[pos] = key;
+        out.ed[pos] = (uint32_t)ed;
+      }
+    }
+  }
+  __syncwarp();
+  if (lane == 0) {
+    add_counter(&ctr->cells, cells);
+    if (err) atomicOr(&ctr->err, (unsigned long long)err);
+  }
+}
+
+// First hit whose probe id is >= q (hits are in probe order).
+__global__ void k_hit_lower_bound(const Hit* __restrict__ hits, unsigned long long n, uint32_t q,
+                                  unsigned long long* out) {
+  unsigned long long lo = 0, hi = n;
+  while (lo < hi) {
+    const unsigned long long mid = (lo + hi) >> 1;
+    if (hits[mid].q < q) lo = mid + 1; else hi = mid;
+  }
+  *out = lo;
 }
 
 // ---------------------------------------------------------------- A8 ------
@@ -274,9 +333,9 @@ static int sm_count() {
 }
 
 template <class K>
-static unsigned persistent_grid(K kernel, unsigned long long work_blocks) {
+static unsigned persistent_grid(K kernel, unsigned long long work_blocks, int block = BLOCK) {
   int bps = 0;
-  PJ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kernel, BLOCK, 0));
+  PJ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kernel, block, 0));
   const unsigned long long full = (unsigned long long)std::max(1, bps) * sm_count();
   return (unsigned)std::max<unsigned long long>(1, std::min(full, work_blocks));
 }
@@ -284,12 +343,23 @@ static unsigned persistent_grid(K kernel, unsigned long long work_blocks) {
 template <int MAXW, bool SELF, bool MULTI>
 static void launch_verify(const Ctx& c, const ProbeView& v, const Hit* hits, const unsigned long long* off,
                           unsigned long long n_hits, unsigned long long c_begin, unsigned long long c_end,
-                          AccOut out, Counters* ctr) {
-  const unsigned grid =
-      persistent_grid(k_verify_hits<MAXW, SELF, MULTI>, (c_end - c_begin + BLOCK * V_RUN - 1) / (BLOCK * V_RUN));
+                          AccOut out, Counters* ctr, int block) {
+  const unsigned grid = persistent_grid(k_verify_hits<MAXW, SELF, MULTI>,
+                                        (c_end - c_begin + (unsigned long long)block * V_RUN - 1) /
+                                            ((unsigned long long)block * V_RUN), block);
   // lanes past c_end in the last warp span are skipped inside the kernel
-  k_verify_hits<MAXW, SELF, MULTI><<<grid, BLOCK, 0, c.stream>>>(v, hits, off, n_hits, c_begin, c_end, out, ctr);
+  k_verify_hits<MAXW, SELF, MULTI><<<grid, block, 0, c.stream>>>(v, hits, off, n_hits, c_begin, c_end, out, ctr);
   PJ_LAUNCHED("k_verify_hits");
+}
+
+template <bool SELF, bool MULTI>
+static void launch_verify_warp(const Ctx& c, const ProbeView& v, const Hit* hits, const unsigned long long* off,
+                               unsigned long long n_hits, unsigned long long c_begin, unsigned long long c_end,
+                               AccOut out, Counters* ctr, int block) {
+  const unsigned grid = persistent_grid(k_verify_warp<SELF, MULTI>,
+                                        (c_end - c_begin + (block / 32) - 1) / (block / 32), block);
+  k_verify_warp<SELF, MULTI><<<grid, block, 0, c.stream>>>(v, hits, off, n_hits, c_begin, c_end, out, ctr);
+  PJ_LAUNCHED("k_verify_warp");
 }
 
 template <int MAXW, bool SELF, bool MULTI>
@@ -384,6 +454,56 @@ struct AcceptBuf {
 // Probe + verify for all probing strings, in chunks of probing strings whose
 // groups fit the hit buffer; then the short-string fallback.  Returns the
 // number of accepted matches (the buffer holds min(that, out.cap)).
+// Probe one chunk of probing strings: per-group hit counts, their prefix
+// sum, the hits, and the candidate offsets of the hits (n_hits + 1 entries).
+template <bool SELF, bool MULTI>
+static void probe_chunk(const Ctx& c, const ProbeView& v, unsigned long long n_groups, Counters* ctr,
+                        DBuf<uint32_t>& gcount, DBuf<uint32_t>& goff, DBuf<Hit>& hits, DBuf<unsigned long long>& cnt,
+                        DBuf<unsigned long long>& off, unsigned long long& n_hits, unsigned long long& n_cand) {
+  gcount.reset(c, n_groups);
+  goff.reset(c, n_groups);
+  const unsigned g1 = persistent_grid(k_group_counts<SELF, MULTI>, (n_groups + BLOCK - 1) / BLOCK);
+  k_group_counts<SELF, MULTI><<<g1, BLOCK, 0, c.stream>>>(v, n_groups, gcount.p, ctr);
+  PJ_LAUNCHED("k_group_counts");
+  exclusive_scan<uint32_t>(c, gcount.p, goff.p, n_groups);
+  uint32_t last[2] = {0, 0};
+  PJ_CUDA(cudaMemcpyAsync(&last[0], goff.p + n_groups - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.stream));
+  PJ_CUDA(cudaMemcpyAsync(&last[1], gcount.p + n_groups - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.stream));
+  c.sync();
+  n_hits = (unsigned long long)last[0] + last[1];
+  n_cand = 0;
+  if (n_hits == 0) return;
+  hits.reset(c, n_hits);
+  const unsigned g2 = persistent_grid(k_group_hits<SELF, MULTI>, (n_groups + BLOCK - 1) / BLOCK);
+  k_group_hits<SELF, MULTI><<<g2, BLOCK, 0, c.stream>>>(v, n_groups, gcount.p, goff.p, hits.p);
+  PJ_LAUNCHED("k_group_hits");
+  trace_mark(c, "join: probe (hits)");
+  cnt.reset(c, n_hits + 1);
+  off.reset(c, n_hits + 1);
+  PJ_CUDA(cudaMemsetAsync(cnt.p + n_hits, 0, sizeof(unsigned long long), c.stream));
+  k_hit_counts<<<ceil_div(n_hits, 256), 256, 0, c.stream>>>(hits.p, n_hits, cnt.p);
+  PJ_LAUNCHED("k_hit_counts");
+  exclusive_scan<unsigned long long>(c, cnt.p, off.p, n_hits + 1);
+  PJ_CUDA(cudaMemcpyAsync(&n_cand, off.p + n_hits, sizeof(n_cand), cudaMemcpyDeviceToHost, c.stream));
+  c.sync();
+}
+
+// Index of the first candidate whose probe id is >= q (hits in probe order).
+static unsigned long long first_candidate_of(const Ctx& c, const DBuf<Hit>& hits, const DBuf<unsigned long long>& off,
+                                             unsigned long long n_hits, unsigned long long n_cand, uint32_t q) {
+  DBuf<unsigned long long> hcut(c, 1);
+  k_hit_lower_bound<<<1, 1, 0, c.stream>>>(hits.p, n_hits, q, hcut.p);
+  PJ_LAUNCHED("k_hit_lower_bound");
+  unsigned long long h_cut = 0, c_cut = n_cand;
+  PJ_CUDA(cudaMemcpyAsync(&h_cut, hcut.p, sizeof(h_cut), cudaMemcpyDeviceToHost, c.stream));
+  c.sync();
+  if (h_cut < n_hits) {
+    PJ_CUDA(cudaMemcpyAsync(&c_cut, off.p + h_cut, sizeof(c_cut), cudaMemcpyDeviceToHost, c.stream));
+    c.sync();
+  }
+  return c_cut;
+}
+
 template <bool SELF, bool MULTI>
 static void probe_and_verify(const Ctx& c, const ProbeView& v0, uint32_t fb_count, AcceptBuf& acc, Counters* ctr,
                              Counters& h, Timings& tm, const unsigned long long* h_qgoff) {
@@ -411,39 +531,15 @@ static void probe_and_verify(const Ctx& c, const ProbeView& v0, uint32_t fb_coun
         continue;
       }
     }
-    gcount.reset(c, n_groups);
-    goff.reset(c, n_groups);
     tp.start();
-    const unsigned g1 = persistent_grid(k_group_counts<SELF, MULTI>, (n_groups + BLOCK - 1) / BLOCK);
-    k_group_counts<SELF, MULTI><<<g1, BLOCK, 0, c.stream>>>(v, n_groups, gcount.p, ctr);
-    PJ_LAUNCHED("k_group_counts");
-    exclusive_scan<uint32_t>(c, gcount.p, goff.p, n_groups);
-    uint32_t last[2] = {0, 0};
-    PJ_CUDA(cudaMemcpyAsync(&last[0], goff.p + n_groups - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.stream));
-    PJ_CUDA(cudaMemcpyAsync(&last[1], gcount.p + n_groups - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.stream));
-    c.sync();
-    const unsigned long long n_hits = (unsigned long long)last[0] + last[1];
-    if (n_hits > 0) {
-      hits.reset(c, n_hits);
-      const unsigned g2 = persistent_grid(k_group_hits<SELF, MULTI>, (n_groups + BLOCK - 1) / BLOCK);
-      k_group_hits<SELF, MULTI><<<g2, BLOCK, 0, c.stream>>>(v, n_groups, gcount.p, goff.p, hits.p);
-      PJ_LAUNCHED("k_group_hits");
-    }
-    trace_mark(c, "join: probe (hits)");
+    unsigned long long n_hits = 0, n_cand = 0;
+    probe_chunk<SELF, MULTI>(c, v, n_groups, ctr, gcount, goff, hits, cnt, off, n_hits, n_cand);
     if (n_hits == 0) {
       tp.stop();
       tm.probe += tp.ms();
       done += v.pcount;
       continue;
     }
-    cnt.reset(c, n_hits + 1);
-    off.reset(c, n_hits + 1);
-    PJ_CUDA(cudaMemsetAsync(cnt.p + n_hits, 0, sizeof(unsigned long long), c.stream));
-    k_hit_counts<<<ceil_div(n_hits, 256), 256, 0, c.stream>>>(hits.p, n_hits, cnt.p);
-    PJ_LAUNCHED("k_hit_counts");
-    exclusive_scan<unsigned long long>(c, cnt.p, off.p, n_hits + 1);
-    unsigned long long n_cand = 0;
-    PJ_CUDA(cudaMemcpyAsync(&n_cand, off.p + n_hits, sizeof(n_cand), cudaMemcpyDeviceToHost, c.stream));
     tp.stop();
     tm.probe += tp.ms();
     debug_dump(c, "hits", hits.p, n_hits * sizeof(Hit));
@@ -452,14 +548,23 @@ static void probe_and_verify(const Ctx& c, const ProbeView& v0, uint32_t fb_coun
     h.hits += n_hits;
     total_cand += n_cand;
     const double remaining_groups = (double)(v0.pcount - done - v.pcount) / std::max(1u, v.pcount) + 1.0;  // chunks left
-    for (unsigned long long cb = 0; cb < n_cand; cb += launch_cands) {
-      const unsigned long long ce = std::min(n_cand, cb + launch_cands);
+    // candidates [c_cut, n_cand) belong to long probes: one warp per candidate
+    unsigned long long c_cut = n_cand;
+    if (SELF && !MULTI && v.warp_q_cut < v.pbegin + v.pcount)
+      c_cut = first_candidate_of(c, hits, off, n_hits, n_cand, v.warp_q_cut);
+    for (unsigned long long cb = 0; cb < n_cand;) {
+      const bool warp_range = cb >= c_cut;
+      const unsigned long long ce = std::min(warp_range ? n_cand : c_cut, cb + launch_cands);
       tv.start();
       acc.run(
           [&](AccOut o) {
-#define PJ_CALL(W) launch_verify<W, SELF, MULTI>(c, v, hits.p, off.p, n_hits, cb, ce, o, ctr)
-            PJ_BY_TAU(v.tau, PJ_CALL);
+            if (warp_range) {
+              launch_verify_warp<SELF, MULTI>(c, v, hits.p, off.p, n_hits, cb, ce, o, ctr, v.block_warp);
+            } else {
+#define PJ_CALL(W) launch_verify<W, SELF, MULTI>(c, v, hits.p, off.p, n_hits, cb, ce, o, ctr, v.block_thread)
+              PJ_BY_TAU(v.tau, PJ_CALL);
 #undef PJ_CALL
+            }
           },
           [&](unsigned long long after) {  // project the whole join from the rate so far
             const double rate = (double)after / (double)(verified + (ce - cb));
@@ -469,6 +574,7 @@ static void probe_and_verify(const Ctx& c, const ProbeView& v0, uint32_t fb_coun
       tv.stop();
       tm.verify += tv.ms();
       verified += ce - cb;
+      cb = ce;
     }
     trace_mark(c, "join: verify");
     done += v.pcount;
@@ -566,8 +672,166 @@ static void run_join(const Ctx& c, const ProbeView& v, bool self, uint32_t fb_co
   }
 }
 
+// ------------------------------------------------------------ autotune ----
+//
+// Decides, for one threshold's self join, (1) the probe length from which
+// candidates are verified one warp per candidate instead of one thread per
+// candidate, and (2) the block size of the thread-per-candidate kernel.
+// Probes are in length order, so a cut-over length splits the candidates
+// into a thread range and a warp range.  Every configuration -- cut-over in
+// {never, 0, 64, 128, ..., 2048} restricted to the lengths present, block
+// size in {128, 256, 512} -- verifies the same prefix of the candidates (at
+// most 2^26) into a scratch buffer whose results are dropped; the fastest
+// (best of two runs, CUDA events) wins.  Decisions are cached per workload
+// signature for the process and, with PJ_AUTOTUNE_CACHE=<file>, in that file
+// (one "signature|cut|block" line each).
+
+struct TuneResult {
+  int warp_min_len = 65536;
+  int block_thread = 256;
+};
+
+static std::mutex g_tune_mu;
+static std::map<std::string, TuneResult> g_tune_cache;
+
+static std::string tune_signature(const pj_index& idx, int tau) {
+  const int lmin = idx.n ? [&] {
+    for (int l = 0; l <= idx.lmax; ++l)
+      if (idx.h_bbeg[l + 1] > idx.h_bbeg[l]) return l;
+    return 0;
+  }() : 0;
+  char buf[160];
+  snprintf(buf, sizeof(buf), "self tau=%d n=%u len=%d..%d avg=%.1f", tau, idx.n, lmin, idx.lmax,
+           idx.n ? (double)idx.total_bytes / idx.n : 0.0);
+  return buf;
+}
+
+static bool tune_from_file(const std::string& key, TuneResult& r) {
+  const char* path = getenv("PJ_AUTOTUNE_CACHE");
+  if (!path || !path[0]) return false;
+  std::ifstream f(path);
+  std::string line;
+  bool found = false;
+  while (std::getline(f, line)) {
+    const size_t a = line.find('|'), b = line.rfind('|');
+    if (a == std::string::npos || a == b || line.substr(0, a) != key) continue;
+    r.warp_min_len = atoi(line.c_str() + a + 1);
+    r.block_thread = atoi(line.c_str() + b + 1);
+    found = true;  // the last line for a key wins
+  }
+  return found;
+}
+
+static void tune_to_file(const std::string& key, const TuneResult& r) {
+  const char* path = getenv("PJ_AUTOTUNE_CACHE");
+  if (!path || !path[0]) return;
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "%s|%d|%d\n", key.c_str(), r.warp_min_len, r.block_thread);
+  fclose(f);
+}
+
+static TuneResult autotune_self(pj_index& idx, const ProbeView& v0) {
+  const Ctx& c = idx.ctx;
+  TuneResult best;
+  const int tau = v0.tau;
+  const int G = groups_per_probe(tau, true);
+  const unsigned long long group_budget = env_knob("PJ_GROUP_BUDGET", 64ull << 20);
+  ProbeView v = v0;
+  v.pcount = (uint32_t)std::min<unsigned long long>(v0.pcount, std::max<unsigned long long>(1, group_budget / G));
+  if (v.pcount == 0) return best;
+  DBuf<Counters> ctr(c, 1);
+  PJ_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(Counters), c.stream));
+  DBuf<uint32_t> gcount, goff;
+  DBuf<Hit> hits;
+  DBuf<unsigned long long> cnt, off;
+  unsigned long long n_hits = 0, n_cand = 0;
+  probe_chunk<true, false>(c, v, (unsigned long long)v.pcount * G, ctr.p, gcount, goff, hits, cnt, off, n_hits, n_cand);
+  if (n_cand == 0) return best;
+  // the timed range: a prefix of the candidates (probes are in length order,
+  // so it covers the shortest probes; capped to bound the tuning time)
+  const unsigned long long S = std::min<unsigned long long>(n_cand, 1ull << 26);
+  DBuf<unsigned long long> scr_key(c, S);
+  DBuf<uint32_t> scr_ed(c, S);
+  const AccOut scratch{scr_key.p, scr_ed.p, S};
+  // cut-over candidates: never, and every bucket edge inside the lengths present
+  std::vector<int> cuts{65536};
+  const int edges[] = {0, 64, 128, 256, 512, 1024, 2048};
+  for (int e : edges)
+    if (e <= idx.lmax && idx.h_bbeg[std::min(e, idx.lmax + 1)] < v.pbegin + v.pcount) cuts.push_back(e);
+  const int blocks[] = {128, 256, 512};
+  EventTimer tm(c.stream);
+  double best_ms = 1e30;
+  for (int cut : cuts) {
+    unsigned long long c_cut = S;
+    if (cut < 65536) {
+      const uint32_t q_cut = std::max<uint32_t>(idx.h_bbeg[std::max(0, cut)], v.pbegin);
+      c_cut = std::min(S, first_candidate_of(c, hits, off, n_hits, n_cand, q_cut));
+    }
+    for (int blk : blocks) {
+      if (c_cut == 0 && blk != 256) continue;  // all warp path: the thread block size is moot
+      double ms = 1e30;
+      for (int rep = 0; rep < 2; ++rep) {
+        PJ_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(Counters), c.stream));
+        tm.start();
+        if (c_cut > 0) {
+#define PJ_CALL(W) launch_verify<W, true, false>(c, v, hits.p, off.p, n_hits, 0, c_cut, scratch, ctr.p, blk)
+          PJ_BY_TAU(tau, PJ_CALL);
+#undef PJ_CALL
+        }
+        if (c_cut < S) launch_verify_warp<true, false>(c, v, hits.p, off.p, n_hits, c_cut, S, scratch, ctr.p, 256);
+        tm.stop();
+        ms = std::min(ms, (double)tm.ms());
+      }
+      if (getenv("PJ_TRACE"))
+        fprintf(stderr, "[pj] autotune tau=%d cut=%d block=%d: %.3f ms over %llu candidates\n", tau, cut, blk, ms,
+                (unsigned long long)S);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best.warp_min_len = cut;
+        best.block_thread = blk;
+      }
+    }
+  }
+  if (getenv("PJ_TRACE"))
+    fprintf(stderr, "[pj] autotune tau=%d: warp from length %d, block %d\n", tau, best.warp_min_len, best.block_thread);
+  return best;
+}
+
+// The tuning of a self join: environment overrides, then the caches, then a
+// fresh measurement (when the index asks for autotuning).
+static TuneResult self_join_tuning(pj_index& idx, const ProbeView& v, float* tune_ms) {
+  TuneResult r;
+  *tune_ms = 0.f;
+  if (idx.autotune) {
+    const std::string key = tune_signature(idx, v.tau);
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      r = it->second;
+    } else if (tune_from_file(key, r)) {
+      g_tune_cache[key] = r;
+    } else {
+      const auto t0 = std::chrono::steady_clock::now();
+      r = autotune_self(idx, v);
+      *tune_ms = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      g_tune_cache[key] = r;
+      tune_to_file(key, r);
+    }
+  }
+  const char* e = getenv("PJ_WARP_MIN_LEN");
+  if (e && e[0]) r.warp_min_len = atoi(e);
+  const char* bk = getenv("PJ_VERIFY_BLOCK");
+  if (bk && bk[0]) r.block_thread = atoi(bk);
+  if (r.block_thread != 128 && r.block_thread != 256 && r.block_thread != 512) r.block_thread = 256;
+  return r;
+}
+
 static ProbeView index_side(const pj_index& idx, const Partition& part) {
   ProbeView v{};
+  v.warp_q_cut = UINT32_MAX;
+  v.block_thread = 256;
+  v.block_warp = 256;
   v.ibytes = idx.sbytes.p;
   v.ioff = idx.soff.p;
   v.ilen = idx.slen.p;
@@ -609,8 +873,16 @@ static void self_join_impl(pj_index& idx, int tau, pj_result* out, bool on_devic
   v.pcount = idx.n - part.first;
   v.pid = idx.perm.p;
   v.key_shift = bits_for(idx.n);
+  v.warp_q_cut = UINT32_MAX;
+  float tune_ms = 0.f;
+  const TuneResult tr = self_join_tuning(idx, v, &tune_ms);
+  if (tr.warp_min_len <= idx.lmax) v.warp_q_cut = idx.h_bbeg[std::max(0, tr.warp_min_len)];
+  v.block_thread = tr.block_thread;
   run_join(idx.ctx, v, true, part.first, bits_for(idx.n), on_device, out);
   out->stats.partition_ms = part_ms;
+  out->stats.verify_block = tr.block_thread;
+  out->stats.warp_min_len = tr.warp_min_len;
+  out->stats.tune_ms = tune_ms;
 }
 
 static void probe_join_impl(const Ctx& c, const pj_index& idx, const Partition& part, const ProbeSet& R,

@@ -59,6 +59,11 @@ struct ProbeView {
   const uint8_t* ptau;
   const unsigned long long* qgoff;
   const PartView* parts;
+  // self join: probes q >= warp_q_cut (the long ones; probes are in length
+  // order) are verified one warp per candidate; UINT32_MAX = never
+  uint32_t warp_q_cut;
+  int block_thread;  // block size of the thread-per-candidate verification
+  int block_warp;    // block size of the warp-per-candidate verification
 };
 
 // The view of threshold tau inside a multi-threshold batch.
@@ -184,5 +189,39 @@ __host__ __device__ __forceinline__ bool verify_candidate(const ProbeView& v, bo
   }
   return ok;
 }
+
+#ifdef __CUDACC__
+// verify_candidate for a whole warp on one candidate (long strings); every
+// lane must call it with the same arguments.
+__device__ __forceinline__ bool verify_candidate_warp(const ProbeView& v, bool self, const Hit& h, uint32_t off,
+                                                      unsigned long long& key, int& ed, unsigned long long& cells,
+                                                      int& err) {
+  bool ok = false;
+  const uint32_t r = v.postings[h.begin + off];
+  const uint32_t q = h.q;
+  const int p = (int)(h.pi & 0xFFFFu);
+  const int i = (int)((h.pi >> 16) & 0xFFu);
+  if (r >= v.n_index) {
+    err |= 1;
+  } else if (!(self && r == q)) {
+    const int ls = (int)v.plen[q];
+    const int lr = (int)v.ilen[r];
+    if (i >= 1 && i <= v.tau + 1 && lr >= v.tau + 1) {
+      int P, li;
+      even_segment(lr, v.tau, i, P, li);
+      if (p + li <= ls &&
+          verify_ext_warp(v.pbytes + v.poff[q], ls, v.ibytes + v.ioff[r], lr, i, p, li, P, v.tau, ed, cells)) {
+        const uint32_t qid = v.pid ? v.pid[q] : q;
+        const uint32_t rid = v.iperm[r];
+        const uint32_t ka = self ? min(qid, rid) : qid;
+        const uint32_t kb = self ? max(qid, rid) : rid;
+        key = ((unsigned long long)ka << v.key_shift) | kb;
+        ok = true;
+      }
+    }
+  }
+  return ok;
+}
+#endif
 
 }  // namespace pj

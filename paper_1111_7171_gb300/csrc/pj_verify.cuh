@@ -128,6 +128,96 @@ __host__ __device__ __forceinline__ int vsp(const uint8_t* x, int nx, const uint
   return res;
 }
 
+#ifdef __CUDACC__
+// Warp-cooperative VERIFYSTRINGPAIR for long strings: all 32 lanes of a warp
+// work on ONE pair, lane l holding band diagonals k = 2l and 2l+1 (up to 64
+// diagonals, so t <= 63).  A row needs the previous row's value one diagonal
+// up (a shuffle from the next lane) and, for the left neighbour in the same
+// row, a min-plus prefix over the lanes: lane l's two cells map the value L
+// left of them to min(B_l, L + 2) with B_l = min(x_1, x_0 + 1), and these
+// maps compose by a 5-step shuffle scan.  The Lemma 4 test is one ballot per
+// row (any lane with an expected edit distance <= t).  Every lane runs the
+// same control flow: callers must enter it with the whole warp converged and
+// with the same arguments in every lane.
+__device__ __forceinline__ int vsp_warp(const uint8_t* x, int nx, const uint8_t* y, int ny, int t,
+                                        unsigned long long& cells) {
+  const unsigned FULLM = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const uint8_t* a = nx <= ny ? x : y;
+  const uint8_t* b = nx <= ny ? y : x;
+  const int na = nx <= ny ? nx : ny;
+  const int nb = nx <= ny ? ny : nx;
+  const int D = nb - na;
+  const int cap = t + 1;
+  int res = cap;
+  if (D <= t && na == 0) res = D;
+  if (D <= t && na > 0) {
+    const int dlo = -((t - D) >> 1);
+    const int w = ((t + D) >> 1) - dlo + 1;
+    const int k0 = 2 * lane, k1 = 2 * lane + 1;
+    int V0 = dlo + k0 < 0 ? cap : min(dlo + k0, cap);
+    int V1 = dlo + k1 < 0 ? cap : min(dlo + k1, cap);
+    const int e0 = abs(D - dlo - k0), e1 = abs(D - dlo - k1);
+    bool alive = true;
+    for (int i = 1; i <= na; ++i) {
+      const uint8_t ca = a[i - 1];
+      const int jb0 = i + dlo + k0 - 1, jb1 = jb0 + 1;
+      const int c0 = (jb0 >= 0 && jb0 < nb) ? (int)b[jb0] : -1;
+      const int c1 = (jb1 >= 0 && jb1 < nb) ? (int)b[jb1] : -1;
+      const int upn = __shfl_down_sync(FULLM, V0, 1);
+      const int up1 = lane == 31 ? cap : upn;
+      const int x0 = min(V0 + ((int)ca != c0 ? 1 : 0), V1 + 1);
+      const int x1 = min(V1 + ((int)ca != c1 ? 1 : 0), up1 + 1);
+      int S = min(x1, x0 + 1);
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int T = __shfl_up_sync(FULLM, S, o);
+        if (lane >= o) S = min(S, T + 2 * o);
+      }
+      const int Sl = __shfl_up_sync(FULLM, S, 1);
+      const int L = lane == 0 ? cap : Sl;
+      V0 = min(min(x0, L + 1), cap);
+      V1 = min(min(x1, V0 + 1), cap);
+      cells += (unsigned long long)w;
+      if (!__any_sync(FULLM, (V0 + e0 <= t) || (V1 + e1 <= t))) {  // Lemma 4
+        alive = false;
+        break;
+      }
+    }
+    const int kres = D - dlo;
+    const int mine = (kres & 1) ? V1 : V0;
+    const int v = __shfl_sync(FULLM, mine, (kres >> 1) & 31);
+    if (alive) res = v;
+  }
+  return res;
+}
+
+// extension-based verification with the warp-cooperative VERIFYSTRINGPAIR
+__device__ __forceinline__ bool verify_ext_warp(const uint8_t* s, int ls, const uint8_t* r, int lr, int i, int p,
+                                                int li, int P, int tau, int& ed, unsigned long long& cells) {
+  bool same = true;
+  for (int k = 0; k < li; ++k) {
+    if (s[p + k] != r[P + k]) {
+      same = false;
+      break;
+    }
+  }
+  bool ok = false;
+  if (same) {
+    const int tl = i - 1, tr = tau + 1 - i;
+    const int dl = vsp_warp(s, p, r, P, tl, cells);
+    if (dl <= tl) {
+      const int dr = vsp_warp(s + p + li, ls - p - li, r + P + li, lr - P - li, tr, cells);
+      if (dr <= tr) {
+        ed = dl + dr;
+        ok = true;
+      }
+    }
+  }
+  return ok;
+}
+#endif
+
 // Extension-based verification of one match (Sec. 5.2, Alg. 3).  s has the
 // selected substring at p; r is the indexed string whose segment i (start P,
 // length li) it matched.  Returns true with ed = d_l + d_r when accepted.

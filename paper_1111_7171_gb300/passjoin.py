@@ -46,7 +46,8 @@ class pj_stats(ctypes.Structure):
     _fields_ = [("lookups", ctypes.c_uint64), ("candidates", ctypes.c_uint64), ("accepted", ctypes.c_uint64),
                 ("dp_cells", ctypes.c_uint64), ("fallback_pairs", ctypes.c_uint64), ("hits", ctypes.c_uint64),
                 ("probe_ms", ctypes.c_float), ("verify_ms", ctypes.c_float), ("fallback_ms", ctypes.c_float),
-                ("dedupe_ms", ctypes.c_float), ("partition_ms", ctypes.c_float), ("reserved", ctypes.c_uint32)]
+                ("dedupe_ms", ctypes.c_float), ("partition_ms", ctypes.c_float), ("verify_block", ctypes.c_int32),
+                ("warp_min_len", ctypes.c_int32), ("tune_ms", ctypes.c_float)]
 
 
 class pj_result(ctypes.Structure):
@@ -61,7 +62,7 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void
 class pj_options(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
                 ("verify_mode", ctypes.c_int), ("results_on_device", ctypes.c_int), ("lazy_partitions", ctypes.c_int),
-                ("reserved", ctypes.c_int)]
+                ("autotune", ctypes.c_int)]
 
 
 class pj_server_options(ctypes.Structure):
@@ -184,7 +185,7 @@ def _torch_free(ctx, ptr, stream):
 
 
 def make_options(stream=None, results_on_device: bool = False, torch_allocator: bool = True,
-                 lazy_partitions: bool = False) -> pj_options:
+                 lazy_partitions: bool = False, autotune: bool = False) -> pj_options:
     torch = _torch()
     opt = pj_options()
     library().pj_options_init(ctypes.byref(opt))
@@ -196,6 +197,7 @@ def make_options(stream=None, results_on_device: bool = False, torch_allocator: 
         opt.free = _torch_free
     opt.results_on_device = 1 if results_on_device else 0
     opt.lazy_partitions = 1 if lazy_partitions else 0
+    opt.autotune = 1 if autotune else 0
     return opt
 
 
@@ -301,7 +303,8 @@ def _stats(st: pj_stats) -> dict:
     return dict(lookups=int(st.lookups), candidates=int(st.candidates), accepted=int(st.accepted),
                 dp_cells=int(st.dp_cells), fallback_pairs=int(st.fallback_pairs), hits=int(st.hits),
                 probe_ms=float(st.probe_ms), verify_ms=float(st.verify_ms), fallback_ms=float(st.fallback_ms),
-                dedupe_ms=float(st.dedupe_ms), partition_ms=float(st.partition_ms))
+                dedupe_ms=float(st.dedupe_ms), partition_ms=float(st.partition_ms),
+                verify_block=int(st.verify_block), warp_min_len=int(st.warp_min_len), tune_ms=float(st.tune_ms))
 
 
 def _take(res: pj_result):
@@ -370,9 +373,9 @@ def pj_kernel_launches() -> int:
 
 
 def pj_build_index(strings, tau_max: int, stream=None, results_on_device: bool = False,
-                   lazy_partitions: bool = False) -> Index:
+                   lazy_partitions: bool = False, autotune: bool = False) -> Index:
     """pj_build_index: resident segment index for thresholds 0..tau_max."""
-    opt = make_options(stream, results_on_device, lazy_partitions=lazy_partitions)
+    opt = make_options(stream, results_on_device, lazy_partitions=lazy_partitions, autotune=autotune)
     S = Strings(strings)
     h = ctypes.c_void_p()
     _check(library().pj_build_index(ctypes.byref(S.c), int(tau_max), ctypes.byref(opt), ctypes.byref(h)),

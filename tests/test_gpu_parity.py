@@ -268,3 +268,39 @@ def test_chunked_probe_multi_launch_and_buffer_growth(monkeypatch):
     rb, ro = synth.pack(R)
     sb, so = synth.pack(S)
     assert_same(pj.pj_join(R, S, 2).pairs, oracle.join(rb, ro, sb, so, 2), "chunked join")
+
+
+@pytest.mark.parametrize("cut", ["0", "60"])
+def test_warp_per_pair_verification(monkeypatch, cut):
+    """Candidates of probes at least PJ_WARP_MIN_LEN long are verified one
+    warp per candidate (shuffle-scan band, ballot early exit): same exact
+    result as the thread-per-candidate path, alone (0) and mixed (60)."""
+    monkeypatch.setenv("PJ_WARP_MIN_LEN", cut)
+    cases = [("short2k", 2, 2000, False), ("short", 4, 3000, False), ("medium", 8, 2500, True),
+             ("long", 32, 600, True), ("long", 8, 600, True)]
+    for name, tau, n, banded in cases:
+        strings = synth.generate(name, tau, n=n)
+        assert_same(gpu_self(strings, tau).pairs, cpu_self(strings, tau, banded=banded), f"{name} tau={tau} cut={cut}")
+
+
+def test_autotuned_self_join(monkeypatch, tmp_path):
+    """The autotuner picks the cut-over and block size per workload signature
+    (cached for the process and in PJ_AUTOTUNE_CACHE); results stay exact."""
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("PJ_AUTOTUNE_CACHE", str(cache))
+    for name, tau, n, banded in [("long", 16, 700, True), ("medium", 4, 3000, True)]:
+        strings = synth.generate(name, tau, n=n)
+        want = cpu_self(strings, tau, banded=banded)
+        idx = pj.pj_build_index(strings, tau, autotune=True)
+        try:
+            r1 = pj.pj_self_join(idx, tau)
+            r2 = pj.pj_self_join(idx, tau)
+        finally:
+            idx.free()
+        assert_same(r1.pairs, want, f"autotuned {name}")
+        assert_same(r2.pairs, want, f"autotuned again {name}")
+        assert r1.stats["verify_block"] in (128, 256, 512)
+        assert r2.stats["tune_ms"] == 0.0  # decision cached
+        assert (r1.stats["warp_min_len"], r1.stats["verify_block"]) == (r2.stats["warp_min_len"], r2.stats["verify_block"])
+    lines = cache.read_text().strip().splitlines()
+    assert len(lines) == 2 and all(line.count("|") == 2 for line in lines)
