@@ -190,16 +190,87 @@ def percentile(xs, q):
     return xs[k]
 
 
+def _serve(pj, idx, reqs, arrivals, use_plans):
+    """Runs reqs through a 3-slot server; arrivals None = all submitted at
+    once.  Returns (wall seconds, per-request latencies in ms, counters)."""
+    srv = pj.Server(idx, slots=3, use_plans=use_plans)
+    lat = []
+    try:
+        for qs, t in reqs[:3]:  # warm-up
+            srv.wait(srv.submit(qs, t))
+        start = time.perf_counter()
+        tickets = []
+        if arrivals is None:
+            tickets = [srv.submit(qs, t) for qs, t in reqs]
+        else:
+            for (qs, t), at in zip(reqs, arrivals):
+                d = start + at - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                tickets.append(srv.submit(qs, t))
+        for tk in tickets:
+            _, tm = srv.wait(tk)
+            lat.append(tm["queue_ms"] + tm["service_ms"])
+        wall = time.perf_counter() - start
+        st = srv.stats()
+    finally:
+        srv.stop()
+    return wall, lat, st
+
+
+def batch_bench(pj, idx, reqs, sizes=(64, 1024, 4096), reps=20):
+    """One batch of B queries (mixed thresholds) end to end through the host
+    API: pj_query_multi (eager: per-call allocations and host reads of the
+    sizes between launches) vs a query plan (one CUDA graph launch).  Both
+    return identical pairs (checked here on every batch)."""
+    flat = [q for qs, _ in reqs for q in qs]
+    taus = np.array([t for qs, t in reqs for _ in qs], dtype=np.uint8)
+    out = {}
+    for B in sizes:
+        if len(flat) < B:
+            continue
+        plan = pj.Plan(idx, max_queries=B, max_bytes=max(1 << 20, 256 * B))
+        try:
+            slices = [(k * 7919 * B // 13) % (len(flat) - B + 1) for k in range(reps)]
+            for s0 in slices[:3]:  # warm-up (and let the plan's capacities settle)
+                plan.query(flat[s0:s0 + B], taus[s0:s0 + B])
+                pj.pj_query_multi(idx, flat[s0:s0 + B], taus[s0:s0 + B])
+            t_eager, t_plan = [], []
+            for s0 in slices:
+                b, t = flat[s0:s0 + B], taus[s0:s0 + B]
+                t0 = time.perf_counter()
+                want = pj.pj_query_multi(idx, b, t)
+                t1 = time.perf_counter()
+                got = plan.query(b, t)
+                t2 = time.perf_counter()
+                if not np.array_equal(got.pairs, want.pairs):
+                    raise RuntimeError(f"query plan differs from pj_query_multi at batch size {B}")
+                t_eager.append(1e3 * (t1 - t0))
+                t_plan.append(1e3 * (t2 - t1))
+            info = plan.info()
+        finally:
+            plan.free()
+        me, mp = percentile(t_eager, 50), percentile(t_plan, 50)
+        out[str(B)] = {"eager_ms_p50": me, "plan_ms_p50": mp, "speedup": me / mp,
+                       "plan_queries_per_s": B / (mp * 1e-3), "eager_queries_per_s": B / (me * 1e-3),
+                       "graph_kernels": info["graph_kernels"], "recaptures": info["recaptures"]}
+    return out
+
+
 def serving_bench(strings, n_requests, seed=4000):
     """Resident index of the workload (tau_max = 4) and a stream of query
     batches (sizes log-uniform 1..4096, tau uniform 1..4, half short-like and
     half medium-like queries, half of them edited copies of indexed strings).
 
     plain  : one pj_query per request, in arrival order, one at a time.
-    served : the continuous-batching server (3 slots).
+    served : the continuous-batching server (3 slots), batches run eagerly.
+    graph  : the same server with each slot's batches replayed through its
+             query plan (one CUDA graph launch per batch).
     Peak throughput: every request submitted at time 0.  Latency: Poisson
-    arrivals at 70% of the served peak request rate; latency = completion -
-    arrival (p50 / p99).  Both forms return identical pairs (tests)."""
+    arrivals at 70% of the eager server's peak request rate (the same
+    arrival times for every form); latency = completion - arrival (p50 /
+    p99).  All forms return identical pairs (tests).  Also the batch
+    microbenchmark of batch_bench."""
     import torch
     from paper_1111_7171_gb300 import passjoin as pj
     from paper_1111_7171_gb300 import synth
@@ -216,41 +287,14 @@ def serving_bench(strings, n_requests, seed=4000):
         for qs, t in reqs:
             pj.pj_query(idx, qs, t)
         plain_s = time.perf_counter() - t0
-        # served, all at once
-        srv = pj.Server(idx, slots=3)
-        try:
-            for qs, t in reqs[:3]:
-                srv.wait(srv.submit(qs, t))
-            t0 = time.perf_counter()
-            tickets = [srv.submit(qs, t) for qs, t in reqs]
-            for tk in tickets:
-                srv.wait(tk)
-            served_s = time.perf_counter() - t0
-            st = srv.stats()
-        finally:
-            srv.stop()
+        served_s, _, st = _serve(pj, idx, reqs, None, False)
+        graph_s, _, stg = _serve(pj, idx, reqs, None, True)
         peak_rps = n_requests / served_s
         rate = 0.7 * peak_rps
         rng = np.random.default_rng(seed + 1)
         arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_requests))
-        # served at the Poisson rate
-        srv = pj.Server(idx, slots=3)
-        lat_served = []
-        try:
-            start = time.perf_counter()
-            tickets = []
-            for (qs, t), at in zip(reqs, arrivals):
-                d = start + at - time.perf_counter()
-                if d > 0:
-                    time.sleep(d)
-                tickets.append(srv.submit(qs, t))
-            for tk in tickets:
-                _, tm = srv.wait(tk)
-                lat_served.append(tm["queue_ms"] + tm["service_ms"])
-            served_wall = time.perf_counter() - start
-            st2 = srv.stats()
-        finally:
-            srv.stop()
+        served_wall, lat_served, st2 = _serve(pj, idx, reqs, arrivals, False)
+        graph_wall, lat_graph, stg2 = _serve(pj, idx, reqs, arrivals, True)
         # plain at the same arrivals
         lat_plain = []
         start = time.perf_counter()
@@ -261,20 +305,26 @@ def serving_bench(strings, n_requests, seed=4000):
             pj.pj_query(idx, qs, t)
             lat_plain.append(1e3 * (time.perf_counter() - start - at))
         plain_wall = time.perf_counter() - start
+        batches = batch_bench(pj, idx, reqs)
     finally:
         idx.free()
+
+    def lat(xs, wall):
+        return {"p50_ms": percentile(xs, 50), "p99_ms": percentile(xs, 99), "queries_per_s": n_queries / wall}
+
     return {
         "requests": n_requests, "queries": n_queries, "index": f"{len(strings)} strings, tau_max 4",
-        "peak_queries_per_s": {"served": n_queries / served_s, "plain": n_queries / plain_s},
+        "peak_queries_per_s": {"served": n_queries / served_s, "graph": n_queries / graph_s,
+                               "plain": n_queries / plain_s},
         "speedup_served_vs_plain": plain_s / served_s,
-        "poisson": {"rate_requests_per_s": rate,
-                    "served": {"p50_ms": percentile(lat_served, 50), "p99_ms": percentile(lat_served, 99),
-                               "queries_per_s": n_queries / served_wall},
-                    "plain": {"p50_ms": percentile(lat_plain, 50), "p99_ms": percentile(lat_plain, 99),
-                              "queries_per_s": n_queries / plain_wall}},
+        "speedup_graph_vs_served": served_s / graph_s,
+        "poisson": {"rate_requests_per_s": rate, "served": lat(lat_served, served_wall),
+                    "graph": lat(lat_graph, graph_wall), "plain": lat(lat_plain, plain_wall)},
         "batches": {"peak_run": st["batches"], "poisson_run": st2["batches"],
+                    "graph_peak_run": stg["batches"], "graph_poisson_run": stg2["batches"],
                     "max_requests_per_batch": max(st["max_batch_requests"], st2["max_batch_requests"]),
                     "max_in_flight": max(st["max_in_flight"], st2["max_in_flight"])},
+        "batch_latency": batches,
     }
 
 

@@ -193,6 +193,60 @@ int pj_query(pj_index* idx, const pj_strings* batch, int tau, pj_result* out);
  */
 int pj_query_multi(pj_index* idx, const pj_strings* batch, const uint8_t* taus, pj_result* out);
 
+/* ----------------------------------------------------------- query plans --
+ * A query plan is pj_query_multi recorded once into a CUDA graph, for
+ * batches of bounded size that arrive again and again (serving).  The eager
+ * path reads sizes back to the host between its launches (hits, candidates,
+ * accepted matches, pairs) and allocates per call; a plan keeps every size
+ * on the device, preallocates all buffers for its capacities, and runs a
+ * whole batch -- threshold groups, probe (Sec. 4.2, Alg. 2), extension
+ * verification (Sec. 5.2, Alg. 3), the short-string fallback, dedupe and
+ * compaction -- as ONE graph launch after the batch's host-to-device copies,
+ * with one stream synchronisation at the end.  Results are written by the
+ * last kernels straight into mapped pinned host memory.  When a batch needs
+ * more room than the capacities (hits, accepted matches or pairs), the plan
+ * enlarges that buffer, records the graph again and reruns the batch, so
+ * results never depend on the capacities.  A plan reads the index only; it
+ * builds every threshold 0..tau_max of a lazy index when it is created.
+ * The index must outlive the plan.  A plan is used by one thread at a time
+ * (calls on one plan are serialised); use one plan per concurrent caller. */
+typedef struct pj_plan pj_plan;
+
+typedef struct {
+  uint32_t max_queries;      /* strings per batch (default 4096, at most 2^24) */
+  uint64_t max_bytes;        /* query bytes per batch (default 1 MiB) */
+  uint64_t hits_capacity;    /* initial capacities (0 = derived from the above); */
+  uint64_t accepted_capacity;/* they grow when a batch needs more */
+  uint64_t pairs_capacity;
+} pj_plan_options;
+
+typedef struct {
+  uint64_t runs;             /* batches run */
+  uint64_t recaptures;       /* graph recordings after the first (capacity growth) */
+  uint32_t graph_nodes;      /* nodes of the current graph */
+  uint32_t graph_kernels;    /* kernel nodes of the current graph (launches per run) */
+  uint64_t hits_capacity, accepted_capacity, pairs_capacity;
+  uint64_t device_bytes;     /* device memory held by the plan */
+  uint64_t host_bytes;       /* pinned host memory held by the plan */
+} pj_plan_info;
+
+void pj_plan_options_init(pj_plan_options* opt);
+/* Create a plan over idx (opt NULL = defaults) on its own CUDA stream.
+ * Errors: PJ_EINVAL (NULL, capacities out of range), PJ_ENOMEM, PJ_ECUDA. */
+int pj_plan_create(pj_index* idx, const pj_plan_options* opt, pj_plan** out);
+/* Run one batch: HOST strings (batch->on_device = 0), at most max_queries of
+ * them and max_bytes bytes, query q with threshold taus[q] (0..tau_max).
+ * *out receives host pairs (a = query position, b = indexed id, ed) sorted
+ * by (a, b) -- exactly what pj_query_multi returns -- and the counters of
+ * pj_stats (the millisecond fields are 0).  Release with pj_result_free.
+ * Errors: PJ_EINVAL (NULL, device batch, batch above the plan's limits, tau
+ * out of range, bad offsets, a string longer than 65535 bytes), PJ_ENOMEM,
+ * PJ_ECUDA (including a failed segment index consistency check). */
+int pj_plan_query(pj_plan* plan, const pj_strings* batch, const uint8_t* taus, pj_result* out);
+int pj_plan_get_info(const pj_plan* plan, pj_plan_info* out);
+/* Release a plan (NULL is ignored). */
+void pj_plan_free(pj_plan* plan);
+
 /* ---------------------------------------------------------------- serving --
  * A continuous-batching query server over a resident index (the R != S join
  * of Sec. 3.2 per request).  Requests are queued by pj_server_submit; each
@@ -213,6 +267,8 @@ typedef struct {
   uint64_t max_batch_bytes;    /* query bytes per batch (default 16 MiB) */
   uint64_t bytes_per_query;    /* device-memory estimate per query for admission (default 64 KiB) */
   uint64_t device_reserve;     /* device memory kept free (default 2 GiB) */
+  int use_plans;               /* 1: each slot runs its batches through its own query plan
+                                  (one CUDA graph launch per batch); 0 (default): pj_query_multi */
 } pj_server_options;
 
 /* Time a request spent queued and being served (host clock), and how many

@@ -23,6 +23,11 @@ struct Error {
 [[noreturn]] void fail(int code, const std::string& msg);
 void check_cuda(cudaError_t e, const char* what, const char* file, int line);
 void count_launch();
+// Launches enqueued while a graph is recorded are not launches: the counter
+// skips them on the recording thread, and each replay of the graph adds its
+// kernel nodes.
+void set_recording(bool on);
+void count_launches(unsigned long long k);
 #define PJ_CUDA(call) ::pj::check_cuda((call), #call, __FILE__, __LINE__)
 // After every kernel launch: count it and surface launch errors.
 #define PJ_LAUNCHED(name)                                                  \

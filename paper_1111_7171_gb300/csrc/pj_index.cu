@@ -31,7 +31,12 @@ const std::string& last_error() { return g_last_error; }
 void fail(int code, const std::string& msg) { throw Error{code, msg}; }
 
 static std::atomic<unsigned long long> g_launches{0};
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static thread_local bool g_recording = false;
+void count_launch() {
+  if (!g_recording) g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+void count_launches(unsigned long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+void set_recording(bool on) { g_recording = on; }
 
 void check_cuda(cudaError_t e, const char* what, const char* file, int line) {
   if (e == cudaSuccess) return;

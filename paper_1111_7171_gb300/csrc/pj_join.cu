@@ -30,6 +30,7 @@
 #include <string>
 
 #include "pj_internal.cuh"
+#include "pj_plan.cuh"
 #include "pj_prims.cuh"
 #include "pj_probe.cuh"
 
@@ -90,10 +91,18 @@ __device__ __forceinline__ void group_of(const ProbeView& v, unsigned long long 
   }
 }
 
+// Sizes that a kernel reads from device memory when it starts: the launch
+// covers a capacity `cap`, n_dev (if not NULL) holds the actual count.
+__device__ __forceinline__ unsigned long long dev_count(unsigned long long cap, const unsigned long long* n_dev) {
+  return n_dev ? min(cap, *n_dev) : cap;
+}
+
 // Pass 1: number of non-empty lookups of every group (probe, length, segment).
 template <bool SELF, bool MULTI>
 __global__ void __launch_bounds__(BLOCK) k_group_counts(const ProbeView v, unsigned long long n_groups,
-                                                        uint32_t* __restrict__ counts, Counters* ctr) {
+                                                        uint32_t* __restrict__ counts, Counters* ctr,
+                                                        const unsigned long long* __restrict__ n_dev) {
+  n_groups = dev_count(n_groups, n_dev);
   unsigned long long lookups = 0;
   int err = 0;
   for (unsigned long long t = (unsigned long long)blockIdx.x * BLOCK + threadIdx.x; t < n_groups;
@@ -120,11 +129,14 @@ __global__ void __launch_bounds__(BLOCK) k_group_counts(const ProbeView v, unsig
 }
 
 // Pass 2: the same lookups again, each non-empty one written as a Hit at the
-// group's prefix-sum offset.
+// group's prefix-sum offset (offsets at or past hits_cap are not written).
 template <bool SELF, bool MULTI>
 __global__ void __launch_bounds__(BLOCK) k_group_hits(const ProbeView v, unsigned long long n_groups,
                                                       const uint32_t* __restrict__ counts,
-                                                      const uint32_t* __restrict__ hit_off, Hit* __restrict__ hits) {
+                                                      const uint32_t* __restrict__ hit_off, Hit* __restrict__ hits,
+                                                      const unsigned long long* __restrict__ n_dev,
+                                                      unsigned long long hits_cap) {
+  n_groups = dev_count(n_groups, n_dev);
   for (unsigned long long t = (unsigned long long)blockIdx.x * BLOCK + threadIdx.x; t < n_groups;
        t += (unsigned long long)gridDim.x * BLOCK) {
     if (counts[t] == 0) continue;
@@ -137,7 +149,7 @@ __global__ void __launch_bounds__(BLOCK) k_group_hits(const ProbeView v, unsigne
     int l, i, P, li, lo, hi;
     int err = 0;
     uint32_t pos = hit_off[t];
-    const uint32_t end = pos + counts[t];
+    const uint32_t end = (uint32_t)min(hits_cap, (unsigned long long)pos + counts[t]);
     const uint32_t tau_tag = MULTI ? ((uint32_t)vt.tau << 24) : 0u;
     if (group_window(vt, SELF, q, ls, g, l, i, P, li, lo, hi)) {
       for (int p = lo; p <= hi && pos < end; ++p) {
@@ -149,9 +161,12 @@ __global__ void __launch_bounds__(BLOCK) k_group_hits(const ProbeView v, unsigne
   }
 }
 
-__global__ void k_hit_counts(const Hit* __restrict__ hits, unsigned long long n, unsigned long long* __restrict__ cnt) {
-  const unsigned long long k = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < n) cnt[k] = hits[k].count;
+__global__ void k_hit_counts(const Hit* __restrict__ hits, unsigned long long n, unsigned long long* __restrict__ cnt,
+                             const unsigned long long* __restrict__ n_dev) {
+  n = dev_count(n, n_dev);
+  for (unsigned long long k = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (unsigned long long)gridDim.x * blockDim.x)
+    cnt[k] = hits[k].count;
 }
 
 // ---------------------------------------------------------------- A6 ------
@@ -168,7 +183,12 @@ template <int MAXW, bool SELF, bool MULTI>
 __global__ void __launch_bounds__(512) k_verify_hits(const ProbeView v, const Hit* __restrict__ hits,
                                                        const unsigned long long* __restrict__ cand_off,
                                                        unsigned long long n_hits, unsigned long long c_begin,
-                                                       unsigned long long n_cand, AccOut out, Counters* ctr) {
+                                                       unsigned long long n_cand, AccOut out, Counters* ctr,
+                                                       const unsigned long long* __restrict__ dn) {
+  if (dn) {  // device sizes: dn[0] hits (clamped to n_hits), dn[1] candidates
+    n_hits = min(n_hits, dn[0]);
+    n_cand = dn[1];
+  }
   unsigned long long cells = 0;
   int err = 0;
   const unsigned lane = threadIdx.x & 31u;
@@ -262,7 +282,9 @@ __global__ void k_hit_lower_bound(const Hit* __restrict__ hits, unsigned long lo
 // Otherwise: every probe x against the indexed strings of length <= tau
 // within the length filter.  One thread per x.
 template <int MAXW, bool SELF, bool MULTI>
-__global__ void __launch_bounds__(BLOCK) k_fallback(const ProbeView v, uint32_t xcount, AccOut out, Counters* ctr) {
+__global__ void __launch_bounds__(BLOCK) k_fallback(const ProbeView v, uint32_t xcount, AccOut out, Counters* ctr,
+                                                    const unsigned long long* __restrict__ n_dev) {
+  xcount = (uint32_t)dev_count(xcount, n_dev);
   unsigned long long cells = 0, pairs = 0;
   for (uint32_t x = blockIdx.x * BLOCK + threadIdx.x; x < xcount; x += gridDim.x * BLOCK) {
     const int tau = MULTI ? (int)v.ptau[x] : v.tau;
@@ -300,24 +322,34 @@ __global__ void __launch_bounds__(BLOCK) k_fallback(const ProbeView v, uint32_t 
 
 // ------------------------------------------------------------ A5 + A7 -----
 
-__global__ void k_run_heads(const unsigned long long* __restrict__ keys, uint64_t n, uint32_t* __restrict__ flags) {
-  const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < n) flags[k] = (k == 0 || keys[k] != keys[k - 1]) ? 1u : 0u;
+__global__ void k_run_heads(const unsigned long long* __restrict__ keys, unsigned long long n,
+                            uint32_t* __restrict__ flags, const unsigned long long* __restrict__ n_dev) {
+  n = dev_count(n, n_dev);
+  for (unsigned long long k = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (unsigned long long)gridDim.x * blockDim.x)
+    flags[k] = (k == 0 || keys[k] != keys[k - 1]) ? 1u : 0u;
 }
 
+// Each run of equal keys becomes one pair with the run's least ed, written
+// at the run's prefix-sum position (positions at or past out_cap are not
+// written).
 __global__ void k_emit_pairs(const unsigned long long* __restrict__ keys, const uint32_t* __restrict__ eds,
-                             const uint32_t* __restrict__ flags, const uint32_t* __restrict__ pos, uint64_t n,
-                             int key_shift, pj_pair* __restrict__ out) {
-  const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n || !flags[k]) return;
-  const unsigned long long key = keys[k];
-  uint32_t ed = eds[k];
-  for (uint64_t j = k + 1; j < n && keys[j] == key; ++j) ed = min(ed, eds[j]);
-  pj_pair pr;
-  pr.a = (uint32_t)(key >> key_shift);
-  pr.b = (uint32_t)(key & ((1ull << key_shift) - 1));
-  pr.ed = ed;
-  out[pos[k]] = pr;
+                             const uint32_t* __restrict__ flags, const uint32_t* __restrict__ pos,
+                             unsigned long long n, int key_shift, pj_pair* __restrict__ out,
+                             const unsigned long long* __restrict__ n_dev, unsigned long long out_cap) {
+  n = dev_count(n, n_dev);
+  for (unsigned long long k = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (unsigned long long)gridDim.x * blockDim.x) {
+    if (!flags[k] || pos[k] >= out_cap) continue;
+    const unsigned long long key = keys[k];
+    uint32_t ed = eds[k];
+    for (unsigned long long j = k + 1; j < n && keys[j] == key; ++j) ed = min(ed, eds[j]);
+    pj_pair pr;
+    pr.a = (uint32_t)(key >> key_shift);
+    pr.b = (uint32_t)(key & ((1ull << key_shift) - 1));
+    pr.ed = ed;
+    out[pos[k]] = pr;
+  }
 }
 
 // ------------------------------------------------------------- launch -----
@@ -348,7 +380,8 @@ static void launch_verify(const Ctx& c, const ProbeView& v, const Hit* hits, con
                                         (c_end - c_begin + (unsigned long long)block * V_RUN - 1) /
                                             ((unsigned long long)block * V_RUN), block);
   // lanes past c_end in the last warp span are skipped inside the kernel
-  k_verify_hits<MAXW, SELF, MULTI><<<grid, block, 0, c.stream>>>(v, hits, off, n_hits, c_begin, c_end, out, ctr);
+  k_verify_hits<MAXW, SELF, MULTI><<<grid, block, 0, c.stream>>>(v, hits, off, n_hits, c_begin, c_end, out, ctr,
+                                                                  nullptr);
   PJ_LAUNCHED("k_verify_hits");
 }
 
@@ -365,7 +398,7 @@ static void launch_verify_warp(const Ctx& c, const ProbeView& v, const Hit* hits
 template <int MAXW, bool SELF, bool MULTI>
 static void launch_fallback(const Ctx& c, const ProbeView& v, uint32_t xcount, AccOut out, Counters* ctr) {
   const unsigned grid = persistent_grid(k_fallback<MAXW, SELF, MULTI>, (xcount + BLOCK - 1) / BLOCK);
-  k_fallback<MAXW, SELF, MULTI><<<grid, BLOCK, 0, c.stream>>>(v, xcount, out, ctr);
+  k_fallback<MAXW, SELF, MULTI><<<grid, BLOCK, 0, c.stream>>>(v, xcount, out, ctr, nullptr);
   PJ_LAUNCHED("k_fallback");
 }
 
@@ -463,7 +496,7 @@ static void probe_chunk(const Ctx& c, const ProbeView& v, unsigned long long n_g
   gcount.reset(c, n_groups);
   goff.reset(c, n_groups);
   const unsigned g1 = persistent_grid(k_group_counts<SELF, MULTI>, (n_groups + BLOCK - 1) / BLOCK);
-  k_group_counts<SELF, MULTI><<<g1, BLOCK, 0, c.stream>>>(v, n_groups, gcount.p, ctr);
+  k_group_counts<SELF, MULTI><<<g1, BLOCK, 0, c.stream>>>(v, n_groups, gcount.p, ctr, nullptr);
   PJ_LAUNCHED("k_group_counts");
   exclusive_scan<uint32_t>(c, gcount.p, goff.p, n_groups);
   uint32_t last[2] = {0, 0};
@@ -475,13 +508,13 @@ static void probe_chunk(const Ctx& c, const ProbeView& v, unsigned long long n_g
   if (n_hits == 0) return;
   hits.reset(c, n_hits);
   const unsigned g2 = persistent_grid(k_group_hits<SELF, MULTI>, (n_groups + BLOCK - 1) / BLOCK);
-  k_group_hits<SELF, MULTI><<<g2, BLOCK, 0, c.stream>>>(v, n_groups, gcount.p, goff.p, hits.p);
+  k_group_hits<SELF, MULTI><<<g2, BLOCK, 0, c.stream>>>(v, n_groups, gcount.p, goff.p, hits.p, nullptr, n_hits);
   PJ_LAUNCHED("k_group_hits");
   trace_mark(c, "join: probe (hits)");
   cnt.reset(c, n_hits + 1);
   off.reset(c, n_hits + 1);
   PJ_CUDA(cudaMemsetAsync(cnt.p + n_hits, 0, sizeof(unsigned long long), c.stream));
-  k_hit_counts<<<ceil_div(n_hits, 256), 256, 0, c.stream>>>(hits.p, n_hits, cnt.p);
+  k_hit_counts<<<ceil_div(n_hits, 256), 256, 0, c.stream>>>(hits.p, n_hits, cnt.p, nullptr);
   PJ_LAUNCHED("k_hit_counts");
   exclusive_scan<unsigned long long>(c, cnt.p, off.p, n_hits + 1);
   PJ_CUDA(cudaMemcpyAsync(&n_cand, off.p + n_hits, sizeof(n_cand), cudaMemcpyDeviceToHost, c.stream));
@@ -628,7 +661,7 @@ static void run_join(const Ctx& c, const ProbeView& v, bool self, uint32_t fb_co
     radix_sort_pairs<unsigned long long>(c, acc_key.p, acc_ed.p, nacc, v.key_shift + a_bits);
     trace_mark(c, "join: sort accepted");
     DBuf<uint32_t> flags(c, nacc), pos(c, nacc);
-    k_run_heads<<<ceil_div(nacc, 256), 256, 0, c.stream>>>(acc_key.p, nacc, flags.p);
+    k_run_heads<<<ceil_div(nacc, 256), 256, 0, c.stream>>>(acc_key.p, nacc, flags.p, nullptr);
     PJ_LAUNCHED("k_run_heads");
     exclusive_scan<uint32_t>(c, flags.p, pos.p, nacc);
     uint32_t last[2] = {0, 0};
@@ -638,7 +671,7 @@ static void run_join(const Ctx& c, const ProbeView& v, bool self, uint32_t fb_co
     count = (uint64_t)last[0] + last[1];
     pairs.reset(c, count);
     k_emit_pairs<<<ceil_div(nacc, 256), 256, 0, c.stream>>>(acc_key.p, acc_ed.p, flags.p, pos.p, nacc, v.key_shift,
-                                                             pairs.p);
+                                                             pairs.p, nullptr, count);
     PJ_LAUNCHED("k_emit_pairs");
   }
   td.stop();
@@ -943,6 +976,119 @@ void query_multi_impl(const Ctx& c, pj_index& idx, const ProbeSet& R, const uint
   v.qgoff = d_qgoff.p;
   v.parts = d_parts.p;
   run_join(c, v, false, has_short ? R.n : 0, bits_for(R.n), on_device, out, qgoff.data());
+}
+
+// ------------------------------------------------------------ query plan --
+//
+// query_multi_impl with every size kept on the device, for recording into a
+// CUDA graph: each launch is sized for a capacity and reads the actual count
+// from PlanSizes / Counters when it starts; nothing is read back by the host.
+// Overflowing a capacity only drops writes; the totals are still counted and
+// the host reruns with larger buffers.
+
+static_assert(sizeof(Counters) == 64, "plan counters are 64 bytes");
+
+// Lengths and group counts of the batch; queries past n get 0 groups, so the
+// group offsets of every q >= n equal the total (group_of searches all cap_q).
+__global__ void k_plan_groups(const uint64_t* __restrict__ off, const uint8_t* __restrict__ tau, uint32_t cap_q,
+                              const PlanSizes* __restrict__ sizes, uint32_t* __restrict__ len,
+                              unsigned long long* __restrict__ gcnt) {
+  const unsigned long long n = sizes->n;
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < cap_q; q += gridDim.x * blockDim.x) {
+    if (q < n) {
+      len[q] = (uint32_t)(off[q + 1] - off[q]);
+      gcnt[q] = (unsigned long long)groups_per_probe((int)tau[q], false);
+    } else {
+      gcnt[q] = 0;
+    }
+  }
+}
+
+__global__ void k_plan_finish(const Counters* __restrict__ ctr, const PlanSizes* __restrict__ sizes,
+                              PlanHeader* header) {
+  PlanHeader h;
+  h.groups = sizes->groups;
+  h.hits = sizes->hits;
+  h.cands = sizes->cands;
+  h.accepted = ctr->accepted;
+  h.pairs = sizes->pairs;
+  h.lookups = ctr->lookups;
+  h.cells = ctr->cells;
+  h.fallback = ctr->fallback;
+  h.err = ctr->err;
+  *header = h;
+}
+
+static unsigned stride_grid(unsigned long long cap) {
+  return (unsigned)std::max<unsigned long long>(1, std::min<unsigned long long>((cap + 255) / 256, 152ull * 8));
+}
+
+void record_query_plan(const Ctx& c, const pj_index& idx, const PlanDev& d) {
+  const int tau_max = (int)idx.parts.size() - 1;
+  ProbeView v = index_side(idx, idx.parts[tau_max]);
+  v.pbytes = d.bytes;
+  v.poff = d.off;
+  v.plen = d.len;
+  v.pbegin = 0;
+  v.pcount = d.cap_q;
+  v.pid = nullptr;
+  v.key_shift = bits_for(idx.n);
+  v.ptau = d.tau;
+  v.qgoff = d.qgoff;
+  v.parts = d.parts;
+  bool has_short = false;
+  for (int t = 0; t <= tau_max; ++t) has_short |= idx.parts[t].first > 0;
+  Counters* ctr = static_cast<Counters*>(d.counters);
+  PlanSizes* sz = d.sizes;
+  PJ_CUDA(cudaMemsetAsync(ctr, 0, sizeof(Counters), c.stream));
+
+  // A4: groups of every query, lookups, hits, candidate offsets
+  k_plan_groups<<<stride_grid(d.cap_q), 256, 0, c.stream>>>(d.off, d.tau, d.cap_q, sz, d.len, d.gcnt);
+  PJ_LAUNCHED("k_plan_groups");
+  exclusive_scan_dn<unsigned long long>(c, d.gcnt, d.qgoff, d.cap_q, nullptr, &sz->groups);
+  const unsigned g1 = persistent_grid(k_group_counts<false, true>, (d.cap_groups + BLOCK - 1) / BLOCK);
+  k_group_counts<false, true><<<g1, BLOCK, 0, c.stream>>>(v, d.cap_groups, d.gcounts, ctr, &sz->groups);
+  PJ_LAUNCHED("k_group_counts");
+  exclusive_scan_dn<uint32_t>(c, d.gcounts, d.goff, d.cap_groups, &sz->groups, &sz->hits);
+  const unsigned g2 = persistent_grid(k_group_hits<false, true>, (d.cap_groups + BLOCK - 1) / BLOCK);
+  k_group_hits<false, true><<<g2, BLOCK, 0, c.stream>>>(v, d.cap_groups, d.gcounts, d.goff, d.hits, &sz->groups,
+                                                        d.cap_hits);
+  PJ_LAUNCHED("k_group_hits");
+  k_hit_counts<<<stride_grid(d.cap_hits), 256, 0, c.stream>>>(d.hits, d.cap_hits, d.hcnt, &sz->hits);
+  PJ_LAUNCHED("k_hit_counts");
+  exclusive_scan_dn<unsigned long long>(c, d.hcnt, d.hoff, d.cap_hits, &sz->hits, &sz->cands);
+
+  // A6 + A8: verification of every candidate, then the short indexed strings
+  const AccOut acc{d.acc_key[0], d.acc_ed[0], d.cap_acc};
+#define PJ_CALL(W)                                                                                              \
+  do {                                                                                                         \
+    const unsigned gv = persistent_grid(k_verify_hits<W, false, true>, ~0ull >> 8, BLOCK);                      \
+    k_verify_hits<W, false, true><<<gv, BLOCK, 0, c.stream>>>(v, d.hits, d.hoff, d.cap_hits, 0, 0, acc, ctr,     \
+                                                              &sz->hits);                                      \
+    PJ_LAUNCHED("k_verify_hits");                                                                              \
+    if (has_short) {                                                                                           \
+      const unsigned gf = persistent_grid(k_fallback<W, false, true>, (d.cap_q + BLOCK - 1) / BLOCK);           \
+      k_fallback<W, false, true><<<gf, BLOCK, 0, c.stream>>>(v, d.cap_q, acc, ctr, &sz->n);                     \
+      PJ_LAUNCHED("k_fallback");                                                                               \
+    }                                                                                                          \
+  } while (0)
+  PJ_BY_TAU(tau_max, PJ_CALL);
+#undef PJ_CALL
+
+  // A5 + A7: sort the accepted matches, keep each key's least ed, compact
+  const int nbits = v.key_shift + bits_for(d.cap_q);
+  const bool second = radix_sort_pairs_dn<unsigned long long>(c, d.acc_key[0], d.acc_ed[0], d.acc_key[1],
+                                                              d.acc_ed[1], d.cap_acc, &ctr->accepted, nbits);
+  const unsigned long long* keys = d.acc_key[second ? 1 : 0];
+  const uint32_t* eds = d.acc_ed[second ? 1 : 0];
+  k_run_heads<<<stride_grid(d.cap_acc), 256, 0, c.stream>>>(keys, d.cap_acc, d.flags, &ctr->accepted);
+  PJ_LAUNCHED("k_run_heads");
+  exclusive_scan_dn<uint32_t>(c, d.flags, d.pos, d.cap_acc, &ctr->accepted, &sz->pairs);
+  k_emit_pairs<<<stride_grid(d.cap_acc), 256, 0, c.stream>>>(keys, eds, d.flags, d.pos, d.cap_acc, v.key_shift,
+                                                             d.out_pairs, &ctr->accepted, d.cap_pairs);
+  PJ_LAUNCHED("k_emit_pairs");
+  k_plan_finish<<<1, 1, 0, c.stream>>>(ctr, sz, d.header);
+  PJ_LAUNCHED("k_plan_finish");
 }
 
 }  // namespace pj

@@ -3,6 +3,12 @@
 // Scan: tiles of 4096 values per 1024-thread block (4 per thread), block
 // totals scanned recursively, then added back.
 //
+// Every kernel also takes an optional device-resident item count (n_dev):
+// the launch is sized for a capacity, and the kernels read the actual count
+// (clamped to the capacity) when they start.  Tiles past the count exit at
+// once.  This lets a captured CUDA graph run the primitives on sizes that are
+// only known on the device.
+//
 // Radix sort: 8-bit digits, one pass per digit.  Each pass runs a histogram
 // kernel (per-tile digit counts, stored digit-major so that one exclusive
 // scan over them yields every (digit, tile) output offset) and a scatter
@@ -12,6 +18,8 @@
 // stable.
 #include "pj_prims.cuh"
 
+#include <algorithm>
+
 namespace pj {
 
 namespace {
@@ -20,11 +28,21 @@ constexpr int SCAN_THREADS = 1024;
 constexpr int SCAN_ITEMS = 4;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 
+__device__ __forceinline__ size_t dev_count(size_t cap, const unsigned long long* n_dev) {
+  return n_dev ? (size_t)min((unsigned long long)cap, *n_dev) : cap;
+}
+
 template <class T>
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(const T* __restrict__ in, T* __restrict__ out,
-                                                             T* __restrict__ tile_sums, size_t n) {
+                                                             T* __restrict__ tile_sums, size_t n,
+                                                             const unsigned long long* __restrict__ n_dev) {
   __shared__ T warp_tot[32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  n = dev_count(n, n_dev);
+  if ((size_t)blockIdx.x * SCAN_TILE >= n) {  // whole block past the count
+    if (tid == 0 && tile_sums) tile_sums[blockIdx.x] = T(0);
+    return;
+  }
   const size_t base = (size_t)blockIdx.x * SCAN_TILE + (size_t)tid * SCAN_ITEMS;
   T v[SCAN_ITEMS];
   T sum = 0;
@@ -54,9 +72,19 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(const T* __restrict
 }
 
 template <class T>
-__global__ void k_scan_add(T* __restrict__ out, const T* __restrict__ tile_off, size_t n) {
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] += tile_off[i / SCAN_TILE];
+__global__ void k_scan_add(T* __restrict__ out, const T* __restrict__ tile_off, size_t n,
+                           const unsigned long long* __restrict__ n_dev) {
+  n = dev_count(n, n_dev);
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] += tile_off[i / SCAN_TILE];
+}
+
+// *total = in[0] + ... + in[n-1], from the exclusive scan's last entry.
+template <class T>
+__global__ void k_scan_total(const T* __restrict__ in, const T* __restrict__ out, size_t n,
+                             const unsigned long long* __restrict__ n_dev, unsigned long long* total) {
+  n = dev_count(n, n_dev);
+  *total = n ? (unsigned long long)out[n - 1] + (unsigned long long)in[n - 1] : 0ull;
 }
 
 __global__ void k_widen(const uint32_t* __restrict__ in, uint64_t* __restrict__ out, size_t n) {
@@ -72,9 +100,15 @@ constexpr int RS_TILE = RS_WARPS * RS_WARP_ITEMS;  // 4096
 
 template <class K>
 __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const K* __restrict__ keys, size_t n, int shift,
-                                                        uint32_t* __restrict__ hist, unsigned ntiles) {
+                                                        uint32_t* __restrict__ hist, unsigned ntiles,
+                                                        const unsigned long long* __restrict__ n_dev) {
   __shared__ uint32_t h[256];
   const int tid = threadIdx.x;
+  n = dev_count(n, n_dev);
+  if ((size_t)blockIdx.x * RS_TILE >= n) {  // empty tile: a zero column
+    hist[(size_t)tid * ntiles + blockIdx.x] = 0;
+    return;
+  }
   h[tid] = 0;
   __syncthreads();
   const size_t base = (size_t)blockIdx.x * RS_TILE;
@@ -92,9 +126,12 @@ template <class K>
 __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
                                                            K* __restrict__ kout, uint32_t* __restrict__ vout,
                                                            size_t n, int shift, const uint32_t* __restrict__ offs,
-                                                           unsigned ntiles) {
+                                                           unsigned ntiles,
+                                                           const unsigned long long* __restrict__ n_dev) {
   __shared__ uint32_t wcnt[RS_WARPS][256];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  n = dev_count(n, n_dev);
+  if ((size_t)blockIdx.x * RS_TILE >= n) return;
   for (int d = tid; d < RS_WARPS * 256; d += RS_THREADS) (&wcnt[0][0])[d] = 0;
   __syncthreads();
   const size_t wbase = (size_t)blockIdx.x * RS_TILE + (size_t)warp * RS_WARP_ITEMS;
@@ -146,48 +183,73 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const K* __restrict__
 }  // namespace
 
 template <class T>
-void exclusive_scan(const Ctx& c, const T* in, T* out, size_t n) {
-  if (n == 0) return;
-  const unsigned tiles = ceil_div(n, SCAN_TILE);
-  if (tiles == 1) {
-    k_scan_tiles<T><<<1, SCAN_THREADS, 0, c.stream>>>(in, out, nullptr, n);
-    PJ_LAUNCHED("k_scan_tiles");
+void exclusive_scan_dn(const Ctx& c, const T* in, T* out, size_t cap, const unsigned long long* n_dev,
+                       unsigned long long* total) {
+  if (cap == 0) {
+    if (total) PJ_CUDA(cudaMemsetAsync(total, 0, sizeof(*total), c.stream));
     return;
   }
-  DBuf<T> sums(c, tiles), sums_off(c, tiles);
-  k_scan_tiles<T><<<tiles, SCAN_THREADS, 0, c.stream>>>(in, out, sums.p, n);
-  PJ_LAUNCHED("k_scan_tiles");
-  exclusive_scan<T>(c, sums.p, sums_off.p, tiles);
-  k_scan_add<T><<<ceil_div(n, 256), 256, 0, c.stream>>>(out, sums_off.p, n);
-  PJ_LAUNCHED("k_scan_add");
+  const unsigned tiles = ceil_div(cap, SCAN_TILE);
+  if (tiles == 1) {
+    k_scan_tiles<T><<<1, SCAN_THREADS, 0, c.stream>>>(in, out, nullptr, cap, n_dev);
+    PJ_LAUNCHED("k_scan_tiles");
+  } else {
+    DBuf<T> sums(c, tiles), sums_off(c, tiles);
+    k_scan_tiles<T><<<tiles, SCAN_THREADS, 0, c.stream>>>(in, out, sums.p, cap, n_dev);
+    PJ_LAUNCHED("k_scan_tiles");
+    exclusive_scan_dn<T>(c, sums.p, sums_off.p, tiles, nullptr, nullptr);
+    // a device count launches a capacity-sized grid: keep it to one wave of
+    // grid-stride blocks
+    const unsigned grid = n_dev ? std::min<unsigned>(ceil_div(cap, 256), 152u * 8) : ceil_div(cap, 256);
+    k_scan_add<T><<<grid, 256, 0, c.stream>>>(out, sums_off.p, cap, n_dev);
+    PJ_LAUNCHED("k_scan_add");
+  }
+  if (total) {
+    k_scan_total<T><<<1, 1, 0, c.stream>>>(in, out, cap, n_dev, total);
+    PJ_LAUNCHED("k_scan_total");
+  }
+}
+
+template <class T>
+void exclusive_scan(const Ctx& c, const T* in, T* out, size_t n) {
+  if (n == 0) return;
+  exclusive_scan_dn<T>(c, in, out, n, nullptr, nullptr);
+}
+
+template <class K>
+bool radix_sort_pairs_dn(const Ctx& c, K* keys, uint32_t* vals, K* keys2, uint32_t* vals2, size_t cap,
+                         const unsigned long long* n_dev, int nbits) {
+  if (cap == 0 || nbits <= 0) return false;
+  if (cap > 0xFFFFFFFFull) fail(PJ_EINVAL, "radix sort: more than 2^32 items");
+  const unsigned ntiles = ceil_div(cap, RS_TILE);
+  DBuf<uint32_t> hist(c, (size_t)256 * ntiles), offs(c, (size_t)256 * ntiles);
+  K* ka = keys;
+  uint32_t* va = vals;
+  K* kb = keys2;
+  uint32_t* vb = vals2;
+  const int passes = (nbits + 7) / 8;
+  for (int p = 0; p < passes; ++p) {
+    const int shift = 8 * p;
+    k_rs_hist<K><<<ntiles, RS_THREADS, 0, c.stream>>>(ka, cap, shift, hist.p, ntiles, n_dev);
+    PJ_LAUNCHED("k_rs_hist");
+    exclusive_scan<uint32_t>(c, hist.p, offs.p, (size_t)256 * ntiles);
+    k_rs_scatter<K><<<ntiles, RS_THREADS, 0, c.stream>>>(ka, va, kb, vb, cap, shift, offs.p, ntiles, n_dev);
+    PJ_LAUNCHED("k_rs_scatter");
+    K* tk = ka; ka = kb; kb = tk;
+    uint32_t* tv = va; va = vb; vb = tv;
+  }
+  return ka != keys;
 }
 
 template <class K>
 void radix_sort_pairs(const Ctx& c, K* keys, uint32_t* vals, size_t n, int nbits) {
   if (n <= 1 || nbits <= 0) return;
   if (n > 0xFFFFFFFFull) fail(PJ_EINVAL, "radix sort: more than 2^32 items");
-  const unsigned ntiles = ceil_div(n, RS_TILE);
   DBuf<K> k2(c, n);
   DBuf<uint32_t> v2(c, n);
-  DBuf<uint32_t> hist(c, (size_t)256 * ntiles), offs(c, (size_t)256 * ntiles);
-  K* ka = keys;
-  uint32_t* va = vals;
-  K* kb = k2.p;
-  uint32_t* vb = v2.p;
-  const int passes = (nbits + 7) / 8;
-  for (int p = 0; p < passes; ++p) {
-    const int shift = 8 * p;
-    k_rs_hist<K><<<ntiles, RS_THREADS, 0, c.stream>>>(ka, n, shift, hist.p, ntiles);
-    PJ_LAUNCHED("k_rs_hist");
-    exclusive_scan<uint32_t>(c, hist.p, offs.p, (size_t)256 * ntiles);
-    k_rs_scatter<K><<<ntiles, RS_THREADS, 0, c.stream>>>(ka, va, kb, vb, n, shift, offs.p, ntiles);
-    PJ_LAUNCHED("k_rs_scatter");
-    K* tk = ka; ka = kb; kb = tk;
-    uint32_t* tv = va; va = vb; vb = tv;
-  }
-  if (ka != keys) {
-    PJ_CUDA(cudaMemcpyAsync(keys, ka, n * sizeof(K), cudaMemcpyDeviceToDevice, c.stream));
-    PJ_CUDA(cudaMemcpyAsync(vals, va, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, c.stream));
+  if (radix_sort_pairs_dn<K>(c, keys, vals, k2.p, v2.p, n, nullptr, nbits)) {
+    PJ_CUDA(cudaMemcpyAsync(keys, k2.p, n * sizeof(K), cudaMemcpyDeviceToDevice, c.stream));
+    PJ_CUDA(cudaMemcpyAsync(vals, v2.p, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, c.stream));
   }
 }
 
@@ -197,6 +259,12 @@ void widen_u32(const Ctx& c, const uint32_t* in, uint64_t* out, size_t n) {
   PJ_LAUNCHED("k_widen");
 }
 
+template void exclusive_scan_dn<uint32_t>(const Ctx&, const uint32_t*, uint32_t*, size_t,
+                                          const unsigned long long*, unsigned long long*);
+template void exclusive_scan_dn<unsigned long long>(const Ctx&, const unsigned long long*, unsigned long long*, size_t,
+                                                    const unsigned long long*, unsigned long long*);
+template bool radix_sort_pairs_dn<unsigned long long>(const Ctx&, unsigned long long*, uint32_t*, unsigned long long*,
+                                                      uint32_t*, size_t, const unsigned long long*, int);
 template void exclusive_scan<uint32_t>(const Ctx&, const uint32_t*, uint32_t*, size_t);
 template void exclusive_scan<uint64_t>(const Ctx&, const uint64_t*, uint64_t*, size_t);
 template void exclusive_scan<unsigned long long>(const Ctx&, const unsigned long long*, unsigned long long*, size_t);

@@ -5,7 +5,8 @@
 // a slot is free it takes every pending request it can admit -- bounded by a
 // query count, a byte count and the device memory currently free -- and runs
 // them as ONE multi-threshold batch (query_multi_impl: one probe pass and
-// one verification pass for all of them).  Requests that arrive while other
+// one verification pass for all of them; with use_plans, one replay of the
+// slot's query plan, a CUDA graph of the same pipeline).  Requests that arrive while other
 // batches run are admitted by the next free slot, so several batches overlap
 // on the device.  Results are split back per request; each request's pairs
 // are exactly what pj_query returns for it alone.
@@ -56,13 +57,15 @@ struct pj_server {
   uint64_t next_ticket = 1;
   uint64_t n_batches = 0, n_requests = 0, n_queries = 0, max_batch_requests = 0;
   uint32_t in_flight = 0, max_in_flight = 0;
+  std::vector<pj_plan*> plans;  // one per slot (use_plans)
 };
 
 namespace pj {
 namespace {
 
 // Runs one batch of requests on the slot's stream; on PJ_ENOMEM splits it.
-void run_batch(pj_server& S, const Ctx& c, std::vector<std::shared_ptr<Request>>& batch, size_t lo, size_t hi) {
+void run_batch(pj_server& S, const Ctx& c, pj_plan* plan, std::vector<std::shared_ptr<Request>>& batch, size_t lo,
+               size_t hi) {
   // concatenate the requests' strings and thresholds
   std::vector<uint64_t> off(1, 0);
   std::vector<uint8_t> bytes, taus;
@@ -87,9 +90,14 @@ void run_batch(pj_server& S, const Ctx& c, std::vector<std::shared_ptr<Request>>
   int code = PJ_OK;
   std::string msg;
   try {
-    ProbeSet P;
-    upload_probe_set(c, in, P);
-    query_multi_impl(c, *S.idx, P, taus.data(), &res, false);
+    if (plan && in.n <= S.opt.max_batch_queries && bytes.size() <= S.opt.max_batch_bytes) {
+      code = pj_plan_query(plan, &in, taus.data(), &res);
+      if (code != PJ_OK) msg = pj_last_error();
+    } else {  // no plan, or one request larger than the plan's limits
+      ProbeSet P;
+      upload_probe_set(c, in, P);
+      query_multi_impl(c, *S.idx, P, taus.data(), &res, false);
+    }
   } catch (const Error& e) {
     code = e.code;
     msg = e.msg;
@@ -100,8 +108,8 @@ void run_batch(pj_server& S, const Ctx& c, std::vector<std::shared_ptr<Request>>
   if (code == PJ_ENOMEM && hi - lo > 1) {  // admission by memory: halve and retry
     pj_result_free(&res);
     const size_t mid = lo + (hi - lo) / 2;
-    run_batch(S, c, batch, lo, mid);
-    run_batch(S, c, batch, mid, hi);
+    run_batch(S, c, plan, batch, lo, mid);
+    run_batch(S, c, plan, batch, mid, hi);
     return;
   }
   // split the pairs (sorted by query position) back per request
@@ -137,8 +145,9 @@ void run_batch(pj_server& S, const Ctx& c, std::vector<std::shared_ptr<Request>>
   S.cv_done.notify_all();
 }
 
-void slot_main(pj_server* Sp) {
+void slot_main(pj_server* Sp, int slot) {
   pj_server& S = *Sp;
+  pj_plan* plan = S.plans.empty() ? nullptr : S.plans[slot];
   cudaSetDevice(S.idx->device);
   cudaStream_t stream = nullptr;
   if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess) stream = nullptr;
@@ -174,7 +183,7 @@ void slot_main(pj_server* Sp) {
       S.in_flight++;
       S.max_in_flight = std::max(S.max_in_flight, S.in_flight);
     }
-    run_batch(S, c, batch, 0, batch.size());
+    run_batch(S, c, plan, batch, 0, batch.size());
     std::lock_guard<std::mutex> g(S.mu);
     S.in_flight--;
   }
@@ -214,11 +223,25 @@ int pj_server_start(pj_index* idx, const pj_server_options* opt, pj_server** out
       for (int t = 0; t < (int)idx->parts.size(); ++t) pj::ensure_partition(*idx, t, nullptr);
       idx->ctx.sync();
     }
-    for (int k = 0; k < S->opt.slots; ++k) S->slots.emplace_back(pj::slot_main, S);
+    if (S->opt.use_plans) {
+      pj_plan_options po;
+      pj_plan_options_init(&po);
+      po.max_queries = S->opt.max_batch_queries;
+      po.max_bytes = S->opt.max_batch_bytes;
+      for (int k = 0; k < S->opt.slots; ++k) {
+        pj_plan* p = nullptr;
+        const int code = pj_plan_create(idx, &po, &p);
+        if (code != PJ_OK) pj::fail(code, std::string("pj_server_start: ") + pj_last_error());
+        S->plans.push_back(p);
+      }
+    }
+    for (int k = 0; k < S->opt.slots; ++k) S->slots.emplace_back(pj::slot_main, S, k);
     *out = S;
     return PJ_OK;
   } catch (const pj::Error& e) {
     pj::set_last_error(e.msg);
+    if (S)
+      for (pj_plan* p : S->plans) pj_plan_free(p);
     delete S;
     return e.code;
   }
@@ -340,6 +363,7 @@ void pj_server_stop(pj_server* S) {
   }
   S->cv_work.notify_all();
   for (auto& t : S->slots) t.join();
+  for (pj_plan* p : S->plans) pj_plan_free(p);
   {
     std::lock_guard<std::mutex> g(S->mu);
     for (auto& kv : S->all)

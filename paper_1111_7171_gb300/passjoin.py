@@ -67,7 +67,19 @@ class pj_options(ctypes.Structure):
 
 class pj_server_options(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int), ("max_batch_queries", ctypes.c_uint32), ("max_batch_bytes", ctypes.c_uint64),
-                ("bytes_per_query", ctypes.c_uint64), ("device_reserve", ctypes.c_uint64)]
+                ("bytes_per_query", ctypes.c_uint64), ("device_reserve", ctypes.c_uint64), ("use_plans", ctypes.c_int)]
+
+
+class pj_plan_options(ctypes.Structure):
+    _fields_ = [("max_queries", ctypes.c_uint32), ("max_bytes", ctypes.c_uint64), ("hits_capacity", ctypes.c_uint64),
+                ("accepted_capacity", ctypes.c_uint64), ("pairs_capacity", ctypes.c_uint64)]
+
+
+class pj_plan_info(ctypes.Structure):
+    _fields_ = [("runs", ctypes.c_uint64), ("recaptures", ctypes.c_uint64), ("graph_nodes", ctypes.c_uint32),
+                ("graph_kernels", ctypes.c_uint32), ("hits_capacity", ctypes.c_uint64),
+                ("accepted_capacity", ctypes.c_uint64), ("pairs_capacity", ctypes.c_uint64),
+                ("device_bytes", ctypes.c_uint64), ("host_bytes", ctypes.c_uint64)]
 
 
 class pj_request_times(ctypes.Structure):
@@ -134,6 +146,16 @@ def library():
             L.pj_query_noalloc.argtypes = [ctypes.c_void_p, P(pj_strings), ctypes.c_int, ctypes.c_void_p,
                                            ctypes.c_uint64, P(ctypes.c_uint64)]
             L.pj_query_noalloc.restype = ctypes.c_int
+            L.pj_plan_options_init.argtypes = [P(pj_plan_options)]
+            L.pj_plan_options_init.restype = None
+            L.pj_plan_create.argtypes = [ctypes.c_void_p, P(pj_plan_options), P(ctypes.c_void_p)]
+            L.pj_plan_create.restype = ctypes.c_int
+            L.pj_plan_query.argtypes = [ctypes.c_void_p, P(pj_strings), ctypes.c_void_p, P(pj_result)]
+            L.pj_plan_query.restype = ctypes.c_int
+            L.pj_plan_get_info.argtypes = [ctypes.c_void_p, P(pj_plan_info)]
+            L.pj_plan_get_info.restype = ctypes.c_int
+            L.pj_plan_free.argtypes = [ctypes.c_void_p]
+            L.pj_plan_free.restype = None
             L.pj_index_build_ms.argtypes = [ctypes.c_void_p]
             L.pj_index_build_ms.restype = ctypes.c_float
             L.pj_kernel_launches.argtypes = []
@@ -432,17 +454,73 @@ def pj_query_multi(index: Index, batch, taus):
     return _take(res)
 
 
+class Plan:
+    """pj_plan_*: the multi-threshold query pipeline recorded into a CUDA
+    graph, replayed once per batch of host strings."""
+
+    def __init__(self, index: Index, max_queries: int = 4096, max_bytes: int = 1 << 20, hits_capacity: int = 0,
+                 accepted_capacity: int = 0, pairs_capacity: int = 0):
+        _torch()
+        L = library()
+        o = pj_plan_options()
+        L.pj_plan_options_init(ctypes.byref(o))
+        o.max_queries, o.max_bytes = max_queries, max_bytes
+        o.hits_capacity, o.accepted_capacity, o.pairs_capacity = hits_capacity, accepted_capacity, pairs_capacity
+        h = ctypes.c_void_p()
+        _check(L.pj_plan_create(index.handle, ctypes.byref(o), ctypes.byref(h)), "pj_plan_create")
+        self._h = h
+        self._index = index
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise RuntimeError("plan already freed")
+        return self._h
+
+    def query(self, batch, taus):
+        """pj_plan_query: host batch, query q at threshold taus[q] (an int
+        applies to every query)."""
+        b = Strings(batch)
+        if np.isscalar(taus):
+            taus = np.full(b.n, int(taus), dtype=np.uint8)
+        t = np.ascontiguousarray(np.asarray(taus, dtype=np.uint8))
+        if len(t) != b.n:
+            raise ValueError("one threshold per query")
+        res = pj_result()
+        _check(library().pj_plan_query(self.handle, ctypes.byref(b.c), ctypes.c_void_p(t.ctypes.data if len(t) else 0),
+                                       ctypes.byref(res)), "pj_plan_query")
+        return _take(res)
+
+    def info(self) -> dict:
+        i = pj_plan_info()
+        _check(library().pj_plan_get_info(self.handle, ctypes.byref(i)), "pj_plan_get_info")
+        return {f: int(getattr(i, f)) for f, _ in pj_plan_info._fields_}
+
+    def free(self):
+        if self._h:
+            library().pj_plan_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
 class Server:
     """pj_server_*: continuous-batching query server over a resident index."""
 
     def __init__(self, index: Index, slots: int = 3, max_batch_queries: int = 1 << 16,
-                 max_batch_bytes: int = 16 << 20, bytes_per_query: int = 64 << 10, device_reserve: int = 2 << 30):
+                 max_batch_bytes: int = 16 << 20, bytes_per_query: int = 64 << 10, device_reserve: int = 2 << 30,
+                 use_plans: bool = False):
         _torch()
         L = library()
         o = pj_server_options()
         L.pj_server_options_init(ctypes.byref(o))
         o.slots, o.max_batch_queries, o.max_batch_bytes = slots, max_batch_queries, max_batch_bytes
         o.bytes_per_query, o.device_reserve = bytes_per_query, device_reserve
+        o.use_plans = 1 if use_plans else 0
         h = ctypes.c_void_p()
         _check(L.pj_server_start(index.handle, ctypes.byref(o), ctypes.byref(h)), "pj_server_start")
         self._h = h

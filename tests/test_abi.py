@@ -95,6 +95,52 @@ int main(void) {
     assert sizes[8] == pj.pj_result.priv.offset
 
 
+def test_every_struct_field_matches_header(tmp_path):
+    """Every field offset and size of every ctypes mirror equals the C compiler's."""
+    import subprocess
+    from paper_1111_7171_gb300 import passjoin as pj
+    structs = [pj.pj_strings, pj.pj_stats, pj.pj_result, pj.pj_options, pj.pj_server_options,
+               pj.pj_request_times, pj.pj_server_counters, pj.pj_plan_options, pj.pj_plan_info]
+    lines = []
+    for st in structs:
+        name = st.__name__
+        lines.append(f'  printf("{name} sizeof %zu\\n", sizeof({name}));')
+        for f, _ in st._fields_:
+            lines.append(f'  printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    src = tmp_path / "fields.c"
+    src.write_text("#include <stdio.h>\n#include <stddef.h>\n#include \"passjoin.h\"\nint main(void) {\n" +
+                   "\n".join(lines) + "\n  return 0;\n}\n")
+    exe = tmp_path / "fields"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines()
+    want = {}
+    for line in out:
+        name, field, value = line.split()
+        want[(name, field)] = int(value)
+    for st in structs:
+        assert want[(st.__name__, "sizeof")] == ctypes.sizeof(st), st.__name__
+        for f, _ in st._fields_:
+            assert want[(st.__name__, f)] == getattr(st, f).offset, (st.__name__, f)
+
+
+def test_plan_entry_points_reject_null_without_device_work(lib):
+    from paper_1111_7171_gb300 import passjoin as pj
+    L = pj.library()
+    o = pj.pj_plan_options()
+    L.pj_plan_options_init(ctypes.byref(o))
+    assert o.max_queries == 4096 and o.max_bytes == 1 << 20 and o.hits_capacity == 0
+    h = ctypes.c_void_p()
+    assert L.pj_plan_create(None, ctypes.byref(o), ctypes.byref(h)) == pj.PJ_EINVAL
+    assert not h.value
+    assert L.pj_plan_query(None, None, None, ctypes.byref(pj.pj_result())) == pj.PJ_EINVAL
+    assert L.pj_plan_get_info(None, ctypes.byref(pj.pj_plan_info())) == pj.PJ_EINVAL
+    L.pj_plan_free(None)
+    so = pj.pj_server_options()
+    so.use_plans = 5
+    L.pj_server_options_init(ctypes.byref(so))
+    assert so.use_plans == 0 and so.slots == 3
+
+
 def test_binding_marshals_string_sets():
     from paper_1111_7171_gb300 import passjoin as pj
     s = pj.Strings([b"abc", b"", b"de"])
