@@ -28,9 +28,30 @@ struct __align__(16) Slot {
   uint32_t count;          // run length
 };
 
+// Reciprocal of the segment count for even_segment_m: m = ceil(2^32 / parts).
+__host__ __device__ __forceinline__ unsigned long long seg_magic(int parts) {
+  return parts < 1 ? 0ull : ((1ull << 32) + (unsigned long long)parts - 1ull) / (unsigned long long)parts;
+}
+
 // Even partition (Sec. 3.1) of a length-l string into tau+1 segments: the
 // first tau+1-k have floor(l/(tau+1)) characters, the last k one more, with
 // k = l - floor(l/(tau+1))*(tau+1).  Segment i is 1-based; P = 0-based start.
+//
+// floor(l / parts) is one multiply by m = seg_magic(parts) (0: computed
+// here): m exceeds 2^32 / parts by less than 1, so l * m / 2^32 exceeds
+// l / parts by less than l / 2^32 < 2^-16 for l < 2^16, while the
+// fractional part of l / parts is at most 1 - 1/parts <= 1 - 2^-6; the
+// floor is exact for every string length (< 2^16) and tau <= 32.
+__host__ __device__ __forceinline__ void even_segment_m(int l, int parts, unsigned long long m, int i, int& P,
+                                                        int& li) {
+  if (m == 0) m = seg_magic(parts);
+  const int base = (int)(((unsigned long long)(unsigned)l * m) >> 32);
+  const int k = l - base * parts;
+  const int first_long = parts - k + 1;  // segments i >= first_long are longer
+  li = base + (i >= first_long ? 1 : 0);
+  P = (i - 1) * base + (i > first_long ? i - first_long : 0);
+}
+
 __host__ __device__ __forceinline__ void even_segment(int l, int tau, int i, int& P, int& li) {
   const int parts = tau + 1;
   const int base = l / parts;

@@ -171,14 +171,15 @@ __global__ void k_hit_counts(const Hit* __restrict__ hits, unsigned long long n,
 
 // ---------------------------------------------------------------- A6 ------
 
-constexpr int V_RUN = 4;  // candidates per lane per step
+constexpr int V_RUN = 8;  // candidates per lane per step
 
 // Lane l of a warp verifies candidates base + l + 32 k (k < V_RUN): the 32
 // lanes take consecutive candidates, which mostly belong to one posting run
 // and so share the probing string, the segment, the position and the
 // indexed length -- the verification loops then have equal trip counts up to
 // early termination.  Each lane finds its first hit by binary search over the
-// candidate offsets and walks forward from there; lanes never communicate.
+// candidate offsets and walks forward from there, reloading the hit only when
+// it crosses into the next one; lanes never communicate.
 template <int MAXW, bool SELF, bool MULTI>
 __global__ void __launch_bounds__(512) k_verify_hits(const ProbeView v, const Hit* __restrict__ hits,
                                                        const unsigned long long* __restrict__ cand_off,
@@ -204,13 +205,25 @@ __global__ void __launch_bounds__(512) k_verify_hits(const ProbeView v, const Hi
       if (cand_off[mid] <= c) lo = mid; else hi = mid;
     }
     unsigned long long h = lo;
+    unsigned long long c_lo = cand_off[h];
+    unsigned long long c_hi = h + 1 < n_hits ? cand_off[h + 1] : n_cand;
+    Hit hit = hits[h];
+    ProbeView vt = MULTI ? view_for_tau(v, (int)(hit.pi >> 24)) : v;
+    HitCtx hc = hit_ctx(vt, hit);
     for (int k = 0; k < V_RUN && c < n_cand; ++k, c += 32) {
-      while (h + 1 < n_hits && cand_off[h + 1] <= c) ++h;
-      const Hit hit = hits[h];
+      if (c >= c_hi) {  // into a later hit
+        do {
+          ++h;
+          c_lo = c_hi;
+          c_hi = h + 1 < n_hits ? cand_off[h + 1] : n_cand;
+        } while (c >= c_hi);
+        hit = hits[h];
+        if (MULTI) vt = view_for_tau(v, (int)(hit.pi >> 24));
+        hc = hit_ctx(vt, hit);
+      }
       unsigned long long key = 0;
       int ed = 0;
-      const ProbeView vt = MULTI ? view_for_tau(v, (int)(hit.pi >> 24)) : v;
-      if (verify_candidate<MAXW>(vt, SELF, hit, (uint32_t)(c - cand_off[h]), key, ed, cells, err)) {
+      if (verify_in_hit<MAXW>(vt, SELF, hc, (uint32_t)(c - c_lo), key, ed, cells, err)) {
         const unsigned long long pos = atomicAdd(&ctr->accepted, 1ull);
         if (pos < out.cap) {
           out.key[pos] = key;
@@ -862,6 +875,7 @@ static TuneResult self_join_tuning(pj_index& idx, const ProbeView& v, float* tun
 
 static ProbeView index_side(const pj_index& idx, const Partition& part) {
   ProbeView v{};
+  v.seg_magic = seg_magic(part.tau + 1);
   v.warp_q_cut = UINT32_MAX;
   v.block_thread = 256;
   v.block_warp = 256;
@@ -952,7 +966,7 @@ void query_multi_impl(const Ctx& c, pj_index& idx, const ProbeSet& R, const uint
     PartView pv{};
     if (present[t]) {
       const Partition& part = idx.parts[t];
-      pv = PartView{part.table.p, part.table.n - 1, part.postings.p, part.n_records, part.first, t};
+      pv = PartView{part.table.p, part.table.n - 1, part.postings.p, part.n_records, part.first, t, seg_magic(t + 1)};
       has_short |= part.first > 0;
     }
     hp[t] = pv;

@@ -228,6 +228,7 @@ void query_noalloc(pj_index& idx, const pj_strings& batch, int tau, pj_pair* out
   v.postings = part.postings.p;
   v.n_postings = part.n_records;
   v.tau = tau;
+  v.seg_magic = seg_magic(tau + 1);
   v.pbytes = R.bytes;
   v.poff = R.off;
   v.plen = R.len.p;

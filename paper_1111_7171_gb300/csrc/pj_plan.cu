@@ -259,7 +259,7 @@ uint64_t grown(uint64_t cap, uint64_t need, uint64_t limit, const char* what) {
   if (need > limit)
     fail(PJ_ENOMEM, std::string("query plan: the batch needs ") + std::to_string(need) + " " + what +
                         ", more than a plan can hold (" + std::to_string(limit) + "); split the batch");
-  return std::min<uint64_t>(limit, std::max<uint64_t>(2 * cap, need + need / 4));
+  return std::min<uint64_t>(limit, 2 * std::max<uint64_t>(cap, need));
 }
 
 void create(pj_plan& P, pj_index& idx, const pj_plan_options& o) {
@@ -284,11 +284,15 @@ void create(pj_plan& P, pj_index& idx, const pj_plan_options& o) {
   PlanDev& d = P.d;
   d.cap_q = o.max_queries;
   d.cap_groups = cap_groups;
-  d.cap_hits = o.hits_capacity ? o.hits_capacity : std::max<uint64_t>(1u << 16, cap_groups);
+  // defaults: about two hits per group and 128 accepted matches per query
+  // (the short-string workload at tau = 4 averages 1.7 and 217 at full
+  // self-join scale); capacities grow when a batch needs more
+  d.cap_hits = o.hits_capacity ? o.hits_capacity : std::max<uint64_t>(1u << 16, 2 * cap_groups);
   d.cap_hits = std::min<uint64_t>(d.cap_hits, cap_groups * (uint64_t)(tau_max + 1));
-  d.cap_acc = o.accepted_capacity ? o.accepted_capacity : std::max<uint64_t>(1u << 16, 16ull * o.max_queries);
+  d.cap_acc = o.accepted_capacity ? o.accepted_capacity
+                                  : std::min<uint64_t>(1ull << 27, std::max<uint64_t>(1u << 16, 128ull * o.max_queries));
   d.cap_acc = std::min(d.cap_acc, MAX_CAP_ACC);
-  d.cap_pairs = o.pairs_capacity ? o.pairs_capacity : d.cap_acc;
+  d.cap_pairs = o.pairs_capacity ? o.pairs_capacity : std::max<uint64_t>(1u << 16, d.cap_acc / 2);
   d.cap_pairs = std::min(d.cap_pairs, MAX_CAP_ACC);
 
   P.bytes.reset(P.ctx, o.max_bytes + 16);
@@ -314,7 +318,7 @@ void create(pj_plan& P, pj_index& idx, const pj_plan_options& o) {
   std::vector<PartView> hp((size_t)tau_max + 1);
   for (int t = 0; t <= tau_max; ++t) {
     const Partition& part = idx.parts[t];
-    hp[t] = PartView{part.table.p, part.table.n - 1, part.postings.p, part.n_records, part.first, t};
+    hp[t] = PartView{part.table.p, part.table.n - 1, part.postings.p, part.n_records, part.first, t, seg_magic(t + 1)};
   }
   P.parts.reset(P.ctx, hp.size());
   PJ_CUDA(cudaMemcpyAsync(P.parts.p, hp.data(), hp.size() * sizeof(PartView), cudaMemcpyHostToDevice, P.stream));

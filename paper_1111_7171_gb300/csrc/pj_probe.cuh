@@ -31,6 +31,7 @@ struct PartView {
   unsigned long long n_postings;
   uint32_t first;  // first sid of length >= tau + 1
   int tau;
+  unsigned long long seg_magic;  // seg_magic(tau + 1)
 };
 
 struct ProbeView {
@@ -53,6 +54,7 @@ struct ProbeView {
   const uint32_t* postings;
   unsigned long long n_postings;
   int tau;
+  unsigned long long seg_magic;  // seg_magic(tau + 1): even partitions without a division
   int key_shift;  // pair key = a << key_shift | b
   // multi-threshold batches (R != S only): probe q has threshold ptau[q],
   // its groups are qgoff[q] .. qgoff[q+1]-1, parts[tau] is tau's index
@@ -75,6 +77,7 @@ __host__ __device__ __forceinline__ ProbeView view_for_tau(const ProbeView& v, i
   t.postings = pv.postings;
   t.n_postings = pv.n_postings;
   t.tau = tau;
+  t.seg_magic = pv.seg_magic;
   return t;
 }
 
@@ -101,7 +104,7 @@ __host__ __device__ __forceinline__ bool group_window(const ProbeView& v, bool s
   uint32_t b1 = v.ibbeg[l + 1];
   if (self && l == ls && b1 > q) b1 = q;  // only strings visited before q
   if (b1 <= b0) return false;
-  even_segment(l, tau, i, P, li);
+  even_segment_m(l, parts, v.seg_magic, i, P, li);
   const int D = ls - l;
   lo = max(0, max(P - (i - 1), P + D - (parts - i)));
   hi = min(ls - li, min(P + (i - 1), P + D + (parts - i)));
@@ -156,29 +159,45 @@ __host__ __device__ __forceinline__ uint32_t lookup(const ProbeView& v, bool sel
   return cnt;
 }
 
-// Verify candidate `off` of hit h.  Returns true with the pair key and
-// ed = d_l + d_r when extension verification accepts it.
+// What the verification of a candidate needs from its hit: the probing
+// string, the matched position p and the segment number i.
+struct HitCtx {
+  uint32_t q, begin;
+  int p, i, ls;
+  const uint8_t* s;
+};
+
+__host__ __device__ __forceinline__ HitCtx hit_ctx(const ProbeView& v, const Hit& h) {
+  HitCtx c;
+  c.q = h.q;
+  c.begin = h.begin;
+  c.p = (int)(h.pi & 0xFFFFu);
+  c.i = (int)((h.pi >> 16) & 0xFFu);
+  c.ls = (int)v.plen[h.q];
+  c.s = v.pbytes + v.poff[h.q];
+  return c;
+}
+
+// Verify candidate `off` of the hit described by hc.  Returns true with the
+// pair key and ed = d_l + d_r when extension verification accepts it.
 template <int MAXW>
-__host__ __device__ __forceinline__ bool verify_candidate(const ProbeView& v, bool self, const Hit& h, uint32_t off,
-                                                          unsigned long long& key, int& ed,
-                                                          unsigned long long& cells, int& err) {
+__host__ __device__ __forceinline__ bool verify_in_hit(const ProbeView& v, bool self, const HitCtx& hc, uint32_t off,
+                                                       unsigned long long& key, int& ed, unsigned long long& cells,
+                                                       int& err) {
   // Single exit: see vsp().
   bool ok = false;
-  const uint32_t r = v.postings[h.begin + off];
-  const uint32_t q = h.q;
-  const int p = (int)(h.pi & 0xFFFFu);
-  const int i = (int)((h.pi >> 16) & 0xFFu);
+  const uint32_t r = v.postings[hc.begin + off];
+  const int i = hc.i;
   if (r >= v.n_index) {
     err |= 1;
-  } else if (!(self && r == q)) {  // a colliding run may hold the probe itself
-    const int ls = (int)v.plen[q];
+  } else if (!(self && r == hc.q)) {  // a colliding run may hold the probe itself
     const int lr = (int)v.ilen[r];
     if (i >= 1 && i <= v.tau + 1 && lr >= v.tau + 1) {  // r is a partitioned string
       int P, li;
-      even_segment(lr, v.tau, i, P, li);
-      if (p + li <= ls &&
-          verify_ext<MAXW>(v.pbytes + v.poff[q], ls, v.ibytes + v.ioff[r], lr, i, p, li, P, v.tau, ed, cells)) {
-        const uint32_t qid = v.pid ? v.pid[q] : q;
+      even_segment_m(lr, v.tau + 1, v.seg_magic, i, P, li);
+      if (hc.p + li <= hc.ls &&
+          verify_ext<MAXW>(hc.s, hc.ls, v.ibytes + v.ioff[r], lr, i, hc.p, li, P, v.tau, ed, cells)) {
+        const uint32_t qid = v.pid ? v.pid[hc.q] : hc.q;
         const uint32_t rid = v.iperm[r];
         const uint32_t ka = self ? min(qid, rid) : qid;
         const uint32_t kb = self ? max(qid, rid) : rid;
@@ -188,6 +207,14 @@ __host__ __device__ __forceinline__ bool verify_candidate(const ProbeView& v, bo
     }
   }
   return ok;
+}
+
+// Verify candidate `off` of hit h (see verify_in_hit).
+template <int MAXW>
+__host__ __device__ __forceinline__ bool verify_candidate(const ProbeView& v, bool self, const Hit& h, uint32_t off,
+                                                          unsigned long long& key, int& ed,
+                                                          unsigned long long& cells, int& err) {
+  return verify_in_hit<MAXW>(v, self, hit_ctx(v, h), off, key, ed, cells, err);
 }
 
 #ifdef __CUDACC__
@@ -208,7 +235,7 @@ __device__ __forceinline__ bool verify_candidate_warp(const ProbeView& v, bool s
     const int lr = (int)v.ilen[r];
     if (i >= 1 && i <= v.tau + 1 && lr >= v.tau + 1) {
       int P, li;
-      even_segment(lr, v.tau, i, P, li);
+      even_segment_m(lr, v.tau + 1, v.seg_magic, i, P, li);
       if (p + li <= ls &&
           verify_ext_warp(v.pbytes + v.poff[q], ls, v.ibytes + v.ioff[r], lr, i, p, li, P, v.tau, ed, cells)) {
         const uint32_t qid = v.pid ? v.pid[q] : q;

@@ -56,6 +56,7 @@ __host__ __device__ __forceinline__ int vsp_band(const uint8_t* a, int na, const
     B[k] = (jb >= 0 && jb < nb) ? b[jb] : (uint8_t)0;
   }
   bool alive = true;
+  int rows = 0;
   for (int i = 1; i <= na; ++i) {
     const uint8_t ca = a[i - 1];
     int left = cap;
@@ -69,7 +70,7 @@ __host__ __device__ __forceinline__ int vsp_band(const uint8_t* a, int na, const
       left = val;
       emin = min(emin, val + eoff[k]);
     }
-    cells += (unsigned long long)w;
+    ++rows;
     if (emin > t) {  // Lemma 4: every expected edit distance of the row exceeds t
       alive = false;
       break;
@@ -79,6 +80,7 @@ __host__ __device__ __forceinline__ int vsp_band(const uint8_t* a, int na, const
     for (int k = 0; k + 1 < W; ++k) B[k] = B[k + 1];
     B[W - 1] = (jn >= 0 && jn < nb) ? b[jn] : (uint8_t)0;
   }
+  cells += (unsigned long long)(rows * w);
   int res = cap;
   if (alive) {
     const int kres = D - dlo;
@@ -193,6 +195,7 @@ __device__ __forceinline__ int vsp_warp(const uint8_t* x, int nx, const uint8_t*
 }
 
 // extension-based verification with the warp-cooperative VERIFYSTRINGPAIR
+// (the side with the smaller threshold first, as in verify_ext)
 __device__ __forceinline__ bool verify_ext_warp(const uint8_t* s, int ls, const uint8_t* r, int lr, int i, int p,
                                                 int li, int P, int tau, int& ed, unsigned long long& cells) {
   bool same = true;
@@ -205,11 +208,15 @@ __device__ __forceinline__ bool verify_ext_warp(const uint8_t* s, int ls, const 
   bool ok = false;
   if (same) {
     const int tl = i - 1, tr = tau + 1 - i;
-    const int dl = vsp_warp(s, p, r, P, tl, cells);
-    if (dl <= tl) {
-      const int dr = vsp_warp(s + p + li, ls - p - li, r + P + li, lr - P - li, tr, cells);
-      if (dr <= tr) {
-        ed = dl + dr;
+    const bool rf = tr < tl;
+    const int t1 = rf ? tr : tl, t2 = rf ? tl : tr;
+    const int d1 = rf ? vsp_warp(s + p + li, ls - p - li, r + P + li, lr - P - li, t1, cells)
+                      : vsp_warp(s, p, r, P, t1, cells);
+    if (d1 <= t1) {
+      const int d2 = rf ? vsp_warp(s, p, r, P, t2, cells)
+                        : vsp_warp(s + p + li, ls - p - li, r + P + li, lr - P - li, t2, cells);
+      if (d2 <= t2) {
+        ed = d1 + d2;
         ok = true;
       }
     }
@@ -221,6 +228,9 @@ __device__ __forceinline__ bool verify_ext_warp(const uint8_t* s, int ls, const 
 // Extension-based verification of one match (Sec. 5.2, Alg. 3).  s has the
 // selected substring at p; r is the indexed string whose segment i (start P,
 // length li) it matched.  Returns true with ed = d_l + d_r when accepted.
+// Both sides must pass (d_l <= i-1 and d_r <= tau+1-i), so they may be
+// checked in either order: the side with the smaller threshold goes first
+// (its band is narrower and it rejects more often).
 template <int MAXW>
 __host__ __device__ __forceinline__ bool verify_ext(const uint8_t* s, int ls, const uint8_t* r, int lr, int i, int p, int li,
                                                     int P, int tau, int& ed, unsigned long long& cells) {
@@ -234,11 +244,19 @@ __host__ __device__ __forceinline__ bool verify_ext(const uint8_t* s, int ls, co
   bool ok = false;
   if (same) {
     const int tl = i - 1, tr = tau + 1 - i;
-    const int dl = vsp<MAXW>(s, p, r, P, tl, cells);
-    if (dl <= tl) {
-      const int dr = vsp<MAXW>(s + p + li, ls - p - li, r + P + li, lr - P - li, tr, cells);
-      if (dr <= tr) {
-        ed = dl + dr;
+    const bool rf = tr < tl;
+    const uint8_t* x1 = rf ? s + p + li : s;
+    const uint8_t* y1 = rf ? r + P + li : r;
+    const int n1 = rf ? ls - p - li : p, m1 = rf ? lr - P - li : P;
+    const uint8_t* x2 = rf ? s : s + p + li;
+    const uint8_t* y2 = rf ? r : r + P + li;
+    const int n2 = rf ? p : ls - p - li, m2 = rf ? P : lr - P - li;
+    const int t1 = rf ? tr : tl, t2 = rf ? tl : tr;
+    const int d1 = vsp<MAXW>(x1, n1, y1, m1, t1, cells);
+    if (d1 <= t1) {
+      const int d2 = vsp<MAXW>(x2, n2, y2, m2, t2, cells);
+      if (d2 <= t2) {
+        ed = d1 + d2;
         ok = true;
       }
     }

@@ -109,3 +109,16 @@ def test_vsp_widths_match_plain_dp(tmp_path):
     bad = {tok.split("=")[1]: None for tok in out if tok.startswith("W=")}
     assert len(bad) == 5
     assert all(tok == "bad=0" for tok in out if tok.startswith("bad="))
+
+
+def test_even_partition_by_reciprocal_matches_division(tmp_path):
+    """The kernels' division-free even partition equals the rule of Sec. 3.1
+    (plain integer division) for every length < 2^16 and 1..33 segments."""
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    exe = tmp_path / "segment_check"
+    subprocess.run([nvcc, "-std=c++17", "-O2", "-I", CSRC, "-I", os.path.join(ROOT, "include"), "-o", str(exe),
+                    os.path.join(ROOT, "tests", "host_logic", "segment_check.cu")], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    assert out.strip().endswith("bad=0"), out
