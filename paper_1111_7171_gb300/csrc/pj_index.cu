@@ -15,6 +15,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "pj_internal.cuh"
 #include "pj_prims.cuh"
@@ -199,18 +200,20 @@ __global__ void k_heads(const uint32_t* __restrict__ flags, const uint32_t* __re
 }
 
 __global__ void k_table_insert(const unsigned long long* __restrict__ keys, const uint32_t* __restrict__ heads,
-                               uint64_t n_unique, Slot* __restrict__ table, unsigned long long mask,
-                               int* __restrict__ err) {
+                               uint64_t n_unique, Slot* __restrict__ table, uint8_t* __restrict__ fp,
+                               unsigned long long mask, int* __restrict__ err) {
   const uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (u >= n_unique) return;
   const uint32_t b = heads[u], e = heads[u + 1];
   const unsigned long long key = keys[b];
-  unsigned long long h = (key >> 7) & mask;
+  const uint32_t mix = key_mix(key);
+  unsigned long long h = mix & mask;
   for (unsigned long long probe = 0; probe <= mask; ++probe) {
     const unsigned long long prev = atomicCAS(&table[h].key, 0ull, key);
     if (prev == 0ull) {
       table[h].begin = b;
       table[h].count = e - b;
+      fp[h] = key_fp(key, mix);
       return;
     }
     h = (h + 1) & mask;
@@ -312,9 +315,33 @@ void build_store(pj_index& idx, const pj_strings& S) {
 
 void check_partition(const Ctx& c, const Partition& part);
 
+// Window size of group (length offset, segment i) when nothing clips it
+// (Sec. 4.2): with a = i - 1, b = tau + 1 - i and D = |s| - l the window
+// [max(P - a, P + D - b), min(P + a, P + D + b)] holds
+// min(a, D + b) + min(a, b - D) + 1 positions.
+static std::vector<uint16_t> group_order(int tau, bool self) {
+  const int parts = tau + 1, G = parts * (self ? parts : 2 * tau + 1);
+  std::vector<std::pair<int, int>> w(G);
+  for (int g = 0; g < G; ++g) {
+    const int D = tau - g / parts, i = 1 + g % parts, a = i - 1, b = parts - i;
+    w[g] = {-std::max(0, std::min(a, D + b) + std::min(a, b - D) + 1), g};
+  }
+  std::stable_sort(w.begin(), w.end());
+  std::vector<uint16_t> order(G);
+  for (int k = 0; k < G; ++k) order[k] = (uint16_t)w[k].second;
+  return order;
+}
+
 void build_partition(pj_index& idx, int tau, Partition& part) {
   const Ctx& c = idx.ctx;
   part.tau = tau;
+  for (int self = 0; self < 2; ++self) {
+    const std::vector<uint16_t> order = group_order(tau, self != 0);
+    part.gorder[self].reset(c, order.size());
+    PJ_CUDA(cudaMemcpyAsync(part.gorder[self].p, order.data(), order.size() * sizeof(uint16_t),
+                            cudaMemcpyHostToDevice, c.stream));
+    c.sync();  // order is a local
+  }
   const int lcut = tau + 1 <= idx.lmax + 1 ? tau + 1 : idx.lmax + 1;
   part.first = idx.h_bbeg[lcut];
   const uint64_t nrec = (uint64_t)(idx.n - part.first) * (uint64_t)(tau + 1);
@@ -324,7 +351,9 @@ void build_partition(pj_index& idx, int tau, Partition& part) {
   if (nrec == 0) {
     part.n_unique = 0;
     part.table.reset(c, 1);
+    part.fp.reset(c, 1);
     PJ_CUDA(cudaMemsetAsync(part.table.p, 0, sizeof(Slot), c.stream));
+    PJ_CUDA(cudaMemsetAsync(part.fp.p, 0, 1, c.stream));
     return;
   }
   DBuf<unsigned long long> keys(c, nrec);
@@ -348,14 +377,17 @@ void build_partition(pj_index& idx, int tau, Partition& part) {
   DBuf<uint32_t> heads(c, n_unique + 1);
   k_heads<<<ceil_div(nrec, 256), 256, 0, c.stream>>>(flags.p, uidx.p, nrec, heads.p);
   PJ_LAUNCHED("k_heads");
+  if (n_unique > (1ull << 31)) fail(PJ_EINVAL, "segment index: more than 2^31 distinct segments");
   uint64_t cap = 1024;
   while (cap < 2 * n_unique) cap <<= 1;
   part.table.reset(c, cap);
+  part.fp.reset(c, cap);
   PJ_CUDA(cudaMemsetAsync(part.table.p, 0, cap * sizeof(Slot), c.stream));
+  PJ_CUDA(cudaMemsetAsync(part.fp.p, 0, cap, c.stream));
   DBuf<int> err(c, 1);
   PJ_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), c.stream));
-  k_table_insert<<<ceil_div(n_unique, 256), 256, 0, c.stream>>>(keys.p, heads.p, n_unique, part.table.p, cap - 1,
-                                                                err.p);
+  k_table_insert<<<ceil_div(n_unique, 256), 256, 0, c.stream>>>(keys.p, heads.p, n_unique, part.table.p, part.fp.p,
+                                                                cap - 1, err.p);
   PJ_LAUNCHED("k_table_insert");
   int h_err = 0;
   PJ_CUDA(cudaMemcpyAsync(&h_err, err.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
@@ -375,18 +407,24 @@ void build_partition(pj_index& idx, int tau, Partition& part) {
 }
 
 // Host-side audit of one partition (environment PJ_CHECK_INDEX=1): the runs
-// tile the postings exactly, every posting is a valid sid, and the table
-// keeps at least half of its slots empty.
+// tile the postings exactly, every posting is a valid sid, every slot's
+// fingerprint matches its key (0 for empty slots), and the table keeps at
+// least half of its slots empty.
 void check_partition(const Ctx& c, const Partition& part) {
   std::vector<Slot> t(part.table.n);
+  std::vector<uint8_t> fp(part.fp.n);
   std::vector<uint32_t> post(part.n_records);
   PJ_CUDA(cudaMemcpyAsync(t.data(), part.table.p, t.size() * sizeof(Slot), cudaMemcpyDeviceToHost, c.stream));
+  PJ_CUDA(cudaMemcpyAsync(fp.data(), part.fp.p, fp.size(), cudaMemcpyDeviceToHost, c.stream));
   if (!post.empty())
     PJ_CUDA(cudaMemcpyAsync(post.data(), part.postings.p, post.size() * 4, cudaMemcpyDeviceToHost, c.stream));
   c.sync();
   uint64_t empty = 0, used = 0, covered = 0;
   std::vector<uint8_t> seen(part.n_records, 0);
-  for (const Slot& s : t) {
+  if (fp.size() != t.size()) fail(PJ_ECUDA, "index audit: fingerprint array size");
+  for (size_t h = 0; h < t.size(); ++h) {
+    const Slot& s = t[h];
+    if (fp[h] != (s.key ? key_fp(s.key, key_mix(s.key)) : 0)) fail(PJ_ECUDA, "index audit: fingerprint mismatch");
     if (s.key == 0) {
       ++empty;
       continue;
@@ -457,7 +495,8 @@ void upload_probe_set(const Ctx& c, const pj_strings& R, ProbeSet& out) {
 
 uint64_t pj_index::device_bytes() const {
   uint64_t b = sbytes.bytes() + soff.bytes() + slen.bytes() + perm.bytes() + bbeg.bytes();
-  for (const auto& p : parts) b += p.table.bytes() + p.postings.bytes();
+  for (const auto& p : parts)
+    b += p.table.bytes() + p.fp.bytes() + p.postings.bytes() + p.gorder[0].bytes() + p.gorder[1].bytes();
   return b;
 }
 

@@ -61,22 +61,74 @@ __host__ __device__ __forceinline__ void even_segment(int l, int tau, int i, int
   P = (i - 1) * base + (i > first_long ? i - first_long : 0);
 }
 
-// 64-bit key of segment number i of a length-l string with the given bytes:
-// FNV-1a over the bytes, then (l, i, len) folded in and the MurmurHash3
-// 64-bit finaliser applied.  Never 0 (0 marks an empty table slot).
-__host__ __device__ __forceinline__ unsigned long long seg_key(const uint8_t* p, int len, int l, int i) {
-  unsigned long long h = 0xcbf29ce484222325ull;
-  for (int k = 0; k < len; ++k) {
-    h ^= p[k];
-    h *= 0x100000001b3ull;
+// Segment keys: key = V << 32 | l << 8 | i for segment i of a length-l
+// string, where V is
+//   * the segment's bytes themselves (first byte lowest) when it has at most
+//     SEG_EXACT_MAX bytes -- then equal keys mean equal segments, and
+//     candidates found through such a key need no byte compare;
+//   * otherwise the polynomial hash V = sum_k x[k] * SEG_B^(n-1-k) mod 2^32,
+//     which the probe rolls from one window position to the next in O(1):
+//     V(x[p+1 .. p+1+n)) = (V(x[p .. p+n)) - x[p] * SEG_B^(n-1)) * SEG_B + x[p+n].
+// l and i are stored exactly, so only hashed segments of the same (l, i)
+// can share a key; that merges their posting runs, and every candidate of a
+// hashed key has its segment bytes compared before verification.  Keys are
+// never 0 (i >= 1), which marks an empty table slot.
+constexpr int SEG_EXACT_MAX = 4;
+constexpr uint32_t SEG_B = 0x9E3779B1u;  // odd
+
+__host__ __device__ __forceinline__ uint32_t seg_value(const uint8_t* p, int len) {
+  uint32_t v = 0;
+  if (len <= SEG_EXACT_MAX) {
+    for (int k = 0; k < len; ++k) v |= (uint32_t)p[k] << (8 * k);
+  } else {
+    for (int k = 0; k < len; ++k) v = v * SEG_B + p[k];
   }
-  h ^= ((unsigned long long)l << 40) ^ ((unsigned long long)i << 20) ^ (unsigned long long)len;
-  h ^= h >> 33;
-  h *= 0xff51afd7ed558ccdull;
-  h ^= h >> 33;
-  h *= 0xc4ceb9fe1a85ec53ull;
-  h ^= h >> 33;
-  return h ? h : 1ull;
+  return v;
+}
+
+// SEG_B^(len-1) mod 2^32 (len >= 1), by repeated squaring.
+__host__ __device__ __forceinline__ uint32_t seg_pow(int len) {
+  uint32_t r = 1, b = SEG_B;
+  for (unsigned e = (unsigned)(len - 1); e; e >>= 1) {
+    if (e & 1u) r *= b;
+    b *= b;
+  }
+  return r;
+}
+
+// The value of the window one position right: drop `out`, append `in`.
+__host__ __device__ __forceinline__ uint32_t seg_roll(uint32_t v, uint8_t out, uint8_t in, int len, uint32_t pw) {
+  if (len <= SEG_EXACT_MAX) return (len < 4 ? v & ((1u << (8 * len)) - 1u) : v) >> 8 | (uint32_t)in << (8 * (len - 1));
+  return (v - (uint32_t)out * pw) * SEG_B + in;
+}
+
+__host__ __device__ __forceinline__ unsigned long long seg_key_of(uint32_t v, int l, int i) {
+  return ((unsigned long long)v << 32) | ((uint32_t)l << 8) | (uint32_t)i;
+}
+
+// 64-bit key of segment number i of a length-l string with the given bytes.
+__host__ __device__ __forceinline__ unsigned long long seg_key(const uint8_t* p, int len, int l, int i) {
+  return seg_key_of(seg_value(p, len), l, i);
+}
+
+// Table slot hash of a key: its two halves combined and passed through the
+// 32-bit finaliser of MurmurHash3.  Tables have at most 2^32 slots.
+__host__ __device__ __forceinline__ uint32_t key_mix(unsigned long long key) {
+  uint32_t h = (uint32_t)(key >> 32) ^ ((uint32_t)key * 0x9E3779B1u);
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+
+// One-byte fingerprint of a key, kept beside each table slot (0 = empty):
+// the top byte of the mix, folded with a multiplicative hash of V so that
+// it stays informative when the slot index also uses the top bits.
+__host__ __device__ __forceinline__ uint8_t key_fp(unsigned long long key, uint32_t mix) {
+  const uint8_t f = (uint8_t)((mix ^ ((uint32_t)(key >> 32) * 0x2545F491u)) >> 24);
+  return f ? f : (uint8_t)1;
 }
 
 // Longest linear-probe sequence a lookup follows.  At load factor <= 1/2 a
@@ -84,11 +136,25 @@ __host__ __device__ __forceinline__ unsigned long long seg_key(const uint8_t* p,
 // lookup that reaches it reports an inconsistent index instead of scanning.
 constexpr int TABLE_MAX_PROBES = 4096;
 
-// 1: found (begin, count); 0: not present; -1: probe limit reached.
-__device__ __forceinline__ int table_find(const Slot* __restrict__ t, unsigned long long mask,
-                                          unsigned long long key, uint32_t& begin, uint32_t& count) {
-  unsigned long long h = (key >> 7) & mask;
+// 1: found (begin, count); 0: not present; -1: probe limit reached.  With
+// fingerprints (fp not NULL) the probe sequence walks the fingerprint bytes
+// (a small array that stays in L2) and reads a 16-byte slot only when the
+// fingerprint matches, so most lookups of absent keys never touch the table.
+__device__ __forceinline__ int table_find(const Slot* __restrict__ t, const uint8_t* __restrict__ fp,
+                                          unsigned long long mask, unsigned long long key, uint32_t& begin,
+                                          uint32_t& count) {
+  const uint32_t mix = key_mix(key);
+  unsigned long long h = mix & mask;
+  const uint8_t f = key_fp(key, mix);
   for (int probe = 0; probe < TABLE_MAX_PROBES; ++probe) {
+    if (fp) {
+      const uint8_t g = __ldg(fp + h);
+      if (g == 0) return 0;
+      if (g != f) {
+        h = (h + 1) & mask;
+        continue;
+      }
+    }
     const uint4 raw = __ldg(reinterpret_cast<const uint4*>(t + h));
     const unsigned long long k = ((unsigned long long)raw.y << 32) | raw.x;
     if (k == key) {
@@ -109,7 +175,11 @@ struct Partition {
   uint64_t n_records = 0;    // (n - first) * (tau + 1)
   uint64_t n_unique = 0;     // distinct keys
   DBuf<Slot> table;          // power-of-two capacity
+  DBuf<uint8_t> fp;          // key_fp of each used slot, 0 for empty ones
   DBuf<uint32_t> postings;   // sids, runs in key order, ascending inside a run
+  // group visiting order for one probe: the (length, segment) groups sorted
+  // by window size, widest first; [0] for R != S probes, [1] for the self join
+  DBuf<uint16_t> gorder[2];
 };
 
 }  // namespace pj

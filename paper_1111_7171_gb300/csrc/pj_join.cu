@@ -68,10 +68,32 @@ __device__ __forceinline__ void add_counter(unsigned long long* c, unsigned long
 // ---------------------------------------------------------------- A4 ------
 
 // Group t of a chunk: its probe q, its index g within q's groups, and the
-// view (threshold) the group belongs to.  MULTI: thresholds differ per probe
-// and q is found by binary search over the per-probe group offsets.
+// view (threshold) the group belongs to; false for the padding groups of the
+// last probe block.
+//
+// MULTI: thresholds differ per probe and q is found by binary search over
+// the per-probe group offsets.  Otherwise, with v.interleave, probes are
+// interleaved: groups come in blocks of PROBE_BLOCK probes, and inside a
+// block the group index g runs outer and the probe inner, so the 32 lanes of
+// a warp look up the same (length, segment) group of 32 different probes.  A
+// group's window size depends on its segment i and on |s| - l, so these
+// lanes run loops of about the same length; 32 consecutive groups of one
+// probe span windows of 1 to tau + 1 positions.  For long strings the lanes
+// then read 32 different strings instead of one, which costs more than the
+// divergence saves, so interleaving is chosen per join by string length;
+// without it, a probe's groups are visited in v.gorder's order (widest
+// windows first), so that consecutive lanes still get windows of about the
+// same size.
+// Hits come out ordered by probe block, so a probe cut-over aligned to a
+// block boundary still splits them in two.
+constexpr uint32_t PROBE_BLOCK = 32;
+
+__host__ __device__ __forceinline__ unsigned long long interleaved_groups(uint32_t pcount, int G) {
+  return (unsigned long long)((pcount + PROBE_BLOCK - 1) / PROBE_BLOCK) * PROBE_BLOCK * (unsigned long long)G;
+}
+
 template <bool SELF, bool MULTI>
-__device__ __forceinline__ void group_of(const ProbeView& v, unsigned long long t, uint32_t& q, int& g,
+__device__ __forceinline__ bool group_of(const ProbeView& v, unsigned long long t, uint32_t& q, int& g,
                                          ProbeView& vt) {
   if (MULTI) {
     const unsigned long long tg = v.qgoff[v.pbegin] + t;
@@ -83,11 +105,24 @@ __device__ __forceinline__ void group_of(const ProbeView& v, unsigned long long 
     q = lo;
     g = (int)(tg - v.qgoff[q]);
     vt = view_for_tau(v, v.ptau[q]);
-  } else {
-    const int G = groups_per_probe(v.tau, SELF);
-    q = v.pbegin + (uint32_t)(t / G);
-    g = (int)(t % G);
+    return true;
+  } else if (!v.interleave) {  // chunks hold fewer than 2^32 groups
+    const uint32_t G = (uint32_t)groups_per_probe(v.tau, SELF);
+    const uint32_t local = (uint32_t)t / G;
+    g = (int)((uint32_t)t - local * G);
+    if (v.gorder) g = (int)v.gorder[g];
+    q = v.pbegin + local;
     vt = v;
+    return local < v.pcount;
+  } else {
+    const uint32_t span = PROBE_BLOCK * (uint32_t)groups_per_probe(v.tau, SELF);
+    const uint32_t blk = (uint32_t)t / span;
+    const uint32_t r = (uint32_t)t - blk * span;
+    g = (int)(r / PROBE_BLOCK);
+    const uint32_t local = blk * PROBE_BLOCK + r % PROBE_BLOCK;
+    q = v.pbegin + local;
+    vt = v;
+    return local < v.pcount;
   }
 }
 
@@ -97,10 +132,14 @@ __device__ __forceinline__ unsigned long long dev_count(unsigned long long cap, 
   return n_dev ? min(cap, *n_dev) : cap;
 }
 
-// Pass 1: number of non-empty lookups of every group (probe, length, segment).
+// Pass 1: number of non-empty lookups of every group (probe, length, segment)
+// and the mask of the window positions that found one.  The window's
+// substrings overlap, so their hashes are rolled from one position to the
+// next instead of being recomputed.
 template <bool SELF, bool MULTI>
 __global__ void __launch_bounds__(BLOCK) k_group_counts(const ProbeView v, unsigned long long n_groups,
-                                                        uint32_t* __restrict__ counts, Counters* ctr,
+                                                        uint32_t* __restrict__ counts,
+                                                        unsigned long long* __restrict__ masks, Counters* ctr,
                                                         const unsigned long long* __restrict__ n_dev) {
   n_groups = dev_count(n_groups, n_dev);
   unsigned long long lookups = 0;
@@ -110,29 +149,39 @@ __global__ void __launch_bounds__(BLOCK) k_group_counts(const ProbeView v, unsig
     uint32_t q;
     int g;
     ProbeView vt;
-    group_of<SELF, MULTI>(v, t, q, g, vt);
-    const int ls = (int)vt.plen[q];
-    const uint8_t* s = vt.pbytes + vt.poff[q];
-    int l, i, P, li, lo, hi;
     uint32_t nh = 0;
-    if (group_window(vt, SELF, q, ls, g, l, i, P, li, lo, hi)) {
-      for (int p = lo; p <= hi; ++p) {
+    unsigned long long mask = 0;
+    int l, i, P, li, lo, hi;
+    if (group_of<SELF, MULTI>(v, t, q, g, vt) && group_window(vt, SELF, q, (int)vt.plen[q], g, l, i, P, li, lo, hi)) {
+      const int ls = (int)vt.plen[q];
+      const uint8_t* s = vt.pbytes + vt.poff[q];
+      uint32_t V = seg_value(s + lo, li);
+      const uint32_t pw = seg_pow(li);
+      for (int p = lo;; ++p) {
         uint32_t b;
-        if (lookup(vt, SELF, s, ls, q, l, i, p, li, b, err)) ++nh;
+        if (lookup_key(vt, SELF, q, ls, l, seg_key_of(V, l, i), b, err)) {
+          ++nh;
+          mask |= 1ull << (p - lo);
+        }
+        if (p == hi) break;
+        V = seg_roll(V, s[p], s[p + li], li, pw);  // p + li <= hi - 1 + li < ls
       }
       lookups += (unsigned long long)(hi - lo + 1);
     }
     counts[t] = nh;
+    masks[t] = mask;
   }
   add_counter(&ctr->lookups, lookups);
   if (err) atomicOr(&ctr->err, (unsigned long long)err);
 }
 
-// Pass 2: the same lookups again, each non-empty one written as a Hit at the
-// group's prefix-sum offset (offsets at or past hits_cap are not written).
+// Pass 2: the positions pass 1 marked are looked up again and written as
+// Hits at the group's prefix-sum offset (offsets at or past hits_cap are not
+// written).
 template <bool SELF, bool MULTI>
 __global__ void __launch_bounds__(BLOCK) k_group_hits(const ProbeView v, unsigned long long n_groups,
                                                       const uint32_t* __restrict__ counts,
+                                                      const unsigned long long* __restrict__ masks,
                                                       const uint32_t* __restrict__ hit_off, Hit* __restrict__ hits,
                                                       const unsigned long long* __restrict__ n_dev,
                                                       unsigned long long hits_cap) {
@@ -143,7 +192,7 @@ __global__ void __launch_bounds__(BLOCK) k_group_hits(const ProbeView v, unsigne
     uint32_t q;
     int g;
     ProbeView vt;
-    group_of<SELF, MULTI>(v, t, q, g, vt);
+    if (!group_of<SELF, MULTI>(v, t, q, g, vt)) continue;
     const int ls = (int)vt.plen[q];
     const uint8_t* s = vt.pbytes + vt.poff[q];
     int l, i, P, li, lo, hi;
@@ -152,9 +201,12 @@ __global__ void __launch_bounds__(BLOCK) k_group_hits(const ProbeView v, unsigne
     const uint32_t end = (uint32_t)min(hits_cap, (unsigned long long)pos + counts[t]);
     const uint32_t tau_tag = MULTI ? ((uint32_t)vt.tau << 24) : 0u;
     if (group_window(vt, SELF, q, ls, g, l, i, P, li, lo, hi)) {
-      for (int p = lo; p <= hi && pos < end; ++p) {
+      unsigned long long m = masks[t];
+      while (m && pos < end) {
+        const int p = lo + (__ffsll((long long)m) - 1);
+        m &= m - 1;
         uint32_t b;
-        const uint32_t c = lookup(vt, SELF, s, ls, q, l, i, p, li, b, err);
+        const uint32_t c = lookup_key(vt, SELF, q, ls, l, seg_key(s + p, li, l, i), b, err);
         if (c) hits[pos++] = Hit{q, b, c, (uint32_t)p | ((uint32_t)i << 16) | tau_tag};
       }
     }
@@ -508,8 +560,9 @@ static void probe_chunk(const Ctx& c, const ProbeView& v, unsigned long long n_g
                         DBuf<unsigned long long>& off, unsigned long long& n_hits, unsigned long long& n_cand) {
   gcount.reset(c, n_groups);
   goff.reset(c, n_groups);
+  DBuf<unsigned long long> gmask(c, n_groups);
   const unsigned g1 = persistent_grid(k_group_counts<SELF, MULTI>, (n_groups + BLOCK - 1) / BLOCK);
-  k_group_counts<SELF, MULTI><<<g1, BLOCK, 0, c.stream>>>(v, n_groups, gcount.p, ctr, nullptr);
+  k_group_counts<SELF, MULTI><<<g1, BLOCK, 0, c.stream>>>(v, n_groups, gcount.p, gmask.p, ctr, nullptr);
   PJ_LAUNCHED("k_group_counts");
   exclusive_scan<uint32_t>(c, gcount.p, goff.p, n_groups);
   uint32_t last[2] = {0, 0};
@@ -521,7 +574,8 @@ static void probe_chunk(const Ctx& c, const ProbeView& v, unsigned long long n_g
   if (n_hits == 0) return;
   hits.reset(c, n_hits);
   const unsigned g2 = persistent_grid(k_group_hits<SELF, MULTI>, (n_groups + BLOCK - 1) / BLOCK);
-  k_group_hits<SELF, MULTI><<<g2, BLOCK, 0, c.stream>>>(v, n_groups, gcount.p, goff.p, hits.p, nullptr, n_hits);
+  k_group_hits<SELF, MULTI><<<g2, BLOCK, 0, c.stream>>>(v, n_groups, gcount.p, gmask.p, goff.p, hits.p, nullptr,
+                                                        n_hits);
   PJ_LAUNCHED("k_group_hits");
   trace_mark(c, "join: probe (hits)");
   cnt.reset(c, n_hits + 1);
@@ -534,7 +588,17 @@ static void probe_chunk(const Ctx& c, const ProbeView& v, unsigned long long n_g
   c.sync();
 }
 
-// Index of the first candidate whose probe id is >= q (hits in probe order).
+// The warp cut-over probe rounded up to the chunk's next probe-block boundary
+// (hits are ordered by probe block; both verification forms give the same
+// results, so moving the cut by a few probes changes nothing but speed).
+static uint32_t aligned_cut(const ProbeView& v, uint32_t q_cut) {
+  if (q_cut <= v.pbegin) return v.pbegin;
+  const unsigned long long k = ((unsigned long long)(q_cut - v.pbegin) + PROBE_BLOCK - 1) / PROBE_BLOCK;
+  return (uint32_t)std::min<unsigned long long>(UINT32_MAX, v.pbegin + k * PROBE_BLOCK);
+}
+
+// Index of the first candidate whose probe id is >= q (hits ordered by probe
+// block, q at a block boundary).
 static unsigned long long first_candidate_of(const Ctx& c, const DBuf<Hit>& hits, const DBuf<unsigned long long>& off,
                                              unsigned long long n_hits, unsigned long long n_cand, uint32_t q) {
   DBuf<unsigned long long> hcut(c, 1);
@@ -555,7 +619,7 @@ static void probe_and_verify(const Ctx& c, const ProbeView& v0, uint32_t fb_coun
                              Counters& h, Timings& tm, const unsigned long long* h_qgoff) {
   EventTimer tp(c.stream), tv(c.stream), tf(c.stream);
   const int G = MULTI ? 1 : groups_per_probe(v0.tau, SELF);
-  const unsigned long long group_budget = env_knob("PJ_GROUP_BUDGET", 64ull << 20);
+  const unsigned long long group_budget = std::min(env_knob("PJ_GROUP_BUDGET", 64ull << 20), 1ull << 31);
   const unsigned long long launch_cands = env_knob("PJ_LAUNCH_CANDS", 1ull << 30);
   const uint32_t chunk_items = (uint32_t)std::max<unsigned long long>(1, group_budget / G);
   DBuf<Hit> hits;
@@ -566,7 +630,8 @@ static void probe_and_verify(const Ctx& c, const ProbeView& v0, uint32_t fb_coun
     ProbeView v = v0;
     v.pbegin = v0.pbegin + done;
     v.pcount = std::min(chunk_items, v0.pcount - done);
-    unsigned long long n_groups = (unsigned long long)v.pcount * G;
+    unsigned long long n_groups =
+        (MULTI || !v.interleave) ? (unsigned long long)v.pcount * G : interleaved_groups(v.pcount, G);
     if (MULTI) {  // probes whose groups fit the budget (at least one)
       uint32_t q1 = v.pbegin + 1;
       while (q1 < v0.pbegin + v0.pcount && h_qgoff[q1 + 1] - h_qgoff[v.pbegin] <= group_budget) ++q1;
@@ -596,8 +661,8 @@ static void probe_and_verify(const Ctx& c, const ProbeView& v0, uint32_t fb_coun
     const double remaining_groups = (double)(v0.pcount - done - v.pcount) / std::max(1u, v.pcount) + 1.0;  // chunks left
     // candidates [c_cut, n_cand) belong to long probes: one warp per candidate
     unsigned long long c_cut = n_cand;
-    if (SELF && !MULTI && v.warp_q_cut < v.pbegin + v.pcount)
-      c_cut = first_candidate_of(c, hits, off, n_hits, n_cand, v.warp_q_cut);
+    const uint32_t q_cut = aligned_cut(v, v.warp_q_cut);
+    if (SELF && !MULTI && q_cut < v.pbegin + v.pcount) c_cut = first_candidate_of(c, hits, off, n_hits, n_cand, q_cut);
     for (unsigned long long cb = 0; cb < n_cand;) {
       const bool warp_range = cb >= c_cut;
       const unsigned long long ce = std::min(warp_range ? n_cand : c_cut, cb + launch_cands);
@@ -782,7 +847,7 @@ static TuneResult autotune_self(pj_index& idx, const ProbeView& v0) {
   TuneResult best;
   const int tau = v0.tau;
   const int G = groups_per_probe(tau, true);
-  const unsigned long long group_budget = env_knob("PJ_GROUP_BUDGET", 64ull << 20);
+  const unsigned long long group_budget = std::min(env_knob("PJ_GROUP_BUDGET", 64ull << 20), 1ull << 31);
   ProbeView v = v0;
   v.pcount = (uint32_t)std::min<unsigned long long>(v0.pcount, std::max<unsigned long long>(1, group_budget / G));
   if (v.pcount == 0) return best;
@@ -792,7 +857,8 @@ static TuneResult autotune_self(pj_index& idx, const ProbeView& v0) {
   DBuf<Hit> hits;
   DBuf<unsigned long long> cnt, off;
   unsigned long long n_hits = 0, n_cand = 0;
-  probe_chunk<true, false>(c, v, (unsigned long long)v.pcount * G, ctr.p, gcount, goff, hits, cnt, off, n_hits, n_cand);
+  probe_chunk<true, false>(c, v, v.interleave ? interleaved_groups(v.pcount, G) : (unsigned long long)v.pcount * G,
+                           ctr.p, gcount, goff, hits, cnt, off, n_hits, n_cand);
   if (n_cand == 0) return best;
   // the timed range: a prefix of the candidates (probes are in length order,
   // so it covers the shortest probes; capped to bound the tuning time)
@@ -811,7 +877,7 @@ static TuneResult autotune_self(pj_index& idx, const ProbeView& v0) {
   for (int cut : cuts) {
     unsigned long long c_cut = S;
     if (cut < 65536) {
-      const uint32_t q_cut = std::max<uint32_t>(idx.h_bbeg[std::max(0, cut)], v.pbegin);
+      const uint32_t q_cut = aligned_cut(v, std::max<uint32_t>(idx.h_bbeg[std::max(0, cut)], v.pbegin));
       c_cut = std::min(S, first_candidate_of(c, hits, off, n_hits, n_cand, q_cut));
     }
     for (int blk : blocks) {
@@ -873,9 +939,17 @@ static TuneResult self_join_tuning(pj_index& idx, const ProbeView& v, float* tun
   return r;
 }
 
+// Probe interleaving (see group_of) for strings of this average length or
+// shorter; PJ_PROBE_INTERLEAVE=0/1 overrides.
+constexpr double INTERLEAVE_MAX_AVG_LEN = 256.0;
+
 static ProbeView index_side(const pj_index& idx, const Partition& part) {
   ProbeView v{};
   v.seg_magic = seg_magic(part.tau + 1);
+  const double avg = idx.n ? (double)idx.total_bytes / idx.n : 0.0;
+  v.interleave = avg <= INTERLEAVE_MAX_AVG_LEN ? 1 : 0;
+  const char* il = getenv("PJ_PROBE_INTERLEAVE");
+  if (il && il[0]) v.interleave = atoi(il) ? 1 : 0;
   v.warp_q_cut = UINT32_MAX;
   v.block_thread = 256;
   v.block_warp = 256;
@@ -887,6 +961,7 @@ static ProbeView index_side(const pj_index& idx, const Partition& part) {
   v.iperm = idx.perm.p;
   v.n_index = idx.n;
   v.table = part.table.p;
+  v.table_fp = part.fp.p;
   v.mask = part.table.n - 1;
   v.postings = part.postings.p;
   v.n_postings = part.n_records;
@@ -920,6 +995,7 @@ static void self_join_impl(pj_index& idx, int tau, pj_result* out, bool on_devic
   v.pcount = idx.n - part.first;
   v.pid = idx.perm.p;
   v.key_shift = bits_for(idx.n);
+  v.gorder = part.gorder[1].p;
   v.warp_q_cut = UINT32_MAX;
   float tune_ms = 0.f;
   const TuneResult tr = self_join_tuning(idx, v, &tune_ms);
@@ -942,6 +1018,7 @@ static void probe_join_impl(const Ctx& c, const pj_index& idx, const Partition& 
   v.pcount = R.n;
   v.pid = nullptr;
   v.key_shift = bits_for(idx.n);
+  v.gorder = part.gorder[0].p;
   const bool has_short = part.first > 0;  // indexed strings too short to partition
   run_join(c, v, false, has_short ? R.n : 0, bits_for(R.n), on_device, out);
 }
@@ -966,7 +1043,8 @@ void query_multi_impl(const Ctx& c, pj_index& idx, const ProbeSet& R, const uint
     PartView pv{};
     if (present[t]) {
       const Partition& part = idx.parts[t];
-      pv = PartView{part.table.p, part.table.n - 1, part.postings.p, part.n_records, part.first, t, seg_magic(t + 1)};
+      pv = PartView{part.table.p, part.fp.p,    part.table.n - 1, part.postings.p,
+                    part.n_records, part.first, t,           seg_magic(t + 1)};
       has_short |= part.first > 0;
     }
     hp[t] = pv;
@@ -1061,12 +1139,12 @@ void record_query_plan(const Ctx& c, const pj_index& idx, const PlanDev& d) {
   PJ_LAUNCHED("k_plan_groups");
   exclusive_scan_dn<unsigned long long>(c, d.gcnt, d.qgoff, d.cap_q, nullptr, &sz->groups);
   const unsigned g1 = persistent_grid(k_group_counts<false, true>, (d.cap_groups + BLOCK - 1) / BLOCK);
-  k_group_counts<false, true><<<g1, BLOCK, 0, c.stream>>>(v, d.cap_groups, d.gcounts, ctr, &sz->groups);
+  k_group_counts<false, true><<<g1, BLOCK, 0, c.stream>>>(v, d.cap_groups, d.gcounts, d.gmask, ctr, &sz->groups);
   PJ_LAUNCHED("k_group_counts");
   exclusive_scan_dn<uint32_t>(c, d.gcounts, d.goff, d.cap_groups, &sz->groups, &sz->hits);
   const unsigned g2 = persistent_grid(k_group_hits<false, true>, (d.cap_groups + BLOCK - 1) / BLOCK);
-  k_group_hits<false, true><<<g2, BLOCK, 0, c.stream>>>(v, d.cap_groups, d.gcounts, d.goff, d.hits, &sz->groups,
-                                                        d.cap_hits);
+  k_group_hits<false, true><<<g2, BLOCK, 0, c.stream>>>(v, d.cap_groups, d.gcounts, d.gmask, d.goff, d.hits,
+                                                        &sz->groups, d.cap_hits);
   PJ_LAUNCHED("k_group_hits");
   k_hit_counts<<<stride_grid(d.cap_hits), 256, 0, c.stream>>>(d.hits, d.cap_hits, d.hcnt, &sz->hits);
   PJ_LAUNCHED("k_hit_counts");

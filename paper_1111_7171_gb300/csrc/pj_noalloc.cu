@@ -224,6 +224,7 @@ void query_noalloc(pj_index& idx, const pj_strings& batch, int tau, pj_pair* out
   v.iperm = idx.perm.p;
   v.n_index = idx.n;
   v.table = part.table.p;
+  v.table_fp = part.fp.p;
   v.mask = part.table.n - 1;
   v.postings = part.postings.p;
   v.n_postings = part.n_records;

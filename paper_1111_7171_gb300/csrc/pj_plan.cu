@@ -104,7 +104,7 @@ struct pj_plan {
   pj::DBuf<uint64_t> off;
   pj::DBuf<pj::PlanSizes> sizes;
   pj::DBuf<uint32_t> len, gcounts, goff, flags, pos, acc_ed0, acc_ed1;
-  pj::DBuf<unsigned long long> gcnt, qgoff, hcnt, hoff, acc_key0, acc_key1;
+  pj::DBuf<unsigned long long> gcnt, qgoff, gmask, hcnt, hoff, acc_key0, acc_key1;
   pj::DBuf<pj::PartView> parts;
   pj::DBuf<unsigned char> counters, arena;
   pj::DBuf<pj::Hit> hits;
@@ -118,7 +118,7 @@ struct pj_plan {
   uint64_t device_bytes() const {
     return bytes.bytes() + tau.bytes() + off.bytes() + sizes.bytes() + len.bytes() + gcounts.bytes() + goff.bytes() +
            flags.bytes() + pos.bytes() + acc_ed0.bytes() + acc_ed1.bytes() + gcnt.bytes() + qgoff.bytes() +
-           hcnt.bytes() + hoff.bytes() + acc_key0.bytes() + acc_key1.bytes() + parts.bytes() + counters.bytes() +
+           gmask.bytes() + hcnt.bytes() + hoff.bytes() + acc_key0.bytes() + acc_key1.bytes() + parts.bytes() + counters.bytes() +
            arena.bytes() + hits.bytes();
   }
   uint64_t host_bytes() const {
@@ -139,7 +139,7 @@ struct pj_plan {
     sizes.release();
     pj::DBuf<uint32_t>* b32[] = {&len, &gcounts, &goff, &flags, &pos, &acc_ed0, &acc_ed1};
     for (auto* b : b32) b->release();
-    pj::DBuf<unsigned long long>* b64[] = {&gcnt, &qgoff, &hcnt, &hoff, &acc_key0, &acc_key1};
+    pj::DBuf<unsigned long long>* b64[] = {&gcnt, &qgoff, &gmask, &hcnt, &hoff, &acc_key0, &acc_key1};
     for (auto* b : b64) b->release();
     parts.release();
     counters.release();
@@ -304,6 +304,7 @@ void create(pj_plan& P, pj_index& idx, const pj_plan_options& o) {
   P.qgoff.reset(P.ctx, d.cap_q);
   P.gcounts.reset(P.ctx, d.cap_groups);
   P.goff.reset(P.ctx, d.cap_groups);
+  P.gmask.reset(P.ctx, d.cap_groups);
   P.counters.reset(P.ctx, 64);
   d.bytes = P.bytes.p;
   d.off = P.off.p;
@@ -314,11 +315,13 @@ void create(pj_plan& P, pj_index& idx, const pj_plan_options& o) {
   d.qgoff = P.qgoff.p;
   d.gcounts = P.gcounts.p;
   d.goff = P.goff.p;
+  d.gmask = P.gmask.p;
   d.counters = P.counters.p;
   std::vector<PartView> hp((size_t)tau_max + 1);
   for (int t = 0; t <= tau_max; ++t) {
     const Partition& part = idx.parts[t];
-    hp[t] = PartView{part.table.p, part.table.n - 1, part.postings.p, part.n_records, part.first, t, seg_magic(t + 1)};
+    hp[t] = PartView{part.table.p, part.fp.p,    part.table.n - 1, part.postings.p,
+                     part.n_records, part.first, t,           seg_magic(t + 1)};
   }
   P.parts.reset(P.ctx, hp.size());
   PJ_CUDA(cudaMemcpyAsync(P.parts.p, hp.data(), hp.size() * sizeof(PartView), cudaMemcpyHostToDevice, P.stream));

@@ -41,6 +41,7 @@ struct PlanDev {
   void* counters;                 // 64 bytes, zeroed by the graph
   uint32_t* gcounts;              // cap_groups
   uint32_t* goff;                 // cap_groups
+  unsigned long long* gmask;      // cap_groups window-position masks
   Hit* hits;                      // cap_hits
   unsigned long long* hcnt;       // cap_hits
   unsigned long long* hoff;       // cap_hits

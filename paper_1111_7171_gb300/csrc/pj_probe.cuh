@@ -26,6 +26,7 @@ struct Hit {
 // One threshold's segment index, as seen by the kernels.
 struct PartView {
   const Slot* table;
+  const uint8_t* fp;  // slot fingerprints
   unsigned long long mask;
   const uint32_t* postings;
   unsigned long long n_postings;
@@ -50,6 +51,7 @@ struct ProbeView {
   const uint32_t* iperm;  // sid -> reported id
   uint32_t n_index;
   const Slot* table;
+  const uint8_t* table_fp;  // slot fingerprints (NULL: probe the slots directly)
   unsigned long long mask;
   const uint32_t* postings;
   unsigned long long n_postings;
@@ -65,6 +67,8 @@ struct ProbeView {
   // order) are verified one warp per candidate; UINT32_MAX = never
   uint32_t warp_q_cut;
   int block_thread;  // block size of the thread-per-candidate verification
+  int interleave;    // probe groups interleaved across probes (see group_of)
+  const uint16_t* gorder;  // groups of one probe in visiting order (NULL: natural order)
   int block_warp;    // block size of the warp-per-candidate verification
 };
 
@@ -73,6 +77,7 @@ __host__ __device__ __forceinline__ ProbeView view_for_tau(const ProbeView& v, i
   ProbeView t = v;
   const PartView& pv = v.parts[tau];
   t.table = pv.table;
+  t.table_fp = pv.fp;
   t.mask = pv.mask;
   t.postings = pv.postings;
   t.n_postings = pv.n_postings;
@@ -111,13 +116,18 @@ __host__ __device__ __forceinline__ bool group_window(const ProbeView& v, bool s
   return hi >= lo;
 }
 
-__host__ __device__ __forceinline__ int table_find_any(const Slot* t, unsigned long long mask, unsigned long long key,
-                                                       uint32_t& begin, uint32_t& count) {
+__host__ __device__ __forceinline__ int table_find_any(const Slot* t, const uint8_t* fp, unsigned long long mask,
+                                                       unsigned long long key, uint32_t& begin, uint32_t& count) {
 #ifdef __CUDA_ARCH__
-  return table_find(t, mask, key, begin, count);
+  return table_find(t, fp, mask, key, begin, count);
 #else
-  unsigned long long h = (key >> 7) & mask;
+  const uint32_t mix = key_mix(key);
+  unsigned long long h = mix & mask;
   for (int probe = 0; probe < TABLE_MAX_PROBES; ++probe) {
+    if (fp && fp[h] != 0 && fp[h] != key_fp(key, mix)) {
+      h = (h + 1) & mask;
+      continue;
+    }
     if (t[h].key == key) {
       begin = t[h].begin;
       count = t[h].count;
@@ -130,15 +140,15 @@ __host__ __device__ __forceinline__ int table_find_any(const Slot* t, unsigned l
 #endif
 }
 
-// Lookup of s[p, li] in L_l^i.  Returns the number of postings to verify
-// (for the self join with l == |s|, only sids below q: runs ascend) and sets
-// begin.  err |= 1 for a run outside the postings, 2 for the probe limit.
-__host__ __device__ __forceinline__ uint32_t lookup(const ProbeView& v, bool self, const uint8_t* s, int ls,
-                                                    uint32_t q, int l, int i, int p, int li, uint32_t& begin,
-                                                    int& err) {
+// Lookup of the key of s[p, li] in L_l^i.  Returns the number of postings to
+// verify (for the self join with l == |s|, only sids below q: runs ascend)
+// and sets begin.  err |= 1 for a run outside the postings, 2 for the probe
+// limit.
+__host__ __device__ __forceinline__ uint32_t lookup_key(const ProbeView& v, bool self, uint32_t q, int ls, int l,
+                                                        unsigned long long key, uint32_t& begin, int& err) {
   uint32_t cnt = 0;
   begin = 0;
-  const int found = table_find_any(v.table, v.mask, seg_key(s + p, li, l, i), begin, cnt);
+  const int found = table_find_any(v.table, v.table_fp, v.mask, key, begin, cnt);
   if (found < 0) {
     err |= 2;
     return 0;
@@ -157,6 +167,13 @@ __host__ __device__ __forceinline__ uint32_t lookup(const ProbeView& v, bool sel
     cnt = x0;
   }
   return cnt;
+}
+
+// Lookup of s[p, li] in L_l^i (lookup_key with the key computed here).
+__host__ __device__ __forceinline__ uint32_t lookup(const ProbeView& v, bool self, const uint8_t* s, int ls,
+                                                    uint32_t q, int l, int i, int p, int li, uint32_t& begin,
+                                                    int& err) {
+  return lookup_key(v, self, q, ls, l, seg_key(s + p, li, l, i), begin, err);
 }
 
 // What the verification of a candidate needs from its hit: the probing
@@ -195,8 +212,10 @@ __host__ __device__ __forceinline__ bool verify_in_hit(const ProbeView& v, bool 
     if (i >= 1 && i <= v.tau + 1 && lr >= v.tau + 1) {  // r is a partitioned string
       int P, li;
       even_segment_m(lr, v.tau + 1, v.seg_magic, i, P, li);
-      if (hc.p + li <= hc.ls &&
-          verify_ext<MAXW>(hc.s, hc.ls, v.ibytes + v.ioff[r], lr, i, hc.p, li, P, v.tau, ed, cells)) {
+      // exact keys (segments of at most SEG_EXACT_MAX bytes) guarantee the
+      // segment match; hashed ones are compared
+      if (hc.p + li <= hc.ls && verify_ext<MAXW>(hc.s, hc.ls, v.ibytes + v.ioff[r], lr, i, hc.p, li, P, v.tau,
+                                                 li > SEG_EXACT_MAX, ed, cells)) {
         const uint32_t qid = v.pid ? v.pid[hc.q] : hc.q;
         const uint32_t rid = v.iperm[r];
         const uint32_t ka = self ? min(qid, rid) : qid;
@@ -237,7 +256,8 @@ __device__ __forceinline__ bool verify_candidate_warp(const ProbeView& v, bool s
       int P, li;
       even_segment_m(lr, v.tau + 1, v.seg_magic, i, P, li);
       if (p + li <= ls &&
-          verify_ext_warp(v.pbytes + v.poff[q], ls, v.ibytes + v.ioff[r], lr, i, p, li, P, v.tau, ed, cells)) {
+          verify_ext_warp(v.pbytes + v.poff[q], ls, v.ibytes + v.ioff[r], lr, i, p, li, P, v.tau, li > SEG_EXACT_MAX,
+                          ed, cells)) {
         const uint32_t qid = v.pid ? v.pid[q] : q;
         const uint32_t rid = v.iperm[r];
         const uint32_t ka = self ? min(qid, rid) : qid;

@@ -25,11 +25,14 @@ using std::min;
 // upward: the length-aware band of Sec. 5.1 is d <= floor((t+D)/2), and the
 // W registers (W >= t + 1) may cover a few more diagonals above it.  Any
 // value computed over a superset of the band is the cost of a real
-// alignment, and the band holds every alignment of cost <= t, so the capped
-// result is unchanged.  Values saturate at t + 1 (exact for the capped
-// result); cells left of column 0 stay at t + 1, which makes M(i, 0) = i
-// fall out of the recurrence, and cells right of column |b| never feed a
-// cell inside the matrix.  So the inner loop has no bounds checks.
+// alignment, and the band holds every alignment of cost <= t, so every value
+// <= t comes out exact.  Cells left of column 0 start at t + 1 and stay at
+// least t + 1 (every input to them is), which makes M(i, 0) = i fall out of
+// the recurrence while i <= t, and a value >= t + 1 never lowers a cell
+// below t + 1; so values are not clamped cell by cell, only the result is.
+// Cells right of column |b| never feed a cell inside the matrix, so the
+// characters of b are read at clamped indices and the inner loop has no
+// bounds checks.
 //
 // After each row the expected edit distance E(i, j) = M(i, j) + |D - (j - i)|
 // is minimised over the row; if every E exceeds t the pair is dissimilar
@@ -44,16 +47,16 @@ __host__ __device__ __forceinline__ int vsp_band(const uint8_t* a, int na, const
   const int cap = t + 1;
   const int dlo = -((t - D) >> 1);
   const int w = ((t + D) >> 1) - dlo + 1;  // length-aware band width, <= t + 1 <= W
+  const int blast = nb - 1;                // nb >= na >= 1
   int V[W];
   int eoff[W];
-  uint8_t B[W];  // B[k] = b[i + dlo + k - 1] for the current row i (0 outside b)
+  uint8_t B[W];  // B[k] = b[i + dlo + k - 1] for the current row i (index clamped to [0, nb))
 #pragma unroll
   for (int k = 0; k < W; ++k) {
     const int j = dlo + k;  // row 0: M(0, j) = j
-    V[k] = j < 0 ? cap : min(j, cap);
+    V[k] = j < 0 ? cap : j;
     eoff[k] = abs(D - dlo - k);
-    const int jb = dlo + k;  // b index for row 1
-    B[k] = (jb >= 0 && jb < nb) ? b[jb] : (uint8_t)0;
+    B[k] = b[min(max(j, 0), blast)];  // b index for row 1
   }
   bool alive = true;
   int rows = 0;
@@ -65,7 +68,7 @@ __host__ __device__ __forceinline__ int vsp_band(const uint8_t* a, int na, const
     for (int k = 0; k < W; ++k) {
       const int up = (k + 1 < W) ? V[k + 1] : cap;
       const int diag = V[k] + (ca != B[k] ? 1 : 0);
-      const int val = min(min(diag, up + 1), min(left + 1, cap));
+      const int val = min(diag, min(up, left) + 1);
       V[k] = val;
       left = val;
       emin = min(emin, val + eoff[k]);
@@ -78,7 +81,7 @@ __host__ __device__ __forceinline__ int vsp_band(const uint8_t* a, int na, const
     const int jn = i + dlo + W - 1;  // next row's last column character
 #pragma unroll
     for (int k = 0; k + 1 < W; ++k) B[k] = B[k + 1];
-    B[W - 1] = (jn >= 0 && jn < nb) ? b[jn] : (uint8_t)0;
+    B[W - 1] = b[min(max(jn, 0), blast)];
   }
   cells += (unsigned long long)(rows * w);
   int res = cap;
@@ -86,7 +89,7 @@ __host__ __device__ __forceinline__ int vsp_band(const uint8_t* a, int na, const
     const int kres = D - dlo;
 #pragma unroll
     for (int k = 0; k < W; ++k)
-      if (k == kres) res = V[k];
+      if (k == kres) res = min(V[k], cap);
   }
   return res;
 }
@@ -197,9 +200,10 @@ __device__ __forceinline__ int vsp_warp(const uint8_t* x, int nx, const uint8_t*
 // extension-based verification with the warp-cooperative VERIFYSTRINGPAIR
 // (the side with the smaller threshold first, as in verify_ext)
 __device__ __forceinline__ bool verify_ext_warp(const uint8_t* s, int ls, const uint8_t* r, int lr, int i, int p,
-                                                int li, int P, int tau, int& ed, unsigned long long& cells) {
+                                                int li, int P, int tau, bool check_segment, int& ed,
+                                                unsigned long long& cells) {
   bool same = true;
-  for (int k = 0; k < li; ++k) {
+  for (int k = 0; check_segment && k < li; ++k) {
     if (s[p + k] != r[P + k]) {
       same = false;
       break;
@@ -227,15 +231,17 @@ __device__ __forceinline__ bool verify_ext_warp(const uint8_t* s, int ls, const 
 
 // Extension-based verification of one match (Sec. 5.2, Alg. 3).  s has the
 // selected substring at p; r is the indexed string whose segment i (start P,
-// length li) it matched.  Returns true with ed = d_l + d_r when accepted.
+// length li) it matched; check_segment false when the lookup already proved
+// the two segments equal.  Returns true with ed = d_l + d_r when accepted.
 // Both sides must pass (d_l <= i-1 and d_r <= tau+1-i), so they may be
 // checked in either order: the side with the smaller threshold goes first
 // (its band is narrower and it rejects more often).
 template <int MAXW>
 __host__ __device__ __forceinline__ bool verify_ext(const uint8_t* s, int ls, const uint8_t* r, int lr, int i, int p, int li,
-                                                    int P, int tau, int& ed, unsigned long long& cells) {
+                                                    int P, int tau, bool check_segment, int& ed,
+                                                    unsigned long long& cells) {
   bool same = true;
-  for (int k = 0; k < li; ++k) {
+  for (int k = 0; check_segment && k < li; ++k) {
     if (s[p + k] != r[P + k]) {  // hash collision, not a match
       same = false;
       break;

@@ -73,7 +73,7 @@ int main(int argc, char** argv) {
   for (size_t k = 0; k < rec.size();) {
     size_t e = k;
     while (e < rec.size() && rec[e].first == rec[k].first) ++e;
-    ull h = (rec[k].first >> 7) & (cap - 1);
+    ull h = key_mix(rec[k].first) & (cap - 1);
     while (table[h].key) h = (h + 1) & (cap - 1);
     table[h].key = rec[k].first;
     table[h].begin = (uint32_t)k;
@@ -120,7 +120,9 @@ int main(int argc, char** argv) {
     v.pcount = (uint32_t)qlen.size();
     v.pid = nullptr;
   }
-  // phase 1: groups -> hits
+  // phase 1: groups -> hits, as the kernels split it: pass 1 rolls the
+  // window's substring hashes and records the positions that found a
+  // posting run; pass 2 looks those positions up again and emits the hits.
   const int G = groups_per_probe(tau, self);
   std::vector<Hit> hits;
   ull lookups = 0;
@@ -128,12 +130,23 @@ int main(int argc, char** argv) {
   for (ull t = 0; t < (ull)v.pcount * G; ++t) {
     const uint32_t q = v.pbegin + (uint32_t)(t / G);
     const int ls = (int)v.plen[q];
+    const uint8_t* s = v.pbytes + v.poff[q];
     int l, i, P, li, lo, hi;
     if (!group_window(v, self, q, ls, (int)(t % G), l, i, P, li, lo, hi)) continue;
-    for (int p = lo; p <= hi; ++p) {
+    ull mask = 0;
+    uint32_t V = seg_value(s + lo, li);
+    const uint32_t pw = seg_pow(li);
+    for (int p = lo;; ++p) {
       ++lookups;
       uint32_t b;
-      const uint32_t c = lookup(v, self, v.pbytes + v.poff[q], ls, q, l, i, p, li, b, err);
+      if (lookup_key(v, self, q, ls, l, seg_key_of(V, l, i), b, err)) mask |= 1ull << (p - lo);
+      if (p == hi) break;
+      V = seg_roll(V, s[p], s[p + li], li, pw);
+    }
+    for (int p = lo; p <= hi; ++p) {
+      if (!(mask >> (p - lo) & 1)) continue;
+      uint32_t b;
+      const uint32_t c = lookup(v, self, s, ls, q, l, i, p, li, b, err);
       if (c) hits.push_back(Hit{q, b, c, (uint32_t)p | ((uint32_t)i << 16)});
     }
   }

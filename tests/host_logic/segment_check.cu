@@ -3,7 +3,11 @@
 // precomputed reciprocal) against the plain integer division of the
 // partition rule of Sec. 3.1, for every string length 0..65535 and every
 // segment count 1..33, every segment i.  Also checks that the segments tile
-// the string.  Prints "bad=<mismatches>".
+// the string.  Then checks the probe's rolling segment value (seg_roll)
+// against the direct one (seg_value) over every window of random strings,
+// for exact (short) and hashed segments; that keys and fingerprints are
+// never 0; and that exact keys of different short segments differ.  Prints
+// "bad=<mismatches>".
 #include <cstdio>
 
 #include "pj_internal.cuh"
@@ -33,6 +37,40 @@ int main() {
       if (end != l) ++bad;
     }
   }
+  unsigned long long x = 88172645463325252ull;  // xorshift64
+  for (int it = 0; it < 20000; ++it) {
+    x ^= x << 13; x ^= x >> 7; x ^= x << 17;
+    const int n = 1 + (int)(x % 300);
+    const int len = it % 3 == 0 ? 1 + (int)((x >> 20) % 6) : 1 + (int)((x >> 20) % n);  // exact and hashed
+    if (len > n) continue;
+    uint8_t buf[300];
+    for (int k = 0; k < n; ++k) {
+      x ^= x << 13; x ^= x >> 7; x ^= x << 17;
+      buf[k] = (uint8_t)(x >> 24);
+    }
+    uint32_t v = pj::seg_value(buf, len);
+    const uint32_t pw = pj::seg_pow(len);
+    for (int p = 0; p + len <= n; ++p) {
+      if (v != pj::seg_value(buf + p, len)) ++bad;
+      const unsigned long long key = pj::seg_key_of(v, n, 1 + p % 33);
+      if (key == 0 || pj::key_fp(key, pj::key_mix(key)) == 0) ++bad;
+      if (p + len < n) v = pj::seg_roll(v, buf[p], buf[p + len], len, pw);
+    }
+  }
+  // exact keys: different short segments never share a key
+  for (int len = 1; len <= pj::SEG_EXACT_MAX; ++len)
+    for (int it = 0; it < 20000; ++it) {
+      uint8_t a[4], b[4];
+      x ^= x << 13; x ^= x >> 7; x ^= x << 17;
+      for (int k = 0; k < 4; ++k) {
+        a[k] = (uint8_t)(x >> (8 * k));
+        b[k] = (uint8_t)(x >> (8 * k + 32));
+      }
+      if (it & 1) b[it % len] = a[it % len];  // near misses too
+      bool same = true;
+      for (int k = 0; k < len; ++k) same &= a[k] == b[k];
+      if ((pj::seg_key(a, len, 7, 2) == pj::seg_key(b, len, 7, 2)) != same) ++bad;
+    }
   printf("bad=%ld\n", bad);
   return 0;
 }

@@ -283,6 +283,31 @@ def test_warp_per_pair_verification(monkeypatch, cut):
         assert_same(gpu_self(strings, tau).pairs, cpu_self(strings, tau, banded=banded), f"{name} tau={tau} cut={cut}")
 
 
+@pytest.mark.parametrize("mode", ["0", "1"])
+def test_probe_interleaving_both_ways(monkeypatch, mode):
+    """Probe groups taken probe by probe (0) or interleaved across 32-probe
+    blocks (1), with and without the warp cut-over inside a block and with
+    chunks that end mid-block: same exact result."""
+    monkeypatch.setenv("PJ_PROBE_INTERLEAVE", mode)
+    cases = [("short", 4, 3001, False, None), ("short2k", 2, 2000, False, "12"), ("medium", 6, 1999, True, "90"),
+             ("long", 16, 333, True, "0")]
+    for name, tau, n, banded, cut in cases:
+        if cut is None:
+            monkeypatch.delenv("PJ_WARP_MIN_LEN", raising=False)
+        else:
+            monkeypatch.setenv("PJ_WARP_MIN_LEN", cut)
+        strings = synth.generate(name, tau, n=n)
+        want = cpu_self(strings, tau, banded=banded)
+        assert_same(gpu_self(strings, tau).pairs, want, f"{name} tau={tau} interleave={mode}")
+    monkeypatch.setenv("PJ_GROUP_BUDGET", str(25 * 45))  # 45 probes per chunk at tau = 4
+    strings = synth.generate("short", 4, n=2000)
+    assert_same(gpu_self(strings, 4).pairs, cpu_self(strings, 4), f"chunked interleave={mode}")
+    R, S = _rs_sets(5, 2)
+    rb, ro = synth.pack(R)
+    sb, so = synth.pack(S)
+    assert_same(pj.pj_join(R, S, 2).pairs, oracle.join(rb, ro, sb, so, 2), f"join interleave={mode}")
+
+
 def test_autotuned_self_join(monkeypatch, tmp_path):
     """The autotuner picks the cut-over and block size per workload signature
     (cached for the process and in PJ_AUTOTUNE_CACHE); results stay exact."""
