@@ -58,8 +58,14 @@ enum {
 
 /* verify_mode values (pj_options.verify_mode) */
 enum {
-  PJ_VERIFY_AUTO = 0,       /* library's choice (currently: extension) */
-  PJ_VERIFY_EXTENSION = 1   /* extension-based verification (Sec. 5.2, Alg. 3) */
+  PJ_VERIFY_AUTO = 0,       /* library's choice: the autotuner's when autotune is set, else
+                               PJ_VERIFY_PAIRS for strings longer than 256 bytes on average
+                               and PJ_VERIFY_EXTENSION otherwise */
+  PJ_VERIFY_EXTENSION = 1,  /* extension-based verification of every candidate match
+                               (Sec. 5.2, Alg. 3) */
+  PJ_VERIFY_PAIRS = 2       /* materialised: the candidate pairs are made distinct by a sort and
+                               each distinct pair is verified once over the whole strings with
+                               the length-aware method (Sec. 5.1); same results */
 };
 
 /* A set of n strings; see the conventions above. */
@@ -119,11 +125,14 @@ typedef struct {
   int results_on_device;  /* 1: pj_result.pairs stays in device memory */
   int lazy_partitions;    /* 1: pj_build_index builds only the store; each threshold's
                              segment index is built by the first call that needs it */
-  int autotune;           /* 1: the first self join of a threshold times the thread- and
-                             warp-per-candidate verification kernels and three block sizes
-                             on candidate samples of each probe-length bucket and keeps the
-                             fastest (cached per workload signature for the process, and in
-                             the file named by the environment variable PJ_AUTOTUNE_CACHE) */
+  int autotune;           /* 1: the first self join of a threshold times, on a prefix of its
+                             candidates (probes in length order), every verification
+                             configuration -- extension verification with the thread- /
+                             warp-per-candidate cut-over at each length-bucket edge and block
+                             sizes 128/256/512, and PJ_VERIFY_PAIRS with a thread or a warp
+                             per pair -- and keeps the fastest (cached per workload signature
+                             for the process, and in the file named by the environment
+                             variable PJ_AUTOTUNE_CACHE) */
 } pj_options;
 
 typedef struct pj_index pj_index; /* opaque, library-owned */

@@ -519,6 +519,7 @@ int pj_build_index(const pj_strings* S, int tau_max, const pj_options* opt, pj_i
     idx->results_on_device = opt ? opt->results_on_device != 0 : false;
     idx->lazy = opt ? opt->lazy_partitions != 0 : false;
     idx->autotune = opt ? opt->autotune != 0 : false;
+    idx->verify_mode = opt ? opt->verify_mode : PJ_VERIFY_AUTO;
     PJ_CUDA(cudaGetDevice(&idx->device));
     pj::EventTimer timer(idx->ctx.stream);
     timer.start();

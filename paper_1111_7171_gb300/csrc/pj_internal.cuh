@@ -192,6 +192,7 @@ struct pj_index {
   bool results_on_device = false;
   bool lazy = false;         // thresholds are built on first use
   bool autotune = false;     // tune the verification of each threshold's self join
+  int verify_mode = PJ_VERIFY_AUTO;
   float build_ms = 0.f;
   uint32_t n = 0;
   int lmax = 0;              // longest string

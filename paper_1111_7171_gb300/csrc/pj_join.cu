@@ -340,6 +340,149 @@ __global__ void k_hit_lower_bound(const Hit* __restrict__ hits, unsigned long lo
   *out = lo;
 }
 
+// ------------------------------------------------------ A5 + A6, mode L --
+//
+// Materialised mode: the candidates of a chunk become pair keys, are sorted
+// and made unique, and every distinct pair is verified ONCE over the whole
+// strings with the length-aware VERIFYSTRINGPAIR (Sec. 5.1), which returns
+// min(tau + 1, ED) exactly.  Near-duplicate long strings share a segment
+// match for almost every one of their tau + 1 segments, so extension
+// verification (one DP pass per match) would verify each such pair up to
+// tau + 1 times; here it is verified once.  Keys are made of sids: probe sid
+// (self join) or probe index (R != S) << pshift | indexed sid.
+
+constexpr unsigned long long NO_PAIR = ~0ull;
+
+// Lane l of a warp writes the keys of candidates base + l + 32 k (the walk
+// of k_verify_hits).
+template <bool SELF>
+__global__ void __launch_bounds__(BLOCK) k_pair_keys(const ProbeView v, const Hit* __restrict__ hits,
+                                                     const unsigned long long* __restrict__ cand_off,
+                                                     unsigned long long n_hits, unsigned long long c_begin,
+                                                     unsigned long long c_end, int pshift,
+                                                     unsigned long long* __restrict__ keys, Counters* ctr) {
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned long long n_warps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+  const unsigned long long span = 32ull * V_RUN;
+  int err = 0;
+  for (unsigned long long base = c_begin + warp * span; base < c_end; base += n_warps * span) {
+    unsigned long long c = base + lane;
+    if (c >= c_end) continue;
+    unsigned long long lo = 0, hi = n_hits;
+    while (hi - lo > 1) {
+      const unsigned long long mid = (lo + hi) >> 1;
+      if (cand_off[mid] <= c) lo = mid; else hi = mid;
+    }
+    unsigned long long h = lo;
+    unsigned long long c_lo = cand_off[h];
+    unsigned long long c_hi = h + 1 < n_hits ? cand_off[h + 1] : c_end;
+    Hit hit = hits[h];
+    for (int k = 0; k < V_RUN && c < c_end; ++k, c += 32) {
+      if (c >= c_hi) {
+        do {
+          ++h;
+          c_lo = c_hi;
+          c_hi = h + 1 < n_hits ? cand_off[h + 1] : c_end;
+        } while (c >= c_hi);
+        hit = hits[h];
+      }
+      const uint32_t r = v.postings[hit.begin + (uint32_t)(c - c_lo)];
+      unsigned long long key = NO_PAIR;
+      if (r >= v.n_index) {
+        err |= 1;
+      } else if (!(SELF && r == hit.q)) {
+        const uint32_t x = SELF ? min(hit.q, r) : hit.q, y = SELF ? max(hit.q, r) : r;
+        key = ((unsigned long long)x << pshift) | y;
+      }
+      keys[c - c_begin] = key;
+    }
+  }
+  if (err) atomicOr(&ctr->err, (unsigned long long)err);
+}
+
+__global__ void k_unique_keys(const unsigned long long* __restrict__ keys, const uint32_t* __restrict__ flags,
+                              const uint32_t* __restrict__ pos, unsigned long long n,
+                              unsigned long long* __restrict__ ukeys) {
+  for (unsigned long long k = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (unsigned long long)gridDim.x * blockDim.x)
+    if (flags[k]) ukeys[pos[k]] = keys[k];
+}
+
+// The strings of a pair key (x from the probe side, y from the index side).
+__device__ __forceinline__ void pair_strings(const ProbeView& v, bool self, unsigned long long key, int pshift,
+                                             uint32_t& x, uint32_t& y, const uint8_t*& sx, int& lx,
+                                             const uint8_t*& sy, int& ly) {
+  x = (uint32_t)(key >> pshift);
+  y = (uint32_t)(key & ((1ull << pshift) - 1));
+  sx = v.pbytes + v.poff[x];
+  lx = (int)v.plen[x];
+  sy = v.ibytes + v.ioff[y];
+  ly = (int)v.ilen[y];
+  (void)self;
+}
+
+__device__ __forceinline__ unsigned long long pair_out_key(const ProbeView& v, bool self, uint32_t x, uint32_t y) {
+  const uint32_t qid = v.pid ? v.pid[x] : x;
+  const uint32_t rid = v.iperm[y];
+  const uint32_t ka = self ? min(qid, rid) : qid;
+  const uint32_t kb = self ? max(qid, rid) : rid;
+  return ((unsigned long long)ka << v.key_shift) | kb;
+}
+
+__device__ __forceinline__ void append_match(Counters* ctr, const AccOut& out, unsigned long long key, int ed) {
+  const unsigned long long pos = atomicAdd(&ctr->accepted, 1ull);
+  if (pos < out.cap) {
+    out.key[pos] = key;
+    out.ed[pos] = (uint32_t)ed;
+  }
+}
+
+// One thread per distinct pair.
+template <int MAXW, bool SELF>
+__global__ void __launch_bounds__(BLOCK) k_verify_pairs(const ProbeView v, const unsigned long long* __restrict__ ukeys,
+                                                        unsigned long long n, int pshift, AccOut out, Counters* ctr) {
+  unsigned long long cells = 0;
+  for (unsigned long long u = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; u < n;
+       u += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long key = ukeys[u];
+    if (key == NO_PAIR) continue;
+    uint32_t x, y;
+    const uint8_t *sx, *sy;
+    int lx, ly;
+    pair_strings(v, SELF, key, pshift, x, y, sx, lx, sy, ly);
+    const int d = vsp<MAXW>(sx, lx, sy, ly, v.tau, cells);
+    if (d <= v.tau) append_match(ctr, out, pair_out_key(v, SELF, x, y), d);
+  }
+  add_counter(&ctr->cells, cells);
+}
+
+// One warp per distinct pair (long strings): the shuffle-scan band of
+// vsp_warp; every lane runs the same code on the same pair.
+template <bool SELF>
+__global__ void __launch_bounds__(BLOCK) k_verify_pairs_warp(const ProbeView v,
+                                                             const unsigned long long* __restrict__ ukeys,
+                                                             unsigned long long n, int pshift, AccOut out,
+                                                             Counters* ctr) {
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned long long n_warps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+  unsigned long long cells = 0;
+  for (unsigned long long u = warp; u < n; u += n_warps) {
+    __syncwarp();
+    const unsigned long long key = ukeys[u];
+    if (key == NO_PAIR) continue;  // uniform across the warp
+    uint32_t x, y;
+    const uint8_t *sx, *sy;
+    int lx, ly;
+    pair_strings(v, SELF, key, pshift, x, y, sx, lx, sy, ly);
+    const int d = vsp_warp(sx, lx, sy, ly, v.tau, cells);
+    if (d <= v.tau && lane == 0) append_match(ctr, out, pair_out_key(v, SELF, x, y), d);
+  }
+  __syncwarp();
+  if (lane == 0) add_counter(&ctr->cells, cells);
+}
+
 // ---------------------------------------------------------------- A8 ------
 
 // Pairs whose indexed string is too short to partition (length <= tau).
@@ -427,6 +570,12 @@ static int sm_count() {
     PJ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   }
   return sms;
+}
+
+// Grid for grid-stride loops over `cap` items, 256 threads a block: one wave
+// of at most 8 blocks per SM.
+static unsigned stride_grid(unsigned long long cap) {
+  return (unsigned)std::max<unsigned long long>(1, std::min<unsigned long long>((cap + 255) / 256, 152ull * 8));
 }
 
 template <class K>
@@ -614,6 +763,58 @@ static unsigned long long first_candidate_of(const Ctx& c, const DBuf<Hit>& hits
   return c_cut;
 }
 
+// Mode L for one chunk's candidates [0, n_cand): pair keys, radix sort,
+// distinct pairs, one whole-string verification each.  Returns the number of
+// distinct pairs.
+constexpr unsigned long long PAIR_MODE_MAX_CANDS = 1ull << 27;  // 32 B of scratch per candidate
+
+template <bool SELF>
+static unsigned long long verify_pairs_chunk(const Ctx& c, const ProbeView& v, const Hit* hits,
+                                             const unsigned long long* off, unsigned long long n_hits,
+                                             unsigned long long n_cand, Counters* ctr, AccOut* scratch,
+                                             AcceptBuf* acc) {
+  const int pshift = bits_for(v.n_index);
+  const int nbits = pshift + (SELF ? pshift : bits_for((unsigned long long)v.pbegin + v.pcount));
+  DBuf<unsigned long long> k0(c, n_cand), k1(c, n_cand);
+  DBuf<uint32_t> v0(c, n_cand), v1(c, n_cand);
+  const unsigned g = persistent_grid(k_pair_keys<SELF>, (n_cand + (unsigned long long)BLOCK * V_RUN - 1) /
+                                                            ((unsigned long long)BLOCK * V_RUN));
+  k_pair_keys<SELF><<<g, BLOCK, 0, c.stream>>>(v, hits, off, n_hits, 0, n_cand, pshift, k0.p, ctr);
+  PJ_LAUNCHED("k_pair_keys");
+  const bool second = radix_sort_pairs_dn<unsigned long long>(c, k0.p, v0.p, k1.p, v1.p, n_cand, nullptr, nbits);
+  unsigned long long* sorted = second ? k1.p : k0.p;
+  unsigned long long* ukeys = second ? k0.p : k1.p;
+  DBuf<uint32_t> flags(c, n_cand), pos(c, n_cand);
+  DBuf<unsigned long long> n_unique(c, 1);
+  k_run_heads<<<stride_grid(n_cand), 256, 0, c.stream>>>(sorted, n_cand, flags.p, nullptr);
+  PJ_LAUNCHED("k_run_heads");
+  exclusive_scan_dn<uint32_t>(c, flags.p, pos.p, n_cand, nullptr, n_unique.p);
+  k_unique_keys<<<stride_grid(n_cand), 256, 0, c.stream>>>(sorted, flags.p, pos.p, n_cand, ukeys);
+  PJ_LAUNCHED("k_unique_keys");
+  unsigned long long U = 0;
+  PJ_CUDA(cudaMemcpyAsync(&U, n_unique.p, sizeof(U), cudaMemcpyDeviceToHost, c.stream));
+  c.sync();
+  auto launch = [&](AccOut o) {
+    if (v.pair_warp) {
+      const unsigned gw = persistent_grid(k_verify_pairs_warp<SELF>, (U + BLOCK / 32 - 1) / (BLOCK / 32));
+      k_verify_pairs_warp<SELF><<<gw, BLOCK, 0, c.stream>>>(v, ukeys, U, pshift, o, ctr);
+      PJ_LAUNCHED("k_verify_pairs_warp");
+    } else {
+#define PJ_CALL(W)                                                                                    \
+  do {                                                                                               \
+    const unsigned gt = persistent_grid(k_verify_pairs<W, SELF>, (U + BLOCK - 1) / BLOCK);           \
+    k_verify_pairs<W, SELF><<<gt, BLOCK, 0, c.stream>>>(v, ukeys, U, pshift, o, ctr);                 \
+    PJ_LAUNCHED("k_verify_pairs");                                                                   \
+  } while (0)
+      PJ_BY_TAU(v.tau, PJ_CALL);
+#undef PJ_CALL
+    }
+  };
+  if (acc) acc->run(launch, [&](unsigned long long after) { return 2 * after; });
+  else launch(*scratch);
+  return U;
+}
+
 template <bool SELF, bool MULTI>
 static void probe_and_verify(const Ctx& c, const ProbeView& v0, uint32_t fb_count, AcceptBuf& acc, Counters* ctr,
                              Counters& h, Timings& tm, const unsigned long long* h_qgoff) {
@@ -659,6 +860,16 @@ static void probe_and_verify(const Ctx& c, const ProbeView& v0, uint32_t fb_coun
     h.hits += n_hits;
     total_cand += n_cand;
     const double remaining_groups = (double)(v0.pcount - done - v.pcount) / std::max(1u, v.pcount) + 1.0;  // chunks left
+    if (!MULTI && v.pair_mode && n_cand <= PAIR_MODE_MAX_CANDS) {  // mode L
+      tv.start();
+      verify_pairs_chunk<SELF>(c, v, hits.p, off.p, n_hits, n_cand, ctr, nullptr, &acc);
+      tv.stop();
+      tm.verify += tv.ms();
+      verified += n_cand;
+      trace_mark(c, "join: verify (distinct pairs)");
+      done += v.pcount;
+      continue;
+    }
     // candidates [c_cut, n_cand) belong to long probes: one warp per candidate
     unsigned long long c_cut = n_cand;
     const uint32_t q_cut = aligned_cut(v, v.warp_q_cut);
@@ -800,6 +1011,8 @@ static void run_join(const Ctx& c, const ProbeView& v, bool self, uint32_t fb_co
 struct TuneResult {
   int warp_min_len = 65536;
   int block_thread = 256;
+  int pair_mode = 0;  // mode L
+  int pair_warp = 0;
 };
 
 static std::mutex g_tune_mu;
@@ -826,8 +1039,14 @@ static bool tune_from_file(const std::string& key, TuneResult& r) {
   while (std::getline(f, line)) {
     const size_t a = line.find('|'), b = line.rfind('|');
     if (a == std::string::npos || a == b || line.substr(0, a) != key) continue;
+    // signature|cut|block|pairs (pairs: 0 extension, 1 thread per pair, 2 warp per pair)
+    const size_t m = line.find('|', a + 1);
+    if (m == std::string::npos || m == b) continue;
     r.warp_min_len = atoi(line.c_str() + a + 1);
-    r.block_thread = atoi(line.c_str() + b + 1);
+    r.block_thread = atoi(line.c_str() + m + 1);
+    const int pm = atoi(line.c_str() + b + 1);
+    r.pair_mode = pm > 0;
+    r.pair_warp = pm == 2;
     found = true;  // the last line for a key wins
   }
   return found;
@@ -838,7 +1057,7 @@ static void tune_to_file(const std::string& key, const TuneResult& r) {
   if (!path || !path[0]) return;
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%s|%d|%d\n", key.c_str(), r.warp_min_len, r.block_thread);
+  fprintf(f, "%s|%d|%d|%d\n", key.c_str(), r.warp_min_len, r.block_thread, r.pair_mode ? 1 + r.pair_warp : 0);
   fclose(f);
 }
 
@@ -905,9 +1124,65 @@ static TuneResult autotune_self(pj_index& idx, const ProbeView& v0) {
       }
     }
   }
+  // mode L on the same candidates: pair keys, sort, distinct pairs, one
+  // whole-string verification each (thread or warp per pair)
+  if (S <= PAIR_MODE_MAX_CANDS) {
+    for (int pw = 0; pw < 2; ++pw) {
+      ProbeView vp = v;
+      vp.pair_mode = 1;
+      vp.pair_warp = pw;
+      double ms = 1e30;
+      for (int rep = 0; rep < 2; ++rep) {
+        PJ_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(Counters), c.stream));
+        AccOut sc = scratch;
+        tm.start();
+        verify_pairs_chunk<true>(c, vp, hits.p, off.p, n_hits, S, ctr.p, &sc, nullptr);
+        tm.stop();
+        ms = std::min(ms, (double)tm.ms());
+      }
+      if (getenv("PJ_TRACE"))
+        fprintf(stderr, "[pj] autotune tau=%d distinct pairs (%s): %.3f ms over %llu candidates\n", tau,
+                pw ? "warp" : "thread", ms, (unsigned long long)S);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best.pair_mode = 1;
+        best.pair_warp = pw;
+      }
+    }
+  }
   if (getenv("PJ_TRACE"))
-    fprintf(stderr, "[pj] autotune tau=%d: warp from length %d, block %d\n", tau, best.warp_min_len, best.block_thread);
+    fprintf(stderr, "[pj] autotune tau=%d: warp from length %d, block %d, distinct pairs %d (warp %d)\n", tau,
+            best.warp_min_len, best.block_thread, best.pair_mode, best.pair_warp);
   return best;
+}
+
+// Strings longer than this on average are verified in mode L by default:
+// near-duplicate long strings match on most of their segments.
+constexpr double PAIR_MODE_MIN_AVG_LEN = 256.0;
+
+static void default_mode(const pj_index& idx, TuneResult& r) {
+  const double avg = idx.n ? (double)idx.total_bytes / idx.n : 0.0;
+  r.pair_mode = avg > PAIR_MODE_MIN_AVG_LEN ? 1 : 0;
+  r.pair_warp = r.pair_mode;
+}
+
+// The index's verify_mode option, then PJ_VERIFY_PAIRS=0|1|2 (extension,
+// thread per pair, warp per pair), override the choice.
+static void force_mode(const pj_index& idx, TuneResult& r) {
+  if (idx.verify_mode == PJ_VERIFY_EXTENSION) {
+    r.pair_mode = 0;
+  } else if (idx.verify_mode == PJ_VERIFY_PAIRS && !r.pair_mode) {
+    TuneResult d;
+    default_mode(idx, d);
+    r.pair_mode = 1;
+    r.pair_warp = d.pair_warp;
+  }
+  const char* pm = getenv("PJ_VERIFY_PAIRS");
+  if (pm && pm[0]) {
+    const int m = atoi(pm);
+    r.pair_mode = m > 0;
+    r.pair_warp = m == 2;
+  }
 }
 
 // The tuning of a self join: environment overrides, then the caches, then a
@@ -931,6 +1206,8 @@ static TuneResult self_join_tuning(pj_index& idx, const ProbeView& v, float* tun
       tune_to_file(key, r);
     }
   }
+  if (!idx.autotune) default_mode(idx, r);
+  force_mode(idx, r);
   const char* e = getenv("PJ_WARP_MIN_LEN");
   if (e && e[0]) r.warp_min_len = atoi(e);
   const char* bk = getenv("PJ_VERIFY_BLOCK");
@@ -1001,6 +1278,8 @@ static void self_join_impl(pj_index& idx, int tau, pj_result* out, bool on_devic
   const TuneResult tr = self_join_tuning(idx, v, &tune_ms);
   if (tr.warp_min_len <= idx.lmax) v.warp_q_cut = idx.h_bbeg[std::max(0, tr.warp_min_len)];
   v.block_thread = tr.block_thread;
+  v.pair_mode = tr.pair_mode;
+  v.pair_warp = tr.pair_warp;
   run_join(idx.ctx, v, true, part.first, bits_for(idx.n), on_device, out);
   out->stats.partition_ms = part_ms;
   out->stats.verify_block = tr.block_thread;
@@ -1019,6 +1298,11 @@ static void probe_join_impl(const Ctx& c, const pj_index& idx, const Partition& 
   v.pid = nullptr;
   v.key_shift = bits_for(idx.n);
   v.gorder = part.gorder[0].p;
+  TuneResult mode;
+  default_mode(idx, mode);
+  force_mode(idx, mode);
+  v.pair_mode = mode.pair_mode;
+  v.pair_warp = mode.pair_warp;
   const bool has_short = part.first > 0;  // indexed strings too short to partition
   run_join(c, v, false, has_short ? R.n : 0, bits_for(R.n), on_device, out);
 }
@@ -1109,10 +1393,6 @@ __global__ void k_plan_finish(const Counters* __restrict__ ctr, const PlanSizes*
   h.fallback = ctr->fallback;
   h.err = ctr->err;
   *header = h;
-}
-
-static unsigned stride_grid(unsigned long long cap) {
-  return (unsigned)std::max<unsigned long long>(1, std::min<unsigned long long>((cap + 255) / 256, 152ull * 8));
 }
 
 void record_query_plan(const Ctx& c, const pj_index& idx, const PlanDev& d) {
@@ -1221,6 +1501,7 @@ int pj_join(const pj_strings* R, const pj_strings* S, int tau, const pj_options*
     tmp = new pj_index();
     tmp->ctx = pj::make_ctx(opt);
     tmp->results_on_device = opt ? opt->results_on_device != 0 : false;
+    tmp->verify_mode = opt ? opt->verify_mode : PJ_VERIFY_AUTO;
     PJ_CUDA(cudaGetDevice(&tmp->device));
     pj::build_store(*tmp, *S);
     tmp->parts.resize(tau + 1);

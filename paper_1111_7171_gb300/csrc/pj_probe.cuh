@@ -69,6 +69,8 @@ struct ProbeView {
   int block_thread;  // block size of the thread-per-candidate verification
   int interleave;    // probe groups interleaved across probes (see group_of)
   const uint16_t* gorder;  // groups of one probe in visiting order (NULL: natural order)
+  int pair_mode;  // 1: mode L (distinct candidate pairs verified once over the whole strings)
+  int pair_warp;  // mode L: one warp per pair instead of one thread
   int block_warp;    // block size of the warp-per-candidate verification
 };
 

@@ -308,6 +308,29 @@ def test_probe_interleaving_both_ways(monkeypatch, mode):
     assert_same(pj.pj_join(R, S, 2).pairs, oracle.join(rb, ro, sb, so, 2), f"join interleave={mode}")
 
 
+@pytest.mark.parametrize("mode", ["1", "2"])
+def test_distinct_pair_verification(monkeypatch, mode):
+    """Mode L: candidate pairs made distinct by a sort and verified once over
+    the whole strings (thread per pair 1, warp per pair 2): same exact
+    result, for self joins (with chunks and a growing accepted buffer) and
+    R x S joins."""
+    monkeypatch.setenv("PJ_VERIFY_PAIRS", mode)
+    cases = [("short2k", 2, 2000, False), ("short", 4, 3000, False), ("medium", 8, 2500, True),
+             ("long", 32, 600, True), ("long", 8, 600, True)]
+    for name, tau, n, banded in cases:
+        strings = synth.generate(name, tau, n=n)
+        r = gpu_self(strings, tau)
+        assert_same(r.pairs, cpu_self(strings, tau, banded=banded), f"{name} tau={tau} pairs={mode}")
+    monkeypatch.setenv("PJ_GROUP_BUDGET", "3000")
+    monkeypatch.setenv("PJ_ACCEPT_INITIAL", "5")
+    strings = synth.generate("short", 3, n=3000)
+    assert_same(gpu_self(strings, 3).pairs, cpu_self(strings, 3), f"chunked pairs={mode}")
+    R, S = _rs_sets(7, 3)
+    rb, ro = synth.pack(R)
+    sb, so = synth.pack(S)
+    assert_same(pj.pj_join(R, S, 3).pairs, oracle.join(rb, ro, sb, so, 3), f"join pairs={mode}")
+
+
 def test_autotuned_self_join(monkeypatch, tmp_path):
     """The autotuner picks the cut-over and block size per workload signature
     (cached for the process and in PJ_AUTOTUNE_CACHE); results stay exact."""
@@ -328,4 +351,4 @@ def test_autotuned_self_join(monkeypatch, tmp_path):
         assert r2.stats["tune_ms"] == 0.0  # decision cached
         assert (r1.stats["warp_min_len"], r1.stats["verify_block"]) == (r2.stats["warp_min_len"], r2.stats["verify_block"])
     lines = cache.read_text().strip().splitlines()
-    assert len(lines) == 2 and all(line.count("|") == 2 for line in lines)
+    assert len(lines) == 2 and all(line.count("|") == 3 for line in lines)
