@@ -495,7 +495,9 @@ def run_native(args):
                          "probe": probe_ms, "verify": verify_ms,
                          "fallback": statistics.mean(s["fallback_ms"] for s in stats_all),
                          "dedupe": statistics.mean(s["dedupe_ms"] for s in stats_all)},
-            "tuning": {"verify_block": int(st["verify_block"]), "warp_per_candidate_from_length": int(st["warp_min_len"]),
+            "tuning": {"verify_mode": "distinct pairs" if st["verify_mode"] == 2 else "extension",
+                       "pair_per": "warp" if st["pair_warp"] else "thread",
+                       "verify_block": int(st["verify_block"]), "warp_per_candidate_from_length": int(st["warp_min_len"]),
                        "note": "autotuned in the warm-up steps (cached per workload signature)"},
             "roofline": roofline,
             "cpu_baseline": cpu,

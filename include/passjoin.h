@@ -101,6 +101,8 @@ typedef struct {
   int32_t verify_block; /* block size of the thread-per-candidate verification */
   int32_t warp_min_len; /* self join: probes at least this long were verified one warp per candidate */
   float tune_ms;        /* time spent autotuning during this call (0 when the decision was cached) */
+  int32_t verify_mode;  /* PJ_VERIFY_EXTENSION or PJ_VERIFY_PAIRS, as run */
+  int32_t pair_warp;    /* PJ_VERIFY_PAIRS: 1 when one warp verified each pair */
 } pj_stats;
 
 typedef struct {

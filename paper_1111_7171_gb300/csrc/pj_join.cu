@@ -876,7 +876,11 @@ static void probe_and_verify(const Ctx& c, const ProbeView& v0, uint32_t fb_coun
     if (SELF && !MULTI && q_cut < v.pbegin + v.pcount) c_cut = first_candidate_of(c, hits, off, n_hits, n_cand, q_cut);
     for (unsigned long long cb = 0; cb < n_cand;) {
       const bool warp_range = cb >= c_cut;
-      const unsigned long long ce = std::min(warp_range ? n_cand : c_cut, cb + launch_cands);
+      // the join's first launch is short, so that the accepted-match buffer is
+      // sized from its acceptance rate before the long launches run
+      const unsigned long long step =
+          verified == 0 ? std::min(launch_cands, std::max(1ull << 22, n_cand / 64)) : launch_cands;
+      const unsigned long long ce = std::min(warp_range ? n_cand : c_cut, cb + step);
       tv.start();
       acc.run(
           [&](AccOut o) {
@@ -1285,6 +1289,8 @@ static void self_join_impl(pj_index& idx, int tau, pj_result* out, bool on_devic
   out->stats.verify_block = tr.block_thread;
   out->stats.warp_min_len = tr.warp_min_len;
   out->stats.tune_ms = tune_ms;
+  out->stats.verify_mode = tr.pair_mode ? PJ_VERIFY_PAIRS : PJ_VERIFY_EXTENSION;
+  out->stats.pair_warp = tr.pair_mode ? tr.pair_warp : 0;
 }
 
 static void probe_join_impl(const Ctx& c, const pj_index& idx, const Partition& part, const ProbeSet& R,
@@ -1305,6 +1311,8 @@ static void probe_join_impl(const Ctx& c, const pj_index& idx, const Partition& 
   v.pair_warp = mode.pair_warp;
   const bool has_short = part.first > 0;  // indexed strings too short to partition
   run_join(c, v, false, has_short ? R.n : 0, bits_for(R.n), on_device, out);
+  out->stats.verify_mode = mode.pair_mode ? PJ_VERIFY_PAIRS : PJ_VERIFY_EXTENSION;
+  out->stats.pair_warp = mode.pair_mode ? mode.pair_warp : 0;
 }
 
 void query_multi_impl(const Ctx& c, pj_index& idx, const ProbeSet& R, const uint8_t* h_tau, pj_result* out,

@@ -94,43 +94,144 @@ __host__ __device__ __forceinline__ int vsp_band(const uint8_t* a, int na, const
   return res;
 }
 
+// VERIFYSTRINGPAIR for narrow bands, with the band width W and the diagonal
+// of the result KRES = D - dlo fixed at compile time.  Row 0 holds
+// M(0, j) = |j| (the real values for j >= 0, and for j < 0 a virtual
+// extension of b that only ever yields values >= min(i + |j|, t + 2) in row
+// i, so cells <= t stay exact).  Then neighbouring cells of a row differ by
+// at most 1 -- left to right by the recurrence, right to left by induction
+// over the rows -- so E(i, k) = V[k] + |KRES - k| is smallest at k = KRES
+// and the Lemma 4 test over the row is the single test V[KRES] > t.
+template <int W, int KRES>
+__host__ __device__ __forceinline__ int vsp_band_k(const uint8_t* a, int na, const uint8_t* b, int nb, int t,
+                                                   int dlo, int w, unsigned long long& cells) {
+  constexpr int KR = KRES < W ? KRES : W - 1;  // instances with KRES >= W are never called
+  const int cap = t + 1;
+  const int blast = nb - 1;
+  int V[W];
+  uint8_t B[W];
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    const int j = dlo + k;
+    V[k] = abs(j);
+    B[k] = b[min(max(j, 0), blast)];
+  }
+  bool alive = true;
+  int rows = 0;
+  for (int i = 1; i <= na; ++i) {
+    const uint8_t ca = a[i - 1];
+    int left = cap;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      const int up = (k + 1 < W) ? V[k + 1] : cap;
+      const int diag = V[k] + (ca != B[k] ? 1 : 0);
+      const int val = min(diag, min(up, left) + 1);
+      V[k] = val;
+      left = val;
+    }
+    ++rows;
+    if (V[KR] > t) {  // Lemma 4 (see above)
+      alive = false;
+      break;
+    }
+    const int jn = i + dlo + W - 1;
+#pragma unroll
+    for (int k = 0; k + 1 < W; ++k) B[k] = B[k + 1];
+    B[W - 1] = b[min(max(jn, 0), blast)];
+  }
+  cells += (unsigned long long)(rows * w);
+  return alive ? min(V[KR], cap) : cap;
+}
+
+// Everything of one VERIFYSTRINGPAIR call that depends only on the lengths
+// and the threshold: in extension verification it is the same for every
+// candidate of a posting run (same probe, position, segment and indexed
+// length), so it is prepared once per run.
+struct VspPlan {
+  int t, na, nb;     // a = the shorter part
+  int dlo, w, kres;  // band start, length-aware width, diagonal of the result
+  int kind;          // 0: D > t, 1: a empty (result D), 2: t = 0 (exact compare), 3: band
+  int W;             // band registers (3: 2, 3, 5, 9, 17 or 33)
+  bool swap;         // a is the y part
+};
+
+__host__ __device__ __forceinline__ VspPlan vsp_plan(int nx, int ny, int t, int maxw) {
+  VspPlan p;
+  p.t = t;
+  p.swap = nx > ny;
+  p.na = p.swap ? ny : nx;
+  p.nb = p.swap ? nx : ny;
+  const int D = p.nb - p.na;
+  p.dlo = -((t - D) >> 1);
+  p.w = ((t + D) >> 1) - p.dlo + 1;
+  p.kres = D - p.dlo;
+  p.kind = D > t ? 0 : p.na == 0 ? 1 : t == 0 ? 2 : 3;
+  const int need = t + 1;
+  p.W = need <= 2 ? 2 : need <= 3 ? 3 : need <= 5 ? 5 : need <= 9 ? 9 : need <= 17 ? 17 : 33;
+  if (p.W > maxw) p.W = maxw;
+  return p;
+}
+
+#define PJ_KRES_CASES_2(W) case 0: r = vsp_band_k<W, 0>(a, p.na, b, p.nb, p.t, p.dlo, p.w, cells); break; \
+                           case 1: r = vsp_band_k<W, 1>(a, p.na, b, p.nb, p.t, p.dlo, p.w, cells); break;
+#define PJ_KRES_CASES_3(W) PJ_KRES_CASES_2(W) \
+                           case 2: r = vsp_band_k<W, 2>(a, p.na, b, p.nb, p.t, p.dlo, p.w, cells); break;
+#define PJ_KRES_CASES_5(W) PJ_KRES_CASES_3(W) \
+                           case 3: r = vsp_band_k<W, 3>(a, p.na, b, p.nb, p.t, p.dlo, p.w, cells); break; \
+                           case 4: r = vsp_band_k<W, 4>(a, p.na, b, p.nb, p.t, p.dlo, p.w, cells); break;
+#define PJ_KRES_CASES_9(W) PJ_KRES_CASES_5(W) \
+                           case 5: r = vsp_band_k<W, 5>(a, p.na, b, p.nb, p.t, p.dlo, p.w, cells); break; \
+                           case 6: r = vsp_band_k<W, 6>(a, p.na, b, p.nb, p.t, p.dlo, p.w, cells); break; \
+                           case 7: r = vsp_band_k<W, 7>(a, p.na, b, p.nb, p.t, p.dlo, p.w, cells); break; \
+                           case 8: r = vsp_band_k<W, 8>(a, p.na, b, p.nb, p.t, p.dlo, p.w, cells); break;
+
+// VERIFYSTRINGPAIR (Alg. 3) of x and y with a prepared plan: min(t + 1, ED).
+template <int MAXW>
+__host__ __device__ __forceinline__ int vsp_run(const VspPlan& p, const uint8_t* x, const uint8_t* y,
+                                                unsigned long long& cells) {
+  const uint8_t* a = p.swap ? y : x;
+  const uint8_t* b = p.swap ? x : y;
+  int r = p.t + 1;
+  if (p.kind == 1) {
+    r = p.nb - p.na;
+  } else if (p.kind == 2) {  // exact match of equal lengths
+    bool eq = true;
+    for (int k = 0; k < p.na; ++k) {
+      if (a[k] != b[k]) {
+        eq = false;
+        break;
+      }
+    }
+    cells += (unsigned long long)p.na;
+    r = eq ? 0 : 1;
+  } else if (p.kind == 3) {
+    if (p.W <= 2 || MAXW <= 2) {
+      switch (p.kres) { PJ_KRES_CASES_2((MAXW < 2 ? MAXW : 2)) }
+    } else if (p.W <= 3 || MAXW <= 3) {
+      switch (p.kres) { PJ_KRES_CASES_3((MAXW < 3 ? MAXW : 3)) }
+    } else if (p.W <= 5 || MAXW <= 5) {
+      switch (p.kres) { PJ_KRES_CASES_5((MAXW < 5 ? MAXW : 5)) }
+    } else if (p.W <= 9 || MAXW <= 9) {
+      switch (p.kres) { PJ_KRES_CASES_9((MAXW < 9 ? MAXW : 9)) }
+    } else if (p.W <= 17 || MAXW <= 17) {
+      r = vsp_band<(MAXW < 17 ? MAXW : 17)>(a, p.na, b, p.nb, p.t, cells);
+    } else {
+      r = vsp_band<MAXW>(a, p.na, b, p.nb, p.t, cells);
+    }
+  }
+  return r;
+}
+
+#undef PJ_KRES_CASES_2
+#undef PJ_KRES_CASES_3
+#undef PJ_KRES_CASES_5
+#undef PJ_KRES_CASES_9
+
+// VERIFYSTRINGPAIR (Alg. 3): min(t + 1, ED(x, y)), t <= MAXW - 1.
 template <int MAXW>
 __host__ __device__ __forceinline__ int vsp(const uint8_t* x, int nx, const uint8_t* y, int ny, int t,
                                             unsigned long long& cells) {
-  const uint8_t* a = nx <= ny ? x : y;
-  const uint8_t* b = nx <= ny ? y : x;
-  const int na = nx <= ny ? nx : ny;
-  const int nb = nx <= ny ? ny : nx;
-  const int D = nb - na;
-  int res = t + 1;
-  if (D <= t) {
-    if (na == 0) {
-      res = D;
-    } else if (t == 0) {  // exact match of equal lengths
-      bool eq = true;
-      for (int k = 0; k < na; ++k) {
-        if (a[k] != b[k]) {
-          eq = false;
-          break;
-        }
-      }
-      cells += (unsigned long long)na;
-      res = eq ? 0 : 1;
-    } else if (t + 1 <= 2 || MAXW <= 2) {
-      res = vsp_band<(MAXW < 2 ? MAXW : 2)>(a, na, b, nb, t, cells);
-    } else if (t + 1 <= 3 || MAXW <= 3) {
-      res = vsp_band<(MAXW < 3 ? MAXW : 3)>(a, na, b, nb, t, cells);
-    } else if (t + 1 <= 5 || MAXW <= 5) {
-      res = vsp_band<(MAXW < 5 ? MAXW : 5)>(a, na, b, nb, t, cells);
-    } else if (t + 1 <= 9 || MAXW <= 9) {
-      res = vsp_band<(MAXW < 9 ? MAXW : 9)>(a, na, b, nb, t, cells);
-    } else if (t + 1 <= 17 || MAXW <= 17) {
-      res = vsp_band<(MAXW < 17 ? MAXW : 17)>(a, na, b, nb, t, cells);
-    } else {
-      res = vsp_band<MAXW>(a, na, b, nb, t, cells);
-    }
-  }
-  return res;
+  return vsp_run<MAXW>(vsp_plan(nx, ny, t, MAXW), x, y, cells);
 }
 
 #ifdef __CUDACC__

@@ -47,7 +47,8 @@ class pj_stats(ctypes.Structure):
                 ("dp_cells", ctypes.c_uint64), ("fallback_pairs", ctypes.c_uint64), ("hits", ctypes.c_uint64),
                 ("probe_ms", ctypes.c_float), ("verify_ms", ctypes.c_float), ("fallback_ms", ctypes.c_float),
                 ("dedupe_ms", ctypes.c_float), ("partition_ms", ctypes.c_float), ("verify_block", ctypes.c_int32),
-                ("warp_min_len", ctypes.c_int32), ("tune_ms", ctypes.c_float)]
+                ("warp_min_len", ctypes.c_int32), ("tune_ms", ctypes.c_float), ("verify_mode", ctypes.c_int32),
+                ("pair_warp", ctypes.c_int32)]
 
 
 class pj_result(ctypes.Structure):
@@ -326,7 +327,8 @@ def _stats(st: pj_stats) -> dict:
                 dp_cells=int(st.dp_cells), fallback_pairs=int(st.fallback_pairs), hits=int(st.hits),
                 probe_ms=float(st.probe_ms), verify_ms=float(st.verify_ms), fallback_ms=float(st.fallback_ms),
                 dedupe_ms=float(st.dedupe_ms), partition_ms=float(st.partition_ms),
-                verify_block=int(st.verify_block), warp_min_len=int(st.warp_min_len), tune_ms=float(st.tune_ms))
+                verify_block=int(st.verify_block), warp_min_len=int(st.warp_min_len), tune_ms=float(st.tune_ms),
+                verify_mode=int(st.verify_mode), pair_warp=int(st.pair_warp))
 
 
 def _take(res: pj_result):
