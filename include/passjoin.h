@@ -103,6 +103,9 @@ typedef struct {
   float tune_ms;        /* time spent autotuning during this call (0 when the decision was cached) */
   int32_t verify_mode;  /* PJ_VERIFY_EXTENSION or PJ_VERIFY_PAIRS, as run */
   int32_t pair_warp;    /* PJ_VERIFY_PAIRS: 1 when one warp verified each pair */
+  uint64_t filtered;    /* candidates rejected before any DP by the character-set bound
+                           ED(x, y) >= max |chars(x) \ chars(y)|, |chars(y) \ chars(x)|
+                           (characters taken mod 64); not part of Pass-Join, exact */
 } pj_stats;
 
 typedef struct {

@@ -160,6 +160,13 @@ __global__ void k_gather(const uint8_t* __restrict__ in_bytes, const uint64_t* _
   }
 }
 
+// Character bitmaps of n strings (bytes[off[k] .. off[k+1])), one thread each.
+__global__ void k_bitmaps(const uint8_t* __restrict__ bytes, const uint64_t* __restrict__ off, uint32_t n,
+                          unsigned long long* __restrict__ bm) {
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+    bm[k] = char_bitmap(bytes + off[k], (int)(off[k + 1] - off[k]));
+}
+
 // bbeg[l] = first sid whose length is >= l, for l = 0 .. lmax + 1.
 __global__ void k_buckets(const uint32_t* __restrict__ slen, uint32_t n, uint32_t* __restrict__ bbeg, int lmax) {
   const uint32_t sid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -302,6 +309,12 @@ void build_store(pj_index& idx, const pj_strings& S) {
     const unsigned blocks = std::min<unsigned>(ceil_div((size_t)n * 32, 256), 152u * 16u);
     k_gather<<<blocks, 256, 0, c.stream>>>(in_bytes, in_off, idx.perm.p, idx.soff.p, idx.sbytes.p, n);
     PJ_LAUNCHED("k_gather");
+  }
+  idx.sbm.reset(c, n ? n : 1);
+  if (n) {
+    k_bitmaps<<<std::min<unsigned>(ceil_div(n, 256), 152u * 8u), 256, 0, c.stream>>>(idx.sbytes.p, idx.soff.p, n,
+                                                                                    idx.sbm.p);
+    PJ_LAUNCHED("k_bitmaps");
   }
   idx.bbeg.reset(c, (size_t)idx.lmax + 2);
   k_buckets<<<ceil_div((size_t)n + 1, 256), 256, 0, c.stream>>>(idx.slen.p, n, idx.bbeg.p, idx.lmax);
@@ -483,6 +496,11 @@ void upload_probe_set(const Ctx& c, const pj_strings& R, ProbeSet& out) {
   c.sync();
   if (h_err) fail(PJ_EINVAL, "pj_strings: offsets decrease or a string is longer than 65535 bytes");
   out.lmax = (int)h_lmax;
+  out.bm.reset(c, R.n ? R.n : 1);
+  if (R.n) {
+    k_bitmaps<<<std::min<unsigned>(ceil_div(R.n, 256), 152u * 8u), 256, 0, c.stream>>>(dbytes, doff, R.n, out.bm.p);
+    PJ_LAUNCHED("k_bitmaps");
+  }
   out.bytes = dbytes;
   out.off = doff;
   out.own_bytes = std::move(bb);
@@ -494,7 +512,7 @@ void upload_probe_set(const Ctx& c, const pj_strings& R, ProbeSet& out) {
 // ------------------------------------------------------------------ C ABI --
 
 uint64_t pj_index::device_bytes() const {
-  uint64_t b = sbytes.bytes() + soff.bytes() + slen.bytes() + perm.bytes() + bbeg.bytes();
+  uint64_t b = sbytes.bytes() + soff.bytes() + slen.bytes() + perm.bytes() + bbeg.bytes() + sbm.bytes();
   for (const auto& p : parts)
     b += p.table.bytes() + p.fp.bytes() + p.postings.bytes() + p.gorder[0].bytes() + p.gorder[1].bytes();
   return b;

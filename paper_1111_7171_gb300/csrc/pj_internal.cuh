@@ -131,6 +131,33 @@ __host__ __device__ __forceinline__ uint8_t key_fp(unsigned long long key, uint3
   return f ? f : (uint8_t)1;
 }
 
+// Character-set bound.  A string's bitmap has bit (c mod 64) set for every
+// byte c it contains.  A bit set in one bitmap and clear in the other stands
+// for at least one character of that string that is absent from the other,
+// and distinct bits stand for distinct characters; each needs its own edit
+// (a substitution removes at most one such character from each side), so
+//   ED(x, y) >= max(popcount(bx & ~by), popcount(by & ~bx)).
+// Candidates whose bound exceeds tau are rejected before any DP.  This test
+// is not part of Pass-Join; it only drops pairs that cannot be similar.
+__host__ __device__ __forceinline__ unsigned long long char_bitmap(const uint8_t* p, int n) {
+  unsigned long long b = 0;
+  for (int k = 0; k < n; ++k) b |= 1ull << (p[k] & 63);
+  return b;
+}
+
+__host__ __device__ __forceinline__ int popcount64(unsigned long long x) {
+#ifdef __CUDA_ARCH__
+  return __popcll(x);
+#else
+  return __builtin_popcountll(x);
+#endif
+}
+
+__host__ __device__ __forceinline__ int bitmap_bound(unsigned long long bx, unsigned long long by) {
+  const int a = popcount64(bx & ~by), b = popcount64(by & ~bx);
+  return a > b ? a : b;
+}
+
 // Longest linear-probe sequence a lookup follows.  At load factor <= 1/2 a
 // run of this many occupied slots does not occur in a correct table, so a
 // lookup that reaches it reports an inconsistent index instead of scanning.
@@ -202,6 +229,7 @@ struct pj_index {
   pj::DBuf<uint32_t> slen;   // lengths by sid
   pj::DBuf<uint32_t> perm;   // sid -> input id
   pj::DBuf<uint32_t> bbeg;   // lmax + 2 bucket starts by length
+  pj::DBuf<unsigned long long> sbm;  // character bitmaps by sid (char_bitmap)
   std::vector<uint32_t> h_bbeg;
   std::vector<pj::Partition> parts;  // index = tau
   uint64_t device_bytes() const;
@@ -224,6 +252,7 @@ struct ProbeSet {
   const uint8_t* bytes = nullptr;  // string k = bytes[off[k] .. off[k+1])
   const uint64_t* off = nullptr;
   DBuf<uint32_t> len;
+  DBuf<unsigned long long> bm;  // character bitmaps
   uint32_t n = 0;
   int lmax = 0;
 };

@@ -44,7 +44,7 @@ struct Counters {
   unsigned long long fallback;
   unsigned long long hits;
   unsigned long long err;  // bit 0: run or posting outside the index; bit 1: probe limit
-  unsigned long long pad;
+  unsigned long long filtered;  // candidates rejected by the character-set bound
 };
 
 struct AccOut {
@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(512) k_verify_hits(const ProbeView v, const Hi
     n_hits = min(n_hits, dn[0]);
     n_cand = dn[1];
   }
-  unsigned long long cells = 0;
+  unsigned long long cells = 0, filtered = 0;
   int err = 0;
   const unsigned lane = threadIdx.x & 31u;
   const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(512) k_verify_hits(const ProbeView v, const Hi
       }
       unsigned long long key = 0;
       int ed = 0;
-      if (verify_in_hit<MAXW>(vt, SELF, hc, (uint32_t)(c - c_lo), key, ed, cells, err)) {
+      if (verify_in_hit<MAXW>(vt, SELF, hc, (uint32_t)(c - c_lo), key, ed, cells, filtered, err)) {
         const unsigned long long pos = atomicAdd(&ctr->accepted, 1ull);
         if (pos < out.cap) {
           out.key[pos] = key;
@@ -285,6 +285,106 @@ __global__ void __launch_bounds__(512) k_verify_hits(const ProbeView v, const Hi
     }
   }
   add_counter(&ctr->cells, cells);
+  add_counter(&ctr->filtered, filtered);
+  if (err) atomicOr(&ctr->err, (unsigned long long)err);
+}
+
+// The same verification with a screen and a per-warp queue: every lane
+// first screens its candidate (valid sid, not the probe, character-set
+// bound) -- cheap and uniform code -- and the survivors are appended to a
+// queue in shared memory; whenever 32 are queued, each lane takes one and
+// runs extension verification.  Screened-out candidates then cost no DP
+// slot, so the warps' DP lanes stay full.  The warp-wide ballot sits in a
+// loop whose trip count is the same for all 32 lanes, and the queue is read
+// before the next writes only after a __syncwarp.
+constexpr int Q_BLOCK = 256;
+constexpr int Q_WARPS = Q_BLOCK / 32;
+constexpr int Q_CAP = 64;  // entries per warp: < 32 left + 32 new
+
+template <int MAXW, bool SELF, bool MULTI>
+__global__ void __launch_bounds__(Q_BLOCK) k_verify_queued(const ProbeView v, const Hit* __restrict__ hits,
+                                                            const unsigned long long* __restrict__ cand_off,
+                                                            unsigned long long n_hits, unsigned long long c_begin,
+                                                            unsigned long long n_cand, AccOut out, Counters* ctr,
+                                                            const unsigned long long* __restrict__ dn) {
+  __shared__ uint32_t q_hit[Q_WARPS][Q_CAP];
+  __shared__ uint32_t q_sid[Q_WARPS][Q_CAP];
+  if (dn) {
+    n_hits = min(n_hits, dn[0]);
+    n_cand = dn[1];
+  }
+  unsigned long long cells = 0, filtered = 0;
+  int err = 0;
+  const unsigned lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
+  const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned long long n_warps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+  const unsigned long long span = 32ull * V_RUN;
+  int qn = 0;  // the same in every lane
+  auto verify_entry = [&](uint32_t h, uint32_t r) {
+    const Hit hit = hits[h];
+    const ProbeView vt = MULTI ? view_for_tau(v, (int)(hit.pi >> 24)) : v;
+    unsigned long long key = 0;
+    int ed = 0;
+    if (verify_screened<MAXW>(vt, SELF, hit_ctx(vt, hit), r, key, ed, cells)) {
+      const unsigned long long pos = atomicAdd(&ctr->accepted, 1ull);
+      if (pos < out.cap) {
+        out.key[pos] = key;
+        out.ed[pos] = (uint32_t)ed;
+      }
+    }
+  };
+  for (unsigned long long base = c_begin + warp * span; base < n_cand; base += n_warps * span) {
+    unsigned long long c = base + lane;
+    unsigned long long h = 0, c_lo = 0, c_hi = 0;
+    Hit hit{};
+    if (c < n_cand) {
+      unsigned long long lo = 0, hi = n_hits;  // last hit whose first candidate is <= c
+      while (hi - lo > 1) {
+        const unsigned long long mid = (lo + hi) >> 1;
+        if (cand_off[mid] <= c) lo = mid; else hi = mid;
+      }
+      h = lo;
+      c_lo = cand_off[h];
+      c_hi = h + 1 < n_hits ? cand_off[h + 1] : n_cand;
+      hit = hits[h];
+    }
+    for (int k = 0; k < V_RUN; ++k, c += 32) {  // the same trip count in every lane
+      bool pass = false;
+      uint32_t r = 0;
+      if (c < n_cand) {
+        if (c >= c_hi) {
+          do {
+            ++h;
+            c_lo = c_hi;
+            c_hi = h + 1 < n_hits ? cand_off[h + 1] : n_cand;
+          } while (c >= c_hi);
+          hit = hits[h];
+        }
+        const ProbeView vt = MULTI ? view_for_tau(v, (int)(hit.pi >> 24)) : v;
+        r = vt.postings[hit.begin + (uint32_t)(c - c_lo)];
+        pass = screen_candidate(vt, SELF, hit.q, r, filtered, err);
+      }
+      __syncwarp();
+      const unsigned m = __ballot_sync(FULL, pass);
+      if (pass) {
+        const int slot = qn + __popc(m & lanemask_lt());
+        q_hit[wib][slot] = (uint32_t)h;
+        q_sid[wib][slot] = r;
+      }
+      qn += __popc(m);
+      __syncwarp();
+      if (qn >= 32) {
+        qn -= 32;
+        const uint32_t eh = q_hit[wib][qn + lane], er = q_sid[wib][qn + lane];
+        __syncwarp();  // taken before the next round's writes
+        verify_entry(eh, er);
+      }
+    }
+  }
+  __syncwarp();
+  if ((int)lane < qn) verify_entry(q_hit[wib][lane], q_sid[wib][lane]);
+  add_counter(&ctr->cells, cells);
+  add_counter(&ctr->filtered, filtered);
   if (err) atomicOr(&ctr->err, (unsigned long long)err);
 }
 
@@ -442,7 +542,7 @@ __device__ __forceinline__ void append_match(Counters* ctr, const AccOut& out, u
 template <int MAXW, bool SELF>
 __global__ void __launch_bounds__(BLOCK) k_verify_pairs(const ProbeView v, const unsigned long long* __restrict__ ukeys,
                                                         unsigned long long n, int pshift, AccOut out, Counters* ctr) {
-  unsigned long long cells = 0;
+  unsigned long long cells = 0, filtered = 0;
   for (unsigned long long u = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; u < n;
        u += (unsigned long long)gridDim.x * blockDim.x) {
     const unsigned long long key = ukeys[u];
@@ -451,10 +551,15 @@ __global__ void __launch_bounds__(BLOCK) k_verify_pairs(const ProbeView v, const
     const uint8_t *sx, *sy;
     int lx, ly;
     pair_strings(v, SELF, key, pshift, x, y, sx, lx, sy, ly);
+    if (v.pbm && bitmap_bound(v.pbm[x], v.ibm[y]) > v.tau) {
+      ++filtered;
+      continue;
+    }
     const int d = vsp<MAXW>(sx, lx, sy, ly, v.tau, cells);
     if (d <= v.tau) append_match(ctr, out, pair_out_key(v, SELF, x, y), d);
   }
   add_counter(&ctr->cells, cells);
+  add_counter(&ctr->filtered, filtered);
 }
 
 // One warp per distinct pair (long strings): the shuffle-scan band of
@@ -476,6 +581,7 @@ __global__ void __launch_bounds__(BLOCK) k_verify_pairs_warp(const ProbeView v,
     const uint8_t *sx, *sy;
     int lx, ly;
     pair_strings(v, SELF, key, pshift, x, y, sx, lx, sy, ly);
+    if (v.pbm && bitmap_bound(v.pbm[x], v.ibm[y]) > v.tau) continue;  // uniform across the warp
     const int d = vsp_warp(sx, lx, sy, ly, v.tau, cells);
     if (d <= v.tau && lane == 0) append_match(ctr, out, pair_out_key(v, SELF, x, y), d);
   }
@@ -590,6 +696,15 @@ template <int MAXW, bool SELF, bool MULTI>
 static void launch_verify(const Ctx& c, const ProbeView& v, const Hit* hits, const unsigned long long* off,
                           unsigned long long n_hits, unsigned long long c_begin, unsigned long long c_end,
                           AccOut out, Counters* ctr, int block) {
+  if (v.queued) {
+    const unsigned gq = persistent_grid(k_verify_queued<MAXW, SELF, MULTI>,
+                                        (c_end - c_begin + (unsigned long long)Q_BLOCK * V_RUN - 1) /
+                                            ((unsigned long long)Q_BLOCK * V_RUN), Q_BLOCK);
+    k_verify_queued<MAXW, SELF, MULTI><<<gq, Q_BLOCK, 0, c.stream>>>(v, hits, off, n_hits, c_begin, c_end, out, ctr,
+                                                                    nullptr);
+    PJ_LAUNCHED("k_verify_queued");
+    return;
+  }
   const unsigned grid = persistent_grid(k_verify_hits<MAXW, SELF, MULTI>,
                                         (c_end - c_begin + (unsigned long long)block * V_RUN - 1) /
                                             ((unsigned long long)block * V_RUN), block);
@@ -975,6 +1090,7 @@ static void run_join(const Ctx& c, const ProbeView& v, bool self, uint32_t fb_co
   out->stats.candidates = h.candidates;
   out->stats.accepted = h.accepted;
   out->stats.dp_cells = h.cells;
+  out->stats.filtered = h.filtered;
   out->stats.fallback_pairs = h.fallback;
   out->stats.hits = h.hits;
   out->stats.probe_ms = tm.probe;
@@ -1234,6 +1350,8 @@ static ProbeView index_side(const pj_index& idx, const Partition& part) {
   v.warp_q_cut = UINT32_MAX;
   v.block_thread = 256;
   v.block_warp = 256;
+  const char* vq = getenv("PJ_VERIFY_QUEUE");
+  v.queued = vq && vq[0] ? atoi(vq) : 1;
   v.ibytes = idx.sbytes.p;
   v.ioff = idx.soff.p;
   v.ilen = idx.slen.p;
@@ -1243,6 +1361,7 @@ static ProbeView index_side(const pj_index& idx, const Partition& part) {
   v.n_index = idx.n;
   v.table = part.table.p;
   v.table_fp = part.fp.p;
+  v.ibm = idx.sbm.p;
   v.mask = part.table.n - 1;
   v.postings = part.postings.p;
   v.n_postings = part.n_records;
@@ -1275,6 +1394,7 @@ static void self_join_impl(pj_index& idx, int tau, pj_result* out, bool on_devic
   v.pbegin = part.first;
   v.pcount = idx.n - part.first;
   v.pid = idx.perm.p;
+  v.pbm = idx.sbm.p;
   v.key_shift = bits_for(idx.n);
   v.gorder = part.gorder[1].p;
   v.warp_q_cut = UINT32_MAX;
@@ -1302,6 +1422,7 @@ static void probe_join_impl(const Ctx& c, const pj_index& idx, const Partition& 
   v.pbegin = 0;
   v.pcount = R.n;
   v.pid = nullptr;
+  v.pbm = R.bm.p;
   v.key_shift = bits_for(idx.n);
   v.gorder = part.gorder[0].p;
   TuneResult mode;
@@ -1355,6 +1476,7 @@ void query_multi_impl(const Ctx& c, pj_index& idx, const ProbeSet& R, const uint
   v.pbegin = 0;
   v.pcount = R.n;
   v.pid = nullptr;
+  v.pbm = R.bm.p;
   v.key_shift = bits_for(idx.n);
   v.ptau = d_tau.p;
   v.qgoff = d_qgoff.p;
@@ -1374,13 +1496,15 @@ static_assert(sizeof(Counters) == 64, "plan counters are 64 bytes");
 
 // Lengths and group counts of the batch; queries past n get 0 groups, so the
 // group offsets of every q >= n equal the total (group_of searches all cap_q).
-__global__ void k_plan_groups(const uint64_t* __restrict__ off, const uint8_t* __restrict__ tau, uint32_t cap_q,
-                              const PlanSizes* __restrict__ sizes, uint32_t* __restrict__ len,
+__global__ void k_plan_groups(const uint8_t* __restrict__ bytes, const uint64_t* __restrict__ off,
+                              const uint8_t* __restrict__ tau, uint32_t cap_q, const PlanSizes* __restrict__ sizes,
+                              uint32_t* __restrict__ len, unsigned long long* __restrict__ bm,
                               unsigned long long* __restrict__ gcnt) {
   const unsigned long long n = sizes->n;
   for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < cap_q; q += gridDim.x * blockDim.x) {
     if (q < n) {
       len[q] = (uint32_t)(off[q + 1] - off[q]);
+      bm[q] = char_bitmap(bytes + off[q], (int)len[q]);
       gcnt[q] = (unsigned long long)groups_per_probe((int)tau[q], false);
     } else {
       gcnt[q] = 0;
@@ -1416,6 +1540,7 @@ void record_query_plan(const Ctx& c, const pj_index& idx, const PlanDev& d) {
   v.ptau = d.tau;
   v.qgoff = d.qgoff;
   v.parts = d.parts;
+  v.pbm = d.bm;
   bool has_short = false;
   for (int t = 0; t <= tau_max; ++t) has_short |= idx.parts[t].first > 0;
   Counters* ctr = static_cast<Counters*>(d.counters);
@@ -1423,7 +1548,7 @@ void record_query_plan(const Ctx& c, const pj_index& idx, const PlanDev& d) {
   PJ_CUDA(cudaMemsetAsync(ctr, 0, sizeof(Counters), c.stream));
 
   // A4: groups of every query, lookups, hits, candidate offsets
-  k_plan_groups<<<stride_grid(d.cap_q), 256, 0, c.stream>>>(d.off, d.tau, d.cap_q, sz, d.len, d.gcnt);
+  k_plan_groups<<<stride_grid(d.cap_q), 256, 0, c.stream>>>(d.bytes, d.off, d.tau, d.cap_q, sz, d.len, d.bm, d.gcnt);
   PJ_LAUNCHED("k_plan_groups");
   exclusive_scan_dn<unsigned long long>(c, d.gcnt, d.qgoff, d.cap_q, nullptr, &sz->groups);
   const unsigned g1 = persistent_grid(k_group_counts<false, true>, (d.cap_groups + BLOCK - 1) / BLOCK);
@@ -1442,10 +1567,10 @@ void record_query_plan(const Ctx& c, const pj_index& idx, const PlanDev& d) {
   const AccOut acc{d.acc_key[0], d.acc_ed[0], d.cap_acc};
 #define PJ_CALL(W)                                                                                              \
   do {                                                                                                         \
-    const unsigned gv = persistent_grid(k_verify_hits<W, false, true>, ~0ull >> 8, BLOCK);                      \
-    k_verify_hits<W, false, true><<<gv, BLOCK, 0, c.stream>>>(v, d.hits, d.hoff, d.cap_hits, 0, 0, acc, ctr,     \
-                                                              &sz->hits);                                      \
-    PJ_LAUNCHED("k_verify_hits");                                                                              \
+    const unsigned gv = persistent_grid(k_verify_queued<W, false, true>, ~0ull >> 8, Q_BLOCK);                  \
+    k_verify_queued<W, false, true><<<gv, Q_BLOCK, 0, c.stream>>>(v, d.hits, d.hoff, d.cap_hits, 0, 0, acc, ctr, \
+                                                                  &sz->hits);                                  \
+    PJ_LAUNCHED("k_verify_queued");                                                                            \
     if (has_short) {                                                                                           \
       const unsigned gf = persistent_grid(k_fallback<W, false, true>, (d.cap_q + BLOCK - 1) / BLOCK);           \
       k_fallback<W, false, true><<<gf, BLOCK, 0, c.stream>>>(v, d.cap_q, acc, ctr, &sz->n);                     \

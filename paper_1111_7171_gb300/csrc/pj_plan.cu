@@ -104,7 +104,7 @@ struct pj_plan {
   pj::DBuf<uint64_t> off;
   pj::DBuf<pj::PlanSizes> sizes;
   pj::DBuf<uint32_t> len, gcounts, goff, flags, pos, acc_ed0, acc_ed1;
-  pj::DBuf<unsigned long long> gcnt, qgoff, gmask, hcnt, hoff, acc_key0, acc_key1;
+  pj::DBuf<unsigned long long> gcnt, qgoff, gmask, hcnt, hoff, acc_key0, acc_key1, bm;
   pj::DBuf<pj::PartView> parts;
   pj::DBuf<unsigned char> counters, arena;
   pj::DBuf<pj::Hit> hits;
@@ -118,7 +118,7 @@ struct pj_plan {
   uint64_t device_bytes() const {
     return bytes.bytes() + tau.bytes() + off.bytes() + sizes.bytes() + len.bytes() + gcounts.bytes() + goff.bytes() +
            flags.bytes() + pos.bytes() + acc_ed0.bytes() + acc_ed1.bytes() + gcnt.bytes() + qgoff.bytes() +
-           gmask.bytes() + hcnt.bytes() + hoff.bytes() + acc_key0.bytes() + acc_key1.bytes() + parts.bytes() + counters.bytes() +
+           gmask.bytes() + bm.bytes() + hcnt.bytes() + hoff.bytes() + acc_key0.bytes() + acc_key1.bytes() + parts.bytes() + counters.bytes() +
            arena.bytes() + hits.bytes();
   }
   uint64_t host_bytes() const {
@@ -139,7 +139,7 @@ struct pj_plan {
     sizes.release();
     pj::DBuf<uint32_t>* b32[] = {&len, &gcounts, &goff, &flags, &pos, &acc_ed0, &acc_ed1};
     for (auto* b : b32) b->release();
-    pj::DBuf<unsigned long long>* b64[] = {&gcnt, &qgoff, &gmask, &hcnt, &hoff, &acc_key0, &acc_key1};
+    pj::DBuf<unsigned long long>* b64[] = {&gcnt, &qgoff, &gmask, &hcnt, &hoff, &acc_key0, &acc_key1, &bm};
     for (auto* b : b64) b->release();
     parts.release();
     counters.release();
@@ -300,6 +300,7 @@ void create(pj_plan& P, pj_index& idx, const pj_plan_options& o) {
   P.tau.reset(P.ctx, d.cap_q);
   P.sizes.reset(P.ctx, 1);
   P.len.reset(P.ctx, d.cap_q);
+  P.bm.reset(P.ctx, d.cap_q);
   P.gcnt.reset(P.ctx, d.cap_q);
   P.qgoff.reset(P.ctx, d.cap_q);
   P.gcounts.reset(P.ctx, d.cap_groups);
@@ -311,6 +312,7 @@ void create(pj_plan& P, pj_index& idx, const pj_plan_options& o) {
   d.tau = P.tau.p;
   d.sizes = P.sizes.p;
   d.len = P.len.p;
+  d.bm = P.bm.p;
   d.gcnt = P.gcnt.p;
   d.qgoff = P.qgoff.p;
   d.gcounts = P.gcounts.p;

@@ -69,6 +69,11 @@ struct ProbeView {
   int block_thread;  // block size of the thread-per-candidate verification
   int interleave;    // probe groups interleaved across probes (see group_of)
   const uint16_t* gorder;  // groups of one probe in visiting order (NULL: natural order)
+  // character bitmaps of the probing and the indexed strings (NULL: no
+  // character-set bound)
+  const unsigned long long* pbm;
+  const unsigned long long* ibm;
+  int queued;     // thread-per-candidate verification with a screen and per-warp queues
   int pair_mode;  // 1: mode L (distinct candidate pairs verified once over the whole strings)
   int pair_warp;  // mode L: one warp per pair instead of one thread
   int block_warp;    // block size of the warp-per-candidate verification
@@ -197,37 +202,58 @@ __host__ __device__ __forceinline__ HitCtx hit_ctx(const ProbeView& v, const Hit
   return c;
 }
 
-// Verify candidate `off` of the hit described by hc.  Returns true with the
-// pair key and ed = d_l + d_r when extension verification accepts it.
+// Extension verification (Sec. 5.2, Alg. 3) of indexed string r against the
+// hit described by hc, r already screened (a valid sid, not the probe
+// itself).  Returns true with the pair key and ed = d_l + d_r when accepted.
 template <int MAXW>
-__host__ __device__ __forceinline__ bool verify_in_hit(const ProbeView& v, bool self, const HitCtx& hc, uint32_t off,
-                                                       unsigned long long& key, int& ed, unsigned long long& cells,
-                                                       int& err) {
+__host__ __device__ __forceinline__ bool verify_screened(const ProbeView& v, bool self, const HitCtx& hc, uint32_t r,
+                                                         unsigned long long& key, int& ed,
+                                                         unsigned long long& cells) {
   // Single exit: see vsp().
   bool ok = false;
-  const uint32_t r = v.postings[hc.begin + off];
   const int i = hc.i;
-  if (r >= v.n_index) {
-    err |= 1;
-  } else if (!(self && r == hc.q)) {  // a colliding run may hold the probe itself
-    const int lr = (int)v.ilen[r];
-    if (i >= 1 && i <= v.tau + 1 && lr >= v.tau + 1) {  // r is a partitioned string
-      int P, li;
-      even_segment_m(lr, v.tau + 1, v.seg_magic, i, P, li);
-      // exact keys (segments of at most SEG_EXACT_MAX bytes) guarantee the
-      // segment match; hashed ones are compared
-      if (hc.p + li <= hc.ls && verify_ext<MAXW>(hc.s, hc.ls, v.ibytes + v.ioff[r], lr, i, hc.p, li, P, v.tau,
-                                                 li > SEG_EXACT_MAX, ed, cells)) {
-        const uint32_t qid = v.pid ? v.pid[hc.q] : hc.q;
-        const uint32_t rid = v.iperm[r];
-        const uint32_t ka = self ? min(qid, rid) : qid;
-        const uint32_t kb = self ? max(qid, rid) : rid;
-        key = ((unsigned long long)ka << v.key_shift) | kb;
-        ok = true;
-      }
+  const int lr = (int)v.ilen[r];
+  if (i >= 1 && i <= v.tau + 1 && lr >= v.tau + 1) {  // r is a partitioned string
+    int P, li;
+    even_segment_m(lr, v.tau + 1, v.seg_magic, i, P, li);
+    // exact keys (segments of at most SEG_EXACT_MAX bytes) guarantee the
+    // segment match; hashed ones are compared
+    if (hc.p + li <= hc.ls && verify_ext<MAXW>(hc.s, hc.ls, v.ibytes + v.ioff[r], lr, i, hc.p, li, P, v.tau,
+                                               li > SEG_EXACT_MAX, ed, cells)) {
+      const uint32_t qid = v.pid ? v.pid[hc.q] : hc.q;
+      const uint32_t rid = v.iperm[r];
+      const uint32_t ka = self ? min(qid, rid) : qid;
+      const uint32_t kb = self ? max(qid, rid) : rid;
+      key = ((unsigned long long)ka << v.key_shift) | kb;
+      ok = true;
     }
   }
   return ok;
+}
+
+// The screen in front of every verification: r must be a valid sid (else
+// err |= 1), not the probe itself (a colliding run may hold it), and pass
+// the character-set bound (else ++filtered).
+__host__ __device__ __forceinline__ bool screen_candidate(const ProbeView& v, bool self, uint32_t q, uint32_t r,
+                                                          unsigned long long& filtered, int& err) {
+  bool pass = false;
+  if (r >= v.n_index) {
+    err |= 1;
+  } else if (!(self && r == q)) {
+    if (v.pbm && bitmap_bound(v.pbm[q], v.ibm[r]) > v.tau) ++filtered;
+    else pass = true;
+  }
+  return pass;
+}
+
+// Verify candidate `off` of the hit described by hc (screen, then
+// verify_screened).
+template <int MAXW>
+__host__ __device__ __forceinline__ bool verify_in_hit(const ProbeView& v, bool self, const HitCtx& hc, uint32_t off,
+                                                       unsigned long long& key, int& ed, unsigned long long& cells,
+                                                       unsigned long long& filtered, int& err) {
+  const uint32_t r = v.postings[hc.begin + off];
+  return screen_candidate(v, self, hc.q, r, filtered, err) && verify_screened<MAXW>(v, self, hc, r, key, ed, cells);
 }
 
 // Verify candidate `off` of hit h (see verify_in_hit).
@@ -235,7 +261,8 @@ template <int MAXW>
 __host__ __device__ __forceinline__ bool verify_candidate(const ProbeView& v, bool self, const Hit& h, uint32_t off,
                                                           unsigned long long& key, int& ed,
                                                           unsigned long long& cells, int& err) {
-  return verify_in_hit<MAXW>(v, self, hit_ctx(v, h), off, key, ed, cells, err);
+  unsigned long long filtered = 0;
+  return verify_in_hit<MAXW>(v, self, hit_ctx(v, h), off, key, ed, cells, filtered, err);
 }
 
 #ifdef __CUDACC__
@@ -251,7 +278,7 @@ __device__ __forceinline__ bool verify_candidate_warp(const ProbeView& v, bool s
   const int i = (int)((h.pi >> 16) & 0xFFu);
   if (r >= v.n_index) {
     err |= 1;
-  } else if (!(self && r == q)) {
+  } else if (!(self && r == q) && !(v.pbm && bitmap_bound(v.pbm[q], v.ibm[r]) > v.tau)) {
     const int ls = (int)v.plen[q];
     const int lr = (int)v.ilen[r];
     if (i >= 1 && i <= v.tau + 1 && lr >= v.tau + 1) {

@@ -48,7 +48,7 @@ class pj_stats(ctypes.Structure):
                 ("probe_ms", ctypes.c_float), ("verify_ms", ctypes.c_float), ("fallback_ms", ctypes.c_float),
                 ("dedupe_ms", ctypes.c_float), ("partition_ms", ctypes.c_float), ("verify_block", ctypes.c_int32),
                 ("warp_min_len", ctypes.c_int32), ("tune_ms", ctypes.c_float), ("verify_mode", ctypes.c_int32),
-                ("pair_warp", ctypes.c_int32)]
+                ("pair_warp", ctypes.c_int32), ("filtered", ctypes.c_uint64)]
 
 
 class pj_result(ctypes.Structure):
@@ -328,7 +328,7 @@ def _stats(st: pj_stats) -> dict:
                 probe_ms=float(st.probe_ms), verify_ms=float(st.verify_ms), fallback_ms=float(st.fallback_ms),
                 dedupe_ms=float(st.dedupe_ms), partition_ms=float(st.partition_ms),
                 verify_block=int(st.verify_block), warp_min_len=int(st.warp_min_len), tune_ms=float(st.tune_ms),
-                verify_mode=int(st.verify_mode), pair_warp=int(st.pair_warp))
+                verify_mode=int(st.verify_mode), pair_warp=int(st.pair_warp), filtered=int(st.filtered))
 
 
 def _take(res: pj_result):

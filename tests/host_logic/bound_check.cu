@@ -1,0 +1,55 @@
+// Host-side check of the character-set bound used before verification
+// (bitmap_bound, pj_internal.cuh): it never exceeds the edit distance of
+// Def. 1 (plain Wagner-Fischer DP), on random strings over small alphabets
+// (few distinct bits) and over all 256 byte values (bits shared by c and
+// c + 64k), and it is exact on pairs that differ only by characters absent
+// from the other string.  Prints "bad=<violations> tight=<exact cases>".
+#include <cstdio>
+#include <random>
+#include <string>
+#include <vector>
+
+#include "pj_internal.cuh"
+
+static int ed(const std::string& a, const std::string& b) {
+  std::vector<int> p(b.size() + 1), c(b.size() + 1);
+  for (size_t j = 0; j <= b.size(); ++j) p[j] = (int)j;
+  for (size_t i = 1; i <= a.size(); ++i) {
+    c[0] = (int)i;
+    for (size_t j = 1; j <= b.size(); ++j)
+      c[j] = std::min(std::min(p[j] + 1, c[j - 1] + 1), p[j - 1] + (a[i - 1] != b[j - 1] ? 1 : 0));
+    std::swap(p, c);
+  }
+  return p[b.size()];
+}
+
+int main() {
+  std::mt19937 g(7);
+  long bad = 0, tight = 0;
+  const int alpha[] = {2, 5, 27, 64, 200, 256};
+  for (int A : alpha)
+    for (int it = 0; it < 40000; ++it) {
+      const int la = g() % 16, lb = g() % 16;
+      std::string a, b;
+      for (int k = 0; k < la; ++k) a += (char)(g() % A);
+      for (int k = 0; k < lb; ++k) b += (char)(g() % A);
+      const int bound = pj::bitmap_bound(pj::char_bitmap((const uint8_t*)a.data(), la),
+                                         pj::char_bitmap((const uint8_t*)b.data(), lb));
+      const int d = ed(a, b);
+      if (bound > d) {
+        if (bad < 5) printf("A=%d bound %d > ed %d\n", A, bound, d);
+        ++bad;
+      }
+      tight += bound == d && d > 0;
+    }
+  // substituting k characters by characters the string lacks: bound = ED = k
+  for (int k = 1; k <= 6; ++k) {
+    std::string a = "abcdefghij", b = a;
+    for (int m = 0; m < k; ++m) b[m] = (char)('A' + m);
+    const int bound = pj::bitmap_bound(pj::char_bitmap((const uint8_t*)a.data(), 10),
+                                       pj::char_bitmap((const uint8_t*)b.data(), 10));
+    if (bound != k || ed(a, b) != k) ++bad;
+  }
+  printf("bad=%ld tight=%ld\n", bad, tight);
+  return 0;
+}

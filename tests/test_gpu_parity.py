@@ -331,6 +331,27 @@ def test_distinct_pair_verification(monkeypatch, mode):
     assert_same(pj.pj_join(R, S, 3).pairs, oracle.join(rb, ro, sb, so, 3), f"join pairs={mode}")
 
 
+@pytest.mark.parametrize("queued", ["0", "1"])
+def test_direct_and_queued_verification(monkeypatch, queued):
+    """Thread-per-candidate verification straight (0) or behind the screen
+    and per-warp queues (1): same exact result, with launch chunks that end
+    inside a warp's candidates."""
+    monkeypatch.setenv("PJ_VERIFY_QUEUE", queued)
+    monkeypatch.setenv("PJ_VERIFY_PAIRS", "0")
+    for name, tau, n, banded in [("short", 4, 4000, False), ("short2k", 2, 2000, False), ("medium", 4, 3000, True)]:
+        strings = synth.generate(name, tau, n=n)
+        assert_same(gpu_self(strings, tau).pairs, cpu_self(strings, tau, banded=banded), f"{name} queued={queued}")
+    monkeypatch.setenv("PJ_LAUNCH_CANDS", "777")
+    strings = synth.generate("short", 3, n=2500)
+    r = gpu_self(strings, 3)
+    assert_same(r.pairs, cpu_self(strings, 3), f"short launches queued={queued}")
+    assert r.stats["filtered"] > 0
+    R, S = _rs_sets(9, 2)
+    rb, ro = synth.pack(R)
+    sb, so = synth.pack(S)
+    assert_same(pj.pj_join(R, S, 2).pairs, oracle.join(rb, ro, sb, so, 2), f"join queued={queued}")
+
+
 def test_autotuned_self_join(monkeypatch, tmp_path):
     """The autotuner picks the cut-over and block size per workload signature
     (cached for the process and in PJ_AUTOTUNE_CACHE); results stay exact."""

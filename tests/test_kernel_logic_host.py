@@ -122,3 +122,17 @@ def test_even_partition_by_reciprocal_matches_division(tmp_path):
                     os.path.join(ROOT, "tests", "host_logic", "segment_check.cu")], check=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
     assert out.strip().endswith("bad=0"), out
+
+
+def test_character_set_bound_never_exceeds_edit_distance(tmp_path):
+    """The bound that rejects candidates before verification is a lower bound
+    of the edit distance of Def. 1 (plain DP), for every alphabet size."""
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    exe = tmp_path / "bound_check"
+    subprocess.run([nvcc, "-std=c++17", "-O2", "-I", CSRC, "-I", os.path.join(ROOT, "include"), "-o", str(exe),
+                    os.path.join(ROOT, "tests", "host_logic", "bound_check.cu")], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    assert out[0] == "bad=0", out
+    assert int(out[1].split("=")[1]) > 1000  # the bound is often exact, so it has teeth
