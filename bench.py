@@ -46,7 +46,7 @@ METRIC = "self-join verified candidate pairs/s"
 UNIT = "pairs/s"
 L2_FLUSH_BYTES = 256 << 20
 INT_LANES_PER_SM = 128      # 32-bit integer lanes per SM (4 sub-partitions x 32)
-OPS_PER_CELL = 8            # integer ops of one length-aware DP cell
+OPS_PER_CELL = 8            # integer ops of one DP cell: delta compare, diagonal add, up/left +1, mins
 
 
 def parse():
@@ -469,7 +469,8 @@ def run_native(args):
         probe_ms = statistics.mean(s["probe_ms"] for s in stats_all)
         cells = statistics.mean(s["dp_cells"] for s in stats_all)
         achieved = cells / (verify_ms / 1e3) / 1e9
-        roofline = {"bound": "alu", "kernel": "k_verify_hits", "achieved": achieved, "peak": alu_peak_gcells,
+        kernel = "k_verify_pairs" if st["verify_mode"] == 2 else "k_verify_queued"
+        roofline = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": alu_peak_gcells,
                     "unit": "Gcell/s", "frac": achieved / alu_peak_gcells, "traffic": None,
                     "peak_source": f"{sm_count} SMs x {INT_LANES_PER_SM} int32 lanes x {sm_mhz:.0f} MHz "
                                    f"({peak_src} SM clock) / {OPS_PER_CELL} ops per DP cell"}

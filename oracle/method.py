@@ -21,7 +21,7 @@ is ``p - 1`` in this module, and its segment start p_i is ``P[i-1]``.
 * ``pass_join_self`` / ``pass_join_rs`` -- Alg. 1 and the R != S variant of
                               Sec. 3.2.
 
-Readings taken where the paper is silent (each also listed in the design doc):
+Readings taken where the paper is silent:
 strings shorter than tau + 1 have no even partition (footnote to Sec. 3.1), so
 pairs whose indexed string is that short are verified directly; the exact
 ``ed`` of a reported pair is the minimum d_l + d_r over the accepted
