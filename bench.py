@@ -133,6 +133,22 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def reduce_over_ranks(units, secs, e2e_secs, world, device):
+    """Whole-job figures of N replicas: the units every rank processed,
+    summed, over the slowest rank's time (max over ranks), for the device-
+    timed and the end-to-end loops.  Needs an initialised process group
+    when world > 1 (NCCL on GPUs; any backend works)."""
+    if world <= 1:
+        return float(units), secs, e2e_secs
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([units, secs, e2e_secs], dtype=torch.float64, device=device)
+    total = t.clone()
+    dist.all_reduce(total, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(total[0]), float(t[1]), float(t[2])
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -448,16 +464,7 @@ def run_native(args):
     barrier()
 
     cand = sum(s["candidates"] for s in stats_all)
-    total_s = sum(step_ms) / 1e3
-    e2e_s = sum(e2e_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([cand, total_s, e2e_s], dtype=torch.float64, device=dev)
-        c_sum = t.clone()
-        dist.all_reduce(c_sum, op=dist.ReduceOp.SUM)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        cand_all, total_s, e2e_s = float(c_sum[0]), float(t[1]), float(t[2])
-    else:
-        cand_all = float(cand)
+    cand_all, total_s, e2e_s = reduce_over_ranks(cand, sum(step_ms) / 1e3, sum(e2e_ms) / 1e3, world, dev)
 
     if rank == 0:
         st = stats_all[-1]

@@ -132,10 +132,34 @@ __device__ __forceinline__ unsigned long long dev_count(unsigned long long cap, 
   return n_dev ? min(cap, *n_dev) : cap;
 }
 
-// Pass 1: number of non-empty lookups of every group (probe, length, segment)
-// and the mask of the window positions that found one.  The window's
-// substrings overlap, so their hashes are rolled from one position to the
-// next instead of being recomputed.
+// Pass 1 for one group: the number of non-empty lookups and the mask of the
+// window positions that found one.  The window's substrings overlap, so
+// their keys are rolled from one position to the next.
+template <bool SELF>
+__device__ __forceinline__ void count_group(const ProbeView& vt, uint32_t q, int g, uint32_t& nh,
+                                            unsigned long long& mask, unsigned long long& lookups, int& err) {
+  nh = 0;
+  mask = 0;
+  int l, i, P, li, lo, hi;
+  if (group_window(vt, SELF, q, (int)vt.plen[q], g, l, i, P, li, lo, hi)) {
+    const int ls = (int)vt.plen[q];
+    const uint8_t* s = vt.pbytes + vt.poff[q];
+    uint32_t V = seg_value(s + lo, li);
+    const uint32_t pw = seg_pow(li);
+    for (int p = lo;; ++p) {
+      uint32_t b;
+      if (lookup_key(vt, SELF, q, ls, l, seg_key_of(V, l, i), b, err)) {
+        ++nh;
+        mask |= 1ull << (p - lo);
+      }
+      if (p == hi) break;
+      V = seg_roll(V, s[p], s[p + li], li, pw);  // p + li <= hi - 1 + li < ls
+    }
+    lookups += (unsigned long long)(hi - lo + 1);
+  }
+}
+
+// Pass 1: counts and masks of every group (probe, length, segment).
 template <bool SELF, bool MULTI>
 __global__ void __launch_bounds__(BLOCK) k_group_counts(const ProbeView v, unsigned long long n_groups,
                                                         uint32_t* __restrict__ counts,
@@ -151,23 +175,7 @@ __global__ void __launch_bounds__(BLOCK) k_group_counts(const ProbeView v, unsig
     ProbeView vt;
     uint32_t nh = 0;
     unsigned long long mask = 0;
-    int l, i, P, li, lo, hi;
-    if (group_of<SELF, MULTI>(v, t, q, g, vt) && group_window(vt, SELF, q, (int)vt.plen[q], g, l, i, P, li, lo, hi)) {
-      const int ls = (int)vt.plen[q];
-      const uint8_t* s = vt.pbytes + vt.poff[q];
-      uint32_t V = seg_value(s + lo, li);
-      const uint32_t pw = seg_pow(li);
-      for (int p = lo;; ++p) {
-        uint32_t b;
-        if (lookup_key(vt, SELF, q, ls, l, seg_key_of(V, l, i), b, err)) {
-          ++nh;
-          mask |= 1ull << (p - lo);
-        }
-        if (p == hi) break;
-        V = seg_roll(V, s[p], s[p + li], li, pw);  // p + li <= hi - 1 + li < ls
-      }
-      lookups += (unsigned long long)(hi - lo + 1);
-    }
+    if (group_of<SELF, MULTI>(v, t, q, g, vt)) count_group<SELF>(vt, q, g, nh, mask, lookups, err);
     counts[t] = nh;
     masks[t] = mask;
   }
