@@ -194,6 +194,21 @@ __global__ void k_seg_records(const uint8_t* __restrict__ sbytes, const uint64_t
 
 // ---------------------------------------------------------------- A3 ------
 
+__global__ void k_post_records(const uint32_t* __restrict__ postings, uint64_t n, const uint64_t* __restrict__ soff,
+                               const uint32_t* __restrict__ slen, const unsigned long long* __restrict__ sbm,
+                               PostRec* __restrict__ recs) {
+  for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t sid = postings[k];
+    const uint64_t off = soff[sid];
+    PostRec r;
+    r.sid = sid;
+    r.off_lo = (uint32_t)off;
+    r.len_hi = (slen[sid] & 0xFFFFu) | ((uint32_t)(off >> 32) << 16);
+    r.bm = fold_bitmap(sbm[sid]);
+    recs[k] = r;
+  }
+}
+
 __global__ void k_head_flags(const unsigned long long* __restrict__ keys, uint64_t n, uint32_t* __restrict__ flags) {
   const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k < n) flags[k] = (k == 0 || keys[k] != keys[k - 1]) ? 1u : 0u;
@@ -365,6 +380,7 @@ void build_partition(pj_index& idx, int tau, Partition& part) {
     part.n_unique = 0;
     part.table.reset(c, 1);
     part.fp.reset(c, 1);
+    part.precs.reset(c, 1);
     PJ_CUDA(cudaMemsetAsync(part.table.p, 0, sizeof(Slot), c.stream));
     PJ_CUDA(cudaMemsetAsync(part.fp.p, 0, 1, c.stream));
     return;
@@ -406,6 +422,11 @@ void build_partition(pj_index& idx, int tau, Partition& part) {
   PJ_CUDA(cudaMemcpyAsync(&h_err, err.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
   c.sync();
   if (h_err) fail(PJ_ECUDA, "segment table insertion failed");
+  if (idx.total_bytes >= (1ull << 48)) fail(PJ_EINVAL, "segment index: store larger than 2^48 bytes");
+  part.precs.reset(c, nrec);
+  k_post_records<<<std::min<unsigned>(ceil_div(nrec, 256), 152u * 16u), 256, 0, c.stream>>>(
+      part.postings.p, nrec, idx.soff.p, idx.slen.p, idx.sbm.p, part.precs.p);
+  PJ_LAUNCHED("k_post_records");
   trace_mark(c, "partition: table");
   if (getenv("PJ_CHECK_INDEX")) check_partition(c, part);
   if (getenv("PJ_DEBUG_DUMP")) {
@@ -514,7 +535,8 @@ void upload_probe_set(const Ctx& c, const pj_strings& R, ProbeSet& out) {
 uint64_t pj_index::device_bytes() const {
   uint64_t b = sbytes.bytes() + soff.bytes() + slen.bytes() + perm.bytes() + bbeg.bytes() + sbm.bytes();
   for (const auto& p : parts)
-    b += p.table.bytes() + p.fp.bytes() + p.postings.bytes() + p.gorder[0].bytes() + p.gorder[1].bytes();
+    b += p.table.bytes() + p.fp.bytes() + p.postings.bytes() + p.precs.bytes() + p.gorder[0].bytes() +
+         p.gorder[1].bytes();
   return b;
 }
 

@@ -195,6 +195,37 @@ __device__ __forceinline__ int table_find(const Slot* __restrict__ t, const uint
   return -1;
 }
 
+// Everything verification needs about one posting, stored beside the
+// postings in the same order so that the candidates of a run are read as
+// one coalesced stream: the sid, where the string starts in the store and
+// its length, and its character bitmap folded to 32 bits (bit c mod 32; the
+// bound of bitmap_bound holds for any mapping of characters to bits).
+struct __align__(16) PostRec {
+  uint32_t sid;
+  uint32_t off_lo;  // string offset in the store, bits 0..31
+  uint32_t len_hi;  // length (bits 0..15) | offset bits 32..47 (bits 16..31)
+  uint32_t bm;
+};
+
+__host__ __device__ __forceinline__ uint32_t fold_bitmap(unsigned long long b) {
+  return (uint32_t)(b | (b >> 32));
+}
+
+__host__ __device__ __forceinline__ int bitmap_bound32(uint32_t bx, uint32_t by) {
+#ifdef __CUDA_ARCH__
+  const int a = __popc(bx & ~by), b = __popc(by & ~bx);
+#else
+  const int a = __builtin_popcount(bx & ~by), b = __builtin_popcount(by & ~bx);
+#endif
+  return a > b ? a : b;
+}
+
+__host__ __device__ __forceinline__ unsigned long long rec_offset(const PostRec& r) {
+  return ((unsigned long long)(r.len_hi >> 16) << 32) | r.off_lo;
+}
+
+__host__ __device__ __forceinline__ int rec_length(const PostRec& r) { return (int)(r.len_hi & 0xFFFFu); }
+
 // One threshold's segment index.
 struct Partition {
   int tau = -1;
@@ -204,6 +235,7 @@ struct Partition {
   DBuf<Slot> table;          // power-of-two capacity
   DBuf<uint8_t> fp;          // key_fp of each used slot, 0 for empty ones
   DBuf<uint32_t> postings;   // sids, runs in key order, ascending inside a run
+  DBuf<PostRec> precs;       // one record per posting, same order
   // group visiting order for one probe: the (length, segment) groups sorted
   // by window size, widest first; [0] for R != S probes, [1] for the self join
   DBuf<uint16_t> gorder[2];

@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(Q_BLOCK) k_verify_queued(const ProbeView v, co
                                                             unsigned long long n_cand, AccOut out, Counters* ctr,
                                                             const unsigned long long* __restrict__ dn) {
   __shared__ uint32_t q_hit[Q_WARPS][Q_CAP];
-  __shared__ uint32_t q_sid[Q_WARPS][Q_CAP];
+  __shared__ uint32_t q_post[Q_WARPS][Q_CAP];
   if (dn) {
     n_hits = min(n_hits, dn[0]);
     n_cand = dn[1];
@@ -328,12 +328,12 @@ __global__ void __launch_bounds__(Q_BLOCK) k_verify_queued(const ProbeView v, co
   const unsigned long long n_warps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
   const unsigned long long span = 32ull * V_RUN;
   int qn = 0;  // the same in every lane
-  auto verify_entry = [&](uint32_t h, uint32_t r) {
+  auto verify_entry = [&](uint32_t h, uint32_t k) {
     const Hit hit = hits[h];
     const ProbeView vt = MULTI ? view_for_tau(v, (int)(hit.pi >> 24)) : v;
     unsigned long long key = 0;
     int ed = 0;
-    if (verify_screened<MAXW>(vt, SELF, hit_ctx(vt, hit), r, key, ed, cells)) {
+    if (verify_rec<MAXW>(vt, SELF, hit_ctx(vt, hit), vt.precs[k], key, ed, cells)) {
       const unsigned long long pos = atomicAdd(&ctr->accepted, 1ull);
       if (pos < out.cap) {
         out.key[pos] = key;
@@ -345,6 +345,7 @@ __global__ void __launch_bounds__(Q_BLOCK) k_verify_queued(const ProbeView v, co
     unsigned long long c = base + lane;
     unsigned long long h = 0, c_lo = 0, c_hi = 0;
     Hit hit{};
+    uint32_t qbm = 0;
     if (c < n_cand) {
       unsigned long long lo = 0, hi = n_hits;  // last hit whose first candidate is <= c
       while (hi - lo > 1) {
@@ -355,10 +356,11 @@ __global__ void __launch_bounds__(Q_BLOCK) k_verify_queued(const ProbeView v, co
       c_lo = cand_off[h];
       c_hi = h + 1 < n_hits ? cand_off[h + 1] : n_cand;
       hit = hits[h];
+      qbm = v.pbm ? fold_bitmap(v.pbm[hit.q]) : 0u;
     }
     for (int k = 0; k < V_RUN; ++k, c += 32) {  // the same trip count in every lane
       bool pass = false;
-      uint32_t r = 0;
+      uint32_t pk = 0;
       if (c < n_cand) {
         if (c >= c_hi) {
           do {
@@ -367,30 +369,38 @@ __global__ void __launch_bounds__(Q_BLOCK) k_verify_queued(const ProbeView v, co
             c_hi = h + 1 < n_hits ? cand_off[h + 1] : n_cand;
           } while (c >= c_hi);
           hit = hits[h];
+          qbm = v.pbm ? fold_bitmap(v.pbm[hit.q]) : 0u;
         }
         const ProbeView vt = MULTI ? view_for_tau(v, (int)(hit.pi >> 24)) : v;
-        r = vt.postings[hit.begin + (uint32_t)(c - c_lo)];
-        pass = screen_candidate(vt, SELF, hit.q, r, filtered, err);
+        pk = hit.begin + (uint32_t)(c - c_lo);
+        const PostRec rec = vt.precs[pk];
+        // screen: a valid sid, not the probe itself, character-set bound
+        if (rec.sid >= vt.n_index) {
+          err |= 1;
+        } else if (!(SELF && rec.sid == hit.q)) {
+          if (v.pbm && bitmap_bound32(qbm, rec.bm) > vt.tau) ++filtered;
+          else pass = true;
+        }
       }
       __syncwarp();
       const unsigned m = __ballot_sync(FULL, pass);
       if (pass) {
         const int slot = qn + __popc(m & lanemask_lt());
         q_hit[wib][slot] = (uint32_t)h;
-        q_sid[wib][slot] = r;
+        q_post[wib][slot] = pk;
       }
       qn += __popc(m);
       __syncwarp();
       if (qn >= 32) {
         qn -= 32;
-        const uint32_t eh = q_hit[wib][qn + lane], er = q_sid[wib][qn + lane];
+        const uint32_t eh = q_hit[wib][qn + lane], ek = q_post[wib][qn + lane];
         __syncwarp();  // taken before the next round's writes
-        verify_entry(eh, er);
+        verify_entry(eh, ek);
       }
     }
   }
   __syncwarp();
-  if ((int)lane < qn) verify_entry(q_hit[wib][lane], q_sid[wib][lane]);
+  if ((int)lane < qn) verify_entry(q_hit[wib][lane], q_post[wib][lane]);
   add_counter(&ctr->cells, cells);
   add_counter(&ctr->filtered, filtered);
   if (err) atomicOr(&ctr->err, (unsigned long long)err);
@@ -1369,6 +1379,7 @@ static ProbeView index_side(const pj_index& idx, const Partition& part) {
   v.n_index = idx.n;
   v.table = part.table.p;
   v.table_fp = part.fp.p;
+  v.precs = part.precs.p;
   v.ibm = idx.sbm.p;
   v.mask = part.table.n - 1;
   v.postings = part.postings.p;
@@ -1464,8 +1475,8 @@ void query_multi_impl(const Ctx& c, pj_index& idx, const ProbeSet& R, const uint
     PartView pv{};
     if (present[t]) {
       const Partition& part = idx.parts[t];
-      pv = PartView{part.table.p, part.fp.p,    part.table.n - 1, part.postings.p,
-                    part.n_records, part.first, t,           seg_magic(t + 1)};
+      pv = PartView{part.table.p, part.fp.p,    part.precs.p, part.table.n - 1,
+                    part.postings.p, part.n_records, part.first, t, seg_magic(t + 1)};
       has_short |= part.first > 0;
     }
     hp[t] = pv;

@@ -27,6 +27,7 @@ struct Hit {
 struct PartView {
   const Slot* table;
   const uint8_t* fp;  // slot fingerprints
+  const PostRec* precs;
   unsigned long long mask;
   const uint32_t* postings;
   unsigned long long n_postings;
@@ -54,6 +55,7 @@ struct ProbeView {
   const uint8_t* table_fp;  // slot fingerprints (NULL: probe the slots directly)
   unsigned long long mask;
   const uint32_t* postings;
+  const PostRec* precs;  // postings' records (same order)
   unsigned long long n_postings;
   int tau;
   unsigned long long seg_magic;  // seg_magic(tau + 1): even partitions without a division
@@ -85,6 +87,7 @@ __host__ __device__ __forceinline__ ProbeView view_for_tau(const ProbeView& v, i
   const PartView& pv = v.parts[tau];
   t.table = pv.table;
   t.table_fp = pv.fp;
+  t.precs = pv.precs;
   t.mask = pv.mask;
   t.postings = pv.postings;
   t.n_postings = pv.n_postings;
@@ -222,6 +225,31 @@ __host__ __device__ __forceinline__ bool verify_screened(const ProbeView& v, boo
                                                li > SEG_EXACT_MAX, ed, cells)) {
       const uint32_t qid = v.pid ? v.pid[hc.q] : hc.q;
       const uint32_t rid = v.iperm[r];
+      const uint32_t ka = self ? min(qid, rid) : qid;
+      const uint32_t kb = self ? max(qid, rid) : rid;
+      key = ((unsigned long long)ka << v.key_shift) | kb;
+      ok = true;
+    }
+  }
+  return ok;
+}
+
+// verify_screened for a posting given by its record (no length or offset
+// lookups: the record carries them).
+template <int MAXW>
+__host__ __device__ __forceinline__ bool verify_rec(const ProbeView& v, bool self, const HitCtx& hc,
+                                                    const PostRec& rec, unsigned long long& key, int& ed,
+                                                    unsigned long long& cells) {
+  bool ok = false;
+  const int i = hc.i;
+  const int lr = rec_length(rec);
+  if (i >= 1 && i <= v.tau + 1 && lr >= v.tau + 1) {
+    int P, li;
+    even_segment_m(lr, v.tau + 1, v.seg_magic, i, P, li);
+    if (hc.p + li <= hc.ls && verify_ext<MAXW>(hc.s, hc.ls, v.ibytes + rec_offset(rec), lr, i, hc.p, li, P, v.tau,
+                                               li > SEG_EXACT_MAX, ed, cells)) {
+      const uint32_t qid = v.pid ? v.pid[hc.q] : hc.q;
+      const uint32_t rid = v.iperm[rec.sid];
       const uint32_t ka = self ? min(qid, rid) : qid;
       const uint32_t kb = self ? max(qid, rid) : rid;
       key = ((unsigned long long)ka << v.key_shift) | kb;
