@@ -762,7 +762,77 @@ static void launch_fallback(const Ctx& c, const ProbeView& v, uint32_t xcount, A
 
 struct ResultPriv {
   Ctx ctx;
+  size_t pinned_bytes = 0;  // host pairs in a block of the pinned pool (0: malloc)
 };
+
+// Host blocks for host results, reused across calls: page-locked and mapped
+// into the device's address space (cudaHostAlloc), so that the last kernel
+// of a join writes the pairs straight into host memory instead of a device
+// buffer followed by a copy.  Page-locking a large block is slow, hence the
+// reuse.  PJ_HOST_POOL=pageable keeps plain malloc blocks instead (written
+// by a copy from the device).  pj_result_free hands blocks back; at most
+// PINNED_POOL_KEEP bytes stay cached, larger blocks are released.
+constexpr size_t PINNED_POOL_KEEP = 8ull << 30;
+constexpr size_t PINNED_MIN = 1ull << 20;  // smaller results use malloc
+
+static std::mutex g_pinned_mu;
+static std::multimap<size_t, void*> g_pinned_free;  // size -> block
+static size_t g_pinned_cached = 0;
+
+static bool pool_pinned() {
+  static const bool on = [] {
+    const char* e = getenv("PJ_HOST_POOL");
+    return !(e && strcmp(e, "pageable") == 0);
+  }();
+  return on;
+}
+
+static void pool_release(void* p) {
+  if (pool_pinned()) cudaFreeHost(p);
+  else free(p);
+}
+
+static void* pinned_get(size_t bytes, size_t* got) {
+  {
+    std::lock_guard<std::mutex> g(g_pinned_mu);
+    auto it = g_pinned_free.lower_bound(bytes);
+    if (it != g_pinned_free.end() && it->first <= 2 * bytes) {  // reuse a block at most twice as large
+      *got = it->first;
+      void* p = it->second;
+      g_pinned_cached -= it->first;
+      g_pinned_free.erase(it);
+      return p;
+    }
+  }
+  void* p = nullptr;
+  if (pool_pinned()) {
+    if (cudaHostAlloc(&p, bytes, cudaHostAllocMapped) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+  } else {
+    p = malloc(bytes);
+    if (!p) return nullptr;
+  }
+  *got = bytes;
+  return p;
+}
+
+static void pinned_put(void* p, size_t bytes) {
+  std::lock_guard<std::mutex> g(g_pinned_mu);
+  while (g_pinned_cached + bytes > PINNED_POOL_KEEP && !g_pinned_free.empty()) {  // evict the smallest
+    auto it = g_pinned_free.begin();
+    pool_release(it->second);
+    g_pinned_cached -= it->first;
+    g_pinned_free.erase(it);
+  }
+  if (g_pinned_cached + bytes > PINNED_POOL_KEEP) {
+    pool_release(p);
+    return;
+  }
+  g_pinned_free.emplace(bytes, p);
+  g_pinned_cached += bytes;
+}
 
 // Sizing knobs, overridable through the environment (used by tests to drive
 // the chunked and growing paths at small sizes):
@@ -1083,6 +1153,8 @@ static void run_join(const Ctx& c, const ProbeView& v, bool self, uint32_t fb_co
   debug_dump(c, "acc_ed", acc_ed.p, std::min<uint64_t>(nacc, cap) * sizeof(uint32_t));
   uint64_t count = 0;
   DBuf<pj_pair> pairs;
+  void* host_block = nullptr;  // host results written by the emit kernel (mapped pool block)
+  size_t host_got = 0;
   if (nacc > 0) {
     radix_sort_pairs<unsigned long long>(c, acc_key.p, acc_ed.p, nacc, v.key_shift + a_bits);
     trace_mark(c, "join: sort accepted");
@@ -1095,9 +1167,24 @@ static void run_join(const Ctx& c, const ProbeView& v, bool self, uint32_t fb_co
     PJ_CUDA(cudaMemcpyAsync(&last[1], flags.p + nacc - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.stream));
     c.sync();
     count = (uint64_t)last[0] + last[1];
-    pairs.reset(c, count);
+    pj_pair* dst = nullptr;
+    if (!results_on_device && pool_pinned() && count * sizeof(pj_pair) >= PINNED_MIN) {  // emit into host memory
+      host_block = pinned_get(count * sizeof(pj_pair), &host_got);
+      void* dp = nullptr;
+      if (host_block && cudaHostGetDevicePointer(&dp, host_block, 0) == cudaSuccess) {
+        dst = static_cast<pj_pair*>(dp);
+      } else if (host_block) {
+        cudaGetLastError();
+        pinned_put(host_block, host_got);
+        host_block = nullptr;
+      }
+    }
+    if (!dst) {
+      pairs.reset(c, count);
+      dst = pairs.p;
+    }
     k_emit_pairs<<<ceil_div(nacc, 256), 256, 0, c.stream>>>(acc_key.p, acc_ed.p, flags.p, pos.p, nacc, v.key_shift,
-                                                             pairs.p, nullptr, count);
+                                                             dst, nullptr, count);
     PJ_LAUNCHED("k_emit_pairs");
   }
   td.stop();
@@ -1122,13 +1209,29 @@ static void run_join(const Ctx& c, const ProbeView& v, bool self, uint32_t fb_co
     out->pairs = pairs.p;
     pairs.p = nullptr;  // ownership moves to the result
     c.sync();
+  } else if (host_block) {
+    out->on_device = 0;
+    out->pairs = static_cast<pj_pair*>(host_block);
+    static_cast<ResultPriv*>(out->priv)->pinned_bytes = host_got;
+    c.sync();
+    trace_mark(c, "join: results to host");
   } else {
     out->on_device = 0;
-    out->pairs = static_cast<pj_pair*>(malloc(std::max<uint64_t>(count, 1) * sizeof(pj_pair)));
-    if (!out->pairs) fail(PJ_ENOMEM, "host result allocation failed");
+    const size_t bytes = std::max<uint64_t>(count, 1) * sizeof(pj_pair);
+    size_t got = 0;
+    void* pinned = bytes >= PINNED_MIN ? pinned_get(bytes, &got) : nullptr;
+    if (pinned) {
+      out->pairs = static_cast<pj_pair*>(pinned);
+      static_cast<ResultPriv*>(out->priv)->pinned_bytes = got;
+    } else {
+      out->pairs = static_cast<pj_pair*>(malloc(bytes));
+      if (!out->pairs) fail(PJ_ENOMEM, "host result allocation failed");
+    }
+    trace_mark(c, pinned ? "join: host block (pinned)" : "join: host block (malloc)");
     if (count)
       PJ_CUDA(cudaMemcpyAsync(out->pairs, pairs.p, count * sizeof(pj_pair), cudaMemcpyDeviceToHost, c.stream));
     c.sync();
+    trace_mark(c, "join: results to host");
   }
 }
 
@@ -1389,6 +1492,7 @@ static ProbeView index_side(const pj_index& idx, const Partition& part) {
 }
 
 static void self_join_impl(pj_index& idx, int tau, pj_result* out, bool on_device) {
+  trace_mark(idx.ctx, "join: start");
   float part_ms = 0.f;
   ensure_partition(idx, tau, &part_ms);
   struct DumpAfter {
@@ -1737,6 +1841,8 @@ void pj_result_free(pj_result* res) {
         priv->ctx.put(res->pairs);
         cudaStreamSynchronize(priv->ctx.stream);
       }
+    } else if (priv && priv->pinned_bytes) {
+      pj::pinned_put(res->pairs, priv->pinned_bytes);
     } else {
       free(res->pairs);
     }

@@ -331,17 +331,32 @@ def _stats(st: pj_stats) -> dict:
                 verify_mode=int(st.verify_mode), pair_warp=int(st.pair_warp), filtered=int(st.filtered))
 
 
+class _HostPairs:
+    """Owner of a host pj_result whose pairs a numpy array views without a
+    copy; pj_result_free runs when the last view is gone."""
+
+    def __init__(self, res: pj_result):
+        self.res = res
+
+    def __del__(self):
+        try:
+            library().pj_result_free(ctypes.byref(self.res))
+        except Exception:
+            pass
+
+
 def _take(res: pj_result):
     if res.on_device:
         return DeviceResult(res)
     n = int(res.count)
+    stats = _stats(res.stats)
     if n:
         raw = (ctypes.c_uint8 * (n * PAIR_DTYPE.itemsize)).from_address(res.pairs)
-        pairs = np.frombuffer(raw, dtype=PAIR_DTYPE).copy()
+        raw._owner = _HostPairs(res)  # the library's buffer lives as long as the array
+        pairs = np.frombuffer(raw, dtype=PAIR_DTYPE)
     else:
         pairs = np.zeros(0, dtype=PAIR_DTYPE)
-    stats = _stats(res.stats)
-    library().pj_result_free(ctypes.byref(res))
+        library().pj_result_free(ctypes.byref(res))
     return JoinResult(pairs, stats)
 
 
