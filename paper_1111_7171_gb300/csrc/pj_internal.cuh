@@ -131,18 +131,26 @@ __host__ __device__ __forceinline__ uint8_t key_fp(unsigned long long key, uint3
   return f ? f : (uint8_t)1;
 }
 
-// Character-set bound.  A string's bitmap has bit (c mod 64) set for every
-// byte c it contains.  A bit set in one bitmap and clear in the other stands
-// for at least one character of that string that is absent from the other,
-// and distinct bits stand for distinct characters; each needs its own edit
-// (a substitution removes at most one such character from each side), so
-//   ED(x, y) >= max(popcount(bx & ~by), popcount(by & ~bx)).
-// Candidates whose bound exceeds tau are rejected before any DP.  This test
-// is not part of Pass-Join; it only drops pairs that cannot be similar.
-__host__ __device__ __forceinline__ unsigned long long char_bitmap(const uint8_t* p, int n) {
-  unsigned long long b = 0;
-  for (int k = 0; k < n; ++k) b |= 1ull << (p[k] & 63);
-  return b;
+// Character-count bound.  A string's signature is a thermometer code of its
+// character counts: characters fall into 16 buckets (c mod 16), and bucket b
+// owns bits 4b .. 4b+3, of which the lowest min(count_b, 4) are set.  For
+// two strings, popcount(sx & ~sy) = sum over buckets of the surplus of x's
+// (saturated) count over y's, and likewise the other way.  An insertion or a
+// deletion changes one bucket's count by one, a substitution moves one count
+// from a bucket to another, so an edit lowers each surplus sum by at most
+// one and
+//   ED(x, y) >= max(popcount(sx & ~sy), popcount(sy & ~sx)).
+// (Bucketing and saturation only shrink the surpluses.)  Candidates whose
+// bound exceeds tau are rejected before any DP.  This test is not part of
+// Pass-Join; it only drops pairs that cannot be similar.
+__host__ __device__ __forceinline__ unsigned long long char_signature(const uint8_t* p, int n) {
+  unsigned long long t = 0;
+  for (int k = 0; k < n; ++k) {
+    const int sh = 4 * (p[k] & 15);
+    const unsigned long long field = (t >> sh) & 15ull;  // 0, 1, 3, 7 or 15
+    if (field != 15ull) t |= (field + 1ull) << sh;       // set the next bit
+  }
+  return t;
 }
 
 __host__ __device__ __forceinline__ int popcount64(unsigned long long x) {
@@ -153,8 +161,8 @@ __host__ __device__ __forceinline__ int popcount64(unsigned long long x) {
 #endif
 }
 
-__host__ __device__ __forceinline__ int bitmap_bound(unsigned long long bx, unsigned long long by) {
-  const int a = popcount64(bx & ~by), b = popcount64(by & ~bx);
+__host__ __device__ __forceinline__ int signature_bound(unsigned long long sx, unsigned long long sy) {
+  const int a = popcount64(sx & ~sy), b = popcount64(sy & ~sx);
   return a > b ? a : b;
 }
 
@@ -195,36 +203,15 @@ __device__ __forceinline__ int table_find(const Slot* __restrict__ t, const uint
   return -1;
 }
 
-// Everything verification needs about one posting, stored beside the
-// postings in the same order so that the candidates of a run are read as
-// one coalesced stream: the sid, where the string starts in the store and
-// its length, and its character bitmap folded to 32 bits (bit c mod 32; the
-// bound of bitmap_bound holds for any mapping of characters to bits).
+// What the screen in front of verification needs about one posting, stored
+// beside the postings in the same order so that the candidates of a run are
+// read as one coalesced stream: the sid, the string's length and its
+// character signature (char_signature).
 struct __align__(16) PostRec {
   uint32_t sid;
-  uint32_t off_lo;  // string offset in the store, bits 0..31
-  uint32_t len_hi;  // length (bits 0..15) | offset bits 32..47 (bits 16..31)
-  uint32_t bm;
+  uint32_t len;
+  unsigned long long sig;
 };
-
-__host__ __device__ __forceinline__ uint32_t fold_bitmap(unsigned long long b) {
-  return (uint32_t)(b | (b >> 32));
-}
-
-__host__ __device__ __forceinline__ int bitmap_bound32(uint32_t bx, uint32_t by) {
-#ifdef __CUDA_ARCH__
-  const int a = __popc(bx & ~by), b = __popc(by & ~bx);
-#else
-  const int a = __builtin_popcount(bx & ~by), b = __builtin_popcount(by & ~bx);
-#endif
-  return a > b ? a : b;
-}
-
-__host__ __device__ __forceinline__ unsigned long long rec_offset(const PostRec& r) {
-  return ((unsigned long long)(r.len_hi >> 16) << 32) | r.off_lo;
-}
-
-__host__ __device__ __forceinline__ int rec_length(const PostRec& r) { return (int)(r.len_hi & 0xFFFFu); }
 
 // One threshold's segment index.
 struct Partition {
@@ -261,7 +248,7 @@ struct pj_index {
   pj::DBuf<uint32_t> slen;   // lengths by sid
   pj::DBuf<uint32_t> perm;   // sid -> input id
   pj::DBuf<uint32_t> bbeg;   // lmax + 2 bucket starts by length
-  pj::DBuf<unsigned long long> sbm;  // character bitmaps by sid (char_bitmap)
+  pj::DBuf<unsigned long long> sbm;  // character signatures by sid (char_signature)
   std::vector<uint32_t> h_bbeg;
   std::vector<pj::Partition> parts;  // index = tau
   uint64_t device_bytes() const;
@@ -284,7 +271,7 @@ struct ProbeSet {
   const uint8_t* bytes = nullptr;  // string k = bytes[off[k] .. off[k+1])
   const uint64_t* off = nullptr;
   DBuf<uint32_t> len;
-  DBuf<unsigned long long> bm;  // character bitmaps
+  DBuf<unsigned long long> bm;  // character signatures
   uint32_t n = 0;
   int lmax = 0;
 };

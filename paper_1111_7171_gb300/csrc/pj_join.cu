@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(Q_BLOCK) k_verify_queued(const ProbeView v, co
     unsigned long long c = base + lane;
     unsigned long long h = 0, c_lo = 0, c_hi = 0;
     Hit hit{};
-    uint32_t qbm = 0;
+    unsigned long long qsig = 0;
     if (c < n_cand) {
       unsigned long long lo = 0, hi = n_hits;  // last hit whose first candidate is <= c
       while (hi - lo > 1) {
@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(Q_BLOCK) k_verify_queued(const ProbeView v, co
       c_lo = cand_off[h];
       c_hi = h + 1 < n_hits ? cand_off[h + 1] : n_cand;
       hit = hits[h];
-      qbm = v.pbm ? fold_bitmap(v.pbm[hit.q]) : 0u;
+      qsig = v.pbm ? v.pbm[hit.q] : 0ull;
     }
     for (int k = 0; k < V_RUN; ++k, c += 32) {  // the same trip count in every lane
       bool pass = false;
@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(Q_BLOCK) k_verify_queued(const ProbeView v, co
             c_hi = h + 1 < n_hits ? cand_off[h + 1] : n_cand;
           } while (c >= c_hi);
           hit = hits[h];
-          qbm = v.pbm ? fold_bitmap(v.pbm[hit.q]) : 0u;
+          qsig = v.pbm ? v.pbm[hit.q] : 0ull;
         }
         const ProbeView vt = MULTI ? view_for_tau(v, (int)(hit.pi >> 24)) : v;
         pk = hit.begin + (uint32_t)(c - c_lo);
@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(Q_BLOCK) k_verify_queued(const ProbeView v, co
         if (rec.sid >= vt.n_index) {
           err |= 1;
         } else if (!(SELF && rec.sid == hit.q)) {
-          if (v.pbm && bitmap_bound32(qbm, rec.bm) > vt.tau) ++filtered;
+          if (v.pbm && signature_bound(qsig, rec.sig) > vt.tau) ++filtered;
           else pass = true;
         }
       }
@@ -569,7 +569,7 @@ __global__ void __launch_bounds__(BLOCK) k_verify_pairs(const ProbeView v, const
     const uint8_t *sx, *sy;
     int lx, ly;
     pair_strings(v, SELF, key, pshift, x, y, sx, lx, sy, ly);
-    if (v.pbm && bitmap_bound(v.pbm[x], v.ibm[y]) > v.tau) {
+    if (v.pbm && signature_bound(v.pbm[x], v.ibm[y]) > v.tau) {
       ++filtered;
       continue;
     }
@@ -599,7 +599,7 @@ __global__ void __launch_bounds__(BLOCK) k_verify_pairs_warp(const ProbeView v,
     const uint8_t *sx, *sy;
     int lx, ly;
     pair_strings(v, SELF, key, pshift, x, y, sx, lx, sy, ly);
-    if (v.pbm && bitmap_bound(v.pbm[x], v.ibm[y]) > v.tau) continue;  // uniform across the warp
+    if (v.pbm && signature_bound(v.pbm[x], v.ibm[y]) > v.tau) continue;  // uniform across the warp
     const int d = vsp_warp(sx, lx, sy, ly, v.tau, cells);
     if (d <= v.tau && lane == 0) append_match(ctr, out, pair_out_key(v, SELF, x, y), d);
   }
@@ -1627,7 +1627,7 @@ __global__ void k_plan_groups(const uint8_t* __restrict__ bytes, const uint64_t*
   for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < cap_q; q += gridDim.x * blockDim.x) {
     if (q < n) {
       len[q] = (uint32_t)(off[q + 1] - off[q]);
-      bm[q] = char_bitmap(bytes + off[q], (int)len[q]);
+      bm[q] = char_signature(bytes + off[q], (int)len[q]);
       gcnt[q] = (unsigned long long)groups_per_probe((int)tau[q], false);
     } else {
       gcnt[q] = 0;

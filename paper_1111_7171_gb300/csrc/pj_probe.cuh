@@ -71,8 +71,8 @@ struct ProbeView {
   int block_thread;  // block size of the thread-per-candidate verification
   int interleave;    // probe groups interleaved across probes (see group_of)
   const uint16_t* gorder;  // groups of one probe in visiting order (NULL: natural order)
-  // character bitmaps of the probing and the indexed strings (NULL: no
-  // character-set bound)
+  // character signatures of the probing and the indexed strings (NULL: no
+  // character-count bound)
   const unsigned long long* pbm;
   const unsigned long long* ibm;
   int queued;     // thread-per-candidate verification with a screen and per-warp queues
@@ -234,19 +234,19 @@ __host__ __device__ __forceinline__ bool verify_screened(const ProbeView& v, boo
   return ok;
 }
 
-// verify_screened for a posting given by its record (no length or offset
-// lookups: the record carries them).
+// verify_screened for a posting given by its record (which carries the
+// length).
 template <int MAXW>
 __host__ __device__ __forceinline__ bool verify_rec(const ProbeView& v, bool self, const HitCtx& hc,
                                                     const PostRec& rec, unsigned long long& key, int& ed,
                                                     unsigned long long& cells) {
   bool ok = false;
   const int i = hc.i;
-  const int lr = rec_length(rec);
+  const int lr = (int)rec.len;
   if (i >= 1 && i <= v.tau + 1 && lr >= v.tau + 1) {
     int P, li;
     even_segment_m(lr, v.tau + 1, v.seg_magic, i, P, li);
-    if (hc.p + li <= hc.ls && verify_ext<MAXW>(hc.s, hc.ls, v.ibytes + rec_offset(rec), lr, i, hc.p, li, P, v.tau,
+    if (hc.p + li <= hc.ls && verify_ext<MAXW>(hc.s, hc.ls, v.ibytes + v.ioff[rec.sid], lr, i, hc.p, li, P, v.tau,
                                                li > SEG_EXACT_MAX, ed, cells)) {
       const uint32_t qid = v.pid ? v.pid[hc.q] : hc.q;
       const uint32_t rid = v.iperm[rec.sid];
@@ -261,14 +261,14 @@ __host__ __device__ __forceinline__ bool verify_rec(const ProbeView& v, bool sel
 
 // The screen in front of every verification: r must be a valid sid (else
 // err |= 1), not the probe itself (a colliding run may hold it), and pass
-// the character-set bound (else ++filtered).
+// the character-count bound (else ++filtered).
 __host__ __device__ __forceinline__ bool screen_candidate(const ProbeView& v, bool self, uint32_t q, uint32_t r,
                                                           unsigned long long& filtered, int& err) {
   bool pass = false;
   if (r >= v.n_index) {
     err |= 1;
   } else if (!(self && r == q)) {
-    if (v.pbm && bitmap_bound(v.pbm[q], v.ibm[r]) > v.tau) ++filtered;
+    if (v.pbm && signature_bound(v.pbm[q], v.ibm[r]) > v.tau) ++filtered;
     else pass = true;
   }
   return pass;
@@ -306,7 +306,7 @@ __device__ __forceinline__ bool verify_candidate_warp(const ProbeView& v, bool s
   const int i = (int)((h.pi >> 16) & 0xFFu);
   if (r >= v.n_index) {
     err |= 1;
-  } else if (!(self && r == q) && !(v.pbm && bitmap_bound(v.pbm[q], v.ibm[r]) > v.tau)) {
+  } else if (!(self && r == q) && !(v.pbm && signature_bound(v.pbm[q], v.ibm[r]) > v.tau)) {
     const int ls = (int)v.plen[q];
     const int lr = (int)v.ilen[r];
     if (i >= 1 && i <= v.tau + 1 && lr >= v.tau + 1) {

@@ -1,9 +1,10 @@
-// Host-side check of the character-set bound used before verification
-// (bitmap_bound, pj_internal.cuh): it never exceeds the edit distance of
-// Def. 1 (plain Wagner-Fischer DP), on random strings over small alphabets
-// (few distinct bits) and over all 256 byte values (bits shared by c and
-// c + 64k), and it is exact on pairs that differ only by characters absent
-// from the other string.  Prints "bad=<violations> tight=<exact cases>".
+// Host-side check of the character-count bound used before verification
+// (signature_bound of char_signature, pj_internal.cuh): it never exceeds the
+// edit distance of Def. 1 (plain Wagner-Fischer DP), on random strings over
+// small alphabets, over all 256 byte values (buckets shared by c and
+// c + 16k) and with runs of repeated characters (saturated counts), and it
+// is exact on pairs that differ only by characters absent from the other
+// string.  Prints "bad=<violations> tight=<exact cases>".
 #include <cstdio>
 #include <random>
 #include <string>
@@ -33,9 +34,10 @@ int main() {
       std::string a, b;
       for (int k = 0; k < la; ++k) a += (char)(g() % A);
       for (int k = 0; k < lb; ++k) b += (char)(g() % A);
-      const int bound = pj::bitmap_bound(pj::char_bitmap((const uint8_t*)a.data(), la),
-                                         pj::char_bitmap((const uint8_t*)b.data(), lb));
-      const int d = ed(a, b);
+      if (it % 5 == 0) b = a.substr(0, la / 2) + std::string(g() % 9, (char)(g() % A)) + a.substr(la / 2);  // runs
+      const int bound = pj::signature_bound(pj::char_signature((const uint8_t*)a.data(), la),
+                                            pj::char_signature((const uint8_t*)b.data(), (int)b.size()));
+      const int d = ed(a, b);  // b may have been rebuilt above
       if (bound > d) {
         if (bad < 5) printf("A=%d bound %d > ed %d\n", A, bound, d);
         ++bad;
@@ -45,9 +47,9 @@ int main() {
   // substituting k characters by characters the string lacks: bound = ED = k
   for (int k = 1; k <= 6; ++k) {
     std::string a = "abcdefghij", b = a;
-    for (int m = 0; m < k; ++m) b[m] = (char)('A' + m);
-    const int bound = pj::bitmap_bound(pj::char_bitmap((const uint8_t*)a.data(), 10),
-                                       pj::char_bitmap((const uint8_t*)b.data(), 10));
+    for (int m = 0; m < k; ++m) b[m] = (char)('k' + m);  // buckets (c mod 16) absent from a
+    const int bound = pj::signature_bound(pj::char_signature((const uint8_t*)a.data(), 10),
+                                          pj::char_signature((const uint8_t*)b.data(), 10));
     if (bound != k || ed(a, b) != k) ++bad;
   }
   printf("bad=%ld tight=%ld\n", bad, tight);
