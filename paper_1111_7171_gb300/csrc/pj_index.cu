@@ -162,7 +162,7 @@ __global__ void k_gather(const uint8_t* __restrict__ in_bytes, const uint64_t* _
 
 // Character signatures of n strings (bytes[off[k] .. off[k+1])), one thread each.
 __global__ void k_bitmaps(const uint8_t* __restrict__ bytes, const uint64_t* __restrict__ off, uint32_t n,
-                          unsigned long long* __restrict__ bm) {
+                          Sig* __restrict__ bm) {
   for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
     bm[k] = char_signature(bytes + off[k], (int)(off[k + 1] - off[k]));
 }
@@ -194,14 +194,13 @@ __global__ void k_seg_records(const uint8_t* __restrict__ sbytes, const uint64_t
 
 // ---------------------------------------------------------------- A3 ------
 
-__global__ void k_post_records(const uint32_t* __restrict__ postings, uint64_t n, const uint32_t* __restrict__ slen,
-                               const unsigned long long* __restrict__ sbm, PostRec* __restrict__ recs) {
+__global__ void k_post_records(const uint32_t* __restrict__ postings, uint64_t n, const Sig* __restrict__ sbm,
+                               PostRec* __restrict__ recs) {
   for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t sid = postings[k];
     PostRec r;
-    r.sid = sid;
-    r.len = slen[sid];
     r.sig = sbm[sid];
+    r.sig.w[3] = sid;
     recs[k] = r;
   }
 }
@@ -421,7 +420,7 @@ void build_partition(pj_index& idx, int tau, Partition& part) {
   if (h_err) fail(PJ_ECUDA, "segment table insertion failed");
   part.precs.reset(c, nrec);
   k_post_records<<<std::min<unsigned>(ceil_div(nrec, 256), 152u * 16u), 256, 0, c.stream>>>(
-      part.postings.p, nrec, idx.slen.p, idx.sbm.p, part.precs.p);
+      part.postings.p, nrec, idx.sbm.p, part.precs.p);
   PJ_LAUNCHED("k_post_records");
   trace_mark(c, "partition: table");
   if (getenv("PJ_CHECK_INDEX")) check_partition(c, part);

@@ -132,37 +132,49 @@ __host__ __device__ __forceinline__ uint8_t key_fp(unsigned long long key, uint3
 }
 
 // Character-count bound.  A string's signature is a thermometer code of its
-// character counts: characters fall into 16 buckets (c mod 16), and bucket b
-// owns bits 4b .. 4b+3, of which the lowest min(count_b, 4) are set.  For
-// two strings, popcount(sx & ~sy) = sum over buckets of the surplus of x's
-// (saturated) count over y's, and likewise the other way.  An insertion or a
-// deletion changes one bucket's count by one, a substitution moves one count
-// from a bucket to another, so an edit lowers each surplus sum by at most
-// one and
+// character counts: characters fall into SIG_BUCKETS = 24 buckets (c mod
+// 24), and bucket b owns bits 4b .. 4b+3 (word b / 8 of w), of which the
+// lowest min(count_b, 4) are set.  For two strings, the popcount of
+// sx & ~sy over the words is the sum over buckets of the surplus of x's
+// (saturated) count over y's, and likewise the other way.  An insertion or
+// a deletion changes one bucket's count by one, a substitution moves one
+// count from a bucket to another, so an edit lowers each surplus sum by at
+// most one and
 //   ED(x, y) >= max(popcount(sx & ~sy), popcount(sy & ~sx)).
 // (Bucketing and saturation only shrink the surpluses.)  Candidates whose
 // bound exceeds tau are rejected before any DP.  This test is not part of
 // Pass-Join; it only drops pairs that cannot be similar.
-__host__ __device__ __forceinline__ unsigned long long char_signature(const uint8_t* p, int n) {
-  unsigned long long t = 0;
+constexpr int SIG_BUCKETS = 24;
+
+struct __align__(16) Sig {
+  uint32_t w[4];  // 96 signature bits in w[0..2]; w[3] is 0
+};
+
+__host__ __device__ __forceinline__ Sig char_signature(const uint8_t* p, int n) {
+  Sig t = {{0u, 0u, 0u, 0u}};
   for (int k = 0; k < n; ++k) {
-    const int sh = 4 * (p[k] & 15);
-    const unsigned long long field = (t >> sh) & 15ull;  // 0, 1, 3, 7 or 15
-    if (field != 15ull) t |= (field + 1ull) << sh;       // set the next bit
+    const int b = (int)(p[k] % SIG_BUCKETS);
+    const int word = b >> 3, sh = 4 * (b & 7);
+    const uint32_t field = (t.w[word] >> sh) & 15u;  // 0, 1, 3, 7 or 15
+    if (field != 15u) t.w[word] |= (field + 1u) << sh;  // set the next bit
   }
   return t;
 }
 
-__host__ __device__ __forceinline__ int popcount64(unsigned long long x) {
+__host__ __device__ __forceinline__ int popcount32(uint32_t x) {
 #ifdef __CUDA_ARCH__
-  return __popcll(x);
+  return __popc(x);
 #else
-  return __builtin_popcountll(x);
+  return __builtin_popcount(x);
 #endif
 }
 
-__host__ __device__ __forceinline__ int signature_bound(unsigned long long sx, unsigned long long sy) {
-  const int a = popcount64(sx & ~sy), b = popcount64(sy & ~sx);
+__host__ __device__ __forceinline__ int signature_bound(const Sig& x, const Sig& y) {
+  int a = 0, b = 0;
+  for (int k = 0; k < 3; ++k) {
+    a += popcount32(x.w[k] & ~y.w[k]);
+    b += popcount32(y.w[k] & ~x.w[k]);
+  }
   return a > b ? a : b;
 }
 
@@ -205,13 +217,13 @@ __device__ __forceinline__ int table_find(const Slot* __restrict__ t, const uint
 
 // What the screen in front of verification needs about one posting, stored
 // beside the postings in the same order so that the candidates of a run are
-// read as one coalesced stream: the sid, the string's length and its
-// character signature (char_signature).
+// read as one coalesced 16-byte stream: the sid and the string's character
+// signature (char_signature, whose unused word w[3] holds the sid).
 struct __align__(16) PostRec {
-  uint32_t sid;
-  uint32_t len;
-  unsigned long long sig;
+  Sig sig;  // sig.w[3] = sid
 };
+
+__host__ __device__ __forceinline__ uint32_t rec_sid(const PostRec& r) { return r.sig.w[3]; }
 
 // One threshold's segment index.
 struct Partition {
@@ -248,7 +260,7 @@ struct pj_index {
   pj::DBuf<uint32_t> slen;   // lengths by sid
   pj::DBuf<uint32_t> perm;   // sid -> input id
   pj::DBuf<uint32_t> bbeg;   // lmax + 2 bucket starts by length
-  pj::DBuf<unsigned long long> sbm;  // character signatures by sid (char_signature)
+  pj::DBuf<pj::Sig> sbm;     // character signatures by sid (char_signature)
   std::vector<uint32_t> h_bbeg;
   std::vector<pj::Partition> parts;  // index = tau
   uint64_t device_bytes() const;
@@ -271,7 +283,7 @@ struct ProbeSet {
   const uint8_t* bytes = nullptr;  // string k = bytes[off[k] .. off[k+1])
   const uint64_t* off = nullptr;
   DBuf<uint32_t> len;
-  DBuf<unsigned long long> bm;  // character signatures
+  DBuf<Sig> bm;  // character signatures
   uint32_t n = 0;
   int lmax = 0;
 };

@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(Q_BLOCK) k_verify_queued(const ProbeView v, co
     unsigned long long c = base + lane;
     unsigned long long h = 0, c_lo = 0, c_hi = 0;
     Hit hit{};
-    unsigned long long qsig = 0;
+    Sig qsig = {{0u, 0u, 0u, 0u}};
     if (c < n_cand) {
       unsigned long long lo = 0, hi = n_hits;  // last hit whose first candidate is <= c
       while (hi - lo > 1) {
@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(Q_BLOCK) k_verify_queued(const ProbeView v, co
       c_lo = cand_off[h];
       c_hi = h + 1 < n_hits ? cand_off[h + 1] : n_cand;
       hit = hits[h];
-      qsig = v.pbm ? v.pbm[hit.q] : 0ull;
+      if (v.pbm) qsig = v.pbm[hit.q];
     }
     for (int k = 0; k < V_RUN; ++k, c += 32) {  // the same trip count in every lane
       bool pass = false;
@@ -369,15 +369,15 @@ __global__ void __launch_bounds__(Q_BLOCK) k_verify_queued(const ProbeView v, co
             c_hi = h + 1 < n_hits ? cand_off[h + 1] : n_cand;
           } while (c >= c_hi);
           hit = hits[h];
-          qsig = v.pbm ? v.pbm[hit.q] : 0ull;
+          if (v.pbm) qsig = v.pbm[hit.q];
         }
         const ProbeView vt = MULTI ? view_for_tau(v, (int)(hit.pi >> 24)) : v;
         pk = hit.begin + (uint32_t)(c - c_lo);
         const PostRec rec = vt.precs[pk];
         // screen: a valid sid, not the probe itself, character-set bound
-        if (rec.sid >= vt.n_index) {
+        if (rec_sid(rec) >= vt.n_index) {
           err |= 1;
-        } else if (!(SELF && rec.sid == hit.q)) {
+        } else if (!(SELF && rec_sid(rec) == hit.q)) {
           if (v.pbm && signature_bound(qsig, rec.sig) > vt.tau) ++filtered;
           else pass = true;
         }
@@ -1621,7 +1621,7 @@ static_assert(sizeof(Counters) == 64, "plan counters are 64 bytes");
 // group offsets of every q >= n equal the total (group_of searches all cap_q).
 __global__ void k_plan_groups(const uint8_t* __restrict__ bytes, const uint64_t* __restrict__ off,
                               const uint8_t* __restrict__ tau, uint32_t cap_q, const PlanSizes* __restrict__ sizes,
-                              uint32_t* __restrict__ len, unsigned long long* __restrict__ bm,
+                              uint32_t* __restrict__ len, Sig* __restrict__ bm,
                               unsigned long long* __restrict__ gcnt) {
   const unsigned long long n = sizes->n;
   for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < cap_q; q += gridDim.x * blockDim.x) {

@@ -104,7 +104,8 @@ struct pj_plan {
   pj::DBuf<uint64_t> off;
   pj::DBuf<pj::PlanSizes> sizes;
   pj::DBuf<uint32_t> len, gcounts, goff, flags, pos, acc_ed0, acc_ed1;
-  pj::DBuf<unsigned long long> gcnt, qgoff, gmask, hcnt, hoff, acc_key0, acc_key1, bm;
+  pj::DBuf<unsigned long long> gcnt, qgoff, gmask, hcnt, hoff, acc_key0, acc_key1;
+  pj::DBuf<pj::Sig> bm;
   pj::DBuf<pj::PartView> parts;
   pj::DBuf<unsigned char> counters, arena;
   pj::DBuf<pj::Hit> hits;
@@ -139,8 +140,9 @@ struct pj_plan {
     sizes.release();
     pj::DBuf<uint32_t>* b32[] = {&len, &gcounts, &goff, &flags, &pos, &acc_ed0, &acc_ed1};
     for (auto* b : b32) b->release();
-    pj::DBuf<unsigned long long>* b64[] = {&gcnt, &qgoff, &gmask, &hcnt, &hoff, &acc_key0, &acc_key1, &bm};
+    pj::DBuf<unsigned long long>* b64[] = {&gcnt, &qgoff, &gmask, &hcnt, &hoff, &acc_key0, &acc_key1};
     for (auto* b : b64) b->release();
+    bm.release();
     parts.release();
     counters.release();
     arena.release();

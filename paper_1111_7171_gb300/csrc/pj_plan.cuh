@@ -35,7 +35,7 @@ struct PlanDev {
   PlanSizes* sizes;
   // pipeline state
   uint32_t* len;                  // cap_q
-  unsigned long long* bm;         // cap_q character bitmaps
+  Sig* bm;                        // cap_q character signatures
   unsigned long long* gcnt;       // cap_q groups per query
   unsigned long long* qgoff;      // cap_q group offsets
   const PartView* parts;          // tau_max + 1 thresholds

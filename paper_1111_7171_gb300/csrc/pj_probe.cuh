@@ -73,8 +73,8 @@ struct ProbeView {
   const uint16_t* gorder;  // groups of one probe in visiting order (NULL: natural order)
   // character signatures of the probing and the indexed strings (NULL: no
   // character-count bound)
-  const unsigned long long* pbm;
-  const unsigned long long* ibm;
+  const Sig* pbm;
+  const Sig* ibm;
   int queued;     // thread-per-candidate verification with a screen and per-warp queues
   int pair_mode;  // 1: mode L (distinct candidate pairs verified once over the whole strings)
   int pair_warp;  // mode L: one warp per pair instead of one thread
@@ -234,22 +234,22 @@ __host__ __device__ __forceinline__ bool verify_screened(const ProbeView& v, boo
   return ok;
 }
 
-// verify_screened for a posting given by its record (which carries the
-// length).
+// verify_screened for a posting given by its record.
 template <int MAXW>
 __host__ __device__ __forceinline__ bool verify_rec(const ProbeView& v, bool self, const HitCtx& hc,
                                                     const PostRec& rec, unsigned long long& key, int& ed,
                                                     unsigned long long& cells) {
   bool ok = false;
   const int i = hc.i;
-  const int lr = (int)rec.len;
+  const uint32_t sid = rec_sid(rec);
+  const int lr = (int)v.ilen[sid];
   if (i >= 1 && i <= v.tau + 1 && lr >= v.tau + 1) {
     int P, li;
     even_segment_m(lr, v.tau + 1, v.seg_magic, i, P, li);
-    if (hc.p + li <= hc.ls && verify_ext<MAXW>(hc.s, hc.ls, v.ibytes + v.ioff[rec.sid], lr, i, hc.p, li, P, v.tau,
+    if (hc.p + li <= hc.ls && verify_ext<MAXW>(hc.s, hc.ls, v.ibytes + v.ioff[sid], lr, i, hc.p, li, P, v.tau,
                                                li > SEG_EXACT_MAX, ed, cells)) {
       const uint32_t qid = v.pid ? v.pid[hc.q] : hc.q;
-      const uint32_t rid = v.iperm[rec.sid];
+      const uint32_t rid = v.iperm[sid];
       const uint32_t ka = self ? min(qid, rid) : qid;
       const uint32_t kb = self ? max(qid, rid) : rid;
       key = ((unsigned long long)ka << v.key_shift) | kb;

@@ -2,7 +2,7 @@
 // (signature_bound of char_signature, pj_internal.cuh): it never exceeds the
 // edit distance of Def. 1 (plain Wagner-Fischer DP), on random strings over
 // small alphabets, over all 256 byte values (buckets shared by c and
-// c + 16k) and with runs of repeated characters (saturated counts), and it
+// c + 24k) and with runs of repeated characters (saturated counts), and it
 // is exact on pairs that differ only by characters absent from the other
 // string.  Prints "bad=<violations> tight=<exact cases>".
 #include <cstdio>
@@ -47,7 +47,7 @@ int main() {
   // substituting k characters by characters the string lacks: bound = ED = k
   for (int k = 1; k <= 6; ++k) {
     std::string a = "abcdefghij", b = a;
-    for (int m = 0; m < k; ++m) b[m] = (char)('k' + m);  // buckets (c mod 16) absent from a
+    for (int m = 0; m < k; ++m) b[m] = (char)('k' + m);  // buckets (c mod 24) absent from a
     const int bound = pj::signature_bound(pj::char_signature((const uint8_t*)a.data(), 10),
                                           pj::char_signature((const uint8_t*)b.data(), 10));
     if (bound != k || ed(a, b) != k) ++bad;
