@@ -103,9 +103,10 @@ typedef struct {
   float tune_ms;        /* time spent autotuning during this call (0 when the decision was cached) */
   int32_t verify_mode;  /* PJ_VERIFY_EXTENSION or PJ_VERIFY_PAIRS, as run */
   int32_t pair_warp;    /* PJ_VERIFY_PAIRS: 1 when one warp verified each pair */
-  uint64_t filtered;    /* candidates rejected before any DP by the character-set bound
-                           ED(x, y) >= max |chars(x) \ chars(y)|, |chars(y) \ chars(x)|
-                           (characters taken mod 64); not part of Pass-Join, exact */
+  uint64_t filtered;    /* candidates rejected before any DP by the character-count bound
+                           ED(x, y) >= max over the two directions of the summed surplus of
+                           one string's character counts over the other's (characters in
+                           24 buckets, counts capped at 4); not part of Pass-Join, exact */
 } pj_stats;
 
 typedef struct {

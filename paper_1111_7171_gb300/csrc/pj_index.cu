@@ -161,7 +161,7 @@ __global__ void k_gather(const uint8_t* __restrict__ in_bytes, const uint64_t* _
 }
 
 // Character signatures of n strings (bytes[off[k] .. off[k+1])), one thread each.
-__global__ void k_bitmaps(const uint8_t* __restrict__ bytes, const uint64_t* __restrict__ off, uint32_t n,
+__global__ void k_signatures(const uint8_t* __restrict__ bytes, const uint64_t* __restrict__ off, uint32_t n,
                           Sig* __restrict__ bm) {
   for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
     bm[k] = char_signature(bytes + off[k], (int)(off[k + 1] - off[k]));
@@ -323,9 +323,9 @@ void build_store(pj_index& idx, const pj_strings& S) {
   }
   idx.sbm.reset(c, n ? n : 1);
   if (n) {
-    k_bitmaps<<<std::min<unsigned>(ceil_div(n, 256), 152u * 8u), 256, 0, c.stream>>>(idx.sbytes.p, idx.soff.p, n,
+    k_signatures<<<std::min<unsigned>(ceil_div(n, 256), 152u * 8u), 256, 0, c.stream>>>(idx.sbytes.p, idx.soff.p, n,
                                                                                     idx.sbm.p);
-    PJ_LAUNCHED("k_bitmaps");
+    PJ_LAUNCHED("k_signatures");
   }
   idx.bbeg.reset(c, (size_t)idx.lmax + 2);
   k_buckets<<<ceil_div((size_t)n + 1, 256), 256, 0, c.stream>>>(idx.slen.p, n, idx.bbeg.p, idx.lmax);
@@ -514,8 +514,8 @@ void upload_probe_set(const Ctx& c, const pj_strings& R, ProbeSet& out) {
   out.lmax = (int)h_lmax;
   out.bm.reset(c, R.n ? R.n : 1);
   if (R.n) {
-    k_bitmaps<<<std::min<unsigned>(ceil_div(R.n, 256), 152u * 8u), 256, 0, c.stream>>>(dbytes, doff, R.n, out.bm.p);
-    PJ_LAUNCHED("k_bitmaps");
+    k_signatures<<<std::min<unsigned>(ceil_div(R.n, 256), 152u * 8u), 256, 0, c.stream>>>(dbytes, doff, R.n, out.bm.p);
+    PJ_LAUNCHED("k_signatures");
   }
   out.bytes = dbytes;
   out.off = doff;

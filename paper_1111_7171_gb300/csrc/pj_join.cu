@@ -44,7 +44,7 @@ struct Counters {
   unsigned long long fallback;
   unsigned long long hits;
   unsigned long long err;  // bit 0: run or posting outside the index; bit 1: probe limit
-  unsigned long long filtered;  // candidates rejected by the character-set bound
+  unsigned long long filtered;  // candidates rejected by the character-count bound
 };
 
 struct AccOut {
@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(512) k_verify_hits(const ProbeView v, const Hi
 }
 
 // The same verification with a screen and a per-warp queue: every lane
-// first screens its candidate (valid sid, not the probe, character-set
+// first screens its candidate (valid sid, not the probe, character-count
 // bound) -- cheap and uniform code -- and the survivors are appended to a
 // queue in shared memory; whenever 32 are queued, each lane takes one and
 // runs extension verification.  Screened-out candidates then cost no DP
@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(Q_BLOCK) k_verify_queued(const ProbeView v, co
         const ProbeView vt = MULTI ? view_for_tau(v, (int)(hit.pi >> 24)) : v;
         pk = hit.begin + (uint32_t)(c - c_lo);
         const PostRec rec = vt.precs[pk];
-        // screen: a valid sid, not the probe itself, character-set bound
+        // screen: a valid sid, not the probe itself, character-count bound
         if (rec_sid(rec) >= vt.n_index) {
           err |= 1;
         } else if (!(SELF && rec_sid(rec) == hit.q)) {
