@@ -308,9 +308,11 @@ __global__ void __launch_bounds__(512) k_verify_hits(const ProbeView v, const Hi
 constexpr int Q_BLOCK = 256;
 constexpr int Q_WARPS = Q_BLOCK / 32;
 constexpr int Q_CAP = 64;  // entries per warp: < 32 left + 32 new
+// Four blocks per SM (64 registers): measured faster than the 68 registers
+// the pipelined screen would take unbounded.
 
 template <int MAXW, bool SELF, bool MULTI>
-__global__ void __launch_bounds__(Q_BLOCK) k_verify_queued(const ProbeView v, const Hit* __restrict__ hits,
+__global__ void __launch_bounds__(Q_BLOCK, 4) k_verify_queued(const ProbeView v, const Hit* __restrict__ hits,
                                                             const unsigned long long* __restrict__ cand_off,
                                                             unsigned long long n_hits, unsigned long long c_begin,
                                                             unsigned long long n_cand, AccOut out, Counters* ctr,
@@ -346,7 +348,24 @@ __global__ void __launch_bounds__(Q_BLOCK) k_verify_queued(const ProbeView v, co
     unsigned long long h = 0, c_lo = 0, c_hi = 0;
     Hit hit{};
     Sig qsig = {{0u, 0u, 0u, 0u}};
-    if (c < n_cand) {
+    // Walk to candidate c (hits in candidate order) and load its record; the
+    // record of the next round is loaded before this round's ballot, so its
+    // latency overlaps the queue work and the verifications.
+    auto walk = [&](unsigned long long cc) {
+      if (cc >= c_hi) {
+        do {
+          ++h;
+          c_lo = c_hi;
+          c_hi = h + 1 < n_hits ? cand_off[h + 1] : n_cand;
+        } while (cc >= c_hi);
+        hit = hits[h];
+        if (v.pbm) qsig = v.pbm[hit.q];
+      }
+    };
+    bool nv = c < n_cand;  // next (here: first) candidate valid
+    uint32_t npk = 0;
+    PostRec nrec{};
+    if (nv) {
       unsigned long long lo = 0, hi = n_hits;  // last hit whose first candidate is <= c
       while (hi - lo > 1) {
         const unsigned long long mid = (lo + hi) >> 1;
@@ -357,28 +376,30 @@ __global__ void __launch_bounds__(Q_BLOCK) k_verify_queued(const ProbeView v, co
       c_hi = h + 1 < n_hits ? cand_off[h + 1] : n_cand;
       hit = hits[h];
       if (v.pbm) qsig = v.pbm[hit.q];
+      npk = hit.begin + (uint32_t)(c - c_lo);
+      nrec = (MULTI ? view_for_tau(v, (int)(hit.pi >> 24)) : v).precs[npk];
     }
-    for (int k = 0; k < V_RUN; ++k, c += 32) {  // the same trip count in every lane
+    for (int k = 0; k < V_RUN; ++k) {  // the same trip count in every lane
+      // this round's candidate
+      const bool cv = nv;
+      const uint32_t pk = npk, ch = (uint32_t)h, cq = hit.q;
+      const int ctau = MULTI ? (int)(hit.pi >> 24) : v.tau;
+      const PostRec rec = nrec;
+      const Sig csig = qsig;
+      // the next round's record
+      c += 32;
+      nv = cv && k + 1 < V_RUN && c < n_cand;
+      if (nv) {
+        walk(c);
+        npk = hit.begin + (uint32_t)(c - c_lo);
+        nrec = (MULTI ? view_for_tau(v, (int)(hit.pi >> 24)) : v).precs[npk];
+      }
       bool pass = false;
-      uint32_t pk = 0;
-      if (c < n_cand) {
-        if (c >= c_hi) {
-          do {
-            ++h;
-            c_lo = c_hi;
-            c_hi = h + 1 < n_hits ? cand_off[h + 1] : n_cand;
-          } while (c >= c_hi);
-          hit = hits[h];
-          if (v.pbm) qsig = v.pbm[hit.q];
-        }
-        const ProbeView vt = MULTI ? view_for_tau(v, (int)(hit.pi >> 24)) : v;
-        pk = hit.begin + (uint32_t)(c - c_lo);
-        const PostRec rec = vt.precs[pk];
-        // screen: a valid sid, not the probe itself, character-count bound
-        if (rec_sid(rec) >= vt.n_index) {
+      if (cv) {  // screen: a valid sid, not the probe itself, character-count bound
+        if (rec_sid(rec) >= v.n_index) {
           err |= 1;
-        } else if (!(SELF && rec_sid(rec) == hit.q)) {
-          if (v.pbm && signature_bound(qsig, rec.sig) > vt.tau) ++filtered;
+        } else if (!(SELF && rec_sid(rec) == cq)) {
+          if (v.pbm && signature_bound(csig, rec.sig) > ctau) ++filtered;
           else pass = true;
         }
       }
@@ -386,7 +407,7 @@ __global__ void __launch_bounds__(Q_BLOCK) k_verify_queued(const ProbeView v, co
       const unsigned m = __ballot_sync(FULL, pass);
       if (pass) {
         const int slot = qn + __popc(m & lanemask_lt());
-        q_hit[wib][slot] = (uint32_t)h;
+        q_hit[wib][slot] = ch;
         q_post[wib][slot] = pk;
       }
       qn += __popc(m);
