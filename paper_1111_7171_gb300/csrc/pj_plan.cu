@@ -83,9 +83,9 @@ static size_t scan_temp_bytes(size_t n, size_t es) {
 }
 
 // Temporaries of radix_sort_pairs_dn over n items: digit histograms and
-// their offsets (256 per 4096-item tile), and their scan.
+// their offsets (256 per 2048-item tile), and their scan.
 static size_t sort_temp_bytes(size_t n) {
-  const size_t h = 256 * ((n + 4095) / 4096);
+  const size_t h = 256 * ((n + 2047) / 2048);
   return 2 * align256(h * 4) + scan_temp_bytes(h, 4);
 }
 

@@ -12,10 +12,11 @@
 // Radix sort: 8-bit digits, one pass per digit.  Each pass runs a histogram
 // kernel (per-tile digit counts, stored digit-major so that one exclusive
 // scan over them yields every (digit, tile) output offset) and a scatter
-// kernel.  Inside a tile each warp owns 512 consecutive items, handled 32 at
-// a time; lanes holding the same digit find each other with match.any, so the
-// rank of an item among equal digits follows input order and the sort is
-// stable.
+// kernel.  Inside a 2048-item tile each warp owns 256 consecutive items,
+// handled 32 at a time; lanes holding the same digit find each other with
+// match.any, so the rank of an item among equal digits follows input order
+// and the sort is stable.  The scatter reorders the tile by digit in shared
+// memory before writing, so each digit's items leave as one contiguous run.
 #include "pj_prims.cuh"
 
 #include <algorithm>
@@ -94,9 +95,9 @@ __global__ void k_widen(const uint32_t* __restrict__ in, uint64_t* __restrict__ 
 
 constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
-constexpr int RS_ROUNDS = 16;  // items per lane
+constexpr int RS_ROUNDS = 8;   // items per lane
 constexpr int RS_WARP_ITEMS = 32 * RS_ROUNDS;
-constexpr int RS_TILE = RS_WARPS * RS_WARP_ITEMS;  // 4096
+constexpr int RS_TILE = RS_WARPS * RS_WARP_ITEMS;  // 2048
 
 template <class K>
 __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const K* __restrict__ keys, size_t n, int shift,
@@ -128,13 +129,20 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const K* __restrict__
                                                            size_t n, int shift, const uint32_t* __restrict__ offs,
                                                            unsigned ntiles,
                                                            const unsigned long long* __restrict__ n_dev) {
+  // The tile is first reordered by digit in shared memory (stably), then
+  // written out digit segment by digit segment, so that neighbouring threads
+  // write neighbouring addresses.
   __shared__ uint32_t wcnt[RS_WARPS][256];
+  __shared__ uint32_t local_start[256], global_start[256];
+  __shared__ K skey[RS_TILE];
+  __shared__ uint32_t sval[RS_TILE];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   n = dev_count(n, n_dev);
   if ((size_t)blockIdx.x * RS_TILE >= n) return;
   for (int d = tid; d < RS_WARPS * 256; d += RS_THREADS) (&wcnt[0][0])[d] = 0;
   __syncthreads();
-  const size_t wbase = (size_t)blockIdx.x * RS_TILE + (size_t)warp * RS_WARP_ITEMS;
+  const size_t tbase = (size_t)blockIdx.x * RS_TILE;
+  const size_t wbase = tbase + (size_t)warp * RS_WARP_ITEMS;
   K key[RS_ROUNDS];
   uint32_t val[RS_ROUNDS];
   uint32_t rank[RS_ROUNDS];
@@ -158,14 +166,25 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const K* __restrict__
   }
   __syncthreads();
   {
-    const int d = tid;  // one thread per digit
-    uint32_t run = offs[(size_t)d * ntiles + blockIdx.x];
+    // one thread per digit: the warps' starts inside the digit, the digit's
+    // count in the tile, its start in the tile (block scan) and in the output
+    const int d = tid;
+    uint32_t run = 0;
 #pragma unroll
     for (int w = 0; w < RS_WARPS; ++w) {
       const uint32_t t = wcnt[w][d];
       wcnt[w][d] = run;
       run += t;
     }
+    __shared__ uint32_t wsum[RS_WARPS];
+    const uint32_t incl = warp_incl_scan(run);
+    if (lane == 31) wsum[warp] = incl;
+    __syncwarp();
+    __syncthreads();
+    uint32_t before = 0;
+    for (int w = 0; w < warp; ++w) before += wsum[w];
+    local_start[d] = before + incl - run;
+    global_start[d] = offs[(size_t)d * ntiles + blockIdx.x];
   }
   __syncthreads();
 #pragma unroll
@@ -173,10 +192,19 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const K* __restrict__
     const size_t i = wbase + (size_t)r * 32 + lane;
     if (i < n) {
       const unsigned d = (unsigned)(key[r] >> shift) & 0xFFu;
-      const uint32_t pos = wcnt[warp][d] + rank[r];
-      kout[pos] = key[r];
-      vout[pos] = val[r];
+      const uint32_t lp = local_start[d] + wcnt[warp][d] + rank[r];
+      skey[lp] = key[r];
+      sval[lp] = val[r];
     }
+  }
+  __syncthreads();
+  const int valid_items = (int)min((size_t)RS_TILE, n - tbase);
+  for (int j = tid; j < valid_items; j += RS_THREADS) {
+    const K k = skey[j];
+    const unsigned d = (unsigned)(k >> shift) & 0xFFu;
+    const uint32_t pos = global_start[d] + (uint32_t)(j - (int)local_start[d]);
+    kout[pos] = k;
+    vout[pos] = sval[j];
   }
 }
 
