@@ -298,21 +298,22 @@ __global__ void __launch_bounds__(512) k_verify_hits(const ProbeView v, const Hi
 }
 
 // The same verification with a screen and a per-warp queue: every lane
-// first screens its candidate (valid sid, not the probe, character-count
-// bound) -- cheap and uniform code -- and the survivors are appended to a
-// queue in shared memory; whenever 32 are queued, each lane takes one and
-// runs extension verification.  Screened-out candidates then cost no DP
-// slot, so the warps' DP lanes stay full.  The warp-wide ballot sits in a
-// loop whose trip count is the same for all 32 lanes, and the queue is read
-// before the next writes only after a __syncwarp.
+// first screens S_RUN consecutive candidates on its own (valid sid, not the
+// probe, character-count bound) -- independent loads of their posting
+// records, no warp collectives -- and one warp scan of the lanes' survivor
+// counts places all survivors in a queue in shared memory; while 32 or more
+// are queued, each lane takes one and runs extension verification.
+// Screened-out candidates then cost no DP slot, so the warps' DP lanes stay
+// full.  The scan and the queue loop run the same number of times in all 32
+// lanes, and queue entries are read before the next writes only after a
+// __syncwarp.
 constexpr int Q_BLOCK = 256;
 constexpr int Q_WARPS = Q_BLOCK / 32;
-constexpr int Q_CAP = 64;  // entries per warp: < 32 left + 32 new
-// Four blocks per SM (64 registers): measured faster than the 68 registers
-// the pipelined screen would take unbounded.
+constexpr int S_RUN = 8;                 // consecutive candidates one lane screens
+constexpr int Q_CAP = 32 * S_RUN + 32;   // < 32 left + up to 32 * S_RUN new
 
 template <int MAXW, bool SELF, bool MULTI>
-__global__ void __launch_bounds__(Q_BLOCK, 4) k_verify_queued(const ProbeView v, const Hit* __restrict__ hits,
+__global__ void __launch_bounds__(Q_BLOCK) k_verify_queued(const ProbeView v, const Hit* __restrict__ hits,
                                                             const unsigned long long* __restrict__ cand_off,
                                                             unsigned long long n_hits, unsigned long long c_begin,
                                                             unsigned long long n_cand, AccOut out, Counters* ctr,
@@ -328,7 +329,7 @@ __global__ void __launch_bounds__(Q_BLOCK, 4) k_verify_queued(const ProbeView v,
   const unsigned lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
   const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const unsigned long long n_warps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
-  const unsigned long long span = 32ull * V_RUN;
+  const unsigned long long span = 32ull * S_RUN;
   int qn = 0;  // the same in every lane
   auto verify_entry = [&](uint32_t h, uint32_t k) {
     const Hit hit = hits[h];
@@ -344,80 +345,71 @@ __global__ void __launch_bounds__(Q_BLOCK, 4) k_verify_queued(const ProbeView v,
     }
   };
   for (unsigned long long base = c_begin + warp * span; base < n_cand; base += n_warps * span) {
-    unsigned long long c = base + lane;
-    unsigned long long h = 0, c_lo = 0, c_hi = 0;
-    Hit hit{};
-    Sig qsig = {{0u, 0u, 0u, 0u}};
-    // Walk to candidate c (hits in candidate order) and load its record; the
-    // record of the next round is loaded before this round's ballot, so its
-    // latency overlaps the queue work and the verifications.
-    auto walk = [&](unsigned long long cc) {
-      if (cc >= c_hi) {
-        do {
-          ++h;
-          c_lo = c_hi;
-          c_hi = h + 1 < n_hits ? cand_off[h + 1] : n_cand;
-        } while (cc >= c_hi);
-        hit = hits[h];
-        if (v.pbm) qsig = v.pbm[hit.q];
-      }
-    };
-    bool nv = c < n_cand;  // next (here: first) candidate valid
-    uint32_t npk = 0;
-    PostRec nrec{};
-    if (nv) {
-      unsigned long long lo = 0, hi = n_hits;  // last hit whose first candidate is <= c
+    const unsigned long long c0 = base + (unsigned long long)lane * S_RUN;
+    uint32_t mask = 0;
+    uint32_t eh[S_RUN], ek[S_RUN];
+    if (c0 < n_cand) {
+      unsigned long long lo = 0, hi = n_hits;  // last hit whose first candidate is <= c0
       while (hi - lo > 1) {
         const unsigned long long mid = (lo + hi) >> 1;
-        if (cand_off[mid] <= c) lo = mid; else hi = mid;
+        if (cand_off[mid] <= c0) lo = mid; else hi = mid;
       }
-      h = lo;
-      c_lo = cand_off[h];
-      c_hi = h + 1 < n_hits ? cand_off[h + 1] : n_cand;
-      hit = hits[h];
+      unsigned long long h = lo;
+      unsigned long long c_lo = cand_off[h];
+      unsigned long long c_hi = h + 1 < n_hits ? cand_off[h + 1] : n_cand;
+      Hit hit = hits[h];
+      Sig qsig = {{0u, 0u, 0u, 0u}};
       if (v.pbm) qsig = v.pbm[hit.q];
-      npk = hit.begin + (uint32_t)(c - c_lo);
-      nrec = (MULTI ? view_for_tau(v, (int)(hit.pi >> 24)) : v).precs[npk];
-    }
-    for (int k = 0; k < V_RUN; ++k) {  // the same trip count in every lane
-      // this round's candidate
-      const bool cv = nv;
-      const uint32_t pk = npk, ch = (uint32_t)h, cq = hit.q;
-      const int ctau = MULTI ? (int)(hit.pi >> 24) : v.tau;
-      const PostRec rec = nrec;
-      const Sig csig = qsig;
-      // the next round's record
-      c += 32;
-      nv = cv && k + 1 < V_RUN && c < n_cand;
-      if (nv) {
-        walk(c);
-        npk = hit.begin + (uint32_t)(c - c_lo);
-        nrec = (MULTI ? view_for_tau(v, (int)(hit.pi >> 24)) : v).precs[npk];
-      }
-      bool pass = false;
-      if (cv) {  // screen: a valid sid, not the probe itself, character-count bound
-        if (rec_sid(rec) >= v.n_index) {
-          err |= 1;
-        } else if (!(SELF && rec_sid(rec) == cq)) {
-          if (v.pbm && signature_bound(csig, rec.sig) > ctau) ++filtered;
-          else pass = true;
+#pragma unroll
+      for (int k = 0; k < S_RUN; ++k) {
+        const unsigned long long c = c0 + k;
+        eh[k] = 0;
+        ek[k] = 0;
+        if (c < n_cand) {
+          if (c >= c_hi) {  // into a later hit
+            do {
+              ++h;
+              c_lo = c_hi;
+              c_hi = h + 1 < n_hits ? cand_off[h + 1] : n_cand;
+            } while (c >= c_hi);
+            hit = hits[h];
+            if (v.pbm) qsig = v.pbm[hit.q];
+          }
+          const ProbeView vt = MULTI ? view_for_tau(v, (int)(hit.pi >> 24)) : v;
+          const uint32_t pk = hit.begin + (uint32_t)(c - c_lo);
+          const PostRec rec = vt.precs[pk];
+          eh[k] = (uint32_t)h;
+          ek[k] = pk;
+          // screen: a valid sid, not the probe itself, character-count bound
+          if (rec_sid(rec) >= vt.n_index) {
+            err |= 1;
+          } else if (!(SELF && rec_sid(rec) == hit.q)) {
+            if (v.pbm && signature_bound(qsig, rec.sig) > vt.tau) ++filtered;
+            else mask |= 1u << k;
+          }
         }
       }
-      __syncwarp();
-      const unsigned m = __ballot_sync(FULL, pass);
-      if (pass) {
-        const int slot = qn + __popc(m & lanemask_lt());
-        q_hit[wib][slot] = ch;
-        q_post[wib][slot] = pk;
+    }
+    __syncwarp();
+    const int cnt = __popc(mask);
+    const int incl = warp_incl_scan(cnt);
+    const int total = __shfl_sync(FULL, incl, 31);
+    int slot = qn + incl - cnt;
+#pragma unroll
+    for (int k = 0; k < S_RUN; ++k) {
+      if ((mask >> k) & 1u) {
+        q_hit[wib][slot] = eh[k];
+        q_post[wib][slot] = ek[k];
+        ++slot;
       }
-      qn += __popc(m);
-      __syncwarp();
-      if (qn >= 32) {
-        qn -= 32;
-        const uint32_t eh = q_hit[wib][qn + lane], ek = q_post[wib][qn + lane];
-        __syncwarp();  // taken before the next round's writes
-        verify_entry(eh, ek);
-      }
+    }
+    qn += total;
+    __syncwarp();
+    while (qn >= 32) {  // the same in every lane
+      qn -= 32;
+      const uint32_t h2 = q_hit[wib][qn + lane], k2 = q_post[wib][qn + lane];
+      __syncwarp();  // taken before any later write
+      verify_entry(h2, k2);
     }
   }
   __syncwarp();
@@ -737,8 +729,8 @@ static void launch_verify(const Ctx& c, const ProbeView& v, const Hit* hits, con
                           AccOut out, Counters* ctr, int block) {
   if (v.queued) {
     const unsigned gq = persistent_grid(k_verify_queued<MAXW, SELF, MULTI>,
-                                        (c_end - c_begin + (unsigned long long)Q_BLOCK * V_RUN - 1) /
-                                            ((unsigned long long)Q_BLOCK * V_RUN), Q_BLOCK);
+                                        (c_end - c_begin + (unsigned long long)Q_BLOCK * S_RUN - 1) /
+                                            ((unsigned long long)Q_BLOCK * S_RUN), Q_BLOCK);
     k_verify_queued<MAXW, SELF, MULTI><<<gq, Q_BLOCK, 0, c.stream>>>(v, hits, off, n_hits, c_begin, c_end, out, ctr,
                                                                     nullptr);
     PJ_LAUNCHED("k_verify_queued");
