@@ -463,6 +463,32 @@ def run_native(args):
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
     barrier()
 
+    # ---- the same join repeated on a resident index: eager, and replayed as
+    # one recorded CUDA graph (graph_joins); store build not included
+    resident = {}
+    for mode, graph in (("eager", False), ("graph", True)):
+        idx = pj.pj_build_index((d_bytes, d_off), args.tau, results_on_device=True, autotune=True,
+                                graph_joins=graph)
+        for _ in range(2):  # tuning, then (graph) the recorded join
+            pj.pj_self_join(idx, args.tau).free()
+        ms, replayed = [], 0
+        for _ in range(args.steps):
+            flush.zero_()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            r = pj.pj_self_join(idx, args.tau)
+            ev1.record(stream)
+            ev1.synchronize()
+            ms.append(ev0.elapsed_time(ev1))
+            replayed += r.stats["graph_replay"]
+            r.free()
+        idx.free()
+        resident[f"{mode}_ms"] = statistics.mean(ms)
+        if graph:
+            resident["graph_replays"] = replayed
+    barrier()
+
     cand = sum(s["candidates"] for s in stats_all)
     cand_all, total_s, e2e_s = reduce_over_ranks(cand, sum(step_ms) / 1e3, sum(e2e_ms) / 1e3, world, dev)
 
@@ -512,6 +538,8 @@ def run_native(args):
             "e2e": {"value": cand_all / e2e_s, "unit": UNIT, "ms_per_step": 1e3 * e2e_s / args.steps,
                     "h2d_bytes_per_step": int(buf.nbytes + off.nbytes),
                     "d2h_bytes_per_step": int(e2e_pairs * 12)},
+            "resident_join": dict(resident, note="join alone on a resident index, mean over the timed steps; "
+                                                 "graph = one recorded CUDA graph replayed per join"),
             "gpu_launches": int(launches),
             "clocks": clk,
             "serving": serving,

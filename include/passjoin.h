@@ -107,6 +107,10 @@ typedef struct {
                            ED(x, y) >= max over the two directions of the summed surplus of
                            one string's character counts over the other's (characters in
                            24 buckets, counts capped at 4); not part of Pass-Join, exact */
+  uint64_t distinct_pairs; /* PJ_VERIFY_PAIRS: distinct candidate pairs verified */
+  int32_t graph_replay; /* 1: the self join ran as a replay of its recorded CUDA graph
+                           (pj_options.graph_joins); the phase times are then 0 */
+  float graph_ms;       /* device time of that replay */
 } pj_stats;
 
 typedef struct {
@@ -139,6 +143,12 @@ typedef struct {
                              per pair -- and keeps the fastest (cached per workload signature
                              for the process, and in the file named by the environment
                              variable PJ_AUTOTUNE_CACHE) */
+  int graph_joins;        /* 1: after the first self join of a threshold, its whole pipeline is
+                             recorded into a CUDA graph sized from that join's counts, and
+                             later self joins of the threshold replay it (one graph launch;
+                             same results; a count above a recorded capacity, which an
+                             unchanged index cannot produce, falls back to the eager path).
+                             Needs one probe chunk and no warp-per-candidate range. */
 } pj_options;
 
 typedef struct pj_index pj_index; /* opaque, library-owned */

@@ -555,6 +555,7 @@ int pj_build_index(const pj_strings* S, int tau_max, const pj_options* opt, pj_i
     idx->lazy = opt ? opt->lazy_partitions != 0 : false;
     idx->autotune = opt ? opt->autotune != 0 : false;
     idx->verify_mode = opt ? opt->verify_mode : PJ_VERIFY_AUTO;
+    idx->graph_joins = opt ? opt->graph_joins != 0 : false;
     PJ_CUDA(cudaGetDevice(&idx->device));
     pj::EventTimer timer(idx->ctx.stream);
     timer.start();
@@ -587,6 +588,7 @@ uint64_t pj_index_device_bytes(const pj_index* idx) { return idx ? idx->device_b
 void pj_index_free(pj_index* idx) {
   if (!idx) return;
   cudaStream_t s = idx->ctx.stream;
+  idx->self_plans.clear();  // recorded self joins first: they read the partitions
   delete idx;  // buffers are released stream-ordered
   cudaStreamSynchronize(s);
 }

@@ -15,6 +15,7 @@
 // byte-compared before verification, so results stay exact.
 #pragma once
 
+#include <memory>
 #include <mutex>
 #include <vector>
 
@@ -251,6 +252,10 @@ struct pj_index {
   bool lazy = false;         // thresholds are built on first use
   bool autotune = false;     // tune the verification of each threshold's self join
   int verify_mode = PJ_VERIFY_AUTO;
+  bool graph_joins = false;  // self joins replay a recorded graph (see pj_options.graph_joins)
+  // recorded self joins by threshold (type-erased: the plan type lives with
+  // the join code); released before the partitions they read
+  std::vector<std::shared_ptr<void>> self_plans;
   float build_ms = 0.f;
   uint32_t n = 0;
   int lmax = 0;              // longest string

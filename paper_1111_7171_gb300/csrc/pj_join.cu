@@ -132,6 +132,54 @@ __device__ __forceinline__ unsigned long long dev_count(unsigned long long cap, 
   return n_dev ? min(cap, *n_dev) : cap;
 }
 
+// The hit of candidate c: the last hit whose first candidate is <= c
+// (cand_off ascending from cand_off[0] = 0).  The whole warp searches for one
+// c: each round every lane tests one of 32 evenly spaced offsets and a
+// ballot keeps the last that is <= c, so about log32(n_hits) dependent
+// loads replace log2(n_hits).  All 32 lanes call it with the same c.
+__device__ __forceinline__ unsigned long long warp_hit_of(const unsigned long long* __restrict__ cand_off,
+                                                          unsigned long long n_hits, unsigned long long c) {
+  const unsigned lane = threadIdx.x & 31u;
+  unsigned long long lo = 0, n = n_hits;  // the hit is in [lo, lo + n)
+  while (n > 1) {
+    const unsigned long long step = (n + 31) >> 5;
+    const bool le = lane * step < n && cand_off[lo + lane * step] <= c;
+    const unsigned b = __ballot_sync(FULL, le);
+    const unsigned long long j = b ? 31 - __clz(b) : 0;  // lane 0 tests lo, which is <= c
+    lo += j * step;
+    n = min(step, n - j * step);
+  }
+  return lo;
+}
+
+// The hit of candidate c >= base, given hb = the hit of base.  Every hit has
+// at least one candidate, so it is one of hb .. hb + (c - base).  The warp
+// loads the first candidates of the 32 hits after hb at once; a lane whose c
+// falls before the last of them finds its hit among those registers in five
+// shuffle steps, any other lane by binary search over the rest of its bounded
+// range.  All 32 lanes call it (each with its own c >= base).
+__device__ __forceinline__ unsigned long long lane_hit_of(const unsigned long long* __restrict__ cand_off,
+                                                          unsigned long long n_hits, unsigned long long hb,
+                                                          unsigned long long base, unsigned long long c) {
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned long long hj = hb + 1 + lane;
+  const unsigned long long first = hj < n_hits ? cand_off[hj] : ~0ull;
+  unsigned p = 0;  // hits among hb+1 .. hb+31 whose first candidate is <= c
+#pragma unroll
+  for (unsigned s = 16; s >= 1; s >>= 1) {
+    const unsigned long long o = __shfl_sync(FULL, first, p + s - 1);
+    if (o <= c) p += s;
+  }
+  const unsigned long long last = __shfl_sync(FULL, first, 31);
+  if (last > c) return hb + p;
+  unsigned long long lo = hb + 32, hi = min(n_hits, hb + (c - base) + 1);
+  while (hi - lo > 1) {
+    const unsigned long long mid = (lo + hi) >> 1;
+    if (cand_off[mid] <= c) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
 // Pass 1 for one group: the number of non-empty lookups and the mask of the
 // window positions that found one.  The window's substrings overlap, so
 // their keys are rolled from one position to the next.
@@ -237,9 +285,9 @@ constexpr int V_RUN = 8;  // candidates per lane per step
 // lanes take consecutive candidates, which mostly belong to one posting run
 // and so share the probing string, the segment, the position and the
 // indexed length -- the verification loops then have equal trip counts up to
-// early termination.  Each lane finds its first hit by binary search over the
-// candidate offsets and walks forward from there, reloading the hit only when
-// it crosses into the next one; lanes never communicate.
+// early termination.  Each lane finds its first hit from the warp's
+// (warp_hit_of, lane_hit_of) and walks forward from there, reloading the hit
+// only when it crosses into the next one.
 template <int MAXW, bool SELF, bool MULTI>
 __global__ void __launch_bounds__(512) k_verify_hits(const ProbeView v, const Hit* __restrict__ hits,
                                                        const unsigned long long* __restrict__ cand_off,
@@ -258,13 +306,8 @@ __global__ void __launch_bounds__(512) k_verify_hits(const ProbeView v, const Hi
   const unsigned long long span = 32ull * V_RUN;
   for (unsigned long long base = c_begin + warp * span; base < n_cand; base += n_warps * span) {
     unsigned long long c = base + lane;
+    unsigned long long h = lane_hit_of(cand_off, n_hits, warp_hit_of(cand_off, n_hits, base), base, c);
     if (c >= n_cand) continue;
-    unsigned long long lo = 0, hi = n_hits;  // last hit whose first candidate is <= c
-    while (hi - lo > 1) {
-      const unsigned long long mid = (lo + hi) >> 1;
-      if (cand_off[mid] <= c) lo = mid; else hi = mid;
-    }
-    unsigned long long h = lo;
     unsigned long long c_lo = cand_off[h];
     unsigned long long c_hi = h + 1 < n_hits ? cand_off[h + 1] : n_cand;
     Hit hit = hits[h];
@@ -346,15 +389,11 @@ __global__ void __launch_bounds__(Q_BLOCK) k_verify_queued(const ProbeView v, co
   };
   for (unsigned long long base = c_begin + warp * span; base < n_cand; base += n_warps * span) {
     const unsigned long long c0 = base + (unsigned long long)lane * S_RUN;
+    const unsigned long long h0 = lane_hit_of(cand_off, n_hits, warp_hit_of(cand_off, n_hits, base), base, c0);
     uint32_t mask = 0;
     uint32_t eh[S_RUN], ek[S_RUN];
     if (c0 < n_cand) {
-      unsigned long long lo = 0, hi = n_hits;  // last hit whose first candidate is <= c0
-      while (hi - lo > 1) {
-        const unsigned long long mid = (lo + hi) >> 1;
-        if (cand_off[mid] <= c0) lo = mid; else hi = mid;
-      }
-      unsigned long long h = lo;
+      unsigned long long h = h0;
       unsigned long long c_lo = cand_off[h];
       unsigned long long c_hi = h + 1 < n_hits ? cand_off[h + 1] : n_cand;
       Hit hit = hits[h];
@@ -435,11 +474,7 @@ __global__ void __launch_bounds__(512) k_verify_warp(const ProbeView v, const Hi
   int err = 0;
   for (unsigned long long c = c_begin + warp; c < c_end; c += n_warps) {
     __syncwarp();
-    unsigned long long lo = 0, hi = n_hits;
-    while (hi - lo > 1) {
-      const unsigned long long mid = (lo + hi) >> 1;
-      if (cand_off[mid] <= c) lo = mid; else hi = mid;
-    }
+    const unsigned long long lo = warp_hit_of(cand_off, n_hits, c);
     const Hit hit = hits[lo];
     const ProbeView vt = MULTI ? view_for_tau(v, (int)(hit.pi >> 24)) : v;
     unsigned long long key = 0;
@@ -491,7 +526,12 @@ __global__ void __launch_bounds__(BLOCK) k_pair_keys(const ProbeView v, const Hi
                                                      const unsigned long long* __restrict__ cand_off,
                                                      unsigned long long n_hits, unsigned long long c_begin,
                                                      unsigned long long c_end, int pshift,
-                                                     unsigned long long* __restrict__ keys, Counters* ctr) {
+                                                     unsigned long long* __restrict__ keys, Counters* ctr,
+                                                     const unsigned long long* __restrict__ dn) {
+  if (dn) {  // device sizes: dn[0] hits (clamped to n_hits), dn[1] candidates (clamped to c_end)
+    n_hits = min(n_hits, dn[0]);
+    c_end = min(c_end, dn[1]);
+  }
   const unsigned lane = threadIdx.x & 31u;
   const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const unsigned long long n_warps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
@@ -499,13 +539,8 @@ __global__ void __launch_bounds__(BLOCK) k_pair_keys(const ProbeView v, const Hi
   int err = 0;
   for (unsigned long long base = c_begin + warp * span; base < c_end; base += n_warps * span) {
     unsigned long long c = base + lane;
+    unsigned long long h = lane_hit_of(cand_off, n_hits, warp_hit_of(cand_off, n_hits, base), base, c);
     if (c >= c_end) continue;
-    unsigned long long lo = 0, hi = n_hits;
-    while (hi - lo > 1) {
-      const unsigned long long mid = (lo + hi) >> 1;
-      if (cand_off[mid] <= c) lo = mid; else hi = mid;
-    }
-    unsigned long long h = lo;
     unsigned long long c_lo = cand_off[h];
     unsigned long long c_hi = h + 1 < n_hits ? cand_off[h + 1] : c_end;
     Hit hit = hits[h];
@@ -534,7 +569,8 @@ __global__ void __launch_bounds__(BLOCK) k_pair_keys(const ProbeView v, const Hi
 
 __global__ void k_unique_keys(const unsigned long long* __restrict__ keys, const uint32_t* __restrict__ flags,
                               const uint32_t* __restrict__ pos, unsigned long long n,
-                              unsigned long long* __restrict__ ukeys) {
+                              unsigned long long* __restrict__ ukeys, const unsigned long long* __restrict__ n_dev) {
+  n = dev_count(n, n_dev);
   for (unsigned long long k = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (unsigned long long)gridDim.x * blockDim.x)
     if (flags[k]) ukeys[pos[k]] = keys[k];
@@ -572,7 +608,9 @@ __device__ __forceinline__ void append_match(Counters* ctr, const AccOut& out, u
 // One thread per distinct pair.
 template <int MAXW, bool SELF>
 __global__ void __launch_bounds__(BLOCK) k_verify_pairs(const ProbeView v, const unsigned long long* __restrict__ ukeys,
-                                                        unsigned long long n, int pshift, AccOut out, Counters* ctr) {
+                                                        unsigned long long n, int pshift, AccOut out, Counters* ctr,
+                                                        const unsigned long long* __restrict__ n_dev) {
+  n = dev_count(n, n_dev);
   unsigned long long cells = 0, filtered = 0;
   for (unsigned long long u = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; u < n;
        u += (unsigned long long)gridDim.x * blockDim.x) {
@@ -599,7 +637,9 @@ template <bool SELF>
 __global__ void __launch_bounds__(BLOCK) k_verify_pairs_warp(const ProbeView v,
                                                              const unsigned long long* __restrict__ ukeys,
                                                              unsigned long long n, int pshift, AccOut out,
-                                                             Counters* ctr) {
+                                                             Counters* ctr,
+                                                             const unsigned long long* __restrict__ n_dev) {
+  n = dev_count(n, n_dev);
   const unsigned lane = threadIdx.x & 31u;
   const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const unsigned long long n_warps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
@@ -852,6 +892,7 @@ static void pinned_put(void* p, size_t bytes) {
 //   PJ_GROUP_BUDGET      groups probed per chunk          (default 64 Mi)
 //   PJ_LAUNCH_CANDS      candidates per verification launch (default 1 Gi)
 //   PJ_ACCEPT_INITIAL    initial accepted-match capacity  (default 4 Mi)
+//   PJ_GRAPH_MAX_GROUPS  groups of a recorded self join   (default 256 Mi)
 static unsigned long long env_knob(const char* name, unsigned long long dflt) {
   const char* e = getenv(name);
   if (!e || !e[0]) return dflt;
@@ -861,6 +902,7 @@ static unsigned long long env_knob(const char* name, unsigned long long dflt) {
 
 struct Timings {
   float probe = 0.f, verify = 0.f, fallback = 0.f, dedupe = 0.f;
+  unsigned long long distinct = 0;  // mode L: distinct pairs verified
 };
 
 // Accepted-match buffer that grows between launches: after a launch that
@@ -995,7 +1037,7 @@ static unsigned long long verify_pairs_chunk(const Ctx& c, const ProbeView& v, c
   DBuf<uint32_t> v0(c, n_cand), v1(c, n_cand);
   const unsigned g = persistent_grid(k_pair_keys<SELF>, (n_cand + (unsigned long long)BLOCK * V_RUN - 1) /
                                                             ((unsigned long long)BLOCK * V_RUN));
-  k_pair_keys<SELF><<<g, BLOCK, 0, c.stream>>>(v, hits, off, n_hits, 0, n_cand, pshift, k0.p, ctr);
+  k_pair_keys<SELF><<<g, BLOCK, 0, c.stream>>>(v, hits, off, n_hits, 0, n_cand, pshift, k0.p, ctr, nullptr);
   PJ_LAUNCHED("k_pair_keys");
   const bool second = radix_sort_pairs_dn<unsigned long long>(c, k0.p, v0.p, k1.p, v1.p, n_cand, nullptr, nbits);
   unsigned long long* sorted = second ? k1.p : k0.p;
@@ -1005,7 +1047,7 @@ static unsigned long long verify_pairs_chunk(const Ctx& c, const ProbeView& v, c
   k_run_heads<<<stride_grid(n_cand), 256, 0, c.stream>>>(sorted, n_cand, flags.p, nullptr);
   PJ_LAUNCHED("k_run_heads");
   exclusive_scan_dn<uint32_t>(c, flags.p, pos.p, n_cand, nullptr, n_unique.p);
-  k_unique_keys<<<stride_grid(n_cand), 256, 0, c.stream>>>(sorted, flags.p, pos.p, n_cand, ukeys);
+  k_unique_keys<<<stride_grid(n_cand), 256, 0, c.stream>>>(sorted, flags.p, pos.p, n_cand, ukeys, nullptr);
   PJ_LAUNCHED("k_unique_keys");
   unsigned long long U = 0;
   PJ_CUDA(cudaMemcpyAsync(&U, n_unique.p, sizeof(U), cudaMemcpyDeviceToHost, c.stream));
@@ -1013,13 +1055,13 @@ static unsigned long long verify_pairs_chunk(const Ctx& c, const ProbeView& v, c
   auto launch = [&](AccOut o) {
     if (v.pair_warp) {
       const unsigned gw = persistent_grid(k_verify_pairs_warp<SELF>, (U + BLOCK / 32 - 1) / (BLOCK / 32));
-      k_verify_pairs_warp<SELF><<<gw, BLOCK, 0, c.stream>>>(v, ukeys, U, pshift, o, ctr);
+      k_verify_pairs_warp<SELF><<<gw, BLOCK, 0, c.stream>>>(v, ukeys, U, pshift, o, ctr, nullptr);
       PJ_LAUNCHED("k_verify_pairs_warp");
     } else {
 #define PJ_CALL(W)                                                                                    \
   do {                                                                                               \
     const unsigned gt = persistent_grid(k_verify_pairs<W, SELF>, (U + BLOCK - 1) / BLOCK);           \
-    k_verify_pairs<W, SELF><<<gt, BLOCK, 0, c.stream>>>(v, ukeys, U, pshift, o, ctr);                 \
+    k_verify_pairs<W, SELF><<<gt, BLOCK, 0, c.stream>>>(v, ukeys, U, pshift, o, ctr, nullptr);        \
     PJ_LAUNCHED("k_verify_pairs");                                                                   \
   } while (0)
       PJ_BY_TAU(v.tau, PJ_CALL);
@@ -1078,7 +1120,7 @@ static void probe_and_verify(const Ctx& c, const ProbeView& v0, uint32_t fb_coun
     const double remaining_groups = (double)(v0.pcount - done - v.pcount) / std::max(1u, v.pcount) + 1.0;  // chunks left
     if (!MULTI && v.pair_mode && n_cand <= PAIR_MODE_MAX_CANDS) {  // mode L
       tv.start();
-      verify_pairs_chunk<SELF>(c, v, hits.p, off.p, n_hits, n_cand, ctr, nullptr, &acc);
+      tm.distinct += verify_pairs_chunk<SELF>(c, v, hits.p, off.p, n_hits, n_cand, ctr, nullptr, &acc);
       tv.stop();
       tm.verify += tv.ms();
       verified += n_cand;
@@ -1209,6 +1251,7 @@ static void run_join(const Ctx& c, const ProbeView& v, bool self, uint32_t fb_co
   out->stats.accepted = h.accepted;
   out->stats.dp_cells = h.cells;
   out->stats.filtered = h.filtered;
+  out->stats.distinct_pairs = tm.distinct;
   out->stats.fallback_pairs = h.fallback;
   out->stats.hits = h.hits;
   out->stats.probe_ms = tm.probe;
@@ -1504,6 +1547,324 @@ static ProbeView index_side(const pj_index& idx, const Partition& part) {
   return v;
 }
 
+// ------------------------------------------------------------ join plans --
+//
+// A self join of an unchanged index repeats exactly.  With graph_joins, its
+// first eager run at a threshold is followed by recording the whole
+// pipeline into a CUDA graph: sizes kept on the device as in query plans,
+// every capacity set from that run's own counts (groups, hits, candidates,
+// distinct pairs, accepted matches, pairs).  Later self joins of the
+// threshold replay the graph -- one launch and one synchronisation -- and
+// copy the pairs out.  A replay whose counts exceed the recorded capacities
+// (which an unchanged index cannot produce) is discarded and the join runs
+// eagerly.  Not recorded: joins with a warp-per-candidate range, or with more
+// than PJ_GRAPH_MAX_GROUPS probe groups (2^28 by default; the graph probes
+// all groups in one pass, where the eager join takes chunks).
+
+__global__ void k_self_finish(const Counters* __restrict__ ctr, const PlanSizes* __restrict__ sizes,
+                              const unsigned long long* __restrict__ unique, PlanHeader* header) {
+  PlanHeader h;
+  h.groups = 0;
+  h.hits = sizes->hits;
+  h.cands = sizes->cands;
+  h.accepted = ctr->accepted;
+  h.pairs = sizes->pairs;
+  h.lookups = ctr->lookups;
+  h.cells = ctr->cells;
+  h.fallback = ctr->fallback;
+  h.err = ctr->err;
+  h.filtered = ctr->filtered;
+  h.unique = *unique;
+  *header = h;
+}
+
+struct SelfPlan {
+  Ctx ctx;  // the index's allocator on the plan's own stream
+  cudaStream_t stream = nullptr;
+  int warp_min_len = 0, block_thread = 0, pair_mode = 0, pair_warp = 0;  // the tuning it was recorded with
+  uint32_t fb_count = 0;
+  int a_bits = 0;
+  unsigned long long n_groups = 0, cap_hits = 0, cap_cands = 0, cap_acc = 0, cap_pairs = 0;
+  DBuf<unsigned char> counters, arena;
+  DBuf<PlanSizes> sizes;
+  DBuf<unsigned long long> nuniq, gmask, hcnt, hoff, pk0, pk1, ukeys, ak0, ak1;
+  DBuf<uint32_t> gcounts, goff, pv0, pv1, pflags, ppos, ae0, ae1, flags, pos;
+  DBuf<Hit> hits;
+  DBuf<pj_pair> out;
+  HostBuf header;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  uint32_t kernels = 0;
+
+  ~SelfPlan() {
+    if (stream) cudaStreamSynchronize(stream);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    DBuf<unsigned long long>* b64[] = {&nuniq, &gmask, &hcnt, &hoff, &pk0, &pk1, &ukeys, &ak0, &ak1};
+    for (auto* b : b64) b->release();
+    DBuf<uint32_t>* b32[] = {&gcounts, &goff, &pv0, &pv1, &pflags, &ppos, &ae0, &ae1, &flags, &pos};
+    for (auto* b : b32) b->release();
+    counters.release();
+    arena.release();
+    sizes.release();
+    hits.release();
+    out.release();
+    if (stream) {
+      cudaStreamSynchronize(stream);
+      cudaStreamDestroy(stream);
+    }
+  }
+};
+
+static void record_self_plan(const Ctx& c, const ProbeView& v, SelfPlan& P) {
+  Counters* ctr = reinterpret_cast<Counters*>(P.counters.p);
+  PlanSizes* sz = P.sizes.p;
+  PJ_CUDA(cudaMemsetAsync(ctr, 0, sizeof(Counters), c.stream));
+  // A4
+  const unsigned g1 = persistent_grid(k_group_counts<true, false>, (P.n_groups + BLOCK - 1) / BLOCK);
+  k_group_counts<true, false><<<g1, BLOCK, 0, c.stream>>>(v, P.n_groups, P.gcounts.p, P.gmask.p, ctr, nullptr);
+  PJ_LAUNCHED("k_group_counts");
+  exclusive_scan_dn<uint32_t>(c, P.gcounts.p, P.goff.p, P.n_groups, nullptr, &sz->hits);
+  const unsigned g2 = persistent_grid(k_group_hits<true, false>, (P.n_groups + BLOCK - 1) / BLOCK);
+  k_group_hits<true, false><<<g2, BLOCK, 0, c.stream>>>(v, P.n_groups, P.gcounts.p, P.gmask.p, P.goff.p, P.hits.p,
+                                                        nullptr, P.cap_hits);
+  PJ_LAUNCHED("k_group_hits");
+  k_hit_counts<<<stride_grid(P.cap_hits), 256, 0, c.stream>>>(P.hits.p, P.cap_hits, P.hcnt.p, &sz->hits);
+  PJ_LAUNCHED("k_hit_counts");
+  exclusive_scan_dn<unsigned long long>(c, P.hcnt.p, P.hoff.p, P.cap_hits, &sz->hits, &sz->cands);
+  // A5 (mode L) + A6 + A8
+  const AccOut acc{P.ak0.p, P.ae0.p, P.cap_acc};
+  if (!P.pair_mode) {
+    PJ_CUDA(cudaMemsetAsync(P.nuniq.p, 0, sizeof(unsigned long long), c.stream));
+#define PJ_CALL(W)                                                                                              \
+  do {                                                                                                         \
+    const unsigned gv = persistent_grid(k_verify_queued<W, true, false>, ~0ull >> 8, Q_BLOCK);                  \
+    k_verify_queued<W, true, false><<<gv, Q_BLOCK, 0, c.stream>>>(v, P.hits.p, P.hoff.p, P.cap_hits, 0, 0, acc,  \
+                                                                  ctr, &sz->hits);                             \
+    PJ_LAUNCHED("k_verify_queued");                                                                            \
+  } while (0)
+    PJ_BY_TAU(v.tau, PJ_CALL);
+#undef PJ_CALL
+  } else {
+    const int pshift = bits_for(v.n_index);
+    const unsigned gk = persistent_grid(k_pair_keys<true>, ~0ull >> 8);
+    k_pair_keys<true><<<gk, BLOCK, 0, c.stream>>>(v, P.hits.p, P.hoff.p, P.cap_hits, 0, P.cap_cands, pshift, P.pk0.p, ctr,
+                                                  &sz->hits);
+    PJ_LAUNCHED("k_pair_keys");
+    const bool second = radix_sort_pairs_dn<unsigned long long>(c, P.pk0.p, P.pv0.p, P.pk1.p, P.pv1.p, P.cap_cands,
+                                                                &sz->cands, 2 * pshift);
+    const unsigned long long* sorted = second ? P.pk1.p : P.pk0.p;
+    k_run_heads<<<stride_grid(P.cap_cands), 256, 0, c.stream>>>(sorted, P.cap_cands, P.pflags.p, &sz->cands);
+    PJ_LAUNCHED("k_run_heads");
+    exclusive_scan_dn<uint32_t>(c, P.pflags.p, P.ppos.p, P.cap_cands, &sz->cands, P.nuniq.p);
+    k_unique_keys<<<stride_grid(P.cap_cands), 256, 0, c.stream>>>(sorted, P.pflags.p, P.ppos.p, P.cap_cands,
+                                                                  P.ukeys.p, &sz->cands);
+    PJ_LAUNCHED("k_unique_keys");
+    if (P.pair_warp) {
+      const unsigned gw = persistent_grid(k_verify_pairs_warp<true>, ~0ull >> 8);
+      k_verify_pairs_warp<true><<<gw, BLOCK, 0, c.stream>>>(v, P.ukeys.p, P.cap_cands, pshift, acc, ctr, P.nuniq.p);
+      PJ_LAUNCHED("k_verify_pairs_warp");
+    } else {
+#define PJ_CALL(W)                                                                                              \
+  do {                                                                                                         \
+    const unsigned gt = persistent_grid(k_verify_pairs<W, true>, ~0ull >> 8);                                   \
+    k_verify_pairs<W, true><<<gt, BLOCK, 0, c.stream>>>(v, P.ukeys.p, P.cap_cands, pshift, acc, ctr, P.nuniq.p);  \
+    PJ_LAUNCHED("k_verify_pairs");                                                                             \
+  } while (0)
+      PJ_BY_TAU(v.tau, PJ_CALL);
+#undef PJ_CALL
+    }
+  }
+  if (P.fb_count) {
+#define PJ_CALL(W)                                                                                              \
+  do {                                                                                                         \
+    const unsigned gf = persistent_grid(k_fallback<W, true, false>, (P.fb_count + BLOCK - 1) / BLOCK);          \
+    k_fallback<W, true, false><<<gf, BLOCK, 0, c.stream>>>(v, P.fb_count, acc, ctr, nullptr);                   \
+    PJ_LAUNCHED("k_fallback");                                                                                 \
+  } while (0)
+    PJ_BY_TAU(v.tau, PJ_CALL);
+#undef PJ_CALL
+  }
+  // A5 + A7
+  const bool second = radix_sort_pairs_dn<unsigned long long>(c, P.ak0.p, P.ae0.p, P.ak1.p, P.ae1.p, P.cap_acc,
+                                                              &ctr->accepted, v.key_shift + P.a_bits);
+  const unsigned long long* keys = second ? P.ak1.p : P.ak0.p;
+  const uint32_t* eds = second ? P.ae1.p : P.ae0.p;
+  k_run_heads<<<stride_grid(P.cap_acc), 256, 0, c.stream>>>(keys, P.cap_acc, P.flags.p, &ctr->accepted);
+  PJ_LAUNCHED("k_run_heads");
+  exclusive_scan_dn<uint32_t>(c, P.flags.p, P.pos.p, P.cap_acc, &ctr->accepted, &sz->pairs);
+  k_emit_pairs<<<stride_grid(P.cap_acc), 256, 0, c.stream>>>(keys, eds, P.flags.p, P.pos.p, P.cap_acc, v.key_shift,
+                                                             P.out.p, &ctr->accepted, P.cap_pairs);
+  PJ_LAUNCHED("k_emit_pairs");
+  k_self_finish<<<1, 1, 0, c.stream>>>(ctr, sz, P.nuniq.p, static_cast<PlanHeader*>(P.header.dev));
+  PJ_LAUNCHED("k_self_finish");
+}
+
+static unsigned long long with_slack(unsigned long long n) { return n + n / 64 + 1024; }
+
+// Records the self join described by v and st (the counts of its eager
+// run); returns nullptr when the join is not eligible.
+static std::shared_ptr<SelfPlan> make_self_plan(pj_index& idx, const ProbeView& v, const TuneResult& tr,
+                                                uint32_t fb_count, const pj_stats& st, uint64_t pairs) {
+  const int G = groups_per_probe(v.tau, true);
+  const unsigned long long n_groups =
+      v.interleave ? interleaved_groups(v.pcount, G) : (unsigned long long)v.pcount * G;
+  if (n_groups == 0) return nullptr;  // nothing to probe
+  // one probe pass over all groups (16 B each), however the eager join chunked them
+  if (n_groups > std::min(env_knob("PJ_GRAPH_MAX_GROUPS", 1ull << 28), 1ull << 31)) return nullptr;
+  if (!tr.pair_mode && aligned_cut(v, v.warp_q_cut) < v.pbegin + v.pcount) return nullptr;  // a warp range
+  if (tr.pair_mode && st.candidates > PAIR_MODE_MAX_CANDS) return nullptr;        // mode L skipped eagerly
+  auto P = std::make_shared<SelfPlan>();
+  PJ_CUDA(cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking));
+  P->ctx = idx.ctx;
+  P->ctx.stream = P->stream;
+  P->warp_min_len = tr.warp_min_len;
+  P->block_thread = tr.block_thread;
+  P->pair_mode = tr.pair_mode;
+  P->pair_warp = tr.pair_warp;
+  P->fb_count = fb_count;
+  P->a_bits = bits_for(idx.n);
+  P->n_groups = n_groups;
+  P->cap_hits = with_slack(st.hits);
+  P->cap_cands = tr.pair_mode ? with_slack(st.candidates) : 1;
+  P->cap_acc = std::min<unsigned long long>(0xFFFFFFFFull, with_slack(st.accepted));
+  P->cap_pairs = with_slack(pairs);
+  const Ctx& c = P->ctx;
+  P->counters.reset(c, 64);
+  P->sizes.reset(c, 1);
+  P->nuniq.reset(c, 1);
+  P->gcounts.reset(c, n_groups);
+  P->goff.reset(c, n_groups);
+  P->gmask.reset(c, n_groups);
+  P->hits.reset(c, P->cap_hits);
+  P->hcnt.reset(c, P->cap_hits);
+  P->hoff.reset(c, P->cap_hits);
+  P->pk0.reset(c, P->cap_cands);
+  P->pk1.reset(c, P->cap_cands);
+  P->pv0.reset(c, P->cap_cands);
+  P->pv1.reset(c, P->cap_cands);
+  P->pflags.reset(c, P->cap_cands);
+  P->ppos.reset(c, P->cap_cands);
+  P->ukeys.reset(c, P->cap_cands);
+  P->ak0.reset(c, P->cap_acc);
+  P->ak1.reset(c, P->cap_acc);
+  P->ae0.reset(c, P->cap_acc);
+  P->ae1.reset(c, P->cap_acc);
+  P->flags.reset(c, P->cap_acc);
+  P->pos.reset(c, P->cap_acc);
+  P->out.reset(c, P->cap_pairs);
+  P->header.reset(sizeof(PlanHeader), true);
+  size_t arena_bytes = scan_temp_bytes(n_groups, 4) + scan_temp_bytes(P->cap_hits, 8) +
+                       2 * scan_temp_bytes(P->cap_cands, 4) + sort_temp_bytes(P->cap_cands) +
+                       scan_temp_bytes(P->cap_acc, 4) + sort_temp_bytes(P->cap_acc) + (1u << 16);
+  for (int attempt = 0;; ++attempt) {
+    P->arena.reset(c, arena_bytes);
+    c.sync();
+    Arena ar;
+    ar.base = P->arena.p;
+    ar.cap = arena_bytes;
+    Ctx rc;
+    rc.stream = P->stream;
+    rc.alloc = arena_alloc;
+    rc.free_fn = arena_free;
+    rc.alloc_ctx = &ar;
+    cudaGraph_t g = nullptr;
+    PJ_CUDA(cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeRelaxed));
+    set_recording(true);
+    bool ok = true;
+    Error err{PJ_OK, ""};
+    try {
+      record_self_plan(rc, v, *P);
+    } catch (const Error& e) {
+      ok = false;
+      err = e;
+    }
+    set_recording(false);
+    const cudaError_t ce = cudaStreamEndCapture(P->stream, &g);
+    if (!ok || ce != cudaSuccess || !g) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      if (!ok && ar.exhausted && attempt < 4) {
+        arena_bytes *= 2;
+        continue;
+      }
+      if (!ok) throw err;
+      fail(PJ_ECUDA, std::string("self-join graph capture failed: ") + cudaGetErrorString(ce));
+    }
+    P->graph = g;
+    if (cudaGraphInstantiate(&P->exec, g, 0) != cudaSuccess) {
+      cudaGetLastError();
+      P->exec = nullptr;
+      fail(PJ_ECUDA, "self-join graph: cudaGraphInstantiate failed");
+    }
+    size_t n = 0;
+    PJ_CUDA(cudaGraphGetNodes(g, nullptr, &n));
+    std::vector<cudaGraphNode_t> nodes(n);
+    PJ_CUDA(cudaGraphGetNodes(g, nodes.data(), &n));
+    for (size_t k = 0; k < n; ++k) {
+      cudaGraphNodeType t;
+      PJ_CUDA(cudaGraphNodeGetType(nodes[k], &t));
+      if (t == cudaGraphNodeTypeKernel) ++P->kernels;
+    }
+    return P;
+  }
+}
+
+// Replays P into *out; false when the counts did not fit (the caller then
+// runs the join eagerly).
+static bool replay_self_plan(SelfPlan& P, const Ctx& rc, bool on_device, pj_result* out) {
+  EventTimer t(P.stream);
+  t.start();
+  PJ_CUDA(cudaGraphLaunch(P.exec, P.stream));
+  count_launches(P.kernels);
+  t.stop();
+  P.ctx.sync();
+  PlanHeader h;
+  memcpy(&h, P.header.p, sizeof(h));
+  if (h.err)
+    fail(PJ_ECUDA, std::string("segment index consistency check failed (") +
+                       ((h.err & 1) ? "posting outside the index" : "probe limit reached") + ")");
+  if (h.hits > P.cap_hits || (P.pair_mode && h.cands > P.cap_cands) || h.accepted > P.cap_acc ||
+      h.pairs > P.cap_pairs)
+    return false;
+  const uint64_t count = h.pairs;
+  out->count = count;
+  out->stats.lookups = h.lookups;
+  out->stats.candidates = h.cands;
+  out->stats.accepted = h.accepted;
+  out->stats.dp_cells = h.cells;
+  out->stats.filtered = h.filtered;
+  out->stats.fallback_pairs = h.fallback;
+  out->stats.hits = h.hits;
+  out->stats.distinct_pairs = h.unique;
+  out->stats.graph_replay = 1;
+  out->stats.graph_ms = t.ms();
+  auto* priv = new ResultPriv{rc};
+  out->priv = priv;
+  const size_t bytes = std::max<uint64_t>(count, 1) * sizeof(pj_pair);
+  if (on_device) {
+    out->on_device = 1;
+    out->pairs = static_cast<pj_pair*>(rc.get(bytes));
+    if (count)
+      PJ_CUDA(cudaMemcpyAsync(out->pairs, P.out.p, count * sizeof(pj_pair), cudaMemcpyDeviceToDevice, rc.stream));
+  } else {
+    out->on_device = 0;
+    size_t got = 0;
+    void* blk = bytes >= PINNED_MIN ? pinned_get(bytes, &got) : nullptr;
+    if (blk) {
+      out->pairs = static_cast<pj_pair*>(blk);
+      priv->pinned_bytes = got;
+    } else {
+      out->pairs = static_cast<pj_pair*>(malloc(bytes));
+      if (!out->pairs) fail(PJ_ENOMEM, "host result allocation failed");
+    }
+    if (count)
+      PJ_CUDA(cudaMemcpyAsync(out->pairs, P.out.p, count * sizeof(pj_pair), cudaMemcpyDeviceToHost, rc.stream));
+  }
+  rc.sync();
+  return true;
+}
+
 static void self_join_impl(pj_index& idx, int tau, pj_result* out, bool on_device) {
   trace_mark(idx.ctx, "join: start");
   float part_ms = 0.f;
@@ -1540,7 +1901,36 @@ static void self_join_impl(pj_index& idx, int tau, pj_result* out, bool on_devic
   v.block_thread = tr.block_thread;
   v.pair_mode = tr.pair_mode;
   v.pair_warp = tr.pair_warp;
+  if (idx.graph_joins) {
+    if (idx.self_plans.size() < idx.parts.size()) idx.self_plans.resize(idx.parts.size());
+    SelfPlan* sp = static_cast<SelfPlan*>(idx.self_plans[tau].get());
+    if (sp && (sp->warp_min_len != tr.warp_min_len || sp->block_thread != tr.block_thread ||
+               sp->pair_mode != tr.pair_mode || sp->pair_warp != tr.pair_warp)) {
+      idx.self_plans[tau].reset();  // recorded with another tuning
+      sp = nullptr;
+    }
+    if (sp) {
+      if (replay_self_plan(*sp, idx.ctx, on_device, out)) {
+        out->stats.partition_ms = part_ms;
+        out->stats.verify_block = tr.block_thread;
+        out->stats.warp_min_len = tr.warp_min_len;
+        out->stats.verify_mode = tr.pair_mode ? PJ_VERIFY_PAIRS : PJ_VERIFY_EXTENSION;
+        out->stats.pair_warp = tr.pair_mode ? tr.pair_warp : 0;
+        return;
+      }
+      pj_result_free(out);  // counts above the recorded capacities: run eagerly, record again
+      idx.self_plans[tau].reset();
+    }
+  }
   run_join(idx.ctx, v, true, part.first, bits_for(idx.n), on_device, out);
+  if (idx.graph_joins && !idx.self_plans[tau]) {
+    try {  // a join that cannot be recorded (memory) still has its result
+      std::shared_ptr<SelfPlan> p = make_self_plan(idx, v, tr, part.first, out->stats, out->count);
+      if (p) idx.self_plans[tau] = std::static_pointer_cast<void>(p);
+    } catch (const Error&) {
+      cudaGetLastError();
+    }
+  }
   out->stats.partition_ms = part_ms;
   out->stats.verify_block = tr.block_thread;
   out->stats.warp_min_len = tr.warp_min_len;
@@ -1660,6 +2050,8 @@ __global__ void k_plan_finish(const Counters* __restrict__ ctr, const PlanSizes*
   h.cells = ctr->cells;
   h.fallback = ctr->fallback;
   h.err = ctr->err;
+  h.filtered = ctr->filtered;
+  h.unique = 0;
   *header = h;
 }
 

@@ -48,7 +48,8 @@ class pj_stats(ctypes.Structure):
                 ("probe_ms", ctypes.c_float), ("verify_ms", ctypes.c_float), ("fallback_ms", ctypes.c_float),
                 ("dedupe_ms", ctypes.c_float), ("partition_ms", ctypes.c_float), ("verify_block", ctypes.c_int32),
                 ("warp_min_len", ctypes.c_int32), ("tune_ms", ctypes.c_float), ("verify_mode", ctypes.c_int32),
-                ("pair_warp", ctypes.c_int32), ("filtered", ctypes.c_uint64)]
+                ("pair_warp", ctypes.c_int32), ("filtered", ctypes.c_uint64),
+                ("distinct_pairs", ctypes.c_uint64), ("graph_replay", ctypes.c_int32), ("graph_ms", ctypes.c_float)]
 
 
 class pj_result(ctypes.Structure):
@@ -63,7 +64,7 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void
 class pj_options(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
                 ("verify_mode", ctypes.c_int), ("results_on_device", ctypes.c_int), ("lazy_partitions", ctypes.c_int),
-                ("autotune", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("graph_joins", ctypes.c_int)]
 
 
 class pj_server_options(ctypes.Structure):
@@ -208,7 +209,7 @@ def _torch_free(ctx, ptr, stream):
 
 
 def make_options(stream=None, results_on_device: bool = False, torch_allocator: bool = True,
-                 lazy_partitions: bool = False, autotune: bool = False) -> pj_options:
+                 lazy_partitions: bool = False, autotune: bool = False, graph_joins: bool = False) -> pj_options:
     torch = _torch()
     opt = pj_options()
     library().pj_options_init(ctypes.byref(opt))
@@ -221,6 +222,7 @@ def make_options(stream=None, results_on_device: bool = False, torch_allocator: 
     opt.results_on_device = 1 if results_on_device else 0
     opt.lazy_partitions = 1 if lazy_partitions else 0
     opt.autotune = 1 if autotune else 0
+    opt.graph_joins = 1 if graph_joins else 0
     return opt
 
 
@@ -328,7 +330,9 @@ def _stats(st: pj_stats) -> dict:
                 probe_ms=float(st.probe_ms), verify_ms=float(st.verify_ms), fallback_ms=float(st.fallback_ms),
                 dedupe_ms=float(st.dedupe_ms), partition_ms=float(st.partition_ms),
                 verify_block=int(st.verify_block), warp_min_len=int(st.warp_min_len), tune_ms=float(st.tune_ms),
-                verify_mode=int(st.verify_mode), pair_warp=int(st.pair_warp), filtered=int(st.filtered))
+                verify_mode=int(st.verify_mode), pair_warp=int(st.pair_warp), filtered=int(st.filtered),
+                distinct_pairs=int(st.distinct_pairs), graph_replay=int(st.graph_replay),
+                graph_ms=float(st.graph_ms))
 
 
 class _HostPairs:
@@ -412,9 +416,10 @@ def pj_kernel_launches() -> int:
 
 
 def pj_build_index(strings, tau_max: int, stream=None, results_on_device: bool = False,
-                   lazy_partitions: bool = False, autotune: bool = False) -> Index:
+                   lazy_partitions: bool = False, autotune: bool = False, graph_joins: bool = False) -> Index:
     """pj_build_index: resident segment index for thresholds 0..tau_max."""
-    opt = make_options(stream, results_on_device, lazy_partitions=lazy_partitions, autotune=autotune)
+    opt = make_options(stream, results_on_device, lazy_partitions=lazy_partitions, autotune=autotune,
+                       graph_joins=graph_joins)
     S = Strings(strings)
     h = ctypes.c_void_p()
     _check(library().pj_build_index(ctypes.byref(S.c), int(tau_max), ctypes.byref(opt), ctypes.byref(h)),
