@@ -232,6 +232,8 @@ __global__ void k_table_insert(const unsigned long long* __restrict__ keys, cons
       table[h].begin = b;
       table[h].count = e - b;
       fp[h] = key_fp(key, mix);
+      const unsigned long long bit = presence_bit(mix, mask);
+      atomicOr(reinterpret_cast<uint32_t*>(fp + mask + 1) + (bit >> 5), 1u << (bit & 31));
       return;
     }
     h = (h + 1) & mask;
@@ -372,13 +374,13 @@ void build_partition(pj_index& idx, int tau, Partition& part) {
   part.n_records = nrec;
   if (nrec > 0xFFFFFFF0ull) fail(PJ_EINVAL, "segment index: more than 2^32 records");
   part.postings.reset(c, nrec);
-  if (nrec == 0) {
+  if (nrec == 0) {  // an empty table of the smallest size: every lookup finds nothing
     part.n_unique = 0;
-    part.table.reset(c, 1);
-    part.fp.reset(c, 1);
+    part.table.reset(c, 1024);
+    part.fp.reset(c, 2 * 1024);
     part.precs.reset(c, 1);
-    PJ_CUDA(cudaMemsetAsync(part.table.p, 0, sizeof(Slot), c.stream));
-    PJ_CUDA(cudaMemsetAsync(part.fp.p, 0, 1, c.stream));
+    PJ_CUDA(cudaMemsetAsync(part.table.p, 0, 1024 * sizeof(Slot), c.stream));
+    PJ_CUDA(cudaMemsetAsync(part.fp.p, 0, 2 * 1024, c.stream));
     return;
   }
   DBuf<unsigned long long> keys(c, nrec);
@@ -406,9 +408,9 @@ void build_partition(pj_index& idx, int tau, Partition& part) {
   uint64_t cap = 1024;
   while (cap < 2 * n_unique) cap <<= 1;
   part.table.reset(c, cap);
-  part.fp.reset(c, cap);
+  part.fp.reset(c, 2 * cap);  // fingerprints, then the presence bitmap
   PJ_CUDA(cudaMemsetAsync(part.table.p, 0, cap * sizeof(Slot), c.stream));
-  PJ_CUDA(cudaMemsetAsync(part.fp.p, 0, cap, c.stream));
+  PJ_CUDA(cudaMemsetAsync(part.fp.p, 0, 2 * cap, c.stream));
   DBuf<int> err(c, 1);
   PJ_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), c.stream));
   k_table_insert<<<ceil_div(n_unique, 256), 256, 0, c.stream>>>(keys.p, heads.p, n_unique, part.table.p, part.fp.p,
@@ -437,8 +439,9 @@ void build_partition(pj_index& idx, int tau, Partition& part) {
 
 // Host-side audit of one partition (environment PJ_CHECK_INDEX=1): the runs
 // tile the postings exactly, every posting is a valid sid, every slot's
-// fingerprint matches its key (0 for empty slots), and the table keeps at
-// least half of its slots empty.
+// fingerprint matches its key (0 for empty slots), the presence bitmap holds
+// exactly the bits of the stored keys, and the table keeps at least half of
+// its slots empty.
 void check_partition(const Ctx& c, const Partition& part) {
   std::vector<Slot> t(part.table.n);
   std::vector<uint8_t> fp(part.fp.n);
@@ -450,10 +453,15 @@ void check_partition(const Ctx& c, const Partition& part) {
   c.sync();
   uint64_t empty = 0, used = 0, covered = 0;
   std::vector<uint8_t> seen(part.n_records, 0);
-  if (fp.size() != t.size()) fail(PJ_ECUDA, "index audit: fingerprint array size");
+  if (fp.size() != 2 * t.size()) fail(PJ_ECUDA, "index audit: fingerprint array size");
+  std::vector<uint8_t> bits(t.size(), 0);  // the presence bitmap the stored keys give
   for (size_t h = 0; h < t.size(); ++h) {
     const Slot& s = t[h];
     if (fp[h] != (s.key ? key_fp(s.key, key_mix(s.key)) : 0)) fail(PJ_ECUDA, "index audit: fingerprint mismatch");
+    if (s.key) {
+      const unsigned long long bit = presence_bit(key_mix(s.key), t.size() - 1);
+      bits[bit >> 3] |= (uint8_t)(1u << (bit & 7));
+    }
     if (s.key == 0) {
       ++empty;
       continue;
@@ -466,6 +474,7 @@ void check_partition(const Ctx& c, const Partition& part) {
       ++covered;
     }
   }
+  if (memcmp(bits.data(), fp.data() + t.size(), t.size()) != 0) fail(PJ_ECUDA, "index audit: presence bitmap");
   fprintf(stderr, "[pj] audit tau=%d: slots=%zu used=%llu empty=%llu runs=%llu covered=%llu of %llu\n", part.tau,
           t.size(), (unsigned long long)used, (unsigned long long)empty, (unsigned long long)part.n_unique,
           (unsigned long long)covered, (unsigned long long)part.n_records);

@@ -15,6 +15,7 @@
 // byte-compared before verification, so results stay exact.
 #pragma once
 
+#include <cstring>
 #include <memory>
 #include <mutex>
 #include <vector>
@@ -184,34 +185,107 @@ __host__ __device__ __forceinline__ int signature_bound(const Sig& x, const Sig&
 // lookup that reaches it reports an inconsistent index instead of scanning.
 constexpr int TABLE_MAX_PROBES = 4096;
 
-// 1: found (begin, count); 0: not present; -1: probe limit reached.  With
-// fingerprints (fp not NULL) the probe sequence walks the fingerprint bytes
-// (a small array that stays in L2) and reads a 16-byte slot only when the
-// fingerprint matches, so most lookups of absent keys never touch the table.
-__device__ __forceinline__ int table_find(const Slot* __restrict__ t, const uint8_t* __restrict__ fp,
-                                          unsigned long long mask, unsigned long long key, uint32_t& begin,
-                                          uint32_t& count) {
+// 0x80 in every byte of w that is zero, 0 elsewhere (exact: the per-byte sum
+// below cannot carry into the next byte).
+__host__ __device__ __forceinline__ unsigned long long zero_bytes(unsigned long long w) {
+  const unsigned long long lo7 = 0x7F7F7F7F7F7F7F7Full;
+  return ~(((w & lo7) + lo7) | w | lo7);
+}
+
+__host__ __device__ __forceinline__ unsigned long long load_fp8(const uint8_t* p) {  // p 8-byte aligned
+#ifdef __CUDA_ARCH__
+  return __ldg(reinterpret_cast<const unsigned long long*>(p));
+#else
+  unsigned long long w;
+  memcpy(&w, p, 8);
+  return w;
+#endif
+}
+
+__host__ __device__ __forceinline__ int first_set64(unsigned long long x) {  // x != 0
+#ifdef __CUDA_ARCH__
+  return __ffsll((long long)x) - 1;
+#else
+  return __builtin_ctzll(x);
+#endif
+}
+
+__host__ __device__ __forceinline__ bool slot_matches(const Slot* t, unsigned long long h, unsigned long long key,
+                                                      uint32_t& begin, uint32_t& count, unsigned long long& k) {
+#ifdef __CUDA_ARCH__
+  const uint4 raw = __ldg(reinterpret_cast<const uint4*>(t + h));
+  k = ((unsigned long long)raw.y << 32) | raw.x;
+  if (k != key) return false;
+  begin = raw.z;
+  count = raw.w;
+#else
+  k = t[h].key;
+  if (k != key) return false;
+  begin = t[h].begin;
+  count = t[h].count;
+#endif
+  return true;
+}
+
+// Layout of a table's fingerprint array for S = mask + 1 slots: bytes
+// [0, S) hold key_fp of each used slot (0 for empty ones), bytes [S, 2S) a
+// presence bitmap of 8 S bits in which every stored key sets bit
+// key_mix(key) & (8 S - 1): 16 to 32 bits per key at load factor 1/4 to
+// 1/2, so an absent key finds its bit clear in about 94% or more of lookups.
+__host__ __device__ __forceinline__ unsigned long long presence_bit(uint32_t mix, unsigned long long mask) {
+  return mix & (((mask + 1) << 3) - 1);
+}
+
+__host__ __device__ __forceinline__ uint32_t load_u32(const uint8_t* p) {  // p 4-byte aligned
+#ifdef __CUDA_ARCH__
+  return __ldg(reinterpret_cast<const uint32_t*>(p));
+#else
+  uint32_t w;
+  memcpy(&w, p, 4);
+  return w;
+#endif
+}
+
+// 1: found (begin, count); 0: not present; -1: probe limit reached.  The
+// probe sequence is linear from slot key_mix(key) & mask.  With fingerprints
+// (fp not NULL; layout above) a lookup first tests the key's presence bit
+// -- one 4-byte load, and most absent keys stop there -- then walks the
+// fingerprint bytes (a small array that stays in L2) eight slots at a
+// time: one aligned 8-byte load gives the slots of a bucket, byte-parallel
+// compares give those that are empty and those whose fingerprint matches,
+// and a 16-byte slot is read only for a match before the first empty slot.
+__host__ __device__ __forceinline__ int table_find(const Slot* __restrict__ t, const uint8_t* __restrict__ fp,
+                                                   unsigned long long mask, unsigned long long key, uint32_t& begin,
+                                                   uint32_t& count) {
   const uint32_t mix = key_mix(key);
   unsigned long long h = mix & mask;
-  const uint8_t f = key_fp(key, mix);
-  for (int probe = 0; probe < TABLE_MAX_PROBES; ++probe) {
-    if (fp) {
-      const uint8_t g = __ldg(fp + h);
-      if (g == 0) return 0;
-      if (g != f) {
-        h = (h + 1) & mask;
-        continue;
-      }
+  unsigned long long k = 0;
+  if (!fp) {
+    for (int probe = 0; probe < TABLE_MAX_PROBES; ++probe) {
+      if (slot_matches(t, h, key, begin, count, k)) return 1;
+      if (k == 0) return 0;
+      h = (h + 1) & mask;
     }
-    const uint4 raw = __ldg(reinterpret_cast<const uint4*>(t + h));
-    const unsigned long long k = ((unsigned long long)raw.y << 32) | raw.x;
-    if (k == key) {
-      begin = raw.z;
-      count = raw.w;
-      return 1;
+    return -1;
+  }
+  const unsigned long long bit = presence_bit(mix, mask);
+  if (!((load_u32(fp + (mask + 1) + ((bit >> 5) << 2)) >> (bit & 31)) & 1u)) return 0;
+  // mask + 1 (the slot count) is a power of two >= 8, so buckets of 8 never wrap
+  const unsigned long long f8 = 0x0101010101010101ull * key_fp(key, mix);
+  unsigned long long b = h & ~7ull;
+  unsigned long long live = ~0ull << (8 * (h & 7));  // the first bucket from slot h on
+  for (int step = 0; step < TABLE_MAX_PROBES / 8; ++step) {
+    const unsigned long long w = load_fp8(fp + b);
+    const unsigned long long empty = zero_bytes(w) & live;
+    unsigned long long match = zero_bytes(w ^ f8) & live;
+    if (empty) match &= (empty & (~empty + 1ull)) - 1ull;  // slots before the first empty one
+    while (match) {
+      if (slot_matches(t, b + (first_set64(match) >> 3), key, begin, count, k)) return 1;
+      match &= match - 1ull;
     }
-    if (k == 0) return 0;
-    h = (h + 1) & mask;
+    if (empty) return 0;
+    b = (b + 8) & mask;
+    live = ~0ull;
   }
   return -1;
 }
@@ -233,7 +307,7 @@ struct Partition {
   uint64_t n_records = 0;    // (n - first) * (tau + 1)
   uint64_t n_unique = 0;     // distinct keys
   DBuf<Slot> table;          // power-of-two capacity
-  DBuf<uint8_t> fp;          // key_fp of each used slot, 0 for empty ones
+  DBuf<uint8_t> fp;          // key_fp of each used slot (0 for empty ones), then the presence bitmap
   DBuf<uint32_t> postings;   // sids, runs in key order, ascending inside a run
   DBuf<PostRec> precs;       // one record per posting, same order
   // group visiting order for one probe: the (length, segment) groups sorted

@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(Q_BLOCK) k_verify_queued(const ProbeView v, co
                                                             unsigned long long n_cand, AccOut out, Counters* ctr,
                                                             const unsigned long long* __restrict__ dn) {
   __shared__ uint32_t q_hit[Q_WARPS][Q_CAP];
-  __shared__ uint32_t q_post[Q_WARPS][Q_CAP];
+  __shared__ uint32_t q_sid[Q_WARPS][Q_CAP];
   if (dn) {
     n_hits = min(n_hits, dn[0]);
     n_cand = dn[1];
@@ -374,12 +374,12 @@ __global__ void __launch_bounds__(Q_BLOCK) k_verify_queued(const ProbeView v, co
   const unsigned long long n_warps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
   const unsigned long long span = 32ull * S_RUN;
   int qn = 0;  // the same in every lane
-  auto verify_entry = [&](uint32_t h, uint32_t k) {
+  auto verify_entry = [&](uint32_t h, uint32_t sid) {
     const Hit hit = hits[h];
     const ProbeView vt = MULTI ? view_for_tau(v, (int)(hit.pi >> 24)) : v;
     unsigned long long key = 0;
     int ed = 0;
-    if (verify_rec<MAXW>(vt, SELF, hit_ctx(vt, hit), vt.precs[k], key, ed, cells)) {
+    if (verify_screened<MAXW>(vt, SELF, hit_ctx(vt, hit), sid, key, ed, cells)) {
       const unsigned long long pos = atomicAdd(&ctr->accepted, 1ull);
       if (pos < out.cap) {
         out.key[pos] = key;
@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(Q_BLOCK) k_verify_queued(const ProbeView v, co
           const uint32_t pk = hit.begin + (uint32_t)(c - c_lo);
           const PostRec rec = vt.precs[pk];
           eh[k] = (uint32_t)h;
-          ek[k] = pk;
+          ek[k] = rec_sid(rec);
           // screen: a valid sid, not the probe itself, character-count bound
           if (rec_sid(rec) >= vt.n_index) {
             err |= 1;
@@ -438,7 +438,7 @@ __global__ void __launch_bounds__(Q_BLOCK) k_verify_queued(const ProbeView v, co
     for (int k = 0; k < S_RUN; ++k) {
       if ((mask >> k) & 1u) {
         q_hit[wib][slot] = eh[k];
-        q_post[wib][slot] = ek[k];
+        q_sid[wib][slot] = ek[k];
         ++slot;
       }
     }
@@ -446,13 +446,13 @@ __global__ void __launch_bounds__(Q_BLOCK) k_verify_queued(const ProbeView v, co
     __syncwarp();
     while (qn >= 32) {  // the same in every lane
       qn -= 32;
-      const uint32_t h2 = q_hit[wib][qn + lane], k2 = q_post[wib][qn + lane];
+      const uint32_t h2 = q_hit[wib][qn + lane], k2 = q_sid[wib][qn + lane];
       __syncwarp();  // taken before any later write
       verify_entry(h2, k2);
     }
   }
   __syncwarp();
-  if ((int)lane < qn) verify_entry(q_hit[wib][lane], q_post[wib][lane]);
+  if ((int)lane < qn) verify_entry(q_hit[wib][lane], q_sid[wib][lane]);
   add_counter(&ctr->cells, cells);
   add_counter(&ctr->filtered, filtered);
   if (err) atomicOr(&ctr->err, (unsigned long long)err);

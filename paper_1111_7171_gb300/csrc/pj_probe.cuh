@@ -128,26 +128,7 @@ __host__ __device__ __forceinline__ bool group_window(const ProbeView& v, bool s
 
 __host__ __device__ __forceinline__ int table_find_any(const Slot* t, const uint8_t* fp, unsigned long long mask,
                                                        unsigned long long key, uint32_t& begin, uint32_t& count) {
-#ifdef __CUDA_ARCH__
   return table_find(t, fp, mask, key, begin, count);
-#else
-  const uint32_t mix = key_mix(key);
-  unsigned long long h = mix & mask;
-  for (int probe = 0; probe < TABLE_MAX_PROBES; ++probe) {
-    if (fp && fp[h] != 0 && fp[h] != key_fp(key, mix)) {
-      h = (h + 1) & mask;
-      continue;
-    }
-    if (t[h].key == key) {
-      begin = t[h].begin;
-      count = t[h].count;
-      return 1;
-    }
-    if (t[h].key == 0) return 0;
-    h = (h + 1) & mask;
-  }
-  return -1;
-#endif
 }
 
 // Lookup of the key of s[p, li] in L_l^i.  Returns the number of postings to
@@ -225,31 +206,6 @@ __host__ __device__ __forceinline__ bool verify_screened(const ProbeView& v, boo
                                                li > SEG_EXACT_MAX, ed, cells)) {
       const uint32_t qid = v.pid ? v.pid[hc.q] : hc.q;
       const uint32_t rid = v.iperm[r];
-      const uint32_t ka = self ? min(qid, rid) : qid;
-      const uint32_t kb = self ? max(qid, rid) : rid;
-      key = ((unsigned long long)ka << v.key_shift) | kb;
-      ok = true;
-    }
-  }
-  return ok;
-}
-
-// verify_screened for a posting given by its record.
-template <int MAXW>
-__host__ __device__ __forceinline__ bool verify_rec(const ProbeView& v, bool self, const HitCtx& hc,
-                                                    const PostRec& rec, unsigned long long& key, int& ed,
-                                                    unsigned long long& cells) {
-  bool ok = false;
-  const int i = hc.i;
-  const uint32_t sid = rec_sid(rec);
-  const int lr = (int)v.ilen[sid];
-  if (i >= 1 && i <= v.tau + 1 && lr >= v.tau + 1) {
-    int P, li;
-    even_segment_m(lr, v.tau + 1, v.seg_magic, i, P, li);
-    if (hc.p + li <= hc.ls && verify_ext<MAXW>(hc.s, hc.ls, v.ibytes + v.ioff[sid], lr, i, hc.p, li, P, v.tau,
-                                               li > SEG_EXACT_MAX, ed, cells)) {
-      const uint32_t qid = v.pid ? v.pid[hc.q] : hc.q;
-      const uint32_t rid = v.iperm[sid];
       const uint32_t ka = self ? min(qid, rid) : qid;
       const uint32_t kb = self ? max(qid, rid) : rid;
       key = ((unsigned long long)ka << v.key_shift) | kb;

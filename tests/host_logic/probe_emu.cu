@@ -80,7 +80,19 @@ int main(int argc, char** argv) {
     table[h].count = (uint32_t)(e - k);
     k = e;
   }
+  // fingerprint bytes and presence bitmap as the index build sets them
+  // (none with PJ_EMU_NO_FP)
+  std::vector<uint8_t> fp(2 * cap, 0);
+  for (ull h = 0; h < cap; ++h)
+    if (table[h].key) {
+      const uint32_t mix = key_mix(table[h].key);
+      fp[h] = key_fp(table[h].key, mix);
+      const ull bit = presence_bit(mix, cap - 1);
+      fp[cap + (bit >> 3)] |= (uint8_t)(1u << (bit & 7));
+    }
+  const bool use_fp = !getenv("PJ_EMU_NO_FP");
   ProbeView v{};
+  v.table_fp = use_fp ? fp.data() : nullptr;
   v.ibytes = sb.data();
   v.ioff = soff.data();
   v.ilen = slen.data();

@@ -228,6 +228,23 @@ def test_invalid_arguments():
     assert e.value.code == pj.PJ_EINVAL
 
 
+def test_index_audit(monkeypatch):
+    """PJ_CHECK_INDEX=1 audits every partition on the host after it is built:
+    runs tile the postings, fingerprints and presence bitmap match the stored
+    keys, at least half the slots are empty.  Includes a partition with no
+    partitioned strings (every string shorter than tau + 1)."""
+    monkeypatch.setenv("PJ_CHECK_INDEX", "1")
+    for strings, tau in [(synth.generate("short", 4, n=3000), 4), (synth.generate("long", 16, n=300), 16),
+                         ([b"", b"a", b"ab"], 3)]:
+        idx = pj.pj_build_index(strings, tau)
+        try:
+            for t in sorted({0, tau // 2, tau}):
+                assert_same(pj.pj_self_join(idx, t).pairs, cpu_self(strings, t, banded=len(strings) == 300),
+                            f"audited tau={t}")
+        finally:
+            idx.free()
+
+
 def test_lazy_partitions_match_eager():
     strings = synth.generate("short", 3, n=3000)
     want = cpu_self(strings, 3)

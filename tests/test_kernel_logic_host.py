@@ -71,6 +71,27 @@ def test_self_join_logic(emu, tmp_path, name, tau, n):
     assert np.array_equal(pairs, want)
 
 
+def test_self_join_logic_without_fingerprints(emu, tmp_path, monkeypatch):
+    monkeypatch.setenv("PJ_EMU_NO_FP", "1")  # plain linear probing over the slots
+    strings = synth.generate("short", 3, n=2000)
+    st, pairs = run_emu(emu, tmp_path, strings, 3)
+    assert np.array_equal(pairs, oracle_self(strings, 3))
+
+
+def test_fingerprint_buckets_match_linear_probing(tmp_path):
+    """table_find reads eight fingerprint bytes per load; its answers must be
+    those of plain linear probing, for present and absent keys, clustered
+    runs and runs that wrap past the last slot."""
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    exe = tmp_path / "table_check"
+    subprocess.run([nvcc, "-std=c++17", "-O2", "-I", CSRC, "-I", os.path.join(ROOT, "include"), "-o", str(exe),
+                    os.path.join(ROOT, "tests", "host_logic", "table_check.cu")], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    assert out[0] == "cases" and int(out[1]) > 100000 and out[2:] == ["bad", "0"]
+
+
 def test_counts_equal_the_algorithm(emu, tmp_path):
     strings = synth.generate("short", 3, n=500)
     st, _ = run_emu(emu, tmp_path, strings, 3)
