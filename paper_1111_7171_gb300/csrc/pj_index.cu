@@ -167,6 +167,39 @@ __global__ void k_signatures(const uint8_t* __restrict__ bytes, const uint64_t* 
     bm[k] = char_signature(bytes + off[k], (int)(off[k + 1] - off[k]));
 }
 
+// Prefix values (seg_value_from_prefix) of n strings: string k's |k| + 1
+// values start at H[off[k] + k].  One warp per string, 32 bytes per step:
+// each byte is the affine map h -> h * SEG_B + byte, and a shuffle scan
+// composes the maps of the step's bytes, which are then applied to the
+// value carried in from the previous step.
+__global__ void k_prefix_values(const uint8_t* __restrict__ bytes, const uint64_t* __restrict__ off, uint32_t n,
+                                uint32_t* __restrict__ H) {
+  const unsigned lane = threadIdx.x & 31u;
+  const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t k = warp; k < n; k += n_warps) {
+    const uint64_t o = off[k], len = off[k + 1] - o;
+    uint32_t* h = H + o + k;
+    if (lane == 0) h[0] = 0;
+    uint32_t carry = 0;
+    for (uint64_t c = 0; c < len; c += 32) {
+      const uint64_t j = c + lane;
+      uint32_t a = j < len ? SEG_B : 1u, v = j < len ? (uint32_t)bytes[o + j] : 0u;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t ap = __shfl_up_sync(FULL, a, d), vp = __shfl_up_sync(FULL, v, d);
+        if ((int)lane >= d) {
+          v = vp * a + v;
+          a = ap * a;
+        }
+      }
+      const uint32_t val = carry * a + v;
+      if (j < len) h[j + 1] = val;
+      carry = __shfl_sync(FULL, val, 31);
+    }
+  }
+}
+
 // bbeg[l] = first sid whose length is >= l, for l = 0 .. lmax + 1.
 __global__ void k_buckets(const uint32_t* __restrict__ slen, uint32_t n, uint32_t* __restrict__ bbeg, int lmax) {
   const uint32_t sid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -328,6 +361,12 @@ void build_store(pj_index& idx, const pj_strings& S) {
     k_signatures<<<std::min<unsigned>(ceil_div(n, 256), 152u * 8u), 256, 0, c.stream>>>(idx.sbytes.p, idx.soff.p, n,
                                                                                     idx.sbm.p);
     PJ_LAUNCHED("k_signatures");
+  }
+  idx.sph.reset(c, (size_t)total + n + 1);
+  if (n) {
+    const unsigned blocks = std::min<unsigned>(ceil_div((size_t)n * 32, 256), 152u * 16u);
+    k_prefix_values<<<blocks, 256, 0, c.stream>>>(idx.sbytes.p, idx.soff.p, n, idx.sph.p);
+    PJ_LAUNCHED("k_prefix_values");
   }
   idx.bbeg.reset(c, (size_t)idx.lmax + 2);
   k_buckets<<<ceil_div((size_t)n + 1, 256), 256, 0, c.stream>>>(idx.slen.p, n, idx.bbeg.p, idx.lmax);
@@ -537,7 +576,7 @@ void upload_probe_set(const Ctx& c, const pj_strings& R, ProbeSet& out) {
 // ------------------------------------------------------------------ C ABI --
 
 uint64_t pj_index::device_bytes() const {
-  uint64_t b = sbytes.bytes() + soff.bytes() + slen.bytes() + perm.bytes() + bbeg.bytes() + sbm.bytes();
+  uint64_t b = sbytes.bytes() + soff.bytes() + slen.bytes() + perm.bytes() + bbeg.bytes() + sbm.bytes() + sph.bytes();
   for (const auto& p : parts)
     b += p.table.bytes() + p.fp.bytes() + p.postings.bytes() + p.precs.bytes() + p.gorder[0].bytes() +
          p.gorder[1].bytes();

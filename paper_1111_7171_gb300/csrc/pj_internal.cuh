@@ -104,6 +104,14 @@ __host__ __device__ __forceinline__ uint32_t seg_roll(uint32_t v, uint8_t out, u
   return (v - (uint32_t)out * pw) * SEG_B + in;
 }
 
+// Prefix values of a string x: H[0] = 0, H[k + 1] = H[k] * SEG_B + x[k]
+// (mod 2^32), so that H[k] = sum_{j<k} x[j] * SEG_B^(k-1-j).  The hashed
+// value of x[p .. p+n) is then H[p + n] - H[p] * SEG_B^n, with SEG_B^n =
+// seg_pow(n) * SEG_B: any window's value in O(1) (n > SEG_EXACT_MAX).
+__host__ __device__ __forceinline__ uint32_t seg_value_from_prefix(const uint32_t* H, int p, int n, uint32_t pw) {
+  return H[p + n] - H[p] * (pw * SEG_B);
+}
+
 __host__ __device__ __forceinline__ unsigned long long seg_key_of(uint32_t v, int l, int i) {
   return ((unsigned long long)v << 32) | ((uint32_t)l << 8) | (uint32_t)i;
 }
@@ -340,6 +348,7 @@ struct pj_index {
   pj::DBuf<uint32_t> perm;   // sid -> input id
   pj::DBuf<uint32_t> bbeg;   // lmax + 2 bucket starts by length
   pj::DBuf<pj::Sig> sbm;     // character signatures by sid (char_signature)
+  pj::DBuf<uint32_t> sph;    // prefix values (seg_value_from_prefix) by sid, |s| + 1 from soff[sid] + sid
   std::vector<uint32_t> h_bbeg;
   std::vector<pj::Partition> parts;  // index = tau
   uint64_t device_bytes() const;

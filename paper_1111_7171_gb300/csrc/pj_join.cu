@@ -192,8 +192,9 @@ __device__ __forceinline__ void count_group(const ProbeView& vt, uint32_t q, int
   if (group_window(vt, SELF, q, (int)vt.plen[q], g, l, i, P, li, lo, hi)) {
     const int ls = (int)vt.plen[q];
     const uint8_t* s = vt.pbytes + vt.poff[q];
-    uint32_t V = seg_value(s + lo, li);
     const uint32_t pw = seg_pow(li);
+    uint32_t V = vt.phash && li > SEG_EXACT_MAX ? seg_value_from_prefix(vt.phash + vt.poff[q] + q, lo, li, pw)
+                                                : seg_value(s + lo, li);
     for (int p = lo;; ++p) {
       uint32_t b;
       if (lookup_key(vt, SELF, q, ls, l, seg_key_of(V, l, i), b, err)) {
@@ -1892,6 +1893,7 @@ static void self_join_impl(pj_index& idx, int tau, pj_result* out, bool on_devic
   v.pcount = idx.n - part.first;
   v.pid = idx.perm.p;
   v.pbm = idx.sbm.p;
+  v.phash = idx.sph.p;
   v.key_shift = bits_for(idx.n);
   v.gorder = part.gorder[1].p;
   v.warp_q_cut = UINT32_MAX;

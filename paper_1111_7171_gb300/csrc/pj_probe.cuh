@@ -53,6 +53,7 @@ struct ProbeView {
   uint32_t n_index;
   const Slot* table;
   const uint8_t* table_fp;  // slot fingerprints (NULL: probe the slots directly)
+  const uint32_t* phash;    // probe-side prefix values from poff[q] + q (NULL: computed per window)
   unsigned long long mask;
   const uint32_t* postings;
   const PostRec* precs;  // postings' records (same order)

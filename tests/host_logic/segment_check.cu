@@ -5,7 +5,8 @@
 // segment count 1..33, every segment i.  Also checks that the segments tile
 // the string.  Then checks the probe's rolling segment value (seg_roll)
 // against the direct one (seg_value) over every window of random strings,
-// for exact (short) and hashed segments; that keys and fingerprints are
+// for exact (short) and hashed segments, and the value taken from prefix
+// values (seg_value_from_prefix) for hashed ones; that keys and fingerprints are
 // never 0; and that exact keys of different short segments differ.  Prints
 // "bad=<mismatches>".
 #include <cstdio>
@@ -50,8 +51,12 @@ int main() {
     }
     uint32_t v = pj::seg_value(buf, len);
     const uint32_t pw = pj::seg_pow(len);
+    uint32_t H[301];  // prefix values, as the store keeps them for the probe
+    H[0] = 0;
+    for (int k = 0; k < n; ++k) H[k + 1] = H[k] * pj::SEG_B + buf[k];
     for (int p = 0; p + len <= n; ++p) {
       if (v != pj::seg_value(buf + p, len)) ++bad;
+      if (len > pj::SEG_EXACT_MAX && pj::seg_value_from_prefix(H, p, len, pw) != v) ++bad;
       const unsigned long long key = pj::seg_key_of(v, n, 1 + p % 33);
       if (key == 0 || pj::key_fp(key, pj::key_mix(key)) == 0) ++bad;
       if (p + len < n) v = pj::seg_roll(v, buf[p], buf[p + len], len, pw);
