@@ -148,7 +148,9 @@ typedef struct {
                              later self joins of the threshold replay it (one graph launch;
                              same results; a count above a recorded capacity, which an
                              unchanged index cannot produce, falls back to the eager path).
-                             Needs one probe chunk and no warp-per-candidate range. */
+                             Not recorded: joins with a warp-per-candidate range, or with more
+                             probe groups than PJ_GRAPH_MAX_GROUPS (environment, default
+                             2^28; the graph probes all groups in one pass). */
 } pj_options;
 
 typedef struct pj_index pj_index; /* opaque, library-owned */

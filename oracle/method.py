@@ -244,7 +244,7 @@ def pass_join_self(strings: list[bytes], tau: int, order: str = "alphabetical",
     """Alg. 1 PASS-JOIN(S, tau) with multi-match selection and extension
     verification.  Returns {(a, b): ed} over input ids with a < b.
 
-    order: "alphabetical" visits by (length, string) as in Alg. 1 line 2;
+    order: "alphabetical" visits by (length, string), the order Alg. 1 sorts into;
     "id" visits by (length, input id).  The result set is the same; the
     visiting order only decides which string of a pair probes the other.
     stats (optional dict) receives "tuples" (candidate (s, r, i, p) matches
@@ -262,7 +262,7 @@ def pass_join_self(strings: list[bytes], tau: int, order: str = "alphabetical",
     for sid in visit:
         s = strings[sid]
         ls = len(s)
-        # Alg. 1 lines 4-7: probe L_l^i for |s| - tau <= l <= |s|
+        # Alg. 1, probing step: L_l^i for |s| - tau <= l <= |s|
         for l in range(max(tau + 1, ls - tau), ls + 1):
             for i, lo, hi, li in select_windows(ls, l, tau, method, clip=True):
                 lists = index.get((l, i))
@@ -286,7 +286,7 @@ def pass_join_self(strings: list[bytes], tau: int, order: str = "alphabetical",
                     key = (min(rid, sid), max(rid, sid))
                     best[key] = d
         visited.append(sid)
-        # Alg. 1 line 8: insert s's segments into L_{|s|}^i
+        # Alg. 1, indexing step: insert s's segments into L_{|s|}^i
         if ls >= tau + 1:
             for i, seg in enumerate(segments(s, tau), start=1):
                 index[(ls, i)][seg].append(sid)

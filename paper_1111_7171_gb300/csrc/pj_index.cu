@@ -2,8 +2,8 @@
 //
 //   A1  lengths + validation, stable counting order by length (radix sort of
 //       (length, id)), offsets by prefix sum, warp-per-string gather of the
-//       bytes into sid order, length buckets (Sec. 3.2 groups S_l; Alg. 1
-//       line 2's sort by length).
+//       bytes into sid order, length buckets (Sec. 3.2 groups S_l; the
+//       sort by length that Alg. 1 starts with).
 //   A2  even partition of every string of length >= tau+1 into tau+1
 //       segments and one (key, sid) record per segment (Sec. 3.1).
 //   A3  records sorted by key -> runs = inverted lists L_l^i(w) (Sec. 3.2),

@@ -97,7 +97,7 @@ __host__ __device__ __forceinline__ ProbeView view_for_tau(const ProbeView& v, i
   return t;
 }
 
-// Groups per probing string: lengths |s|-tau..|s| (self join, Alg. 1 line 4)
+// Groups per probing string: lengths |s|-tau..|s| (self join, Alg. 1)
 // or |s|-tau..|s|+tau (R != S, Sec. 3.2), times tau + 1 segments.
 __host__ __device__ __forceinline__ int groups_per_probe(int tau, bool self) {
   return (tau + 1) * (self ? tau + 1 : 2 * tau + 1);
