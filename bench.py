@@ -212,8 +212,10 @@ def _serve(pj, idx, reqs, arrivals, use_plans):
     srv = pj.Server(idx, slots=3, use_plans=use_plans)
     lat = []
     try:
-        for qs, t in reqs[:3]:  # warm-up
-            srv.wait(srv.submit(qs, t))
+        # warm-up: the whole stream once, untimed, so that buffers and (with
+        # plans) every slot's graph capacities have settled
+        for tk in [srv.submit(qs, t) for qs, t in reqs]:
+            srv.wait(tk)
         start = time.perf_counter()
         tickets = []
         if arrivals is None:

@@ -356,6 +356,54 @@ constexpr int Q_WARPS = Q_BLOCK / 32;
 constexpr int S_RUN = 8;                 // consecutive candidates one lane screens
 constexpr int Q_CAP = 32 * S_RUN + 32;   // < 32 left + up to 32 * S_RUN new
 
+// The screen of one lane: candidates c0 .. c0 + S_RUN - 1 (h0 = the hit of
+// c0), each a valid sid, not the probe itself and within the
+// character-count bound; survivors get bit k of mask, with their hit in
+// eh[k] and their sid in ek[k].
+template <bool SELF, bool MULTI>
+__device__ __forceinline__ void screen_run(const ProbeView& v, const Hit* __restrict__ hits,
+                                           const unsigned long long* __restrict__ cand_off,
+                                           unsigned long long n_hits, unsigned long long n_cand,
+                                           unsigned long long c0, unsigned long long h0, uint32_t (&eh)[S_RUN],
+                                           uint32_t (&ek)[S_RUN], uint32_t& mask, unsigned long long& filtered,
+                                           int& err) {
+#pragma unroll
+  for (int k = 0; k < S_RUN; ++k) eh[k] = ek[k] = 0;
+  if (c0 >= n_cand) return;
+  unsigned long long h = h0;
+  unsigned long long c_lo = cand_off[h];
+  unsigned long long c_hi = h + 1 < n_hits ? cand_off[h + 1] : n_cand;
+  Hit hit = hits[h];
+  Sig qsig = {{0u, 0u, 0u, 0u}};
+  if (v.pbm) qsig = v.pbm[hit.q];
+#pragma unroll
+  for (int k = 0; k < S_RUN; ++k) {
+    const unsigned long long c = c0 + k;
+    if (c < n_cand) {
+      if (c >= c_hi) {  // into a later hit
+        do {
+          ++h;
+          c_lo = c_hi;
+          c_hi = h + 1 < n_hits ? cand_off[h + 1] : n_cand;
+        } while (c >= c_hi);
+        hit = hits[h];
+        if (v.pbm) qsig = v.pbm[hit.q];
+      }
+      const ProbeView vt = MULTI ? view_for_tau(v, (int)(hit.pi >> 24)) : v;
+      const uint32_t pk = hit.begin + (uint32_t)(c - c_lo);
+      const PostRec rec = vt.precs[pk];
+      eh[k] = (uint32_t)h;
+      ek[k] = rec_sid(rec);
+      if (rec_sid(rec) >= vt.n_index) {
+        err |= 1;
+      } else if (!(SELF && rec_sid(rec) == hit.q)) {
+        if (v.pbm && signature_bound(qsig, rec.sig) > vt.tau) ++filtered;
+        else mask |= 1u << k;
+      }
+    }
+  }
+}
+
 template <int MAXW, bool SELF, bool MULTI>
 __global__ void __launch_bounds__(Q_BLOCK) k_verify_queued(const ProbeView v, const Hit* __restrict__ hits,
                                                             const unsigned long long* __restrict__ cand_off,
@@ -393,43 +441,7 @@ __global__ void __launch_bounds__(Q_BLOCK) k_verify_queued(const ProbeView v, co
     const unsigned long long h0 = lane_hit_of(cand_off, n_hits, warp_hit_of(cand_off, n_hits, base), base, c0);
     uint32_t mask = 0;
     uint32_t eh[S_RUN], ek[S_RUN];
-    if (c0 < n_cand) {
-      unsigned long long h = h0;
-      unsigned long long c_lo = cand_off[h];
-      unsigned long long c_hi = h + 1 < n_hits ? cand_off[h + 1] : n_cand;
-      Hit hit = hits[h];
-      Sig qsig = {{0u, 0u, 0u, 0u}};
-      if (v.pbm) qsig = v.pbm[hit.q];
-#pragma unroll
-      for (int k = 0; k < S_RUN; ++k) {
-        const unsigned long long c = c0 + k;
-        eh[k] = 0;
-        ek[k] = 0;
-        if (c < n_cand) {
-          if (c >= c_hi) {  // into a later hit
-            do {
-              ++h;
-              c_lo = c_hi;
-              c_hi = h + 1 < n_hits ? cand_off[h + 1] : n_cand;
-            } while (c >= c_hi);
-            hit = hits[h];
-            if (v.pbm) qsig = v.pbm[hit.q];
-          }
-          const ProbeView vt = MULTI ? view_for_tau(v, (int)(hit.pi >> 24)) : v;
-          const uint32_t pk = hit.begin + (uint32_t)(c - c_lo);
-          const PostRec rec = vt.precs[pk];
-          eh[k] = (uint32_t)h;
-          ek[k] = rec_sid(rec);
-          // screen: a valid sid, not the probe itself, character-count bound
-          if (rec_sid(rec) >= vt.n_index) {
-            err |= 1;
-          } else if (!(SELF && rec_sid(rec) == hit.q)) {
-            if (v.pbm && signature_bound(qsig, rec.sig) > vt.tau) ++filtered;
-            else mask |= 1u << k;
-          }
-        }
-      }
-    }
+    screen_run<SELF, MULTI>(v, hits, cand_off, n_hits, n_cand, c0, h0, eh, ek, mask, filtered, err);
     __syncwarp();
     const int cnt = __popc(mask);
     const int incl = warp_incl_scan(cnt);
