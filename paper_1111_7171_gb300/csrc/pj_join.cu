@@ -2181,10 +2181,12 @@ int pj_join(const pj_strings* R, const pj_strings* S, int tau, const pj_options*
     pj::build_store(*tmp, *S);
     tmp->parts.resize(tau + 1);
     pj::build_partition(*tmp, tau, tmp->parts[tau]);
-    pj::ProbeSet P;
-    pj::upload_probe_set(tmp->ctx, *R, P);
-    pj::probe_join_impl(tmp->ctx, *tmp, tmp->parts[tau], P, out, tmp->results_on_device);
-    tmp->ctx.sync();
+    {  // the probe set's buffers refer to tmp->ctx: released before tmp
+      pj::ProbeSet P;
+      pj::upload_probe_set(tmp->ctx, *R, P);
+      pj::probe_join_impl(tmp->ctx, *tmp, tmp->parts[tau], P, out, tmp->results_on_device);
+      tmp->ctx.sync();
+    }
     delete tmp;
     return PJ_OK;
   } catch (const pj::Error& e) {
