@@ -265,8 +265,10 @@ __global__ void k_table_insert(const unsigned long long* __restrict__ keys, cons
       table[h].begin = b;
       table[h].count = e - b;
       fp[h] = key_fp(key, mix);
-      const unsigned long long bit = presence_bit(mix, mask);
-      atomicOr(reinterpret_cast<uint32_t*>(fp + mask + 1) + (bit >> 5), 1u << (bit & 31));
+      unsigned long long word;
+      uint32_t bits;
+      presence_of(mix, mask, word, bits);
+      atomicOr(reinterpret_cast<uint32_t*>(fp + mask + 1) + word, bits);
       return;
     }
     h = (h + 1) & mask;
@@ -498,8 +500,10 @@ void check_partition(const Ctx& c, const Partition& part) {
     const Slot& s = t[h];
     if (fp[h] != (s.key ? key_fp(s.key, key_mix(s.key)) : 0)) fail(PJ_ECUDA, "index audit: fingerprint mismatch");
     if (s.key) {
-      const unsigned long long bit = presence_bit(key_mix(s.key), t.size() - 1);
-      bits[bit >> 3] |= (uint8_t)(1u << (bit & 7));
+      unsigned long long word;
+      uint32_t wbits;
+      presence_of(key_mix(s.key), t.size() - 1, word, wbits);
+      for (int k = 0; k < 4; ++k) bits[4 * word + k] |= (uint8_t)(wbits >> (8 * k));
     }
     if (s.key == 0) {
       ++empty;

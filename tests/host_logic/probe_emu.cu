@@ -87,8 +87,10 @@ int main(int argc, char** argv) {
     if (table[h].key) {
       const uint32_t mix = key_mix(table[h].key);
       fp[h] = key_fp(table[h].key, mix);
-      const ull bit = presence_bit(mix, cap - 1);
-      fp[cap + (bit >> 3)] |= (uint8_t)(1u << (bit & 7));
+      ull word;
+      uint32_t bits;
+      presence_of(mix, cap - 1, word, bits);
+      for (int k = 0; k < 4; ++k) fp[cap + 4 * word + k] |= (uint8_t)(bits >> (8 * k));
     }
   const bool use_fp = !getenv("PJ_EMU_NO_FP");
   ProbeView v{};

@@ -67,8 +67,10 @@ int main() {
       if (t[h].key) {
         const uint32_t mix = key_mix(t[h].key);
         fp[h] = key_fp(t[h].key, mix);
-        const ull bit = presence_bit(mix, mask);
-        fp[cap + (bit >> 3)] |= (uint8_t)(1u << (bit & 7));
+        ull word;
+        uint32_t bits;
+        presence_of(mix, mask, word, bits);
+        for (int k = 0; k < 4; ++k) fp[cap + 4 * word + k] |= (uint8_t)(bits >> (8 * k));
       }
     auto check = [&](ull key) {
       uint32_t b0 = 0, c0 = 0, b1 = 0, c1 = 0, b2 = 0, c2 = 0;
@@ -85,9 +87,12 @@ int main() {
     for (int k = 0; k < 200000; ++k) {
       const ull key = rng() | 1ull;
       const uint32_t mix = key_mix(key);
-      const ull h = mix & mask, bit = presence_bit(mix, mask);
-      if ((t[h].key && fp[h] == key_fp(key, mix) && t[h].key != key) || (fp[cap + (bit >> 3)] >> (bit & 7) & 1))
-        check(key);
+      const ull h = mix & mask;
+      ull word;
+      uint32_t bits, have;
+      presence_of(mix, mask, word, bits);
+      memcpy(&have, &fp[cap + 4 * word], 4);
+      if ((t[h].key && fp[h] == key_fp(key, mix) && t[h].key != key) || (have & bits) == bits) check(key);
     }
   }
   printf("cases %llu bad %llu\n", cases, bad);
