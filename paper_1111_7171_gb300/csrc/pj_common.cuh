@@ -87,9 +87,11 @@ void trace_note(const char* what);
 void debug_dump(const Ctx& c, const char* name, const void* dev, size_t bytes);
 
 // Device array of T obtained from a Ctx; freed (stream-ordered) on scope exit.
+// It keeps a copy of the context that allocated it (allocator and stream),
+// so it may outlive that Ctx object.
 template <class T>
 struct DBuf {
-  const Ctx* ctx = nullptr;
+  Ctx ctx;
   T* p = nullptr;
   size_t n = 0;
 
@@ -113,12 +115,12 @@ struct DBuf {
 
   void reset(const Ctx& c, size_t count) {
     release();
-    ctx = &c;
+    ctx = c;
     n = count;
     p = static_cast<T*>(c.get((count ? count : 1) * sizeof(T)));
   }
   void release() {
-    if (p && ctx) ctx->put(p);
+    if (p) ctx.put(p);
     p = nullptr;
     n = 0;
   }
