@@ -906,6 +906,8 @@ static void pinned_put(void* p, size_t bytes) {
 //   PJ_LAUNCH_CANDS      candidates per verification launch (default 1 Gi)
 //   PJ_ACCEPT_INITIAL    initial accepted-match capacity  (default 4 Mi)
 //   PJ_GRAPH_MAX_GROUPS  groups of a recorded self join   (default 256 Mi)
+//   PJ_GRAPH_TIGHT       1: record self joins with half their counts as
+//                        capacities, so that every replay overflows
 static unsigned long long env_knob(const char* name, unsigned long long dflt) {
   const char* e = getenv(name);
   if (!e || !e[0]) return dflt;
@@ -1713,7 +1715,12 @@ static void record_self_plan(const Ctx& c, const ProbeView& v, SelfPlan& P) {
   PJ_LAUNCHED("k_self_finish");
 }
 
-static unsigned long long with_slack(unsigned long long n) { return n + n / 64 + 1024; }
+// Recorded capacity for a count of the eager run: the count plus slack; with
+// PJ_GRAPH_TIGHT=1 (tests) half the count, so that replays overflow and take
+// the eager path.
+static unsigned long long with_slack(unsigned long long n) {
+  return env_knob("PJ_GRAPH_TIGHT", 0) ? std::max(1ull, n / 2) : n + n / 64 + 1024;
+}
 
 // Records the self join described by v and st (the counts of its eager
 // run); returns nullptr when the join is not eligible.

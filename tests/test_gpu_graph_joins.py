@@ -6,9 +6,10 @@ results, tolerance 0), and report the same counts.  Covered: extension
 verification with indexed strings too short to partition (the fallback
 kernel), distinct-pair verification with a thread and with a warp per pair,
 host and device results, several thresholds of one index, an eager join
-taken in several probe chunks, joins that are not recorded (too many probe
-groups, a warp-per-candidate range), an index without graph joins, and
-launch accounting.
+taken in several probe chunks, replays whose counts overflow the recorded
+capacities (falling back to the eager join), joins that are not recorded
+(too many probe groups, a warp-per-candidate range), an index without
+graph joins, and launch accounting.
 """
 import numpy as np
 import pytest
@@ -145,6 +146,22 @@ def test_graph_replay_after_chunked_eager_join(monkeypatch):
         strings = synth.generate("short", 3, n=3000)
         check_replays(joins(strings, 3), cpu_self(strings, 3), f"chunked eager pairs={mode}",
                       COUNTS if mode == "0" else probe_counts)
+
+
+@pytest.mark.parametrize("mode", ["0", "1"])
+def test_replays_that_overflow_fall_back(monkeypatch, mode):
+    """Graphs recorded with half the eager run's counts as capacities (hits,
+    candidates, accepted matches, pairs): every replay overflows, is
+    discarded, and the join runs eagerly -- same pairs, graph_replay 0."""
+    monkeypatch.setenv("PJ_GRAPH_TIGHT", "1")
+    monkeypatch.setenv("PJ_VERIFY_PAIRS", mode)
+    strings = synth.generate("short", 3, n=3000) + [b"", b"ab"]
+    want = cpu_self(strings, 3)
+    rs = joins(strings, 3, runs=4)
+    assert all(r.stats["graph_replay"] == 0 for r in rs)
+    assert all(np.array_equal(r.pairs, want) for r in rs)
+    for key in COUNTS:
+        assert all(r.stats[key] == rs[0].stats[key] for r in rs), key
 
 
 def test_graph_replay_empty_and_tiny():
