@@ -200,6 +200,13 @@ __global__ void k_prefix_values(const uint8_t* __restrict__ bytes, const uint64_
   }
 }
 
+// ref[k] = off[k] << 16 | len[k] (lengths < 2^16, offsets < 2^48).
+__global__ void k_refs(const uint64_t* __restrict__ off, const uint32_t* __restrict__ len, uint32_t n,
+                       unsigned long long* __restrict__ ref) {
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+    ref[k] = ((unsigned long long)off[k] << 16) | len[k];
+}
+
 // bbeg[l] = first sid whose length is >= l, for l = 0 .. lmax + 1.
 __global__ void k_buckets(const uint32_t* __restrict__ slen, uint32_t n, uint32_t* __restrict__ bbeg, int lmax) {
   const uint32_t sid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -363,6 +370,13 @@ void build_store(pj_index& idx, const pj_strings& S) {
     k_signatures<<<std::min<unsigned>(ceil_div(n, 256), 152u * 8u), 256, 0, c.stream>>>(idx.sbytes.p, idx.soff.p, n,
                                                                                     idx.sbm.p);
     PJ_LAUNCHED("k_signatures");
+  }
+  if (total >> 48) fail(PJ_EINVAL, "pj_strings: more than 2^48 bytes");
+  idx.sref.reset(c, n ? n : 1);
+  if (n) {
+    k_refs<<<std::min<unsigned>(ceil_div(n, 256), 152u * 8u), 256, 0, c.stream>>>(idx.soff.p, idx.slen.p, n,
+                                                                                idx.sref.p);
+    PJ_LAUNCHED("k_refs");
   }
   idx.sph.reset(c, (size_t)total + n + 1);
   if (n) {
@@ -580,7 +594,8 @@ void upload_probe_set(const Ctx& c, const pj_strings& R, ProbeSet& out) {
 // ------------------------------------------------------------------ C ABI --
 
 uint64_t pj_index::device_bytes() const {
-  uint64_t b = sbytes.bytes() + soff.bytes() + slen.bytes() + perm.bytes() + bbeg.bytes() + sbm.bytes() + sph.bytes();
+  uint64_t b = sbytes.bytes() + soff.bytes() + slen.bytes() + perm.bytes() + bbeg.bytes() + sbm.bytes() + sph.bytes() +
+               sref.bytes();
   for (const auto& p : parts)
     b += p.table.bytes() + p.fp.bytes() + p.postings.bytes() + p.precs.bytes() + p.gorder[0].bytes() +
          p.gorder[1].bytes();

@@ -356,6 +356,7 @@ struct pj_index {
   pj::DBuf<uint32_t> bbeg;   // lmax + 2 bucket starts by length
   pj::DBuf<pj::Sig> sbm;     // character signatures by sid (char_signature)
   pj::DBuf<uint32_t> sph;    // prefix values (seg_value_from_prefix) by sid, |s| + 1 from soff[sid] + sid
+  pj::DBuf<unsigned long long> sref;  // soff[sid] << 16 | slen[sid] by sid
   std::vector<uint32_t> h_bbeg;
   std::vector<pj::Partition> parts;  // index = tau
   uint64_t device_bytes() const;

@@ -1547,6 +1547,7 @@ static ProbeView index_side(const pj_index& idx, const Partition& part) {
   v.ibytes = idx.sbytes.p;
   v.ioff = idx.soff.p;
   v.ilen = idx.slen.p;
+  v.iref = idx.sref.p;
   v.ibbeg = idx.bbeg.p;
   v.ilmax = idx.lmax;
   v.iperm = idx.perm.p;

@@ -219,6 +219,7 @@ void query_noalloc(pj_index& idx, const pj_strings& batch, int tau, pj_pair* out
   v.ibytes = idx.sbytes.p;
   v.ioff = idx.soff.p;
   v.ilen = idx.slen.p;
+  v.iref = idx.sref.p;
   v.ibbeg = idx.bbeg.p;
   v.ilmax = idx.lmax;
   v.iperm = idx.perm.p;

@@ -47,6 +47,7 @@ struct ProbeView {
   const uint8_t* ibytes;
   const uint64_t* ioff;
   const uint32_t* ilen;
+  const unsigned long long* iref;  // ioff << 16 | ilen in one word (NULL: read ioff and ilen)
   const uint32_t* ibbeg;  // first sid of each length, ilmax + 2 entries
   int ilmax;
   const uint32_t* iperm;  // sid -> reported id
@@ -197,13 +198,24 @@ __host__ __device__ __forceinline__ bool verify_screened(const ProbeView& v, boo
   // Single exit: see vsp().
   bool ok = false;
   const int i = hc.i;
-  const int lr = (int)v.ilen[r];
+  // r's length and bytes: one load of its packed reference, so that the
+  // byte loads do not wait for a second dependent load
+  int lr;
+  const uint8_t* rb;
+  if (v.iref) {
+    const unsigned long long ref = v.iref[r];
+    lr = (int)(ref & 0xFFFFu);
+    rb = v.ibytes + (ref >> 16);
+  } else {
+    lr = (int)v.ilen[r];
+    rb = v.ibytes + v.ioff[r];
+  }
   if (i >= 1 && i <= v.tau + 1 && lr >= v.tau + 1) {  // r is a partitioned string
     int P, li;
     even_segment_m(lr, v.tau + 1, v.seg_magic, i, P, li);
     // exact keys (segments of at most SEG_EXACT_MAX bytes) guarantee the
     // segment match; hashed ones are compared
-    if (hc.p + li <= hc.ls && verify_ext<MAXW>(hc.s, hc.ls, v.ibytes + v.ioff[r], lr, i, hc.p, li, P, v.tau,
+    if (hc.p + li <= hc.ls && verify_ext<MAXW>(hc.s, hc.ls, rb, lr, i, hc.p, li, P, v.tau,
                                                li > SEG_EXACT_MAX, ed, cells)) {
       const uint32_t qid = v.pid ? v.pid[hc.q] : hc.q;
       const uint32_t rid = v.iperm[r];

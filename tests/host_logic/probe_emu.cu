@@ -93,8 +93,11 @@ int main(int argc, char** argv) {
       for (int k = 0; k < 4; ++k) fp[cap + 4 * word + k] |= (uint8_t)(bits >> (8 * k));
     }
   const bool use_fp = !getenv("PJ_EMU_NO_FP");
+  std::vector<ull> ref(n);  // packed offset << 16 | length, as the store keeps it
+  for (uint32_t k = 0; k < n; ++k) ref[k] = ((ull)soff[k] << 16) | slen[k];
   ProbeView v{};
   v.table_fp = use_fp ? fp.data() : nullptr;
+  v.iref = use_fp ? ref.data() : nullptr;  // the no-fingerprint run also covers the unpacked reads
   v.ibytes = sb.data();
   v.ioff = soff.data();
   v.ilen = slen.data();
