@@ -150,7 +150,9 @@ typedef struct {
                              unchanged index cannot produce, falls back to the eager path).
                              Not recorded: joins with a warp-per-candidate range, or with more
                              probe groups than PJ_GRAPH_MAX_GROUPS (environment, default
-                             2^28; the graph probes all groups in one pass). */
+                             2^28; the graph probes all groups in one pass).  A recorded join
+                             keeps its device buffers (about the eager join's peak scratch;
+                             ~10 GB for 1M short strings at tau = 4) until pj_index_free. */
 } pj_options;
 
 typedef struct pj_index pj_index; /* opaque, library-owned */
