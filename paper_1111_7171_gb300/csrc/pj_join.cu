@@ -1946,10 +1946,10 @@ static void self_join_impl(pj_index& idx, int tau, pj_result* out, bool on_devic
   }
   run_join(idx.ctx, v, true, part.first, bits_for(idx.n), on_device, out);
   if (idx.graph_joins && !idx.self_plans[tau]) {
-    try {  // a join that cannot be recorded (memory) still has its result
+    try {  // a join that cannot be recorded (device or host memory) still has its result
       std::shared_ptr<SelfPlan> p = make_self_plan(idx, v, tr, part.first, out->stats, out->count);
       if (p) idx.self_plans[tau] = std::static_pointer_cast<void>(p);
-    } catch (const Error&) {
+    } catch (...) {
       cudaGetLastError();
     }
   }
