@@ -432,10 +432,10 @@ void build_partition(pj_index& idx, int tau, Partition& part) {
   if (nrec == 0) {  // an empty table of the smallest size: every lookup finds nothing
     part.n_unique = 0;
     part.table.reset(c, 1024);
-    part.fp.reset(c, 2 * 1024);
+    part.fp.reset(c, fp_array_bytes(1024));
     part.precs.reset(c, 1);
     PJ_CUDA(cudaMemsetAsync(part.table.p, 0, 1024 * sizeof(Slot), c.stream));
-    PJ_CUDA(cudaMemsetAsync(part.fp.p, 0, 2 * 1024, c.stream));
+    PJ_CUDA(cudaMemsetAsync(part.fp.p, 0, fp_array_bytes(1024), c.stream));
     return;
   }
   DBuf<unsigned long long> keys(c, nrec);
@@ -463,9 +463,9 @@ void build_partition(pj_index& idx, int tau, Partition& part) {
   uint64_t cap = 1024;
   while (cap < 2 * n_unique) cap <<= 1;
   part.table.reset(c, cap);
-  part.fp.reset(c, 2 * cap);  // fingerprints, then the presence bitmap
+  part.fp.reset(c, fp_array_bytes(cap));  // fingerprints, then the presence bitmap
   PJ_CUDA(cudaMemsetAsync(part.table.p, 0, cap * sizeof(Slot), c.stream));
-  PJ_CUDA(cudaMemsetAsync(part.fp.p, 0, 2 * cap, c.stream));
+  PJ_CUDA(cudaMemsetAsync(part.fp.p, 0, fp_array_bytes(cap), c.stream));
   DBuf<int> err(c, 1);
   PJ_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), c.stream));
   k_table_insert<<<ceil_div(n_unique, 256), 256, 0, c.stream>>>(keys.p, heads.p, n_unique, part.table.p, part.fp.p,
@@ -508,8 +508,8 @@ void check_partition(const Ctx& c, const Partition& part) {
   c.sync();
   uint64_t empty = 0, used = 0, covered = 0;
   std::vector<uint8_t> seen(part.n_records, 0);
-  if (fp.size() != 2 * t.size()) fail(PJ_ECUDA, "index audit: fingerprint array size");
-  std::vector<uint8_t> bits(t.size(), 0);  // the presence bitmap the stored keys give
+  if (fp.size() != fp_array_bytes(t.size())) fail(PJ_ECUDA, "index audit: fingerprint array size");
+  std::vector<uint8_t> bits(PRESENCE_BYTES * t.size(), 0);  // the presence bitmap the stored keys give
   for (size_t h = 0; h < t.size(); ++h) {
     const Slot& s = t[h];
     if (fp[h] != (s.key ? key_fp(s.key, key_mix(s.key)) : 0)) fail(PJ_ECUDA, "index audit: fingerprint mismatch");
@@ -531,7 +531,7 @@ void check_partition(const Ctx& c, const Partition& part) {
       ++covered;
     }
   }
-  if (memcmp(bits.data(), fp.data() + t.size(), t.size()) != 0) fail(PJ_ECUDA, "index audit: presence bitmap");
+  if (memcmp(bits.data(), fp.data() + t.size(), bits.size()) != 0) fail(PJ_ECUDA, "index audit: presence bitmap");
   fprintf(stderr, "[pj] audit tau=%d: slots=%zu used=%llu empty=%llu runs=%llu covered=%llu of %llu\n", part.tau,
           t.size(), (unsigned long long)used, (unsigned long long)empty, (unsigned long long)part.n_unique,
           (unsigned long long)covered, (unsigned long long)part.n_records);

@@ -236,16 +236,24 @@ __host__ __device__ __forceinline__ bool slot_matches(const Slot* t, unsigned lo
 }
 
 // Layout of a table's fingerprint array for S = mask + 1 slots: bytes
-// [0, S) hold key_fp of each used slot (0 for empty ones), bytes [S, 2S) a
-// presence bitmap of S / 4 32-bit words (16 to 32 bits per key at load
-// factor 1/4 to 1/2) in which every stored key sets two bits of one word:
-// word mix & (S/4 - 1), bits mix >> 27 and (mix >> 22) & 31, mix =
-// key_mix(key).  An absent key finds one of its two bits clear in about
+// [0, S) hold key_fp of each used slot (0 for empty ones), the next
+// PRESENCE_BYTES * S bytes a presence bitmap of W = PRESENCE_BYTES * S / 4
+// 32-bit words (8 * PRESENCE_BYTES bits per slot: 16 to 32 per key per
+// byte at load factor 1/4 to 1/2) in which every stored key sets two bits
+// of one word: word mix & (W - 1), bits mix >> 27 and (mix >> 22) & 31,
+// mix = key_mix(key).  An absent key finds one of its two bits clear in about
 // 98% or more of lookups, so in most steps of a warp's probe loop no lane
 // goes on to the fingerprint walk.
+constexpr unsigned PRESENCE_BYTES = 1;  // bitmap bytes per slot
+
+// Bytes of a table's fingerprint array (fingerprints, then the bitmap).
+__host__ __device__ __forceinline__ unsigned long long fp_array_bytes(unsigned long long slots) {
+  return (1 + PRESENCE_BYTES) * slots;
+}
+
 __host__ __device__ __forceinline__ void presence_of(uint32_t mix, unsigned long long mask, unsigned long long& word,
                                                      uint32_t& bits) {
-  word = mix & (((mask + 1) >> 2) - 1);
+  word = mix & (((mask + 1) * PRESENCE_BYTES / 4) - 1);
   bits = (1u << (mix >> 27)) | (1u << ((mix >> 22) & 31u));
 }
 

@@ -82,7 +82,7 @@ int main(int argc, char** argv) {
   }
   // fingerprint bytes and presence bitmap as the index build sets them
   // (none with PJ_EMU_NO_FP)
-  std::vector<uint8_t> fp(2 * cap, 0);
+  std::vector<uint8_t> fp(fp_array_bytes(cap), 0);
   for (ull h = 0; h < cap; ++h)
     if (table[h].key) {
       const uint32_t mix = key_mix(table[h].key);

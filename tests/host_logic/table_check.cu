@@ -62,7 +62,7 @@ int main() {
       t[h].count = (uint32_t)(key >> 40) + 1;
       keys.push_back(key);
     }
-    std::vector<uint8_t> fp(2 * cap, 0);  // fingerprints, then the presence bitmap
+    std::vector<uint8_t> fp(fp_array_bytes(cap), 0);  // fingerprints, then the presence bitmap
     for (ull h = 0; h < cap; ++h)
       if (t[h].key) {
         const uint32_t mix = key_mix(t[h].key);
