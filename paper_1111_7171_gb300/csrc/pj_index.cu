@@ -259,7 +259,7 @@ __global__ void k_heads(const uint32_t* __restrict__ flags, const uint32_t* __re
 
 __global__ void k_table_insert(const unsigned long long* __restrict__ keys, const uint32_t* __restrict__ heads,
                                uint64_t n_unique, Slot* __restrict__ table, uint8_t* __restrict__ fp,
-                               unsigned long long mask, int* __restrict__ err) {
+                               unsigned pb, unsigned long long mask, int* __restrict__ err) {
   const uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (u >= n_unique) return;
   const uint32_t b = heads[u], e = heads[u + 1];
@@ -274,7 +274,7 @@ __global__ void k_table_insert(const unsigned long long* __restrict__ keys, cons
       fp[h] = key_fp(key, mix);
       unsigned long long word;
       uint32_t bits;
-      presence_of(mix, mask, word, bits);
+      presence_of(mix, mask, pb, word, bits);
       atomicOr(reinterpret_cast<uint32_t*>(fp + mask + 1) + word, bits);
       return;
     }
@@ -394,6 +394,11 @@ void build_store(pj_index& idx, const pj_strings& S) {
   c.sync();
 }
 
+// Average indexed length above which a table gets 2 presence-bitmap bytes
+// per slot instead of 1 (long strings: 6% faster probes at tau = 32; medium
+// ones: 3% slower with the larger table).
+constexpr uint64_t PRESENCE2_MIN_AVG_LEN = 256;
+
 void check_partition(const Ctx& c, const Partition& part);
 
 // Window size of group (length offset, segment i) when nothing clips it
@@ -429,13 +434,17 @@ void build_partition(pj_index& idx, int tau, Partition& part) {
   part.n_records = nrec;
   if (nrec > 0xFFFFFFF0ull) fail(PJ_EINVAL, "segment index: more than 2^32 records");
   part.postings.reset(c, nrec);
+  // Presence bitmap of 2 bytes per slot for indexes of long strings, whose
+  // probes make many lookups per stored key (fewer false positives), else 1
+  // (a smaller table for L2).
+  part.presence_bytes = idx.n && idx.total_bytes > PRESENCE2_MIN_AVG_LEN * idx.n ? 2 : 1;
   if (nrec == 0) {  // an empty table of the smallest size: every lookup finds nothing
     part.n_unique = 0;
     part.table.reset(c, 1024);
-    part.fp.reset(c, fp_array_bytes(1024));
+    part.fp.reset(c, fp_array_bytes(1024, part.presence_bytes));
     part.precs.reset(c, 1);
     PJ_CUDA(cudaMemsetAsync(part.table.p, 0, 1024 * sizeof(Slot), c.stream));
-    PJ_CUDA(cudaMemsetAsync(part.fp.p, 0, fp_array_bytes(1024), c.stream));
+    PJ_CUDA(cudaMemsetAsync(part.fp.p, 0, fp_array_bytes(1024, part.presence_bytes), c.stream));
     return;
   }
   DBuf<unsigned long long> keys(c, nrec);
@@ -463,13 +472,13 @@ void build_partition(pj_index& idx, int tau, Partition& part) {
   uint64_t cap = 1024;
   while (cap < 2 * n_unique) cap <<= 1;
   part.table.reset(c, cap);
-  part.fp.reset(c, fp_array_bytes(cap));  // fingerprints, then the presence bitmap
+  part.fp.reset(c, fp_array_bytes(cap, part.presence_bytes));  // fingerprints, then the presence bitmap
   PJ_CUDA(cudaMemsetAsync(part.table.p, 0, cap * sizeof(Slot), c.stream));
-  PJ_CUDA(cudaMemsetAsync(part.fp.p, 0, fp_array_bytes(cap), c.stream));
+  PJ_CUDA(cudaMemsetAsync(part.fp.p, 0, fp_array_bytes(cap, part.presence_bytes), c.stream));
   DBuf<int> err(c, 1);
   PJ_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), c.stream));
   k_table_insert<<<ceil_div(n_unique, 256), 256, 0, c.stream>>>(keys.p, heads.p, n_unique, part.table.p, part.fp.p,
-                                                                cap - 1, err.p);
+                                                                part.presence_bytes, cap - 1, err.p);
   PJ_LAUNCHED("k_table_insert");
   int h_err = 0;
   PJ_CUDA(cudaMemcpyAsync(&h_err, err.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
@@ -508,15 +517,16 @@ void check_partition(const Ctx& c, const Partition& part) {
   c.sync();
   uint64_t empty = 0, used = 0, covered = 0;
   std::vector<uint8_t> seen(part.n_records, 0);
-  if (fp.size() != fp_array_bytes(t.size())) fail(PJ_ECUDA, "index audit: fingerprint array size");
-  std::vector<uint8_t> bits(PRESENCE_BYTES * t.size(), 0);  // the presence bitmap the stored keys give
+  const unsigned pb = part.presence_bytes;
+  if (fp.size() != fp_array_bytes(t.size(), pb)) fail(PJ_ECUDA, "index audit: fingerprint array size");
+  std::vector<uint8_t> bits(pb * t.size(), 0);  // the presence bitmap the stored keys give
   for (size_t h = 0; h < t.size(); ++h) {
     const Slot& s = t[h];
     if (fp[h] != (s.key ? key_fp(s.key, key_mix(s.key)) : 0)) fail(PJ_ECUDA, "index audit: fingerprint mismatch");
     if (s.key) {
       unsigned long long word;
       uint32_t wbits;
-      presence_of(key_mix(s.key), t.size() - 1, word, wbits);
+      presence_of(key_mix(s.key), t.size() - 1, pb, word, wbits);
       for (int k = 0; k < 4; ++k) bits[4 * word + k] |= (uint8_t)(wbits >> (8 * k));
     }
     if (s.key == 0) {

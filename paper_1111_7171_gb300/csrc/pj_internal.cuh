@@ -236,24 +236,23 @@ __host__ __device__ __forceinline__ bool slot_matches(const Slot* t, unsigned lo
 }
 
 // Layout of a table's fingerprint array for S = mask + 1 slots: bytes
-// [0, S) hold key_fp of each used slot (0 for empty ones), the next
-// PRESENCE_BYTES * S bytes a presence bitmap of W = PRESENCE_BYTES * S / 4
-// 32-bit words (8 * PRESENCE_BYTES bits per slot: 16 to 32 per key per
-// byte at load factor 1/4 to 1/2) in which every stored key sets two bits
-// of one word: word mix & (W - 1), bits mix >> 27 and (mix >> 22) & 31,
-// mix = key_mix(key).  An absent key finds one of its two bits clear in about
+// [0, S) hold key_fp of each used slot (0 for empty ones), the next pb * S
+// bytes (pb = 1 or 2, chosen per table) a presence bitmap of W = pb * S / 4
+// 32-bit words (8 pb bits per slot: 16 to 32 bits per key per byte at load
+// factor 1/4 to 1/2) in which every stored key sets two bits of one word:
+// word mix & (W - 1), bits mix >> 27 and (mix >> 22) & 31, mix =
+// key_mix(key).  An absent key finds one of its two bits clear in about
 // 98% or more of lookups, so in most steps of a warp's probe loop no lane
 // goes on to the fingerprint walk.
-constexpr unsigned PRESENCE_BYTES = 1;  // bitmap bytes per slot
-
-// Bytes of a table's fingerprint array (fingerprints, then the bitmap).
-__host__ __device__ __forceinline__ unsigned long long fp_array_bytes(unsigned long long slots) {
-  return (1 + PRESENCE_BYTES) * slots;
+// Bytes of a table's fingerprint array (fingerprints, then the bitmap of pb
+// bytes per slot).
+__host__ __device__ __forceinline__ unsigned long long fp_array_bytes(unsigned long long slots, unsigned pb) {
+  return (1 + pb) * slots;
 }
 
-__host__ __device__ __forceinline__ void presence_of(uint32_t mix, unsigned long long mask, unsigned long long& word,
-                                                     uint32_t& bits) {
-  word = mix & (((mask + 1) * PRESENCE_BYTES / 4) - 1);
+__host__ __device__ __forceinline__ void presence_of(uint32_t mix, unsigned long long mask, unsigned pb,
+                                                     unsigned long long& word, uint32_t& bits) {
+  word = mix & (((mask + 1) * pb / 4) - 1);
   bits = (1u << (mix >> 27)) | (1u << ((mix >> 22) & 31u));
 }
 
@@ -276,8 +275,8 @@ __host__ __device__ __forceinline__ uint32_t load_u32(const uint8_t* p) {  // p 
 // compares give those that are empty and those whose fingerprint matches,
 // and a 16-byte slot is read only for a match before the first empty slot.
 __host__ __device__ __forceinline__ int table_find(const Slot* __restrict__ t, const uint8_t* __restrict__ fp,
-                                                   unsigned long long mask, unsigned long long key, uint32_t& begin,
-                                                   uint32_t& count) {
+                                                   unsigned pb, unsigned long long mask, unsigned long long key,
+                                                   uint32_t& begin, uint32_t& count) {
   const uint32_t mix = key_mix(key);
   unsigned long long h = mix & mask;
   unsigned long long k = 0;
@@ -291,7 +290,7 @@ __host__ __device__ __forceinline__ int table_find(const Slot* __restrict__ t, c
   }
   unsigned long long word;
   uint32_t bits;
-  presence_of(mix, mask, word, bits);
+  presence_of(mix, mask, pb, word, bits);
   if ((load_u32(fp + (mask + 1) + (word << 2)) & bits) != bits) return 0;
   // mask + 1 (the slot count) is a power of two >= 8, so buckets of 8 never wrap
   const unsigned long long f8 = 0x0101010101010101ull * key_fp(key, mix);
@@ -331,6 +330,7 @@ struct Partition {
   uint64_t n_unique = 0;     // distinct keys
   DBuf<Slot> table;          // power-of-two capacity
   DBuf<uint8_t> fp;          // key_fp of each used slot (0 for empty ones), then the presence bitmap
+  unsigned presence_bytes = 1;  // bitmap bytes per slot (2 for indexes of long strings)
   DBuf<uint32_t> postings;   // sids, runs in key order, ascending inside a run
   DBuf<PostRec> precs;       // one record per posting, same order
   // group visiting order for one probe: the (length, segment) groups sorted

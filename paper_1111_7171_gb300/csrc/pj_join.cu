@@ -1554,6 +1554,7 @@ static ProbeView index_side(const pj_index& idx, const Partition& part) {
   v.n_index = idx.n;
   v.table = part.table.p;
   v.table_fp = part.fp.p;
+  v.table_pb = part.presence_bytes;
   v.precs = part.precs.p;
   v.ibm = idx.sbm.p;
   v.mask = part.table.n - 1;
@@ -2004,7 +2005,7 @@ void query_multi_impl(const Ctx& c, pj_index& idx, const ProbeSet& R, const uint
     PartView pv{};
     if (present[t]) {
       const Partition& part = idx.parts[t];
-      pv = PartView{part.table.p, part.fp.p,    part.precs.p, part.table.n - 1,
+      pv = PartView{part.table.p, part.fp.p, part.presence_bytes, part.precs.p, part.table.n - 1,
                     part.postings.p, part.n_records, part.first, t, seg_magic(t + 1)};
       has_short |= part.first > 0;
     }

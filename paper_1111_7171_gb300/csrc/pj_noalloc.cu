@@ -226,6 +226,7 @@ void query_noalloc(pj_index& idx, const pj_strings& batch, int tau, pj_pair* out
   v.n_index = idx.n;
   v.table = part.table.p;
   v.table_fp = part.fp.p;
+  v.table_pb = part.presence_bytes;
   v.precs = part.precs.p;
   v.ibm = idx.sbm.p;
   v.pbm = R.bm.p;

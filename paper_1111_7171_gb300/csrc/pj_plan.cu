@@ -255,7 +255,7 @@ void create(pj_plan& P, pj_index& idx, const pj_plan_options& o) {
   std::vector<PartView> hp((size_t)tau_max + 1);
   for (int t = 0; t <= tau_max; ++t) {
     const Partition& part = idx.parts[t];
-    hp[t] = PartView{part.table.p, part.fp.p,    part.precs.p, part.table.n - 1,
+    hp[t] = PartView{part.table.p, part.fp.p, part.presence_bytes, part.precs.p, part.table.n - 1,
                      part.postings.p, part.n_records, part.first, t, seg_magic(t + 1)};
   }
   P.parts.reset(P.ctx, hp.size());

@@ -26,7 +26,8 @@ struct Hit {
 // One threshold's segment index, as seen by the kernels.
 struct PartView {
   const Slot* table;
-  const uint8_t* fp;  // slot fingerprints
+  const uint8_t* fp;  // slot fingerprints, then the presence bitmap
+  unsigned pb;        // presence bitmap bytes per slot
   const PostRec* precs;
   unsigned long long mask;
   const uint32_t* postings;
@@ -53,7 +54,8 @@ struct ProbeView {
   const uint32_t* iperm;  // sid -> reported id
   uint32_t n_index;
   const Slot* table;
-  const uint8_t* table_fp;  // slot fingerprints (NULL: probe the slots directly)
+  const uint8_t* table_fp;  // slot fingerprints, then the presence bitmap (NULL: probe the slots directly)
+  unsigned table_pb;        // presence bitmap bytes per slot
   const uint32_t* phash;    // probe-side prefix values from poff[q] + q (NULL: computed per window)
   unsigned long long mask;
   const uint32_t* postings;
@@ -89,6 +91,7 @@ __host__ __device__ __forceinline__ ProbeView view_for_tau(const ProbeView& v, i
   const PartView& pv = v.parts[tau];
   t.table = pv.table;
   t.table_fp = pv.fp;
+  t.table_pb = pv.pb;
   t.precs = pv.precs;
   t.mask = pv.mask;
   t.postings = pv.postings;
@@ -128,9 +131,10 @@ __host__ __device__ __forceinline__ bool group_window(const ProbeView& v, bool s
   return hi >= lo;
 }
 
-__host__ __device__ __forceinline__ int table_find_any(const Slot* t, const uint8_t* fp, unsigned long long mask,
-                                                       unsigned long long key, uint32_t& begin, uint32_t& count) {
-  return table_find(t, fp, mask, key, begin, count);
+__host__ __device__ __forceinline__ int table_find_any(const Slot* t, const uint8_t* fp, unsigned pb,
+                                                       unsigned long long mask, unsigned long long key,
+                                                       uint32_t& begin, uint32_t& count) {
+  return table_find(t, fp, pb, mask, key, begin, count);
 }
 
 // Lookup of the key of s[p, li] in L_l^i.  Returns the number of postings to
@@ -141,7 +145,7 @@ __host__ __device__ __forceinline__ uint32_t lookup_key(const ProbeView& v, bool
                                                         unsigned long long key, uint32_t& begin, int& err) {
   uint32_t cnt = 0;
   begin = 0;
-  const int found = table_find_any(v.table, v.table_fp, v.mask, key, begin, cnt);
+  const int found = table_find_any(v.table, v.table_fp, v.table_pb, v.mask, key, begin, cnt);
   if (found < 0) {
     err |= 2;
     return 0;

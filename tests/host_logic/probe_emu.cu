@@ -82,14 +82,15 @@ int main(int argc, char** argv) {
   }
   // fingerprint bytes and presence bitmap as the index build sets them
   // (none with PJ_EMU_NO_FP)
-  std::vector<uint8_t> fp(fp_array_bytes(cap), 0);
+  const unsigned pb = soff[n] > 256 * (ull)n ? 2 : 1;  // as the index build chooses
+  std::vector<uint8_t> fp(fp_array_bytes(cap, pb), 0);
   for (ull h = 0; h < cap; ++h)
     if (table[h].key) {
       const uint32_t mix = key_mix(table[h].key);
       fp[h] = key_fp(table[h].key, mix);
       ull word;
       uint32_t bits;
-      presence_of(mix, cap - 1, word, bits);
+      presence_of(mix, cap - 1, pb, word, bits);
       for (int k = 0; k < 4; ++k) fp[cap + 4 * word + k] |= (uint8_t)(bits >> (8 * k));
     }
   const bool use_fp = !getenv("PJ_EMU_NO_FP");
@@ -97,6 +98,7 @@ int main(int argc, char** argv) {
   for (uint32_t k = 0; k < n; ++k) ref[k] = ((ull)soff[k] << 16) | slen[k];
   ProbeView v{};
   v.table_fp = use_fp ? fp.data() : nullptr;
+  v.table_pb = pb;
   v.iref = use_fp ? ref.data() : nullptr;  // the no-fingerprint run also covers the unpacked reads
   v.ibytes = sb.data();
   v.ioff = soff.data();

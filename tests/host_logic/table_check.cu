@@ -62,21 +62,22 @@ int main() {
       t[h].count = (uint32_t)(key >> 40) + 1;
       keys.push_back(key);
     }
-    std::vector<uint8_t> fp(fp_array_bytes(cap), 0);  // fingerprints, then the presence bitmap
+    const unsigned pb = 1 + (trial / 4) % 2;  // 1 or 2 bitmap bytes per slot, every size and fill
+    std::vector<uint8_t> fp(fp_array_bytes(cap, pb), 0);  // fingerprints, then the presence bitmap
     for (ull h = 0; h < cap; ++h)
       if (t[h].key) {
         const uint32_t mix = key_mix(t[h].key);
         fp[h] = key_fp(t[h].key, mix);
         ull word;
         uint32_t bits;
-        presence_of(mix, mask, word, bits);
+        presence_of(mix, mask, pb, word, bits);
         for (int k = 0; k < 4; ++k) fp[cap + 4 * word + k] |= (uint8_t)(bits >> (8 * k));
       }
     auto check = [&](ull key) {
       uint32_t b0 = 0, c0 = 0, b1 = 0, c1 = 0, b2 = 0, c2 = 0;
       const int want = plain_find(t, mask, key, b0, c0);
-      const int got = table_find(t.data(), fp.data(), mask, key, b1, c1);
-      const int got_nofp = table_find(t.data(), nullptr, mask, key, b2, c2);
+      const int got = table_find(t.data(), fp.data(), pb, mask, key, b1, c1);
+      const int got_nofp = table_find(t.data(), nullptr, pb, mask, key, b2, c2);
       ++cases;
       if (got != want || got_nofp != want || (want == 1 && (b1 != b0 || c1 != c0 || b2 != b0 || c2 != c0))) ++bad;
     };
@@ -90,7 +91,7 @@ int main() {
       const ull h = mix & mask;
       ull word;
       uint32_t bits, have;
-      presence_of(mix, mask, word, bits);
+      presence_of(mix, mask, pb, word, bits);
       memcpy(&have, &fp[cap + 4 * word], 4);
       if ((t[h].key && fp[h] == key_fp(key, mix) && t[h].key != key) || (have & bits) == bits) check(key);
     }
