@@ -417,7 +417,13 @@ def pj_kernel_launches() -> int:
 
 def pj_build_index(strings, tau_max: int, stream=None, results_on_device: bool = False,
                    lazy_partitions: bool = False, autotune: bool = False, graph_joins: bool = False) -> Index:
-    """pj_build_index: resident segment index for thresholds 0..tau_max."""
+    """pj_build_index: resident segment index for thresholds 0..tau_max.
+
+    results_on_device: results stay in device memory (DeviceResult).
+    lazy_partitions: a threshold's segment index is built on its first use.
+    autotune: each threshold's self join picks its verification form by timing.
+    graph_joins: after a threshold's first self join, later self joins of it
+    replay that join recorded as one CUDA graph (pj_options.graph_joins)."""
     opt = make_options(stream, results_on_device, lazy_partitions=lazy_partitions, autotune=autotune,
                        graph_joins=graph_joins)
     S = Strings(strings)
