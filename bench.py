@@ -7,9 +7,12 @@ the `short` workload: 1,000,000 strings over 27 symbols with Zipf(1.1)
 characters, lengths N(15, 4) clipped to [5, 40], 30% in near-duplicate
 clusters, at tau = 4.
 
-Metric: verified candidate pairs per second (candidates = (probe, indexed
-string, segment, position) matches that extension verification examines),
-with the self-join time per step beside it.
+Metric: verified similar pairs per second -- the pairs the self join reports
+(every pair with ED <= tau, its ED verified exactly) over the step time --
+with the self-join time per step beside it.  The work counts are reported
+separately: Alg. 1 candidate tuples (probe, indexed string, segment,
+position) per second, and the candidates that reach a DP (those the
+character-count screen keeps) per second.
 
 `value` times the step with the strings already in HBM and the result left
 in device memory; `e2e` times the same step through the C ABI with host
@@ -42,11 +45,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-METRIC = "self-join verified candidate pairs/s"
+METRIC = "self-join verified similar pairs/s"
 UNIT = "pairs/s"
 L2_FLUSH_BYTES = 256 << 20
-INT_LANES_PER_SM = 128      # 32-bit integer lanes per SM (4 sub-partitions x 32)
-OPS_PER_CELL = 8            # integer ops of one DP cell: delta compare, diagonal add, up/left +1, mins
+OPS_PER_CELL = 6            # integer ops of one DP cell: delta compare, diagonal add, up/left +1, two mins
+SCREEN_BYTES = 16           # one posting record (sid + character signature) read per candidate
 
 
 def parse():
@@ -158,8 +161,12 @@ def dist_env():
 
 def cpu_baseline(strings, tau, target_s, seed=123):
     """The oracle (length filter + full Wagner-Fischer DP on every pair) on a
-    bounded sample: every string of the set against Q sampled probe strings.
-    Rate = DP-verified pairs per second; also the extrapolated self-join time."""
+    bounded sample: every string of the set against Q sampled probe strings
+    (each probe's own entry excluded).  Rate = similar pairs found per second:
+    over a uniform sample of probes this equals the whole self join's pairs
+    over its time (each pair has two ends, and the sample does the
+    corresponding share of the join's pair comparisons); also the DP-verified
+    pairs per second and the extrapolated self-join time."""
     import oracle
     from paper_1111_7171_gb300 import synth
     buf, off = synth.pack(strings)
@@ -182,18 +189,20 @@ def cpu_baseline(strings, tau, target_s, seed=123):
         idx = rng.choice(n, size=q, replace=False)
         qb, qo = synth.pack([strings[k] for k in idx.tolist()])
         t0 = time.perf_counter()
-        oracle.similar_to(qb, qo, buf, off, tau, banded=False)
+        found = oracle.similar_to(qb, qo, buf, off, tau, banded=False, exclude=idx)
         dt = time.perf_counter() - t0
         if dt >= target_s * 0.5 or q >= n:
             break
         q = min(n, int(q * max(2.0, min(16.0, target_s / max(dt, 1e-3)))))
-    pairs = pairs_for(idx)
+    pairs = pairs_for(idx) - q  # each probe's comparison with itself is excluded
     full_pairs = int(sum(int(cum[min(int(L) + tau + 1, len(cum) - 1)] - cum[max(0, int(L) - tau)]) for L in lens)) // 2
-    rate = pairs / dt
-    return {"value": rate, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{q} probe strings x all {n} strings (length filter, then full DP on {pairs} pairs) "
-                      f"in {dt:.1f} s; self join extrapolated to {full_pairs / rate:.0f} s",
-            "seconds": dt, "pairs": pairs, "self_join_s_extrapolated": full_pairs / rate}
+    dp_rate = pairs / dt
+    return {"value": len(found) / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{q} probe strings x all {n} strings (length filter, then full DP on {pairs} pairs, "
+                      f"{len(found)} similar pairs found) in {dt:.1f} s; {dp_rate:.3g} DP-verified pairs/s; "
+                      f"self join extrapolated to {full_pairs / dp_rate:.0f} s",
+            "seconds": dt, "pairs": pairs, "found": len(found), "dp_pairs_per_s": dp_rate,
+            "self_join_s_extrapolated": full_pairs / dp_rate}
 
 
 # --------------------------------------------------------------- serving --
@@ -362,8 +371,7 @@ def run_reference(args):
             per_step.append(res)
             base = res
     secs = sum(r["seconds"] for r in per_step)
-    pairs = sum(r["pairs"] for r in per_step)
-    value = pairs / secs
+    value = sum(r["found"] for r in per_step) / secs
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
@@ -429,6 +437,12 @@ def run_native(args):
     for _ in range(args.warmup):
         device_step()
     barrier()
+    cal = pj.pj_calibrate()  # the rooflines' ceilings, measured on this GPU (outside the timed region)
+    sel_idx = pj.pj_build_index((d_bytes, d_off), args.tau, lazy_partitions=True)
+    selection = dict(pj.pj_count_selection(sel_idx, args.tau),
+                     note="substrings each selection method of Sec. 4 would look up in this self join")
+    sel_idx.free()
+    barrier()
 
     # ---- timed device-resident steps
     clocks = ClockSampler(local)
@@ -491,24 +505,42 @@ def run_native(args):
             resident["graph_replays"] = replayed
     barrier()
 
-    cand = sum(s["candidates"] for s in stats_all)
-    cand_all, total_s, e2e_s = reduce_over_ranks(cand, sum(step_ms) / 1e3, sum(e2e_ms) / 1e3, world, dev)
+    found = sum(int(c) for c in counts)
+    found_all, total_s, e2e_s = reduce_over_ranks(found, sum(step_ms) / 1e3, sum(e2e_ms) / 1e3, world, dev)
 
     if rank == 0:
         st = stats_all[-1]
         peaks, peak_src = measured_peaks()
-        sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-        sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-        alu_peak_gcells = sm_count * INT_LANES_PER_SM * sm_mhz * 1e6 / OPS_PER_CELL / 1e9
         verify_ms = statistics.mean(s["verify_ms"] for s in stats_all)
         probe_ms = statistics.mean(s["probe_ms"] for s in stats_all)
         cells = statistics.mean(s["dp_cells"] for s in stats_all)
+        cands = statistics.mean(s["candidates"] for s in stats_all)
+        pair_mode = st["verify_mode"] == 2
+        # candidates that reach a DP: those the character-count screen keeps
+        # (mode L: the distinct pairs it keeps)
+        dp_verified = (st["distinct_pairs"] if pair_mode else st["candidates"]) - st["filtered"]
+        kernel = ("k_verify_pairs_warp" if st["pair_warp"] else "k_verify_pairs") if pair_mode else "k_verify_queued"
+        alu_peak_gcells = cal["dp_cells_per_s"] / 1e9
+        sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+        derived_gcells = cal["sm_count"] * 128 * sm_max * 1e6 / OPS_PER_CELL / 1e9
         achieved = cells / (verify_ms / 1e3) / 1e9
-        kernel = "k_verify_pairs" if st["verify_mode"] == 2 else "k_verify_queued"
         roofline = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": alu_peak_gcells,
                     "unit": "Gcell/s", "frac": achieved / alu_peak_gcells, "traffic": None,
-                    "peak_source": f"{sm_count} SMs x {INT_LANES_PER_SM} int32 lanes x {sm_mhz:.0f} MHz "
-                                   f"({peak_src} SM clock) / {OPS_PER_CELL} ops per DP cell"}
+                    "work": "DP cells evaluated by the verification (counted exactly), per second of verification",
+                    "peak_source": f"measured (pj_calibrate): the verification's banded cell recurrence with "
+                                   f"operands in registers, {alu_peak_gcells:.0f} Gcell/s at {cal['sm_mhz']:.0f} MHz "
+                                   f"on {cal['sm_count']} SMs (unit count x clock: {cal['sm_count']} SMs x 128 "
+                                   f"int32 lanes x {sm_max:.0f} MHz / {OPS_PER_CELL} ops per cell = "
+                                   f"{derived_gcells:.0f} Gcell/s; measured int32 rate "
+                                   f"{cal['int32_ops_per_s'] / 1e12:.1f} Tops/s)"}
+        screen_bytes = (st["distinct_pairs"] if pair_mode else cands) * SCREEN_BYTES
+        screen_gbs = screen_bytes / (verify_ms / 1e3) / 1e9
+        roofline_screen = {"bound": "l2", "kernel": kernel, "achieved": screen_gbs,
+                           "peak": cal["l2_read_bytes_per_s"] / 1e9, "unit": "GB/s",
+                           "frac": screen_gbs / (cal["l2_read_bytes_per_s"] / 1e9),
+                           "work": f"{SCREEN_BYTES} B posting record per candidate screened, per second of "
+                                   "verification",
+                           "peak_source": "measured (pj_calibrate): 16-byte loads over a 64 MiB L2-resident buffer"}
         serving = None
         if not args.no_serve and args.workload == "short":
             serving = serving_bench(strings, args.serve_requests)
@@ -518,12 +550,15 @@ def run_native(args):
             cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
         ms_per_step = 1e3 * total_s / args.steps
         line = {
-            "metric": METRIC, "value": cand_all / total_s, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "metric": METRIC, "value": found_all / total_s, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": workload_config(args, n),
             "self_join_ms": ms_per_step,
             "pairs": int(counts[-1]),
+            "alg1_tuples_per_s": cands / (ms_per_step / 1e3),
+            "dp_verified_per_s": dp_verified / (ms_per_step / 1e3),
+            "selection": selection,
             "work": {"candidates": int(st["candidates"]), "lookups": int(st["lookups"]), "hits": int(st["hits"]),
                      "accepted": int(st["accepted"]), "dp_cells": int(st["dp_cells"])},
             "phase_ms": {"store_build": statistics.mean(build_ms),
@@ -536,8 +571,10 @@ def run_native(args):
                        "verify_block": int(st["verify_block"]), "warp_per_candidate_from_length": int(st["warp_min_len"]),
                        "note": "autotuned in the warm-up steps (cached per workload signature)"},
             "roofline": roofline,
+            "roofline_screen": roofline_screen,
+            "calibration": cal,
             "cpu_baseline": cpu,
-            "e2e": {"value": cand_all / e2e_s, "unit": UNIT, "ms_per_step": 1e3 * e2e_s / args.steps,
+            "e2e": {"value": found_all / e2e_s, "unit": UNIT, "ms_per_step": 1e3 * e2e_s / args.steps,
                     "h2d_bytes_per_step": int(buf.nbytes + off.nbytes),
                     "d2h_bytes_per_step": int(e2e_pairs * 12)},
             "resident_join": dict(resident, note="join alone on a resident index, mean over the timed steps; "

@@ -111,6 +111,10 @@ typedef struct {
   int32_t graph_replay; /* 1: the self join ran as a replay of its recorded CUDA graph
                            (pj_options.graph_joins); the phase times are then 0 */
   float graph_ms;       /* device time of that replay */
+  uint64_t device_peak; /* with pj_options.device_budget set: the most device bytes held at once
+                           through the budgeted allocator (over the index's life so far, or over
+                           the call for pj_join and pj_self_join_stream); 0 without a budget */
+  uint32_t windows;     /* pj_self_join_stream: length windows joined; 0 for other calls */
 } pj_stats;
 
 typedef struct {
@@ -141,8 +145,7 @@ typedef struct {
                              warp-per-candidate cut-over at each length-bucket edge and block
                              sizes 128/256/512, and PJ_VERIFY_PAIRS with a thread or a warp
                              per pair -- and keeps the fastest (cached per workload signature
-                             for the process, and in the file named by the environment
-                             variable PJ_AUTOTUNE_CACHE) */
+                             for the process, and in the file autotune_cache names) */
   int graph_joins;        /* 1: after the first self join of a threshold, its whole pipeline is
                              recorded into a CUDA graph sized from that join's counts, and
                              later self joins of the threshold replay it (one graph launch;
@@ -153,6 +156,16 @@ typedef struct {
                              2^28; the graph probes all groups in one pass).  A recorded join
                              keeps its device buffers (about the eager join's peak scratch;
                              ~10 GB for 1M short strings at tau = 4) until pj_index_free. */
+  uint64_t device_budget; /* 0 = no limit.  Most device memory held at once through this
+                             index's allocator (pj_build_index: its store, every threshold's
+                             segment index, the scratch of every join, device results) or
+                             through one pj_join / pj_self_join_stream call's.  An allocation
+                             that would pass it fails the call with PJ_ENOMEM (nothing is
+                             allocated); pj_self_join_stream instead narrows its length windows
+                             until each window fits. */
+  const char* autotune_cache; /* file that keeps autotuning decisions across processes (read,
+                                 then appended; copied at pj_build_index).  NULL = the file
+                                 named by the environment variable PJ_AUTOTUNE_CACHE, if any */
 } pj_options;
 
 typedef struct pj_index pj_index; /* opaque, library-owned */
@@ -186,6 +199,47 @@ int pj_build_index(const pj_strings* S, int tau_max, const pj_options* opt, pj_i
  * Errors: PJ_EINVAL (NULL, tau out of range), PJ_ENOMEM, PJ_ECUDA.
  */
 int pj_self_join(pj_index* idx, int tau, pj_result* out);
+
+/*
+ * pj_self_join_shard -- one of n_shards disjoint parts of pj_self_join: the
+ * pairs whose later string, in the visiting order of Alg. 1 (by length, then
+ * id), is among the shard's probing strings -- the partitioned strings
+ * (length >= tau + 1) split into n_shards equal consecutive ranges of that
+ * order.  Shard 0 also holds every pair with a string too short to partition
+ * (length <= tau).  Each pair is found by exactly one probe (the later
+ * string probes the earlier, Alg. 1), so the shards' results are disjoint
+ * and their union is exactly pj_self_join's result; each shard's pairs are
+ * sorted by (a, b).  Shards of one index can run one after another or on
+ * several GPUs, each with its own copy of the index.
+ *   shard : 0..n_shards-1.  Other arguments and errors as pj_self_join
+ *   (PJ_EINVAL also for n_shards = 0 or shard >= n_shards).
+ */
+int pj_self_join_shard(pj_index* idx, int tau, uint32_t shard, uint32_t n_shards, pj_result* out);
+
+/*
+ * pj_self_join_stream -- Def. 1 with R = S for a set that is never held on
+ * the device as a whole.  When strings are visited by length (Alg. 1), a
+ * string of length |s| probes only the inverted lists of lengths |s| - tau
+ * .. |s| (Sec. 3.2).  So the strings, ordered by (length, id) on the host,
+ * are cut into windows of consecutive probing strings; a window's device set
+ * is its probing strings plus the strings before them whose length is at
+ * least its first probe's length - tau.  Each window builds a temporary store
+ * and segment index of its device set and self-joins it with only its own
+ * strings probing; the host maps the pairs back to input ids and merges the
+ * windows' results.  The result equals pj_self_join's exactly.
+ *   S   : HOST strings (on_device = 0).  tau : 0..PJ_TAU_LIMIT.
+ *   opt : stream, allocator, verify_mode, autotune; device_budget bounds the
+ *         device memory of the call (0 = three quarters of the free device
+ *         memory): windows are sized from an estimate of their bytes and a
+ *         window that still exceeds the budget is split in two and retried.
+ *         Results are always in host memory (results_on_device is ignored).
+ *   out : pairs a < b sorted by (a, b); stats summed over the windows, with
+ *         stats.windows and stats.device_peak.
+ * Errors: PJ_EINVAL (NULL, device strings, tau out of range, bad offsets),
+ * PJ_ENOMEM (a window of one probing string does not fit the budget, or a
+ * host allocation failed), PJ_ECUDA.
+ */
+int pj_self_join_stream(const pj_strings* S, int tau, const pj_options* opt, pj_result* out);
 
 /*
  * pj_join -- Def. 1 for two sets (Sec. 3.2: index S, probe every r of R over
@@ -351,9 +405,11 @@ void pj_server_stop(pj_server* srv);
  *               buffer is too small, so the caller can retry).
  * All temporaries live in one device array of PJ_NOALLOC_SCRATCH_BYTES bytes
  * inside the library; every GPU that loads the library holds it until the
- * process exits.  The first call on a device looks up that array's device
- * address (cudaGetSymbolAddress); make that first call before any stream
- * capture.  Every call shares the array and leaves its contents behind;
+ * process exits.  Every call looks up that array's device address on the
+ * current device (cudaGetSymbolAddress, which allocates nothing); the first
+ * call on a device also loads the library's kernels there, so make that
+ * first call before any stream capture.  Every call shares the array and
+ * leaves its contents behind;
  * calls are serialised on the host, but calls whose GPU work overlaps (other
  * processes, or work still running on another stream) race on it.
  * Errors: PJ_EINVAL (NULL, tau out of range, host batch, batch too large,
@@ -364,6 +420,63 @@ void pj_server_stop(pj_server* srv);
 #define PJ_NOALLOC_MAX_QUERIES 65536
 int pj_query_noalloc(pj_index* idx, const pj_strings* batch, int tau, pj_pair* out_pairs, uint64_t out_cap,
                      uint64_t* out_count);
+
+/*
+ * pj_count_selection -- the substring-selection ablation of Sec. 4 for the
+ * self join of the indexed set at threshold tau (the counts the paper plots
+ * for its selection methods).  For every probing string s, every length l
+ * in [max(tau + 1, |s| - tau), |s|] such that some string of length l is
+ * visited before s (Alg. 1's visiting order by length, then id), and every
+ * segment i of the even partition of l (Sec. 3.1), it sums the number of
+ * start positions p (substrings s[p, l_i] that exist in s) each method
+ * selects:
+ *   length_based   : every substring of length l_i (Sec. 4);
+ *   shift_based    : p in [P_i - tau, P_i + tau] (Sec. 4);
+ *   position_aware : p in [P_i - floor((tau - D)/2), P_i + floor((tau + D)/2)],
+ *                    D = |s| - l (Sec. 4.1);
+ *   multi_match    : the multi-match-aware window of Sec. 4.2 (Lemma 2),
+ *                    which is what pj_self_join looks up;
+ *   groups         : the (s, l, i) combinations counted.
+ * Counts only: nothing is looked up.  Needs no segment index (a lazy index
+ * is fine).  Errors: PJ_EINVAL (NULL, tau outside 0..tau_max), PJ_ECUDA.
+ */
+typedef struct {
+  uint64_t length_based;
+  uint64_t shift_based;
+  uint64_t position_aware;
+  uint64_t multi_match;
+  uint64_t groups;
+} pj_selection;
+int pj_count_selection(pj_index* idx, int tau, pj_selection* out);
+
+/*
+ * pj_calibrate -- measures, on the current device, the ceilings that the
+ * join's rooflines are reported against (the paper has no counterpart; it is
+ * a measurement aid).  Kernels run 8 blocks of 256 threads per SM:
+ *   dp_cells_per_s      : cells of the banded VERIFYSTRINGPAIR recurrence
+ *                         (Sec. 5.1; the verification kernels' cell code, a
+ *                         band of 5 diagonals, Lemma 4 test per row) with both
+ *                         strings in registers;
+ *   int32_ops_per_s     : 32-bit integer operations (independent xor + add
+ *                         chains of register operands);
+ *   l2_read_bytes_per_s : read bandwidth of a 64 MiB buffer held in the L2
+ *                         with 16-byte loads;
+ *   sm_mhz              : SM clock during the DP run (clock64 against the
+ *                         global nanosecond timer);
+ *   sm_count            : multiprocessors.
+ * Each figure is the best of three launches on a stream of its own; the call
+ * takes well under a second and allocates 64 MiB of device memory
+ * (cudaMallocAsync) for its duration.  Errors: PJ_EINVAL (NULL), PJ_ENOMEM,
+ * PJ_ECUDA.
+ */
+typedef struct {
+  double dp_cells_per_s;
+  double int32_ops_per_s;
+  double l2_read_bytes_per_s;
+  double sm_mhz;
+  int32_t sm_count;
+} pj_calibration;
+int pj_calibrate(pj_calibration* out);
 
 /* Number of strings / largest tau of an index (0 for NULL). */
 uint32_t pj_index_size(const pj_index* idx);

@@ -82,8 +82,6 @@ def lib():
                                             ctypes.c_int32, ctypes.c_int, i64p, pp, ctypes.c_int64,
                                             ctypes.c_int]
             L.oracle_similar_to.restype = ctypes.c_int64
-            L.oracle_count_length_filtered.argtypes = [u64p, ctypes.c_int64, ctypes.c_int32]
-            L.oracle_count_length_filtered.restype = ctypes.c_int64
             L.oracle_num_threads.argtypes = []
             L.oracle_num_threads.restype = ctypes.c_int
             _lib = L
@@ -174,11 +172,6 @@ def similar_to(qbytes, qoff, sbytes, soff, tau: int, banded: bool = True, exclud
         ex, exp = None, None
     return _run_with_retry(lambda out, cap: lib().oracle_similar_to(
         qbp, qop, len(qo) - 1, sbp, sop, len(so) - 1, tau, int(banded), exp, out, cap, nthreads))
-
-
-def count_length_filtered(offsets, tau: int) -> int:
-    o, op = _u64(offsets)
-    return int(lib().oracle_count_length_filtered(op, len(o) - 1, tau))
 
 
 def num_threads() -> int:

@@ -295,6 +295,31 @@ def pass_join_self(strings: list[bytes], tau: int, order: str = "alphabetical",
     return best
 
 
+def selection_counts(strings: list[bytes], tau: int) -> dict:
+    """Substrings each selection method of Sec. 4 selects over Alg. 1's self
+    join (visiting by length, then input id): for every probing string s,
+    every l in [max(tau + 1, |s| - tau), |s|] whose inverted lists are
+    non-empty when s probes them (some string of length l visited before s),
+    and every segment i, the number of existing substrings s[p, l_i] in the
+    method's window (``select_windows`` with clipping).  Returns the totals per
+    method ("length", "shift", "position", "multi") and "groups", the number
+    of (s, l, i) combinations counted."""
+    visit = sorted(range(len(strings)), key=lambda k: (len(strings[k]), k))
+    counts = {"length": 0, "shift": 0, "position": 0, "multi": 0, "groups": 0}
+    indexed_lengths: set[int] = set()
+    for sid in visit:
+        ls = len(strings[sid])
+        for l in range(max(tau + 1, ls - tau), ls + 1):
+            if l not in indexed_lengths:
+                continue
+            counts["groups"] += tau + 1
+            for m in ("length", "shift", "position", "multi"):
+                counts[m] += sum(max(0, hi - lo + 1) for _, lo, hi, _ in select_windows(ls, l, tau, m, clip=True))
+        if ls >= tau + 1:
+            indexed_lengths.add(ls)
+    return counts
+
+
 def pass_join_rs(R: list[bytes], S: list[bytes], tau: int, stats: dict | None = None):
     """R != S join (Sec. 3.2): index S, probe each r in R against the lengths
     [|r| - tau, |r| + tau] with the Sec. 4.2 windows at signed D = |r| - l.

@@ -250,24 +250,6 @@ int64_t oracle_join(const uint8_t* rbytes, const uint64_t* roff, int64_t nr,
   return join_driver(rbytes, roff, nr, sbytes, soff, ns, 0, tau, banded, out, cap, nthreads);
 }
 
-/* Number of (x, y) pairs that survive the length filter (self: x < y);
- * the brute force runs one DP per such pair. */
-int64_t oracle_count_length_filtered(const uint64_t* off, int64_t n, int32_t tau) {
-  int64_t total = 0;
-#ifdef _OPENMP
-#pragma omp parallel for schedule(dynamic, 64) reduction(+ : total)
-#endif
-  for (int64_t x = 0; x < n; ++x) {
-    int64_t lx = (int64_t)(off[x + 1] - off[x]);
-    for (int64_t y = x + 1; y < n; ++y) {
-      int64_t ly = (int64_t)(off[y + 1] - off[y]);
-      int64_t dl = lx > ly ? lx - ly : ly - lx;
-      if (dl <= tau) total++;
-    }
-  }
-  return total;
-}
-
 int oracle_num_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();

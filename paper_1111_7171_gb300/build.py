@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB_DIR = os.path.join(HERE, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "libpassjoin.so")
-SOURCES = ["pj_prims.cu", "pj_index.cu", "pj_join.cu", "pj_noalloc.cu", "pj_serve.cu", "pj_plan.cu"]
+SOURCES = ["pj_prims.cu", "pj_index.cu", "pj_join.cu", "pj_noalloc.cu", "pj_serve.cu", "pj_plan.cu",
+           "pj_stream.cu", "pj_calib.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr"]

@@ -6,7 +6,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <memory>
+#include <mutex>
 #include <string>
+#include <unordered_map>
 #include <utility>
 
 #include "passjoin.h"
@@ -38,12 +41,24 @@ void count_launches(unsigned long long k);
 
 // -------------------------------------------------------------- allocator --
 
+// A device-memory budget (pj_options.device_budget): the bytes held at once
+// through every context that shares it, the most ever held, and the limit
+// past which an allocation fails with PJ_ENOMEM instead of being made.
+struct Budget {
+  std::mutex mu;
+  size_t limit = 0;
+  size_t cur = 0;
+  size_t peak = 0;
+  std::unordered_map<void*, size_t> live;
+};
+
 // Device memory and the stream every piece of work of one call is ordered on.
 struct Ctx {
   cudaStream_t stream = nullptr;
   pj_alloc_fn alloc = nullptr;
   pj_free_fn free_fn = nullptr;
   void* alloc_ctx = nullptr;
+  std::shared_ptr<Budget> budget;  // NULL: no limit, nothing counted
 
   void* get(size_t bytes) const;
   void put(void* p) const;
@@ -131,6 +146,13 @@ struct DBuf {
 // ------------------------------------------------------------ small utils --
 
 inline unsigned ceil_div(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
+
+// Streaming multiprocessors of the current device (looked up once per
+// device), and the grid cap of a grid-stride kernel that keeps `per_sm`
+// blocks on every SM.
+int sm_count();
+inline unsigned sm_grid_cap(unsigned per_sm) { return (unsigned)sm_count() * per_sm; }
+
 inline int bits_for(uint64_t v) {  // bits needed to hold values < v (at least 1)
   int b = 1;
   while (b < 64 && (uint64_t(1) << b) < v) ++b;

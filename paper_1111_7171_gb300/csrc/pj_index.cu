@@ -36,6 +36,24 @@ static thread_local bool g_recording = false;
 void count_launch() {
   if (!g_recording) g_launches.fetch_add(1, std::memory_order_relaxed);
 }
+int sm_count() {
+  constexpr int MAX_DEVICES = 64;
+  static std::atomic<int> cached[MAX_DEVICES];  // 0 = not looked up yet
+  int dev = 0;
+  PJ_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= MAX_DEVICES) {
+    int sms = 0;
+    PJ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    return sms;
+  }
+  int sms = cached[dev].load(std::memory_order_relaxed);
+  if (!sms) {
+    PJ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    cached[dev].store(sms, std::memory_order_relaxed);
+  }
+  return sms;
+}
+
 void count_launches(unsigned long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 void set_recording(bool on) { g_recording = on; }
 
@@ -49,6 +67,24 @@ void check_cuda(cudaError_t e, const char* what, const char* file, int line) {
 
 void* Ctx::get(size_t bytes) const {
   void* p = nullptr;
+  if (budget) {  // reserve first, so that concurrent callers cannot pass the limit together
+    std::lock_guard<std::mutex> g(budget->mu);
+    if (budget->cur + bytes > budget->limit)
+      fail(PJ_ENOMEM, "device budget of " + std::to_string(budget->limit) + " bytes exceeded: " +
+                          std::to_string(budget->cur) + " held, " + std::to_string(bytes) + " more asked");
+    budget->cur += bytes;
+    budget->peak = std::max(budget->peak, budget->cur);
+  }
+  struct Unreserve {  // gives the reservation back if the allocation fails
+    const Ctx* c;
+    size_t n;
+    bool keep = false;
+    ~Unreserve() {
+      if (keep || !c->budget) return;
+      std::lock_guard<std::mutex> g(c->budget->mu);
+      c->budget->cur -= n;
+    }
+  } unreserve{this, bytes};
   if (alloc) {
     p = alloc(alloc_ctx, bytes, (void*)stream);
     if (!p) fail(PJ_ENOMEM, "device allocator returned NULL for " + std::to_string(bytes) + " bytes");
@@ -59,11 +95,24 @@ void* Ctx::get(size_t bytes) const {
       fail(PJ_ENOMEM, "cudaMallocAsync of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
     }
   }
+  if (budget) {
+    std::lock_guard<std::mutex> g(budget->mu);
+    budget->live[p] = bytes;
+  }
+  unreserve.keep = true;
   return p;
 }
 
 void Ctx::put(void* p) const {
   if (!p) return;
+  if (budget) {
+    std::lock_guard<std::mutex> g(budget->mu);
+    auto it = budget->live.find(p);
+    if (it != budget->live.end()) {
+      budget->cur -= it->second;
+      budget->live.erase(it);
+    }
+  }
   if (alloc) {
     free_fn(alloc_ctx, p, (void*)stream);
   } else {
@@ -79,6 +128,10 @@ Ctx make_ctx(const pj_options* opt) {
     c.free_fn = opt->free;
     c.alloc_ctx = opt->alloc_ctx;
     if ((c.alloc == nullptr) != (c.free_fn == nullptr)) fail(PJ_EINVAL, "pj_options: alloc and free must be set together");
+    if (opt->device_budget) {
+      c.budget = std::make_shared<Budget>();
+      c.budget->limit = (size_t)opt->device_budget;
+    }
   }
   return c;
 }
@@ -361,26 +414,26 @@ void build_store(pj_index& idx, const pj_strings& S) {
 
   idx.sbytes.reset(c, total ? total : 1);
   if (n) {
-    const unsigned blocks = std::min<unsigned>(ceil_div((size_t)n * 32, 256), 152u * 16u);
+    const unsigned blocks = std::min<unsigned>(ceil_div((size_t)n * 32, 256), sm_grid_cap(16));
     k_gather<<<blocks, 256, 0, c.stream>>>(in_bytes, in_off, idx.perm.p, idx.soff.p, idx.sbytes.p, n);
     PJ_LAUNCHED("k_gather");
   }
   idx.sbm.reset(c, n ? n : 1);
   if (n) {
-    k_signatures<<<std::min<unsigned>(ceil_div(n, 256), 152u * 8u), 256, 0, c.stream>>>(idx.sbytes.p, idx.soff.p, n,
+    k_signatures<<<std::min<unsigned>(ceil_div(n, 256), sm_grid_cap(8)), 256, 0, c.stream>>>(idx.sbytes.p, idx.soff.p, n,
                                                                                     idx.sbm.p);
     PJ_LAUNCHED("k_signatures");
   }
   if (total >> 48) fail(PJ_EINVAL, "pj_strings: more than 2^48 bytes");
   idx.sref.reset(c, n ? n : 1);
   if (n) {
-    k_refs<<<std::min<unsigned>(ceil_div(n, 256), 152u * 8u), 256, 0, c.stream>>>(idx.soff.p, idx.slen.p, n,
+    k_refs<<<std::min<unsigned>(ceil_div(n, 256), sm_grid_cap(8)), 256, 0, c.stream>>>(idx.soff.p, idx.slen.p, n,
                                                                                 idx.sref.p);
     PJ_LAUNCHED("k_refs");
   }
   idx.sph.reset(c, (size_t)total + n + 1);
   if (n) {
-    const unsigned blocks = std::min<unsigned>(ceil_div((size_t)n * 32, 256), 152u * 16u);
+    const unsigned blocks = std::min<unsigned>(ceil_div((size_t)n * 32, 256), sm_grid_cap(16));
     k_prefix_values<<<blocks, 256, 0, c.stream>>>(idx.sbytes.p, idx.soff.p, n, idx.sph.p);
     PJ_LAUNCHED("k_prefix_values");
   }
@@ -485,7 +538,7 @@ void build_partition(pj_index& idx, int tau, Partition& part) {
   c.sync();
   if (h_err) fail(PJ_ECUDA, "segment table insertion failed");
   part.precs.reset(c, nrec);
-  k_post_records<<<std::min<unsigned>(ceil_div(nrec, 256), 152u * 16u), 256, 0, c.stream>>>(
+  k_post_records<<<std::min<unsigned>(ceil_div(nrec, 256), sm_grid_cap(16)), 256, 0, c.stream>>>(
       part.postings.p, nrec, idx.sbm.p, part.precs.p);
   PJ_LAUNCHED("k_post_records");
   trace_mark(c, "partition: table");
@@ -590,7 +643,7 @@ void upload_probe_set(const Ctx& c, const pj_strings& R, ProbeSet& out) {
   out.lmax = (int)h_lmax;
   out.bm.reset(c, R.n ? R.n : 1);
   if (R.n) {
-    k_signatures<<<std::min<unsigned>(ceil_div(R.n, 256), 152u * 8u), 256, 0, c.stream>>>(dbytes, doff, R.n, out.bm.p);
+    k_signatures<<<std::min<unsigned>(ceil_div(R.n, 256), sm_grid_cap(8)), 256, 0, c.stream>>>(dbytes, doff, R.n, out.bm.p);
     PJ_LAUNCHED("k_signatures");
   }
   out.bytes = dbytes;
@@ -631,6 +684,7 @@ int pj_build_index(const pj_strings* S, int tau_max, const pj_options* opt, pj_i
     idx->results_on_device = opt ? opt->results_on_device != 0 : false;
     idx->lazy = opt ? opt->lazy_partitions != 0 : false;
     idx->autotune = opt ? opt->autotune != 0 : false;
+    if (opt && opt->autotune_cache) idx->autotune_cache = opt->autotune_cache;
     idx->verify_mode = opt ? opt->verify_mode : PJ_VERIFY_AUTO;
     idx->graph_joins = opt ? opt->graph_joins != 0 : false;
     PJ_CUDA(cudaGetDevice(&idx->device));

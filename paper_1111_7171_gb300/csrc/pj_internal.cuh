@@ -348,6 +348,7 @@ struct pj_index {
   bool results_on_device = false;
   bool lazy = false;         // thresholds are built on first use
   bool autotune = false;     // tune the verification of each threshold's self join
+  std::string autotune_cache;  // file of tuning decisions (empty: PJ_AUTOTUNE_CACHE)
   int verify_mode = PJ_VERIFY_AUTO;
   bool graph_joins = false;  // self joins replay a recorded graph (see pj_options.graph_joins)
   // recorded self joins by threshold (type-erased: the plan type lives with
@@ -400,5 +401,13 @@ void query_multi_impl(const Ctx& c, pj_index& idx, const ProbeSet& R, const uint
                       bool on_device);
 
 void set_last_error(const std::string& msg);
+
+// Self join of idx over the probes with sids in [q_lo, q_hi): the pairs whose
+// later string (sid order) lies in that range; `fallback` adds the pairs
+// with a string too short to partition (all of them, whatever the range).
+void self_join_range(pj_index& idx, int tau, uint32_t q_lo, uint32_t q_hi, bool fallback, pj_result* out,
+                     bool on_device);
+// Makes *out a host result over `pairs` (malloc'd; pj_result_free frees it).
+void host_result(pj_result* out, pj_pair* pairs, uint64_t count);
 
 }  // namespace pj

@@ -278,6 +278,36 @@ __global__ void k_hit_counts(const Hit* __restrict__ hits, unsigned long long n,
     cnt[k] = hits[k].count;
 }
 
+// ------------------------------------------------- selection ablation -----
+//
+// For every group (probing string, indexed length, segment) of the self
+// join whose lists are non-empty, the number of substrings each selection
+// method of Sec. 4 would look up: length-based, shift-based, position-aware
+// (Sec. 4.1) and multi-match-aware (Sec. 4.2, what the join looks up).
+struct SelCounts {
+  unsigned long long w[4];
+  unsigned long long groups;
+};
+
+__global__ void __launch_bounds__(BLOCK) k_selection_counts(const ProbeView v, unsigned long long n_groups,
+                                                            SelCounts* out) {
+  const unsigned long long G = (unsigned long long)groups_per_probe(v.tau, true);
+  unsigned long long c[4] = {0, 0, 0, 0}, groups = 0;
+  for (unsigned long long t = (unsigned long long)blockIdx.x * BLOCK + threadIdx.x; t < n_groups;
+       t += (unsigned long long)gridDim.x * BLOCK) {
+    const uint32_t q = v.pbegin + (uint32_t)(t / G);
+    int w[4];
+    if (group_selection_sizes(v, true, q, (int)v.plen[q], (int)(t % G), w)) {
+      ++groups;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) c[m] += (unsigned long long)w[m];
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < 4; ++m) add_counter(&out->w[m], c[m]);
+  add_counter(&out->groups, groups);
+}
+
 // ---------------------------------------------------------------- A6 ------
 
 constexpr int V_RUN = 8;  // candidates per lane per step
@@ -752,20 +782,10 @@ __global__ void k_emit_pairs(const unsigned long long* __restrict__ keys, const 
 
 // ------------------------------------------------------------- launch -----
 
-static int sm_count() {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    PJ_CUDA(cudaGetDevice(&dev));
-    PJ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  }
-  return sms;
-}
-
 // Grid for grid-stride loops over `cap` items, 256 threads a block: one wave
 // of at most 8 blocks per SM.
 static unsigned stride_grid(unsigned long long cap) {
-  return (unsigned)std::max<unsigned long long>(1, std::min<unsigned long long>((cap + 255) / 256, 152ull * 8));
+  return (unsigned)std::max<unsigned long long>(1, std::min<unsigned long long>((cap + 255) / 256, sm_grid_cap(8)));
 }
 
 template <class K>
@@ -1209,7 +1229,13 @@ static void run_join(const Ctx& c, const ProbeView& v, bool self, uint32_t fb_co
   Timings tm;
   DBuf<Counters> ctr(c, 1);
   PJ_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(Counters), c.stream));
-  AcceptBuf acc(c, ctr.p, env_knob("PJ_ACCEPT_INITIAL", 4ull << 20));
+  unsigned long long acc_initial = env_knob("PJ_ACCEPT_INITIAL", 4ull << 20);
+  if (c.budget) {  // under a device budget, start at 1/64 of what is left of it (the buffer grows)
+    std::lock_guard<std::mutex> g(c.budget->mu);
+    const size_t left = c.budget->limit > c.budget->cur ? c.budget->limit - c.budget->cur : 0;
+    acc_initial = std::max<unsigned long long>(1024, std::min<unsigned long long>(acc_initial, left / 64 / 12));
+  }
+  AcceptBuf acc(c, ctr.p, acc_initial);
   if (self) probe_and_verify<true, false>(c, v, fb_count, acc, ctr.p, h, tm, nullptr);
   else if (v.ptau) probe_and_verify<false, true>(c, v, fb_count, acc, ctr.p, h, tm, h_qgoff);
   else probe_and_verify<false, false>(c, v, fb_count, acc, ctr.p, h, tm, nullptr);
@@ -1317,8 +1343,9 @@ static void run_join(const Ctx& c, const ProbeView& v, bool self, uint32_t fb_co
 // size in {128, 256, 512} -- verifies the same prefix of the candidates (at
 // most 2^26) into a scratch buffer whose results are dropped; the fastest
 // (best of two runs, CUDA events) wins.  Decisions are cached per workload
-// signature for the process and, with PJ_AUTOTUNE_CACHE=<file>, in that file
-// (one "signature|cut|block" line each).
+// signature for the process and, when the index names a cache file
+// (pj_options.autotune_cache, else the environment variable
+// PJ_AUTOTUNE_CACHE), in that file (one "signature|cut|block|mode" line each).
 
 struct TuneResult {
   int warp_min_len = 65536;
@@ -1342,8 +1369,13 @@ static std::string tune_signature(const pj_index& idx, int tau) {
   return buf;
 }
 
-static bool tune_from_file(const std::string& key, TuneResult& r) {
-  const char* path = getenv("PJ_AUTOTUNE_CACHE");
+// The autotune cache file: the index's option, else PJ_AUTOTUNE_CACHE.
+static const char* tune_cache_path(const pj_index& idx) {
+  if (!idx.autotune_cache.empty()) return idx.autotune_cache.c_str();
+  return getenv("PJ_AUTOTUNE_CACHE");
+}
+
+static bool tune_from_file(const char* path, const std::string& key, TuneResult& r) {
   if (!path || !path[0]) return false;
   std::ifstream f(path);
   std::string line;
@@ -1364,8 +1396,7 @@ static bool tune_from_file(const std::string& key, TuneResult& r) {
   return found;
 }
 
-static void tune_to_file(const std::string& key, const TuneResult& r) {
-  const char* path = getenv("PJ_AUTOTUNE_CACHE");
+static void tune_to_file(const char* path, const std::string& key, const TuneResult& r) {
   if (!path || !path[0]) return;
   FILE* f = fopen(path, "a");
   if (!f) return;
@@ -1508,14 +1539,14 @@ static TuneResult self_join_tuning(pj_index& idx, const ProbeView& v, float* tun
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
       r = it->second;
-    } else if (tune_from_file(key, r)) {
+    } else if (tune_from_file(tune_cache_path(idx), key, r)) {
       g_tune_cache[key] = r;
     } else {
       const auto t0 = std::chrono::steady_clock::now();
       r = autotune_self(idx, v);
       *tune_ms = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
       g_tune_cache[key] = r;
-      tune_to_file(key, r);
+      tune_to_file(tune_cache_path(idx), key, r);
     }
   }
   if (!idx.autotune) default_mode(idx, r);
@@ -1887,8 +1918,16 @@ static bool replay_self_plan(SelfPlan& P, const Ctx& rc, bool on_device, pj_resu
   return true;
 }
 
-static void self_join_impl(pj_index& idx, int tau, pj_result* out, bool on_device) {
+// The self join over probes with sids in [q_lo, q_hi) (all of them by
+// default).  Every similar pair is found by exactly one probe -- the later of
+// its two strings in sid order -- so joins over disjoint probe ranges return
+// disjoint pair sets whose union is the whole join.  Pairs with a string too
+// short to partition are verified directly by the join whose `fallback` is
+// set (by default: the one whose range starts at sid 0).
+static void self_join_impl(pj_index& idx, int tau, pj_result* out, bool on_device, uint32_t q_lo = 0,
+                           uint32_t q_hi = UINT32_MAX, int fallback = -1) {
   trace_mark(idx.ctx, "join: start");
+  const bool whole = q_lo == 0 && q_hi >= idx.n && fallback != 0;
   float part_ms = 0.f;
   ensure_partition(idx, tau, &part_ms);
   struct DumpAfter {
@@ -1910,8 +1949,10 @@ static void self_join_impl(pj_index& idx, int tau, pj_result* out, bool on_devic
   v.pbytes = idx.sbytes.p;
   v.poff = idx.soff.p;
   v.plen = idx.slen.p;
-  v.pbegin = part.first;
-  v.pcount = idx.n - part.first;
+  const uint32_t q_end = std::min<uint32_t>(q_hi, idx.n);
+  v.pbegin = std::min(std::max(part.first, q_lo), q_end);
+  v.pcount = q_end - v.pbegin;
+  const uint32_t fb_count = (fallback < 0 ? q_lo == 0 : fallback != 0) ? part.first : 0u;
   v.pid = idx.perm.p;
   v.pbm = idx.sbm.p;
   v.phash = idx.sph.p;
@@ -1919,12 +1960,17 @@ static void self_join_impl(pj_index& idx, int tau, pj_result* out, bool on_devic
   v.gorder = part.gorder[1].p;
   v.warp_q_cut = UINT32_MAX;
   float tune_ms = 0.f;
-  const TuneResult tr = self_join_tuning(idx, v, &tune_ms);
+  TuneResult tr;
+  if (v.pcount) {
+    tr = self_join_tuning(idx, v, &tune_ms);
+  } else {  // nothing to probe: only the fallback (if any) runs
+    default_mode(idx, tr);
+  }
   if (tr.warp_min_len <= idx.lmax) v.warp_q_cut = idx.h_bbeg[std::max(0, tr.warp_min_len)];
   v.block_thread = tr.block_thread;
   v.pair_mode = tr.pair_mode;
   v.pair_warp = tr.pair_warp;
-  if (idx.graph_joins) {
+  if (idx.graph_joins && whole) {
     if (idx.self_plans.size() < idx.parts.size()) idx.self_plans.resize(idx.parts.size());
     SelfPlan* sp = static_cast<SelfPlan*>(idx.self_plans[tau].get());
     if (sp && (sp->warp_min_len != tr.warp_min_len || sp->block_thread != tr.block_thread ||
@@ -1945,8 +1991,8 @@ static void self_join_impl(pj_index& idx, int tau, pj_result* out, bool on_devic
       idx.self_plans[tau].reset();
     }
   }
-  run_join(idx.ctx, v, true, part.first, bits_for(idx.n), on_device, out);
-  if (idx.graph_joins && !idx.self_plans[tau]) {
+  run_join(idx.ctx, v, true, fb_count, bits_for(idx.n), on_device, out);
+  if (idx.graph_joins && whole && !idx.self_plans[tau]) {
     try {  // a join that cannot be recorded (device or host memory) still has its result
       std::shared_ptr<SelfPlan> p = make_self_plan(idx, v, tr, part.first, out->stats, out->count);
       if (p) idx.self_plans[tau] = std::static_pointer_cast<void>(p);
@@ -1960,6 +2006,19 @@ static void self_join_impl(pj_index& idx, int tau, pj_result* out, bool on_devic
   out->stats.tune_ms = tune_ms;
   out->stats.verify_mode = tr.pair_mode ? PJ_VERIFY_PAIRS : PJ_VERIFY_EXTENSION;
   out->stats.pair_warp = tr.pair_mode ? tr.pair_warp : 0;
+}
+
+void self_join_range(pj_index& idx, int tau, uint32_t q_lo, uint32_t q_hi, bool fallback, pj_result* out,
+                     bool on_device) {
+  ensure_partition(idx, tau, nullptr);
+  self_join_impl(idx, tau, out, on_device, q_lo, q_hi, fallback ? 1 : 0);
+}
+
+void host_result(pj_result* out, pj_pair* pairs, uint64_t count) {
+  out->pairs = pairs;
+  out->count = count;
+  out->on_device = 0;
+  out->priv = new ResultPriv{};
 }
 
 static void probe_join_impl(const Ctx& c, const pj_index& idx, const Partition& part, const ProbeSet& R,
@@ -2164,6 +2223,7 @@ int pj_self_join(pj_index* idx, int tau, pj_result* out) {
     if (tau < 0 || tau >= (int)idx->parts.size()) pj::fail(PJ_EINVAL, "pj_self_join: tau outside 0..tau_max");
     std::lock_guard<std::mutex> g(idx->mu);
     pj::self_join_impl(*idx, tau, out, idx->results_on_device);
+    if (idx->ctx.budget) out->stats.device_peak = idx->ctx.budget->peak;
     return PJ_OK;
   } catch (const pj::Error& e) {
     pj::set_last_error(e.msg);
@@ -2173,6 +2233,43 @@ int pj_self_join(pj_index* idx, int tau, pj_result* out) {
     pj::set_last_error("host allocation failed");
     pj_result_free(out);
     return PJ_ENOMEM;
+  }
+}
+
+int pj_count_selection(pj_index* idx, int tau, pj_selection* out) {
+  if (out) memset(out, 0, sizeof(*out));
+  try {
+    if (!idx || !out) pj::fail(PJ_EINVAL, "pj_count_selection: NULL argument");
+    if (tau < 0 || tau >= (int)idx->parts.size()) pj::fail(PJ_EINVAL, "pj_count_selection: tau outside 0..tau_max");
+    std::lock_guard<std::mutex> g(idx->mu);
+    const pj::Ctx& c = idx->ctx;
+    pj::ProbeView v{};
+    v.plen = idx->slen.p;
+    v.ibbeg = idx->bbeg.p;
+    v.ilmax = idx->lmax;
+    v.tau = tau;
+    v.seg_magic = pj::seg_magic(tau + 1);
+    v.pbegin = tau + 1 <= idx->lmax ? idx->h_bbeg[tau + 1] : idx->n;  // shorter probes select nothing
+    v.pcount = idx->n - v.pbegin;
+    const unsigned long long n_groups = (unsigned long long)v.pcount * pj::groups_per_probe(tau, true);
+    pj::DBuf<pj::SelCounts> d(c, 1);
+    PJ_CUDA(cudaMemsetAsync(d.p, 0, sizeof(pj::SelCounts), c.stream));
+    if (n_groups) {
+      pj::k_selection_counts<<<pj::stride_grid(n_groups), pj::BLOCK, 0, c.stream>>>(v, n_groups, d.p);
+      PJ_LAUNCHED("k_selection_counts");
+    }
+    pj::SelCounts h{};
+    PJ_CUDA(cudaMemcpyAsync(&h, d.p, sizeof(h), cudaMemcpyDeviceToHost, c.stream));
+    c.sync();
+    out->length_based = h.w[0];
+    out->shift_based = h.w[1];
+    out->position_aware = h.w[2];
+    out->multi_match = h.w[3];
+    out->groups = h.groups;
+    return PJ_OK;
+  } catch (const pj::Error& e) {
+    pj::set_last_error(e.msg);
+    return e.code;
   }
 }
 
@@ -2196,6 +2293,7 @@ int pj_join(const pj_strings* R, const pj_strings* S, int tau, const pj_options*
       pj::probe_join_impl(tmp->ctx, *tmp, tmp->parts[tau], P, out, tmp->results_on_device);
       tmp->ctx.sync();
     }
+    if (tmp->ctx.budget) out->stats.device_peak = tmp->ctx.budget->peak;
     delete tmp;
     return PJ_OK;
   } catch (const pj::Error& e) {

@@ -30,29 +30,21 @@ constexpr int NA_BLOCK = 256;
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
-// Device address of g_noalloc_scratch per device (the host-side symbol is a
-// stand-in, not a device address).
-struct ScratchSlot {
-  bool ready = false;
-  unsigned char* base = nullptr;
-};
+// Device address of g_noalloc_scratch on the current device.  The host-side
+// symbol is only a stand-in, so host code asks the runtime for the address;
+// the lookup allocates nothing and is repeated on every call, so that a
+// device reset or a new primary context never leaves a stale address behind.
+// (The first lookup on a device also loads this library's kernels there.)
 std::mutex g_noalloc_mu;
-ScratchSlot g_noalloc_slots[64];
 
-unsigned char* scratch_base(int device) {
-  if (device < 0 || device >= 64) fail(PJ_EINVAL, "pj_query_noalloc: device index out of range");
-  ScratchSlot& s = g_noalloc_slots[device];
-  if (!s.ready) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      cudaGetLastError();
-      fail(PJ_ECUDA, std::string("pj_query_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
-    }
-    s.base = static_cast<unsigned char*>(p);
-    s.ready = true;
+unsigned char* scratch_base() {
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    cudaGetLastError();
+    fail(PJ_ECUDA, std::string("pj_query_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
   }
-  return s.base;
+  return static_cast<unsigned char*>(p);
 }
 
 // Bump allocator over the scratch array; frees are no-ops, the arena is
@@ -169,12 +161,12 @@ void na_launch(const Ctx& c, const ProbeView& v, bool fallback, unsigned long lo
                unsigned long long cap, NaCounters* ctr) {
   const unsigned long long n_groups = (unsigned long long)v.pcount * groups_per_probe(v.tau, false);
   if (n_groups) {
-    const unsigned grid = (unsigned)std::min<unsigned long long>((n_groups + NA_BLOCK - 1) / NA_BLOCK, 152ull * 8);
+    const unsigned grid = (unsigned)std::min<unsigned long long>((n_groups + NA_BLOCK - 1) / NA_BLOCK, sm_grid_cap(8));
     k_na_probe_verify<MAXW><<<grid, NA_BLOCK, 0, c.stream>>>(v, n_groups, keys, eds, cap, ctr);
     PJ_LAUNCHED("k_na_probe_verify");
   }
   if (fallback && v.pcount) {
-    const unsigned grid = (unsigned)std::min<unsigned>((v.pcount + NA_BLOCK - 1) / NA_BLOCK, 152u * 8);
+    const unsigned grid = (unsigned)std::min<unsigned>((v.pcount + NA_BLOCK - 1) / NA_BLOCK, sm_grid_cap(8));
     k_na_fallback<MAXW><<<grid, NA_BLOCK, 0, c.stream>>>(v, keys, eds, cap, ctr);
     PJ_LAUNCHED("k_na_fallback");
   }
@@ -195,7 +187,7 @@ void query_noalloc(pj_index& idx, const pj_strings& batch, int tau, pj_pair* out
   int dev = 0;
   PJ_CUDA(cudaGetDevice(&dev));
   if (dev != idx.device) fail(PJ_EINVAL, "pj_query_noalloc: the index lives on another device");
-  Bump bump{scratch_base(dev), NOALLOC_SCRATCH_BYTES, 0};
+  Bump bump{scratch_base(), NOALLOC_SCRATCH_BYTES, 0};
   Ctx c;
   c.stream = idx.ctx.stream;
   c.alloc = bump_alloc;

@@ -228,7 +228,7 @@ void exclusive_scan_dn(const Ctx& c, const T* in, T* out, size_t cap, const unsi
     exclusive_scan_dn<T>(c, sums.p, sums_off.p, tiles, nullptr, nullptr);
     // a device count launches a capacity-sized grid: keep it to one wave of
     // grid-stride blocks
-    const unsigned grid = n_dev ? std::min<unsigned>(ceil_div(cap, 256), 152u * 8) : ceil_div(cap, 256);
+    const unsigned grid = n_dev ? std::min<unsigned>(ceil_div(cap, 256), sm_grid_cap(8)) : ceil_div(cap, 256);
     k_scan_add<T><<<grid, 256, 0, c.stream>>>(out, sums_off.p, cap, n_dev);
     PJ_LAUNCHED("k_scan_add");
   }

@@ -107,15 +107,12 @@ __host__ __device__ __forceinline__ int groups_per_probe(int tau, bool self) {
   return (tau + 1) * (self ? tau + 1 : 2 * tau + 1);
 }
 
-// Group g of probing string q (length ls): indexed length l, segment i, its
-// even-partition start P and length li, and the multi-match window
-// [lo, hi] of start positions in q (Sec. 4.2):
-//   lo = max(P - (i-1), P + D - (tau+1-i)),  hi = min(P + (i-1), P + D + (tau+1-i)),
-// clipped to [0, ls - li], with D = ls - l.  False when the group selects
-// nothing (no such length indexed, no string of it visited before q, or an
-// empty window).
-__host__ __device__ __forceinline__ bool group_window(const ProbeView& v, bool self, uint32_t q, int ls, int g,
-                                                      int& l, int& i, int& P, int& li, int& lo, int& hi) {
+// The lists of group g of probing string q (length ls): indexed length l,
+// segment i, its even-partition start P and length li.  False when L_l^i is
+// empty when q probes it (no such length indexed, or no string of it visited
+// before q).
+__host__ __device__ __forceinline__ bool group_lists(const ProbeView& v, bool self, uint32_t q, int ls, int g,
+                                                     int& l, int& i, int& P, int& li) {
   const int tau = v.tau, parts = tau + 1;
   l = ls - tau + g / parts;
   i = 1 + g % parts;
@@ -125,10 +122,44 @@ __host__ __device__ __forceinline__ bool group_window(const ProbeView& v, bool s
   if (self && l == ls && b1 > q) b1 = q;  // only strings visited before q
   if (b1 <= b0) return false;
   even_segment_m(l, parts, v.seg_magic, i, P, li);
+  return true;
+}
+
+// Group g's multi-match window [lo, hi] of start positions in q (Sec. 4.2):
+//   lo = max(P - (i-1), P + D - (tau+1-i)),  hi = min(P + (i-1), P + D + (tau+1-i)),
+// clipped to [0, ls - li], with D = ls - l.  False when the group selects
+// nothing (empty lists or an empty window).
+__host__ __device__ __forceinline__ bool group_window(const ProbeView& v, bool self, uint32_t q, int ls, int g,
+                                                      int& l, int& i, int& P, int& li, int& lo, int& hi) {
+  if (!group_lists(v, self, q, ls, g, l, i, P, li)) return false;
+  const int parts = v.tau + 1;
   const int D = ls - l;
   lo = max(0, max(P - (i - 1), P + D - (parts - i)));
   hi = min(ls - li, min(P + (i - 1), P + D + (parts - i)));
   return hi >= lo;
+}
+
+// floor(a / 2) for any sign of a
+__host__ __device__ __forceinline__ int floor_half(int a) { return a >= 0 ? a / 2 : -((1 - a) / 2); }
+
+// Sizes of the start-position windows that each selection method of Sec. 4
+// picks for group g (substrings s[p, l_i] that exist in s, 0 <= p <= |s| -
+// l_i): w[0] length-based (every position), w[1] shift-based ([P_i - tau,
+// P_i + tau]), w[2] position-aware (Sec. 4.1, [P_i - floor((tau - D)/2),
+// P_i + floor((tau + D)/2)]), w[3] multi-match-aware (Sec. 4.2, the window
+// the join looks up); D = |s| - l.  False when the group's lists are empty.
+__host__ __device__ __forceinline__ bool group_selection_sizes(const ProbeView& v, bool self, uint32_t q, int ls,
+                                                               int g, int (&w)[4]) {
+  int l, i, P, li;
+  w[0] = w[1] = w[2] = w[3] = 0;
+  if (!group_lists(v, self, q, ls, g, l, i, P, li)) return false;
+  const int tau = v.tau, parts = tau + 1, D = ls - l, last = ls - li;
+  if (last < 0) return true;
+  const int lo[4] = {0, P - tau, P - floor_half(tau - D), max(P - (i - 1), P + D - (parts - i))};
+  const int hi[4] = {last, P + tau, P + floor_half(tau + D), min(P + (i - 1), P + D + (parts - i))};
+#pragma unroll
+  for (int m = 0; m < 4; ++m) w[m] = max(0, min(hi[m], last) - max(lo[m], 0) + 1);
+  return true;
 }
 
 __host__ __device__ __forceinline__ int table_find_any(const Slot* t, const uint8_t* fp, unsigned pb,

@@ -49,7 +49,8 @@ class pj_stats(ctypes.Structure):
                 ("dedupe_ms", ctypes.c_float), ("partition_ms", ctypes.c_float), ("verify_block", ctypes.c_int32),
                 ("warp_min_len", ctypes.c_int32), ("tune_ms", ctypes.c_float), ("verify_mode", ctypes.c_int32),
                 ("pair_warp", ctypes.c_int32), ("filtered", ctypes.c_uint64),
-                ("distinct_pairs", ctypes.c_uint64), ("graph_replay", ctypes.c_int32), ("graph_ms", ctypes.c_float)]
+                ("distinct_pairs", ctypes.c_uint64), ("graph_replay", ctypes.c_int32), ("graph_ms", ctypes.c_float),
+                ("device_peak", ctypes.c_uint64), ("windows", ctypes.c_uint32)]
 
 
 class pj_result(ctypes.Structure):
@@ -64,7 +65,8 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void
 class pj_options(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
                 ("verify_mode", ctypes.c_int), ("results_on_device", ctypes.c_int), ("lazy_partitions", ctypes.c_int),
-                ("autotune", ctypes.c_int), ("graph_joins", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("graph_joins", ctypes.c_int), ("device_budget", ctypes.c_uint64),
+                ("autotune_cache", ctypes.c_char_p)]
 
 
 class pj_server_options(ctypes.Structure):
@@ -82,6 +84,17 @@ class pj_plan_info(ctypes.Structure):
                 ("graph_kernels", ctypes.c_uint32), ("hits_capacity", ctypes.c_uint64),
                 ("accepted_capacity", ctypes.c_uint64), ("pairs_capacity", ctypes.c_uint64),
                 ("device_bytes", ctypes.c_uint64), ("host_bytes", ctypes.c_uint64)]
+
+
+class pj_selection(ctypes.Structure):
+    _fields_ = [("length_based", ctypes.c_uint64), ("shift_based", ctypes.c_uint64),
+                ("position_aware", ctypes.c_uint64), ("multi_match", ctypes.c_uint64), ("groups", ctypes.c_uint64)]
+
+
+class pj_calibration(ctypes.Structure):
+    _fields_ = [("dp_cells_per_s", ctypes.c_double), ("int32_ops_per_s", ctypes.c_double),
+                ("l2_read_bytes_per_s", ctypes.c_double),
+                ("sm_mhz", ctypes.c_double), ("sm_count", ctypes.c_int32)]
 
 
 class pj_request_times(ctypes.Structure):
@@ -158,6 +171,15 @@ def library():
             L.pj_plan_get_info.restype = ctypes.c_int
             L.pj_plan_free.argtypes = [ctypes.c_void_p]
             L.pj_plan_free.restype = None
+            L.pj_self_join_shard.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint32,
+                                             P(pj_result)]
+            L.pj_self_join_shard.restype = ctypes.c_int
+            L.pj_self_join_stream.argtypes = [P(pj_strings), ctypes.c_int, P(pj_options), P(pj_result)]
+            L.pj_self_join_stream.restype = ctypes.c_int
+            L.pj_calibrate.argtypes = [P(pj_calibration)]
+            L.pj_calibrate.restype = ctypes.c_int
+            L.pj_count_selection.argtypes = [ctypes.c_void_p, ctypes.c_int, P(pj_selection)]
+            L.pj_count_selection.restype = ctypes.c_int
             L.pj_index_build_ms.argtypes = [ctypes.c_void_p]
             L.pj_index_build_ms.restype = ctypes.c_float
             L.pj_kernel_launches.argtypes = []
@@ -209,7 +231,8 @@ def _torch_free(ctx, ptr, stream):
 
 
 def make_options(stream=None, results_on_device: bool = False, torch_allocator: bool = True,
-                 lazy_partitions: bool = False, autotune: bool = False, graph_joins: bool = False) -> pj_options:
+                 lazy_partitions: bool = False, autotune: bool = False, graph_joins: bool = False,
+                 device_budget: int = 0, autotune_cache: str | None = None) -> pj_options:
     torch = _torch()
     opt = pj_options()
     library().pj_options_init(ctypes.byref(opt))
@@ -223,6 +246,10 @@ def make_options(stream=None, results_on_device: bool = False, torch_allocator: 
     opt.lazy_partitions = 1 if lazy_partitions else 0
     opt.autotune = 1 if autotune else 0
     opt.graph_joins = 1 if graph_joins else 0
+    opt.device_budget = int(device_budget)
+    # the library copies the path at pj_build_index; the bytes object lives
+    # as long as the options
+    opt.autotune_cache = os.fsencode(autotune_cache) if autotune_cache else None
     return opt
 
 
@@ -332,7 +359,7 @@ def _stats(st: pj_stats) -> dict:
                 verify_block=int(st.verify_block), warp_min_len=int(st.warp_min_len), tune_ms=float(st.tune_ms),
                 verify_mode=int(st.verify_mode), pair_warp=int(st.pair_warp), filtered=int(st.filtered),
                 distinct_pairs=int(st.distinct_pairs), graph_replay=int(st.graph_replay),
-                graph_ms=float(st.graph_ms))
+                graph_ms=float(st.graph_ms), device_peak=int(st.device_peak), windows=int(st.windows))
 
 
 class _HostPairs:
@@ -416,16 +443,20 @@ def pj_kernel_launches() -> int:
 
 
 def pj_build_index(strings, tau_max: int, stream=None, results_on_device: bool = False,
-                   lazy_partitions: bool = False, autotune: bool = False, graph_joins: bool = False) -> Index:
+                   lazy_partitions: bool = False, autotune: bool = False, graph_joins: bool = False,
+                   device_budget: int = 0, autotune_cache: str | None = None) -> Index:
     """pj_build_index: resident segment index for thresholds 0..tau_max.
 
     results_on_device: results stay in device memory (DeviceResult).
     lazy_partitions: a threshold's segment index is built on its first use.
     autotune: each threshold's self join picks its verification form by timing.
     graph_joins: after a threshold's first self join, later self joins of it
-    replay that join recorded as one CUDA graph (pj_options.graph_joins)."""
+    replay that join recorded as one CUDA graph (pj_options.graph_joins).
+    device_budget: most device bytes the index and its calls may hold at once
+    (0 = no limit; beyond it a call fails with PJ_ENOMEM).
+    autotune_cache: file keeping autotuning decisions across processes."""
     opt = make_options(stream, results_on_device, lazy_partitions=lazy_partitions, autotune=autotune,
-                       graph_joins=graph_joins)
+                       graph_joins=graph_joins, device_budget=device_budget, autotune_cache=autotune_cache)
     S = Strings(strings)
     h = ctypes.c_void_p()
     _check(library().pj_build_index(ctypes.byref(S.c), int(tau_max), ctypes.byref(opt), ctypes.byref(h)),
@@ -440,9 +471,49 @@ def pj_self_join(index: Index, tau: int):
     return _take(res)
 
 
-def pj_join(R, S, tau: int, stream=None, results_on_device: bool = False):
+def pj_calibrate() -> dict:
+    """pj_calibrate: measured DP-cell rate, int32 throughput, L2 read
+    bandwidth and SM clock of the current device (the rooflines' ceilings)."""
+    _torch()
+    out = pj_calibration()
+    _check(library().pj_calibrate(ctypes.byref(out)), "pj_calibrate")
+    return {f: (int(getattr(out, f)) if f == "sm_count" else float(getattr(out, f))) for f, _ in pj_calibration._fields_}
+
+
+def pj_count_selection(index: Index, tau: int) -> dict:
+    """pj_count_selection: substrings each selection method of Sec. 4 would
+    look up over the self join at threshold tau (length-based, shift-based,
+    position-aware, multi-match-aware) and the groups counted."""
+    out = pj_selection()
+    _check(library().pj_count_selection(index.handle, int(tau), ctypes.byref(out)), "pj_count_selection")
+    return {f: int(getattr(out, f)) for f, _ in pj_selection._fields_}
+
+
+def pj_self_join_shard(index: Index, tau: int, shard: int, n_shards: int):
+    """pj_self_join_shard: the part of pj_self_join whose later string (in
+    Alg. 1's visiting order) is among shard `shard` of `n_shards` equal probe
+    ranges; the shards are disjoint and together give the whole join."""
+    res = pj_result()
+    _check(library().pj_self_join_shard(index.handle, int(tau), int(shard), int(n_shards), ctypes.byref(res)),
+           "pj_self_join_shard")
+    return _take(res)
+
+
+def pj_self_join_stream(strings, tau: int, device_budget: int = 0, stream=None, autotune: bool = False):
+    """pj_self_join_stream: the self join of host strings, window by window of
+    lengths, holding at most `device_budget` device bytes at once (0 = three
+    quarters of the free device memory).  Host result."""
+    opt = make_options(stream, autotune=autotune, device_budget=device_budget)
+    S = Strings(strings)
+    res = pj_result()
+    _check(library().pj_self_join_stream(ctypes.byref(S.c), int(tau), ctypes.byref(opt), ctypes.byref(res)),
+           "pj_self_join_stream")
+    return _take(res)
+
+
+def pj_join(R, S, tau: int, stream=None, results_on_device: bool = False, device_budget: int = 0):
     """pj_join: all (a in R, b in S) with ED <= tau."""
-    opt = make_options(stream, results_on_device)
+    opt = make_options(stream, results_on_device, device_budget=device_budget)
     r, s = Strings(R), Strings(S)
     res = pj_result()
     _check(library().pj_join(ctypes.byref(r.c), ctypes.byref(s.c), int(tau), ctypes.byref(opt), ctypes.byref(res)),

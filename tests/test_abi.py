@@ -59,6 +59,11 @@ def test_null_arguments_rejected_without_device_work(lib):
     s = pj.Strings([b"ab"])
     assert L.pj_build_index(ctypes.byref(s.c), 33, None, ctypes.byref(h)) == pj.PJ_EINVAL
     assert L.pj_join(ctypes.byref(s.c), ctypes.byref(s.c), -1, None, ctypes.byref(pj.pj_result())) == pj.PJ_EINVAL
+    assert L.pj_count_selection(None, 1, ctypes.byref(pj.pj_selection())) == pj.PJ_EINVAL
+    assert L.pj_calibrate(None) == pj.PJ_EINVAL
+    assert L.pj_self_join_shard(None, 1, 0, 1, ctypes.byref(pj.pj_result())) == pj.PJ_EINVAL
+    assert L.pj_self_join_stream(None, 1, None, ctypes.byref(pj.pj_result())) == pj.PJ_EINVAL
+    assert L.pj_self_join_stream(ctypes.byref(s.c), 33, None, ctypes.byref(pj.pj_result())) == pj.PJ_EINVAL
     L.pj_result_free(None)
     L.pj_index_free(None)
 
@@ -100,7 +105,8 @@ def test_every_struct_field_matches_header(tmp_path):
     import subprocess
     from paper_1111_7171_gb300 import passjoin as pj
     structs = [pj.pj_strings, pj.pj_stats, pj.pj_result, pj.pj_options, pj.pj_server_options,
-               pj.pj_request_times, pj.pj_server_counters, pj.pj_plan_options, pj.pj_plan_info]
+               pj.pj_request_times, pj.pj_server_counters, pj.pj_plan_options, pj.pj_plan_info,
+               pj.pj_selection, pj.pj_calibration]
     lines = []
     for st in structs:
         name = st.__name__

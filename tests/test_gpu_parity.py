@@ -390,3 +390,109 @@ def test_autotuned_self_join(monkeypatch, tmp_path):
         assert (r1.stats["warp_min_len"], r1.stats["verify_block"]) == (r2.stats["warp_min_len"], r2.stats["verify_block"])
     lines = cache.read_text().strip().splitlines()
     assert len(lines) == 2 and all(line.count("|") == 3 for line in lines)
+
+
+@pytest.mark.parametrize("queued", ["0", "1"])
+def test_thread_extension_verification_wide_bands(monkeypatch, queued):
+    """Extension verification with one thread per candidate at thresholds
+    above 8 (Sec. 5.2, Alg. 3): the sides run the band of 17 (tau <= 16) or
+    33 (tau <= 32) diagonals held in one thread's registers.  The library
+    sends long strings to whole-pair or warp verification by default, so
+    both are switched off here; straight (0) and behind the screen queue (1)."""
+    monkeypatch.setenv("PJ_VERIFY_PAIRS", "0")
+    monkeypatch.setenv("PJ_WARP_MIN_LEN", "65536")
+    monkeypatch.setenv("PJ_VERIFY_QUEUE", queued)
+    for name, tau, n in [("medium", 8, 3000), ("long", 16, 800), ("long", 32, 600), ("medium", 12, 2000)]:
+        strings = synth.generate(name, tau, n=n)
+        r = gpu_self(strings, tau)
+        assert r.stats["verify_mode"] == 1, "extension verification expected"
+        assert r.stats["warp_min_len"] == 65536, "thread per candidate expected"
+        assert r.stats["accepted"] > 0
+        assert_same(r.pairs, cpu_self(strings, tau, banded=True), f"{name} tau={tau} thread extension")
+
+
+@pytest.mark.parametrize("name,tau,n", [("short2k", 2, 2000), ("short", 1, 3000), ("short", 4, 3000),
+                                        ("medium", 6, 1500), ("long", 16, 300)])
+def test_selection_counts_match_algorithm(name, tau, n):
+    """The selection ablation of Sec. 4 (Fig. 12's four methods) counted on
+    the device equals the counts of the oracle's own windows over Alg. 1's
+    visiting order, and the multi-match-aware count is exactly what the self
+    join looks up."""
+    strings = synth.generate(name, tau, n=n)
+    want = M.selection_counts(strings, tau)
+    idx = pj.pj_build_index(strings, tau, lazy_partitions=True)
+    try:
+        got = pj.pj_count_selection(idx, tau)
+        r = pj.pj_self_join(idx, tau)
+    finally:
+        idx.free()
+    assert got == {"length_based": want["length"], "shift_based": want["shift"],
+                   "position_aware": want["position"], "multi_match": want["multi"], "groups": want["groups"]}
+    assert got["length_based"] > got["shift_based"] >= got["position_aware"] >= got["multi_match"] > 0
+    assert r.stats["lookups"] == got["multi_match"]
+
+
+def _with_short_strings(strings, tau):
+    # strings too short to partition (length <= tau) exercise the fallback
+    return strings + [b"", b"a", b"ab", b"abc"[:tau], b"zz"]
+
+
+@pytest.mark.parametrize("name,tau,n,banded", [("short", 3, 5000, False), ("medium", 6, 2000, True),
+                                               ("long", 16, 500, True)])
+def test_shards_partition_the_self_join(name, tau, n, banded):
+    """pj_self_join_shard: the probe ranges of k shards give disjoint pair
+    sets whose union is exactly the self join (each pair is found by the
+    later of its strings, Alg. 1), for k = 1, 3 and 7."""
+    strings = _with_short_strings(synth.generate(name, tau, n=n), tau)
+    want = cpu_self(strings, tau, banded=banded)
+    idx = pj.pj_build_index(strings, tau)
+    try:
+        for k in (1, 3, 7):
+            parts = [pj.pj_self_join_shard(idx, tau, s, k).pairs for s in range(k)]
+            assert all((np.diff(p["a"].astype(np.int64) * (1 << 32) + p["b"]) > 0).all() for p in parts if len(p) > 1)
+            got = np.concatenate(parts)
+            got = got[np.lexsort((got["b"], got["a"]))]
+            assert_same(got, want, f"{name} tau={tau} shards={k}")
+    finally:
+        idx.free()
+
+
+def test_stream_self_join_under_a_small_budget():
+    """pj_self_join_stream: windows of consecutive probing strings (by length)
+    joined one at a time under a device budget far below the whole join's
+    needs; the result equals the oracle's and pj_self_join's, the windows are
+    several, and the device memory held never passed the budget."""
+    tau = 3
+    strings = _with_short_strings(synth.generate("short", tau, n=12000), tau)
+    budget = 24 << 20
+    r = pj.pj_self_join_stream(strings, tau, device_budget=budget)
+    assert r.stats["windows"] >= 3
+    assert 0 < r.stats["device_peak"] <= budget
+    assert_same(r.pairs, cpu_self(strings, tau, banded=True), "stream")
+    assert_same(r.pairs, gpu_self(strings, tau).pairs, "stream vs pj_self_join")
+    # no budget: one window of the whole set
+    r1 = pj.pj_self_join_stream(strings, tau)
+    assert r1.stats["windows"] == 1
+    assert_same(r1.pairs, r.pairs, "stream, one window")
+
+
+def test_device_budget_refuses_instead_of_allocating():
+    """pj_options.device_budget: an index whose join would need more device
+    memory than the budget fails with PJ_ENOMEM (nothing beyond the budget is
+    allocated), and a generous budget gives the exact result and reports its
+    peak."""
+    strings = synth.generate("short", 4, n=20000)
+    small = pj.pj_build_index(strings, 4, device_budget=16 << 20, lazy_partitions=True)  # the store fits
+    try:
+        with pytest.raises(pj.PJError) as e:
+            pj.pj_self_join(small, 4)
+        assert e.value.code == pj.PJ_ENOMEM and "budget" in str(e.value)
+    finally:
+        small.free()
+    big = pj.pj_build_index(strings, 4, device_budget=2 << 30)
+    try:
+        r = pj.pj_self_join(big, 4)
+    finally:
+        big.free()
+    assert 0 < r.stats["device_peak"] <= 2 << 30
+    assert_same(r.pairs, cpu_self(strings, 4), "budgeted self join")

@@ -120,6 +120,8 @@ def test_rs_join_logic(emu, tmp_path):
 
 
 def test_vsp_widths_match_plain_dp(tmp_path):
+    """VERIFYSTRINGPAIR (Sec. 5.1, Alg. 3) at every compiled band width, 2 to
+    33 diagonals, equals min(t + 1, ED) of the plain DP."""
     nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
     if not os.path.exists(nvcc):
         pytest.skip("nvcc not available")
@@ -127,9 +129,12 @@ def test_vsp_widths_match_plain_dp(tmp_path):
     subprocess.run([nvcc, "-std=c++17", "-O2", "-I", CSRC, "-o", str(exe),
                     os.path.join(ROOT, "tests", "host_logic", "vsp_check.cu")], check=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
-    bad = {tok.split("=")[1]: None for tok in out if tok.startswith("W=")}
-    assert len(bad) == 5
+    widths = [tok.split("=")[1] for tok in out if tok.startswith("W=")]
+    assert widths == ["2", "3", "5", "9", "17", "33"]
     assert all(tok == "bad=0" for tok in out if tok.startswith("bad="))
+    # the long edited pairs put many distances next to the threshold, where a
+    # wrong band edge or early exit would show
+    assert all(int(tok.split("=")[1]) > 5000 for tok in out if tok.startswith("near="))
 
 
 def test_even_partition_by_reciprocal_matches_division(tmp_path):

@@ -246,6 +246,24 @@ def test_selection_count_formulas():
                 assert w("multi", False) == M.lemma2_count(tau, D)          # never clipped for D >= 0
 
 
+def test_selection_counts_two_strings_of_length_15():
+    """Sec. 6.1's worked count for |s| = l = 15, tau = 1: the length-based
+    method selects (tau+1)(|s|+1) - l = 17 substrings and the multi-match
+    method floor((tau^2 - D^2)/2) + tau + 1 = 2.  The shift-based window
+    [P_i - 1, P_i + 1] holds 2 tau + 1 = 3 positions per segment (6 in the
+    paper's count), of which 2 per segment exist in s (p >= 0 and p <= |s| -
+    l_i: segment 1 starts at 0, segment 2 ends at |s|); the position-aware
+    window of Sec. 4.1 has floor((tau - D)/2) + floor((tau + D)/2) + 1 = 1
+    position per segment at D = 0 (the paper's (tau+1)^2 = 4 holds for even
+    tau - D).  Only the second string probes (the first has nothing visited
+    before it)."""
+    a, b = b"abcdefghijklmno", b"bcdefghijklmnop"
+    got = M.selection_counts([a, b], 1)
+    assert got == {"length": 17, "shift": 4, "position": 2, "multi": 2, "groups": 2}
+    # a length not visited before the probe selects nothing
+    assert M.selection_counts([a, b"xyz"], 1)["groups"] == 0
+
+
 def test_lemma3_subset_chain():
     for tau in range(0, 7):
         for l in range(tau + 1, 40):
