@@ -371,65 +371,111 @@ __global__ void __launch_bounds__(512) k_verify_hits(const ProbeView v, const Hi
   if (err) atomicOr(&ctr->err, (unsigned long long)err);
 }
 
-// The same verification with a screen and a per-warp queue: every lane
-// first screens S_RUN consecutive candidates on its own (valid sid, not the
-// probe, character-count bound) -- independent loads of their posting
-// records, no warp collectives -- and one warp scan of the lanes' survivor
-// counts places all survivors in a queue in shared memory; while 32 or more
-// are queued, each lane takes one and runs extension verification.
-// Screened-out candidates then cost no DP slot, so the warps' DP lanes stay
-// full.  The scan and the queue loop run the same number of times in all 32
-// lanes, and queue entries are read before the next writes only after a
-// __syncwarp.
+// The same verification with a screen and a per-warp queue.  Each warp owns
+// one contiguous range of candidates (the launch's candidates split evenly
+// over the warps, in steps of 32 * S_RUN) and walks it step by step: in a
+// step, lane l screens candidates base + l + 32 k (k < S_RUN) -- valid sid,
+// not the probe itself, character-count bound -- so that every load of a
+// posting record is one coalesced 512-byte request for the warp.  Every lane
+// tracks the hit of its own candidates as they advance (hits are in candidate
+// order), so a warp searches the candidate offsets only once, at the start
+// of its range.  One warp scan of the lanes' survivor counts places the
+// survivors in a queue in shared memory, each with its probe, sid and
+// (position, segment, threshold); while 32 or more are queued, each lane
+// takes one and runs extension verification.  Screened-out candidates cost
+// no DP slot, so the warps' DP lanes stay full.  The scan and the queue loop
+// run the same number of times in all 32 lanes, and queue entries are read
+// before the next writes only after a __syncwarp.
 constexpr int Q_BLOCK = 256;
 constexpr int Q_WARPS = Q_BLOCK / 32;
-constexpr int S_RUN = 8;                 // consecutive candidates one lane screens
+constexpr int S_RUN = 8;                 // candidates one lane screens per step
 constexpr int Q_CAP = 32 * S_RUN + 32;   // < 32 left + up to 32 * S_RUN new
 
-// The screen of one lane: candidates c0 .. c0 + S_RUN - 1 (h0 = the hit of
-// c0), each a valid sid, not the probe itself and within the
-// character-count bound; survivors get bit k of mask, with their hit in
-// eh[k] and their sid in ek[k].
-template <bool SELF, bool MULTI>
-__device__ __forceinline__ void screen_run(const ProbeView& v, const Hit* __restrict__ hits,
-                                           const unsigned long long* __restrict__ cand_off,
-                                           unsigned long long n_hits, unsigned long long n_cand,
-                                           unsigned long long c0, unsigned long long h0, uint32_t (&eh)[S_RUN],
-                                           uint32_t (&ek)[S_RUN], uint32_t& mask, unsigned long long& filtered,
-                                           int& err) {
+// One lane's position in the hits: hit h covers the candidates below c_hi
+// (from the previous hit's c_hi on); candidate c of it is posting
+// rec_base + c (mod 2^32: posting indices are 32-bit).
+struct LaneHit {
+  uint32_t h;
+  unsigned long long c_hi;
+  uint32_t rec_base;
+  uint32_t q, pi;
+  uint32_t sig[3];
+};
+
+__device__ __forceinline__ void lane_hit_set(const ProbeView& v, const Hit* __restrict__ hits,
+                                             unsigned long long c_lo, LaneHit& lh) {
+  const Hit hit = hits[lh.h];
+  lh.rec_base = hit.begin - (uint32_t)c_lo;
+  lh.q = hit.q;
+  lh.pi = hit.pi;
+  if (v.pbm) {
+    const Sig g = v.pbm[hit.q];
+    lh.sig[0] = g.w[0];
+    lh.sig[1] = g.w[1];
+    lh.sig[2] = g.w[2];
+  }
+}
+
+__device__ __forceinline__ void lane_hit_load(const ProbeView& v, const Hit* __restrict__ hits,
+                                              const unsigned long long* __restrict__ cand_off,
+                                              unsigned long long n_hits, unsigned long long n_cand,
+                                              unsigned long long h, LaneHit& lh) {
+  lh.h = (uint32_t)h;
+  lh.c_hi = h + 1 < n_hits ? cand_off[h + 1] : n_cand;
+  lane_hit_set(v, hits, cand_off[h], lh);
+}
+
+// Advance lh to the hit of candidate c (c at or after the current hit's first).
+__device__ __forceinline__ void lane_hit_advance(const ProbeView& v, const Hit* __restrict__ hits,
+                                                 const unsigned long long* __restrict__ cand_off,
+                                                 unsigned long long n_hits, unsigned long long n_cand,
+                                                 unsigned long long c, LaneHit& lh) {
+  if (c < lh.c_hi) return;
+  unsigned long long c_lo;
+  do {
+    ++lh.h;
+    c_lo = lh.c_hi;
+    lh.c_hi = (unsigned long long)lh.h + 1 < n_hits ? cand_off[lh.h + 1] : n_cand;
+  } while (c >= lh.c_hi);
+  lane_hit_set(v, hits, c_lo, lh);
+}
+
+__device__ __forceinline__ int signature_bound3(const uint32_t (&x)[3], const Sig& y) {
+  int a = 0, b = 0;
 #pragma unroll
-  for (int k = 0; k < S_RUN; ++k) eh[k] = ek[k] = 0;
-  if (c0 >= n_cand) return;
-  unsigned long long h = h0;
-  unsigned long long c_lo = cand_off[h];
-  unsigned long long c_hi = h + 1 < n_hits ? cand_off[h + 1] : n_cand;
-  Hit hit = hits[h];
-  Sig qsig = {{0u, 0u, 0u, 0u}};
-  if (v.pbm) qsig = v.pbm[hit.q];
-#pragma unroll
-  for (int k = 0; k < S_RUN; ++k) {
-    const unsigned long long c = c0 + k;
-    if (c < n_cand) {
-      if (c >= c_hi) {  // into a later hit
-        do {
-          ++h;
-          c_lo = c_hi;
-          c_hi = h + 1 < n_hits ? cand_off[h + 1] : n_cand;
-        } while (c >= c_hi);
-        hit = hits[h];
-        if (v.pbm) qsig = v.pbm[hit.q];
-      }
-      const ProbeView vt = MULTI ? view_for_tau(v, (int)(hit.pi >> 24)) : v;
-      const uint32_t pk = hit.begin + (uint32_t)(c - c_lo);
-      const PostRec rec = vt.precs[pk];
-      eh[k] = (uint32_t)h;
-      ek[k] = rec_sid(rec);
-      if (rec_sid(rec) >= vt.n_index) {
-        err |= 1;
-      } else if (!(SELF && rec_sid(rec) == hit.q)) {
-        if (v.pbm && signature_bound(qsig, rec.sig) > vt.tau) ++filtered;
-        else mask |= 1u << k;
-      }
+  for (int k = 0; k < 3; ++k) {
+    a += __popc(x[k] & ~y.w[k]);
+    b += __popc(y.w[k] & ~x[k]);
+  }
+  return a > b ? a : b;
+}
+
+// Extension verification of one queue entry: probe q, indexed sid r, and
+// the match's position, segment and threshold packed in pi.
+template <int MAXW, bool SELF, bool MULTI>
+__device__ __forceinline__ void verify_queued_entry(const ProbeView& v, uint32_t q, uint32_t r, uint32_t pi,
+                                                    AccOut out, Counters* ctr, unsigned long long& cells) {
+  const ProbeView vt = MULTI ? view_for_tau(v, (int)(pi >> 24)) : v;
+  HitCtx hc;
+  hc.q = q;
+  hc.begin = 0;
+  hc.p = (int)(pi & 0xFFFFu);
+  hc.i = (int)((pi >> 16) & 0xFFu);
+  if (vt.pref) {
+    const unsigned long long ref = vt.pref[q];
+    hc.ls = (int)(ref & 0xFFFFu);
+    hc.s = vt.pbytes + (ref >> 16);
+  } else {
+    hc.ls = (int)vt.plen[q];
+    hc.s = vt.pbytes + vt.poff[q];
+  }
+  unsigned long long key = 0;
+  int ed = 0;
+  if (verify_screened<MAXW>(vt, SELF, hc, r, key, ed, cells)) {
+    const unsigned long long pos = atomicAdd(&ctr->accepted, 1ull);
+    if (pos < out.cap) {
+      out.key[pos] = key;
+      out.ed[pos] = (uint32_t)ed;
     }
   }
 }
@@ -440,8 +486,9 @@ __global__ void __launch_bounds__(Q_BLOCK) k_verify_queued(const ProbeView v, co
                                                             unsigned long long n_hits, unsigned long long c_begin,
                                                             unsigned long long n_cand, AccOut out, Counters* ctr,
                                                             const unsigned long long* __restrict__ dn) {
-  __shared__ uint32_t q_hit[Q_WARPS][Q_CAP];
+  __shared__ uint32_t q_q[Q_WARPS][Q_CAP];
   __shared__ uint32_t q_sid[Q_WARPS][Q_CAP];
+  __shared__ uint32_t q_pi[Q_WARPS][Q_CAP];
   if (dn) {
     n_hits = min(n_hits, dn[0]);
     n_cand = dn[1];
@@ -452,50 +499,59 @@ __global__ void __launch_bounds__(Q_BLOCK) k_verify_queued(const ProbeView v, co
   const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const unsigned long long n_warps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
   const unsigned long long span = 32ull * S_RUN;
+  // this warp's range [r0, r1): the candidates split evenly, in whole steps
+  const unsigned long long total = n_cand > c_begin ? n_cand - c_begin : 0;
+  const unsigned long long per_warp = ((total + n_warps - 1) / n_warps + span - 1) / span * span;
+  const unsigned long long r0 = c_begin + min(total, warp * per_warp);
+  const unsigned long long r1 = c_begin + min(total, (warp + 1) * per_warp);
   int qn = 0;  // the same in every lane
-  auto verify_entry = [&](uint32_t h, uint32_t sid) {
-    const Hit hit = hits[h];
-    const ProbeView vt = MULTI ? view_for_tau(v, (int)(hit.pi >> 24)) : v;
-    unsigned long long key = 0;
-    int ed = 0;
-    if (verify_screened<MAXW>(vt, SELF, hit_ctx(vt, hit), sid, key, ed, cells)) {
-      const unsigned long long pos = atomicAdd(&ctr->accepted, 1ull);
-      if (pos < out.cap) {
-        out.key[pos] = key;
-        out.ed[pos] = (uint32_t)ed;
-      }
+  if (r0 < r1) {
+    LaneHit lh;
+    {
+      const unsigned long long c = min(r0 + lane, r1 - 1);
+      lane_hit_load(v, hits, cand_off, n_hits, n_cand,
+                    lane_hit_of(cand_off, n_hits, warp_hit_of(cand_off, n_hits, r0), r0, c), lh);
     }
-  };
-  for (unsigned long long base = c_begin + warp * span; base < n_cand; base += n_warps * span) {
-    const unsigned long long c0 = base + (unsigned long long)lane * S_RUN;
-    const unsigned long long h0 = lane_hit_of(cand_off, n_hits, warp_hit_of(cand_off, n_hits, base), base, c0);
-    uint32_t mask = 0;
-    uint32_t eh[S_RUN], ek[S_RUN];
-    screen_run<SELF, MULTI>(v, hits, cand_off, n_hits, n_cand, c0, h0, eh, ek, mask, filtered, err);
-    __syncwarp();
-    const int cnt = __popc(mask);
-    const int incl = warp_incl_scan(cnt);
-    const int total = __shfl_sync(FULL, incl, 31);
-    int slot = qn + incl - cnt;
+    for (unsigned long long base = r0; base < r1; base += span) {
+      // screen; each survivor goes straight into the queue (one ballot per 32)
 #pragma unroll
-    for (int k = 0; k < S_RUN; ++k) {
-      if ((mask >> k) & 1u) {
-        q_hit[wib][slot] = eh[k];
-        q_sid[wib][slot] = ek[k];
-        ++slot;
+      for (int k = 0; k < S_RUN; ++k) {
+        const unsigned long long c = base + lane + 32ull * k;
+        bool pass = false;
+        uint32_t r = 0;
+        if (c < r1) {
+          lane_hit_advance(v, hits, cand_off, n_hits, n_cand, c, lh);
+          const ProbeView vt = MULTI ? view_for_tau(v, (int)(lh.pi >> 24)) : v;
+          const PostRec rec = vt.precs[lh.rec_base + (uint32_t)c];
+          r = rec_sid(rec);
+          if (r >= vt.n_index) {
+            err |= 1;
+          } else if (!(SELF && r == lh.q)) {
+            if (v.pbm && signature_bound3(lh.sig, rec.sig) > vt.tau) ++filtered;
+            else pass = true;
+          }
+        }
+        const unsigned b = __ballot_sync(FULL, pass);
+        if (pass) {
+          const int slot = qn + __popc(b & lanemask_lt());
+          q_q[wib][slot] = lh.q;
+          q_sid[wib][slot] = r;
+          q_pi[wib][slot] = lh.pi;
+        }
+        qn += __popc(b);
       }
-    }
-    qn += total;
-    __syncwarp();
-    while (qn >= 32) {  // the same in every lane
-      qn -= 32;
-      const uint32_t h2 = q_hit[wib][qn + lane], k2 = q_sid[wib][qn + lane];
-      __syncwarp();  // taken before any later write
-      verify_entry(h2, k2);
+      __syncwarp();
+      while (qn >= 32) {  // the same in every lane
+        qn -= 32;
+        const uint32_t q2 = q_q[wib][qn + lane], r2 = q_sid[wib][qn + lane], p2 = q_pi[wib][qn + lane];
+        __syncwarp();  // taken before any later write
+        verify_queued_entry<MAXW, SELF, MULTI>(v, q2, r2, p2, out, ctr, cells);
+      }
     }
   }
   __syncwarp();
-  if ((int)lane < qn) verify_entry(q_hit[wib][lane], q_sid[wib][lane]);
+  if ((int)lane < qn) verify_queued_entry<MAXW, SELF, MULTI>(v, q_q[wib][lane], q_sid[wib][lane], q_pi[wib][lane],
+                                                             out, ctr, cells);
   add_counter(&ctr->cells, cells);
   add_counter(&ctr->filtered, filtered);
   if (err) atomicOr(&ctr->err, (unsigned long long)err);
@@ -1954,6 +2010,7 @@ static void self_join_impl(pj_index& idx, int tau, pj_result* out, bool on_devic
   v.pcount = q_end - v.pbegin;
   const uint32_t fb_count = (fallback < 0 ? q_lo == 0 : fallback != 0) ? part.first : 0u;
   v.pid = idx.perm.p;
+  v.pref = idx.sref.p;
   v.pbm = idx.sbm.p;
   v.phash = idx.sph.p;
   v.key_shift = bits_for(idx.n);

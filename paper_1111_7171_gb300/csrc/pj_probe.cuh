@@ -44,6 +44,7 @@ struct ProbeView {
   const uint32_t* plen;
   uint32_t pbegin, pcount;  // probe ids pbegin .. pbegin + pcount - 1
   const uint32_t* pid;      // probe id -> reported id (NULL: identity)
+  const unsigned long long* pref;  // poff << 16 | plen in one word (NULL: read poff and plen)
   // indexed strings, sid order
   const uint8_t* ibytes;
   const uint64_t* ioff;

@@ -143,6 +143,56 @@ __host__ __device__ __forceinline__ int vsp_band_k(const uint8_t* a, int na, con
   return alive ? min(V[KR], cap) : cap;
 }
 
+// vsp_band_k with the result diagonal kres chosen at run time: one code path
+// for every band shape of width W, so that the lanes of a warp verifying
+// different matches run it together instead of one compile-time instance
+// after another.  Lemma 4 is the same single test, on V[kres] (selected by
+// an unrolled compare; the registers are not indexed dynamically).
+template <int W>
+__host__ __device__ __forceinline__ int vsp_band_r(const uint8_t* a, int na, const uint8_t* b, int nb, int t,
+                                                   int dlo, int w, int kres, unsigned long long& cells) {
+  const int cap = t + 1;
+  const int blast = nb - 1;
+  int V[W];
+  uint8_t B[W];
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    const int j = dlo + k;
+    V[k] = abs(j);
+    B[k] = b[min(max(j, 0), blast)];
+  }
+  bool alive = true;
+  int rows = 0;
+  int vres = cap;
+  for (int i = 1; i <= na; ++i) {
+    const uint8_t ca = a[i - 1];
+    int left = cap;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      const int up = (k + 1 < W) ? V[k + 1] : cap;
+      const int diag = V[k] + (ca != B[k] ? 1 : 0);
+      const int val = min(diag, min(up, left) + 1);
+      V[k] = val;
+      left = val;
+    }
+    ++rows;
+    vres = cap;
+#pragma unroll
+    for (int k = 0; k < W; ++k)
+      if (k == kres) vres = V[k];
+    if (vres > t) {  // Lemma 4 (see vsp_band_k)
+      alive = false;
+      break;
+    }
+    const int jn = i + dlo + W - 1;
+#pragma unroll
+    for (int k = 0; k + 1 < W; ++k) B[k] = B[k + 1];
+    B[W - 1] = b[min(max(jn, 0), blast)];
+  }
+  cells += (unsigned long long)(rows * w);
+  return alive ? min(vres, cap) : cap;
+}
+
 // Everything of one VERIFYSTRINGPAIR call that depends only on the lengths
 // and the threshold: in extension verification it is the same for every
 // candidate of a posting run (same probe, position, segment and indexed
@@ -204,6 +254,11 @@ __host__ __device__ __forceinline__ int vsp_run(const VspPlan& p, const uint8_t*
     }
     cells += (unsigned long long)p.na;
     r = eq ? 0 : 1;
+  } else if (p.kind == 3 && MAXW <= 5) {
+    // narrow bands: one code path for every band width and result diagonal,
+    // so that the lanes of a warp verifying different matches do not run the
+    // compile-time instances below one after another
+    r = vsp_band_r<MAXW>(a, p.na, b, p.nb, p.t, p.dlo, p.w, p.kres, cells);
   } else if (p.kind == 3) {
     if (p.W <= 2 || MAXW <= 2) {
       switch (p.kres) { PJ_KRES_CASES_2((MAXW < 2 ? MAXW : 2)) }
