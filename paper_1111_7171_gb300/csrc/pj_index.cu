@@ -287,14 +287,61 @@ __global__ void k_seg_records(const uint8_t* __restrict__ sbytes, const uint64_t
 
 // ---------------------------------------------------------------- A3 ------
 
-__global__ void k_post_records(const uint32_t* __restrict__ postings, uint64_t n, const Sig* __restrict__ sbm,
+// The side signatures of every partitioned string around each of its
+// segments: for sid first + x and segment i, sides[x * (tau + 1) + i - 1] =
+// (signature of the bytes before the segment, signature of the bytes after
+// it).  One thread per string: the prefix codes come from one pass forward,
+// the suffix codes from one pass backward.
+__global__ void k_side_sigs(const uint8_t* __restrict__ sbytes, const uint64_t* __restrict__ soff,
+                            const uint32_t* __restrict__ slen, uint32_t first, uint32_t n, int tau,
+                            ulonglong2* __restrict__ sides) {
+  for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; first + x < n; x += gridDim.x * blockDim.x) {
+    const uint32_t sid = first + x;
+    const uint8_t* s = sbytes + soff[sid];
+    const int l = (int)slen[sid];
+    ulonglong2* out = sides + (uint64_t)x * (tau + 1);
+    unsigned long long t = 0;
+    int k = 0;
+    for (int i = 1; i <= tau + 1; ++i) {  // prefixes: bytes [0, P_i)
+      int P, li;
+      even_segment(l, tau, i, P, li);
+      for (; k < P; ++k) {
+        const int sh = 4 * (int)(s[k] % SIDE_BUCKETS);
+        const unsigned long long field = (t >> sh) & 15ull;
+        if (field != 15ull) t |= (field + 1ull) << sh;
+      }
+      out[i - 1].x = t;
+    }
+    t = 0;
+    k = l;
+    for (int i = tau + 1; i >= 1; --i) {  // suffixes: bytes [P_i + l_i, l)
+      int P, li;
+      even_segment(l, tau, i, P, li);
+      for (; k > P + li; --k) {
+        const int sh = 4 * (int)(s[k - 1] % SIDE_BUCKETS);
+        const unsigned long long field = (t >> sh) & 15ull;
+        if (field != 15ull) t |= (field + 1ull) << sh;
+      }
+      out[i - 1].y = t;
+    }
+  }
+}
+
+// Posting records in posting order: the sid and its side signatures around
+// the segment of the record's key (segment number in the key's low byte), or
+// none (0) when sides is NULL.
+__global__ void k_post_records(const uint32_t* __restrict__ postings, const unsigned long long* __restrict__ keys,
+                               uint64_t n, uint32_t first, int tau, const ulonglong2* __restrict__ sides,
                                PostRec* __restrict__ recs) {
   for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t sid = postings[k];
-    PostRec r;
-    r.sig = sbm[sid];
-    r.sig.w[3] = sid;
-    recs[k] = r;
+    if (!sides) {
+      recs[k] = make_rec(sid, 0ull, 0ull);
+      continue;
+    }
+    const int i = (int)(keys[k] & 0xFFu);
+    const ulonglong2 sd = sides[(uint64_t)(sid - first) * (tau + 1) + i - 1];
+    recs[k] = make_rec(sid, sd.x, sd.y);
   }
 }
 
@@ -451,6 +498,9 @@ void build_store(pj_index& idx, const pj_strings& S) {
 // per slot instead of 1 (long strings: 6% faster probes at tau = 32; medium
 // ones: 3% slower with the larger table).
 constexpr uint64_t PRESENCE2_MIN_AVG_LEN = 256;
+// Indexes of strings longer than this on average are verified whole-pair by
+// default (PJ_VERIFY_AUTO) and build no side signatures.
+constexpr uint64_t SIDES_MAX_AVG_LEN = 256;
 
 void check_partition(const Ctx& c, const Partition& part);
 
@@ -538,9 +588,23 @@ void build_partition(pj_index& idx, int tau, Partition& part) {
   c.sync();
   if (h_err) fail(PJ_ECUDA, "segment table insertion failed");
   part.precs.reset(c, nrec);
-  k_post_records<<<std::min<unsigned>(ceil_div(nrec, 256), sm_grid_cap(16)), 256, 0, c.stream>>>(
-      part.postings.p, nrec, idx.sbm.p, part.precs.p);
-  PJ_LAUNCHED("k_post_records");
+  // Side signatures serve the extension screen; indexes of long strings are
+  // verified whole-pair by default, and their records skip them.
+  part.sides = !(idx.n && idx.total_bytes > SIDES_MAX_AVG_LEN * idx.n);
+  if (!part.sides) {
+    k_post_records<<<std::min<unsigned>(ceil_div(nrec, 256), sm_grid_cap(16)), 256, 0, c.stream>>>(
+        part.postings.p, keys.p, nrec, part.first, tau, nullptr, part.precs.p);
+    PJ_LAUNCHED("k_post_records");
+  } else {
+    DBuf<ulonglong2> sides(c, nrec);
+    const uint32_t np = idx.n - part.first;
+    k_side_sigs<<<std::min<unsigned>(ceil_div(np, 128), sm_grid_cap(16)), 128, 0, c.stream>>>(
+        idx.sbytes.p, idx.soff.p, idx.slen.p, part.first, idx.n, tau, sides.p);
+    PJ_LAUNCHED("k_side_sigs");
+    k_post_records<<<std::min<unsigned>(ceil_div(nrec, 256), sm_grid_cap(16)), 256, 0, c.stream>>>(
+        part.postings.p, keys.p, nrec, part.first, tau, sides.p, part.precs.p);
+    PJ_LAUNCHED("k_post_records");
+  }
   trace_mark(c, "partition: table");
   if (getenv("PJ_CHECK_INDEX")) check_partition(c, part);
   if (getenv("PJ_DEBUG_DUMP")) {

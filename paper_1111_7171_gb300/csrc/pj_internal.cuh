@@ -312,15 +312,68 @@ __host__ __device__ __forceinline__ int table_find(const Slot* __restrict__ t, c
   return -1;
 }
 
-// What the screen in front of verification needs about one posting, stored
-// beside the postings in the same order so that the candidates of a run are
-// read as one coalesced 16-byte stream: the sid and the string's character
-// signature (char_signature, whose unused word w[3] holds the sid).
+// Side signatures, for the screen in front of extension verification.
+// Extension verification (Sec. 5.2, Alg. 3) accepts a match of segment i
+// only if ED(s_l, r_l) <= i - 1 and ED(s_r, r_r) <= tau + 1 - i, where s_l,
+// r_l are the parts left of the matched substring and segment, and s_r, r_r
+// the parts right of them.  The character-count bound above holds for each
+// side on its own, with thresholds that add up to tau, so testing the two
+// sides rejects far more matches than testing the whole strings.  A side
+// signature is a 48-bit thermometer code: characters fall into SIDE_BUCKETS
+// = 12 buckets (c mod 12), bucket b owns bits 4b .. 4b+3, of which the lowest
+// min(count_b, 4) are set; the bound of two sides is the larger of the two
+// popcounts of x & ~y and y & ~x.
+constexpr int SIDE_BUCKETS = 12;
+
+__host__ __device__ __forceinline__ unsigned long long side_signature(const uint8_t* p, int n) {
+  unsigned long long t = 0;
+  for (int k = 0; k < n; ++k) {
+    const int sh = 4 * (int)(p[k] % SIDE_BUCKETS);
+    const unsigned long long field = (t >> sh) & 15ull;  // 0, 1, 3, 7 or 15
+    if (field != 15ull) t |= (field + 1ull) << sh;       // set the next bit
+  }
+  return t;
+}
+
+__host__ __device__ __forceinline__ int popcount64(unsigned long long x) {
+#ifdef __CUDA_ARCH__
+  return __popcll(x);
+#else
+  return __builtin_popcountll(x);
+#endif
+}
+
+__host__ __device__ __forceinline__ int side_bound(unsigned long long x, unsigned long long y) {
+  const int a = popcount64(x & ~y), b = popcount64(y & ~x);
+  return a > b ? a : b;
+}
+
+// What the screen in front of extension verification needs about one
+// posting, stored beside the postings in the same order so that the
+// candidates of a run are read as one coalesced 16-byte stream: the sid and
+// the side signatures of the indexed string around the posting's segment
+// (48 bits left of it in w[0] and the low half of w[1], 48 bits right of it
+// in the high half of w[1] and w[2]).
 struct __align__(16) PostRec {
-  Sig sig;  // sig.w[3] = sid
+  uint32_t sid;
+  uint32_t w[3];
 };
 
-__host__ __device__ __forceinline__ uint32_t rec_sid(const PostRec& r) { return r.sig.w[3]; }
+__host__ __device__ __forceinline__ uint32_t rec_sid(const PostRec& r) { return r.sid; }
+__host__ __device__ __forceinline__ unsigned long long rec_left(const PostRec& r) {
+  return (unsigned long long)r.w[0] | ((unsigned long long)(r.w[1] & 0xFFFFu) << 32);
+}
+__host__ __device__ __forceinline__ unsigned long long rec_right(const PostRec& r) {
+  return (unsigned long long)(r.w[1] >> 16) | ((unsigned long long)r.w[2] << 16);
+}
+__host__ __device__ __forceinline__ PostRec make_rec(uint32_t sid, unsigned long long left, unsigned long long right) {
+  PostRec r;
+  r.sid = sid;
+  r.w[0] = (uint32_t)left;
+  r.w[1] = (uint32_t)((left >> 32) & 0xFFFFu) | (uint32_t)((right & 0xFFFFu) << 16);
+  r.w[2] = (uint32_t)(right >> 16);
+  return r;
+}
 
 // One threshold's segment index.
 struct Partition {
@@ -333,6 +386,8 @@ struct Partition {
   unsigned presence_bytes = 1;  // bitmap bytes per slot (2 for indexes of long strings)
   DBuf<uint32_t> postings;   // sids, runs in key order, ascending inside a run
   DBuf<PostRec> precs;       // one record per posting, same order
+  bool sides = false;        // the records carry side signatures (else 0): indexes of strings that
+                             // are verified by extension verification by default
   // group visiting order for one probe: the (length, segment) groups sorted
   // by window size, widest first; [0] for R != S probes, [1] for the self join
   DBuf<uint16_t> gorder[2];

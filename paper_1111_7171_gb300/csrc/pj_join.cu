@@ -264,7 +264,14 @@ __global__ void __launch_bounds__(BLOCK) k_group_hits(const ProbeView v, unsigne
         m &= m - 1;
         uint32_t b;
         const uint32_t c = lookup_key(vt, SELF, q, ls, l, seg_key(s + p, li, l, i), b, err);
-        if (c) hits[pos++] = Hit{q, b, c, (uint32_t)p | ((uint32_t)i << 16) | tau_tag};
+        if (c) {
+          Hit hh{q, b, c, (uint32_t)p | ((uint32_t)i << 16) | tau_tag, 0ull, 0ull};
+          if (vt.hit_sides) {
+            hh.sl = side_signature(s, p);
+            hh.sr = side_signature(s + p + li, ls - p - li);
+          }
+          hits[pos++] = hh;
+        }
       }
     }
   }
@@ -371,83 +378,46 @@ __global__ void __launch_bounds__(512) k_verify_hits(const ProbeView v, const Hi
   if (err) atomicOr(&ctr->err, (unsigned long long)err);
 }
 
-// The same verification with a screen and a per-warp queue.  Each warp owns
-// one contiguous range of candidates (the launch's candidates split evenly
-// over the warps, in steps of 32 * S_RUN) and walks it step by step: in a
-// step, lane l screens candidates base + l + 32 k (k < S_RUN) -- valid sid,
-// not the probe itself, character-count bound -- so that every load of a
-// posting record is one coalesced 512-byte request for the warp.  Every lane
-// tracks the hit of its own candidates as they advance (hits are in candidate
-// order), so a warp searches the candidate offsets only once, at the start
-// of its range.  One warp scan of the lanes' survivor counts places the
-// survivors in a queue in shared memory, each with its probe, sid and
-// (position, segment, threshold); while 32 or more are queued, each lane
-// takes one and runs extension verification.  Screened-out candidates cost
-// no DP slot, so the warps' DP lanes stay full.  The scan and the queue loop
-// run the same number of times in all 32 lanes, and queue entries are read
-// before the next writes only after a __syncwarp.
+// The same verification with a screen and a per-warp queue.  The candidates
+// are dealt to the warps round robin in chunks of Q_CHUNK; a warp walks a
+// chunk in steps of 32 * S_RUN: in a step, lane l screens candidates base +
+// l + 32 k (k < S_RUN) -- valid sid, not the probe itself, the side bounds
+// of the extension screen -- so that every load of a posting record is one
+// coalesced 512-byte request for the warp.  The warp searches the candidate
+// offsets once per chunk; after that, every lane walks from hit to hit on its
+// own as its candidates advance (hits are in candidate order).  Chunks of a
+// few thousand candidates keep the warps' loads even: survivors and their
+// DP work cluster in places.  Survivors enter a queue in shared memory (one ballot per
+// 32 candidates), each with its probe, sid and (position, segment,
+// threshold); while 32 or more are queued, each lane takes one and runs
+// extension verification.  Screened-out candidates cost no DP slot, so the
+// warps' DP lanes stay full.  The ballots and the queue loop run the same
+// number of times in all 32 lanes, and queue entries are read before the
+// next writes only after a __syncwarp.
 constexpr int Q_BLOCK = 256;
 constexpr int Q_WARPS = Q_BLOCK / 32;
 constexpr int S_RUN = 8;                 // candidates one lane screens per step
 constexpr int Q_CAP = 32 * S_RUN + 32;   // < 32 left + up to 32 * S_RUN new
+constexpr unsigned long long Q_CHUNK = 8ull * 32 * S_RUN;  // candidates a warp takes at a time
 
-// One lane's position in the hits: hit h covers the candidates below c_hi
-// (from the previous hit's c_hi on); candidate c of it is posting
-// rec_base + c (mod 2^32: posting indices are 32-bit).
+// One lane's hit: index h, its posting for candidate c is rec_base + c
+// (mod 2^32: posting indices are 32-bit), and what the screen needs of it.
 struct LaneHit {
   uint32_t h;
-  unsigned long long c_hi;
   uint32_t rec_base;
   uint32_t q, pi;
-  uint32_t sig[3];
+  unsigned long long sl, sr;  // the probe's side signatures around the match
 };
 
-__device__ __forceinline__ void lane_hit_set(const ProbeView& v, const Hit* __restrict__ hits,
-                                             unsigned long long c_lo, LaneHit& lh) {
-  const Hit hit = hits[lh.h];
+__device__ __forceinline__ void lane_hit_set(const Hit* __restrict__ hits, uint32_t h, unsigned long long c_lo,
+                                             LaneHit& lh) {
+  const Hit hit = hits[h];
+  lh.h = h;
   lh.rec_base = hit.begin - (uint32_t)c_lo;
   lh.q = hit.q;
   lh.pi = hit.pi;
-  if (v.pbm) {
-    const Sig g = v.pbm[hit.q];
-    lh.sig[0] = g.w[0];
-    lh.sig[1] = g.w[1];
-    lh.sig[2] = g.w[2];
-  }
-}
-
-__device__ __forceinline__ void lane_hit_load(const ProbeView& v, const Hit* __restrict__ hits,
-                                              const unsigned long long* __restrict__ cand_off,
-                                              unsigned long long n_hits, unsigned long long n_cand,
-                                              unsigned long long h, LaneHit& lh) {
-  lh.h = (uint32_t)h;
-  lh.c_hi = h + 1 < n_hits ? cand_off[h + 1] : n_cand;
-  lane_hit_set(v, hits, cand_off[h], lh);
-}
-
-// Advance lh to the hit of candidate c (c at or after the current hit's first).
-__device__ __forceinline__ void lane_hit_advance(const ProbeView& v, const Hit* __restrict__ hits,
-                                                 const unsigned long long* __restrict__ cand_off,
-                                                 unsigned long long n_hits, unsigned long long n_cand,
-                                                 unsigned long long c, LaneHit& lh) {
-  if (c < lh.c_hi) return;
-  unsigned long long c_lo;
-  do {
-    ++lh.h;
-    c_lo = lh.c_hi;
-    lh.c_hi = (unsigned long long)lh.h + 1 < n_hits ? cand_off[lh.h + 1] : n_cand;
-  } while (c >= lh.c_hi);
-  lane_hit_set(v, hits, c_lo, lh);
-}
-
-__device__ __forceinline__ int signature_bound3(const uint32_t (&x)[3], const Sig& y) {
-  int a = 0, b = 0;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    a += __popc(x[k] & ~y.w[k]);
-    b += __popc(y.w[k] & ~x[k]);
-  }
-  return a > b ? a : b;
+  lh.sl = hit.sl;
+  lh.sr = hit.sr;
 }
 
 // Extension verification of one queue entry: probe q, indexed sid r, and
@@ -499,36 +469,53 @@ __global__ void __launch_bounds__(Q_BLOCK) k_verify_queued(const ProbeView v, co
   const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const unsigned long long n_warps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
   const unsigned long long span = 32ull * S_RUN;
-  // this warp's range [r0, r1): the candidates split evenly, in whole steps
-  const unsigned long long total = n_cand > c_begin ? n_cand - c_begin : 0;
-  const unsigned long long per_warp = ((total + n_warps - 1) / n_warps + span - 1) / span * span;
-  const unsigned long long r0 = c_begin + min(total, warp * per_warp);
-  const unsigned long long r1 = c_begin + min(total, (warp + 1) * per_warp);
   int qn = 0;  // the same in every lane
-  if (r0 < r1) {
-    LaneHit lh;
+  LaneHit lh;
+  lh.h = UINT32_MAX;
+  // chunks of Q_CHUNK candidates, dealt to the warps round robin
+  for (unsigned long long r0 = c_begin + warp * Q_CHUNK; r0 < n_cand; r0 += n_warps * Q_CHUNK) {
+    const unsigned long long r1 = min(n_cand, r0 + Q_CHUNK);
+    // each lane's hit: its first candidate's, found by a warp search; then
+    // every lane walks forward on its own as its candidates advance
+    unsigned long long l_hi;  // first candidate after the lane's hit
     {
-      const unsigned long long c = min(r0 + lane, r1 - 1);
-      lane_hit_load(v, hits, cand_off, n_hits, n_cand,
-                    lane_hit_of(cand_off, n_hits, warp_hit_of(cand_off, n_hits, r0), r0, c), lh);
+      const unsigned long long cf = min(r0 + lane, r1 - 1);
+      const unsigned long long h = lane_hit_of(cand_off, n_hits, warp_hit_of(cand_off, n_hits, r0), r0, cf);
+      lane_hit_set(hits, (uint32_t)h, cand_off[h], lh);
+      l_hi = h + 1 < n_hits ? cand_off[h + 1] : n_cand;
     }
     for (unsigned long long base = r0; base < r1; base += span) {
       // screen; each survivor goes straight into the queue (one ballot per 32)
 #pragma unroll
       for (int k = 0; k < S_RUN; ++k) {
-        const unsigned long long c = base + lane + 32ull * k;
+        const unsigned long long c0 = base + 32ull * k;
+        if (c0 >= r1) break;  // the same in every lane
+        const unsigned long long c = c0 + lane;
         bool pass = false;
         uint32_t r = 0;
         if (c < r1) {
-          lane_hit_advance(v, hits, cand_off, n_hits, n_cand, c, lh);
+          if (c >= l_hi) {  // into a later hit: walk to it
+            unsigned long long h = lh.h, lo;
+            do {
+              ++h;
+              lo = l_hi;
+              l_hi = h + 1 < n_hits ? cand_off[h + 1] : n_cand;
+            } while (c >= l_hi);
+            lane_hit_set(hits, (uint32_t)h, lo, lh);
+          }
           const ProbeView vt = MULTI ? view_for_tau(v, (int)(lh.pi >> 24)) : v;
           const PostRec rec = vt.precs[lh.rec_base + (uint32_t)c];
           r = rec_sid(rec);
           if (r >= vt.n_index) {
             err |= 1;
           } else if (!(SELF && r == lh.q)) {
-            if (v.pbm && signature_bound3(lh.sig, rec.sig) > vt.tau) ++filtered;
-            else pass = true;
+            // the side bounds against the two sides' thresholds i - 1 and tau + 1 - i
+            const int i = (int)((lh.pi >> 16) & 0xFFu);
+            if (v.pbm && v.hit_sides && (side_bound(lh.sl, rec_left(rec)) > i - 1 ||
+                          side_bound(lh.sr, rec_right(rec)) > vt.tau + 1 - i))
+              ++filtered;
+            else
+              pass = true;
           }
         }
         const unsigned b = __ballot_sync(FULL, pass);
@@ -1631,6 +1618,7 @@ static ProbeView index_side(const pj_index& idx, const Partition& part) {
   v.block_warp = 256;
   const char* vq = getenv("PJ_VERIFY_QUEUE");
   v.queued = vq && vq[0] ? atoi(vq) : 1;
+  v.hit_sides = v.queued && part.sides;  // off for mode L, which verifies whole strings
   v.ibytes = idx.sbytes.p;
   v.ioff = idx.soff.p;
   v.ilen = idx.slen.p;
@@ -2027,6 +2015,7 @@ static void self_join_impl(pj_index& idx, int tau, pj_result* out, bool on_devic
   v.block_thread = tr.block_thread;
   v.pair_mode = tr.pair_mode;
   v.pair_warp = tr.pair_warp;
+  if (v.pair_mode) v.hit_sides = 0;
   if (idx.graph_joins && whole) {
     if (idx.self_plans.size() < idx.parts.size()) idx.self_plans.resize(idx.parts.size());
     SelfPlan* sp = static_cast<SelfPlan*>(idx.self_plans[tau].get());
@@ -2095,6 +2084,7 @@ static void probe_join_impl(const Ctx& c, const pj_index& idx, const Partition& 
   force_mode(idx, mode);
   v.pair_mode = mode.pair_mode;
   v.pair_warp = mode.pair_warp;
+  if (v.pair_mode) v.hit_sides = 0;
   const bool has_short = part.first > 0;  // indexed strings too short to partition
   run_join(c, v, false, has_short ? R.n : 0, bits_for(R.n), on_device, out);
   out->stats.verify_mode = mode.pair_mode ? PJ_VERIFY_PAIRS : PJ_VERIFY_EXTENSION;

@@ -15,12 +15,16 @@
 namespace pj {
 
 // A lookup with a non-empty posting run.  pi = p | (i << 16) | (tau << 24);
-// the tau byte is used by multi-threshold batches only.
-struct Hit {
+// the tau byte is used by multi-threshold batches only.  sl and sr are the
+// side signatures (side_signature) of the probe left of the selected
+// substring, s[0, p), and right of it, s[p + l_i, |s|), for the screen in
+// front of extension verification.
+struct __align__(16) Hit {
   uint32_t q;
   uint32_t begin;
   uint32_t count;
   uint32_t pi;
+  unsigned long long sl, sr;
 };
 
 // One threshold's segment index, as seen by the kernels.
@@ -81,6 +85,7 @@ struct ProbeView {
   const Sig* pbm;
   const Sig* ibm;
   int queued;     // thread-per-candidate verification with a screen and per-warp queues
+  int hit_sides;  // hits carry the probe's side signatures (Hit::sl, sr) and the queued screen tests them
   int pair_mode;  // 1: mode L (distinct candidate pairs verified once over the whole strings)
   int pair_warp;  // mode L: one warp per pair instead of one thread
   int block_warp;    // block size of the warp-per-candidate verification

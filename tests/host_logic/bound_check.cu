@@ -1,5 +1,6 @@
-// Host-side check of the character-count bound used before verification
-// (signature_bound of char_signature, pj_internal.cuh): it never exceeds the
+// Host-side check of the character-count bounds used before verification
+// (signature_bound of char_signature, and side_bound of side_signature for
+// the parts around a match, pj_internal.cuh): they never exceed the
 // edit distance of Def. 1 (plain Wagner-Fischer DP), on random strings over
 // small alphabets, over all 256 byte values (buckets shared by c and
 // c + 24k) and with runs of repeated characters (saturated counts), and it
@@ -26,7 +27,7 @@ static int ed(const std::string& a, const std::string& b) {
 
 int main() {
   std::mt19937 g(7);
-  long bad = 0, tight = 0;
+  long bad = 0, tight = 0, side_tight = 0;
   const int alpha[] = {2, 5, 27, 64, 200, 256};
   for (int A : alpha)
     for (int it = 0; it < 40000; ++it) {
@@ -42,6 +43,14 @@ int main() {
         if (bad < 5) printf("A=%d bound %d > ed %d\n", A, bound, d);
         ++bad;
       }
+      // the side signatures of the extension screen (12 buckets, counts capped at 4)
+      const int sbound = pj::side_bound(pj::side_signature((const uint8_t*)a.data(), la),
+                                        pj::side_signature((const uint8_t*)b.data(), (int)b.size()));
+      if (sbound > d) {
+        if (bad < 5) printf("A=%d side bound %d > ed %d\n", A, sbound, d);
+        ++bad;
+      }
+      side_tight += sbound == d && d > 0;
       tight += bound == d && d > 0;
     }
   // substituting k characters by characters the string lacks: bound = ED = k
@@ -52,6 +61,7 @@ int main() {
                                           pj::char_signature((const uint8_t*)b.data(), 10));
     if (bound != k || ed(a, b) != k) ++bad;
   }
+  printf("side_tight=%ld\n", side_tight);
   printf("bad=%ld tight=%ld\n", bad, tight);
   return 0;
 }
