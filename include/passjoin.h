@@ -220,7 +220,8 @@ int pj_self_join_shard(pj_index* idx, int tau, uint32_t shard, uint32_t n_shards
  * pj_self_join_stream -- Def. 1 with R = S for a set that is never held on
  * the device as a whole.  When strings are visited by length (Alg. 1), a
  * string of length |s| probes only the inverted lists of lengths |s| - tau
- * .. |s| (Sec. 3.2).  So the strings, ordered by (length, id) on the host,
+ * .. |s| (Sec. 3.2).  So the strings, ordered on the host as the store orders
+ * them (by length, then first eight bytes, then id),
  * are cut into windows of consecutive probing strings; a window's device set
  * is its probing strings plus the strings before them whose length is at
  * least its first probe's length - tau.  Each window builds a temporary store

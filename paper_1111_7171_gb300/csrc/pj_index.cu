@@ -1,9 +1,10 @@
 // Packed string store and segment index (the build half of the hot path).
 //
-//   A1  lengths + validation, stable counting order by length (radix sort of
-//       (length, id)), offsets by prefix sum, warp-per-string gather of the
-//       bytes into sid order, length buckets (Sec. 3.2 groups S_l; the
-//       sort by length that Alg. 1 starts with).
+//   A1  lengths + validation, the sid order (stable radix sorts by the
+//       first eight bytes, then by length: by length, then first eight
+//       bytes, then id), offsets by prefix sum, warp-per-string gather of
+//       the bytes into sid order, length buckets (Sec. 3.2 groups S_l; the
+//       sort by length, then alphabetically, that Alg. 1 starts with).
 //   A2  even partition of every string of length >= tau+1 into tau+1
 //       segments and one (key, sid) record per segment (Sec. 3.1).
 //   A3  records sorted by key -> runs = inverted lists L_l^i(w) (Sec. 3.2),
@@ -177,6 +178,27 @@ void debug_dump(const Ctx& c, const char* name, const void* dev, size_t bytes) {
 // ---------------------------------------------------------------- A1 ------
 
 namespace {
+
+// Sort key of input string k: its first eight bytes, first byte highest,
+// zero-padded (so that a stable sort by it, then by length, orders each
+// length's strings alphabetically by their first eight bytes, ties by id).
+__global__ void k_prefix_keys(const uint8_t* __restrict__ bytes, const uint64_t* __restrict__ off, uint32_t n,
+                              unsigned long long* __restrict__ keys) {
+  const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const uint64_t a = off[k];
+  const uint64_t len = off[k + 1] - a;
+  unsigned long long key = 0;
+  for (int j = 0; j < 8; ++j) key = (key << 8) | (j < (int)len ? bytes[a + j] : 0u);
+  keys[k] = key;
+}
+
+// Lengths in the current order of ids: len[j] = |string ids[j]|.
+__global__ void k_lengths_of(const uint64_t* __restrict__ off, const uint32_t* __restrict__ ids, uint32_t n,
+                             uint32_t* __restrict__ len) {
+  const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) len[j] = (uint32_t)(off[ids[j] + 1] - off[ids[j]]);
+}
 
 __global__ void k_lengths(const uint64_t* __restrict__ off, uint32_t n, uint32_t* __restrict__ len,
                           uint32_t* __restrict__ ids, int* __restrict__ err, unsigned* __restrict__ lmax) {
@@ -449,7 +471,20 @@ void build_store(pj_index& idx, const pj_strings& S) {
   if (h_err) fail(PJ_EINVAL, "pj_strings: offsets decrease or a string is longer than 65535 bytes");
   idx.lmax = (int)h_lmax;
 
-  // stable order by length (ties keep input order)
+  // sid order: by length, then by the first eight bytes, then by id -- a
+  // fixed order within each length, as Alg. 1's "visited before" needs; the
+  // paper visits alphabetically (Sec. 3.2), and near-alphabetical order puts
+  // strings with long common prefixes next to each other, which the
+  // whole-pair verification exploits (shared prefixes, Sec. 5.3).  Two
+  // stable radix sorts: by the prefix key, then by length.
+  if (n) {
+    DBuf<unsigned long long> pkey(c, n);
+    k_prefix_keys<<<ceil_div(n, 256), 256, 0, c.stream>>>(in_bytes, in_off, n, pkey.p);
+    PJ_LAUNCHED("k_prefix_keys");
+    radix_sort_pairs<unsigned long long>(c, pkey.p, idx.perm.p, n, 64);
+    k_lengths_of<<<ceil_div(n, 256), 256, 0, c.stream>>>(in_off, idx.perm.p, n, idx.slen.p);
+    PJ_LAUNCHED("k_lengths_of");
+  }
   radix_sort_pairs<uint32_t>(c, idx.slen.p, idx.perm.p, n, bits_for((uint64_t)idx.lmax + 1));
   trace_mark(c, "build: lengths + sort");
 

@@ -1,7 +1,9 @@
 // Internal data layout of the GB300 Pass-Join index.
 //
-// Strings live in HBM in "sorted-id" (sid) order: ascending length, ties by
-// input id.  Strings of one length l therefore occupy the contiguous sid
+// Strings live in HBM in "sorted-id" (sid) order: ascending length, then
+// ascending first eight bytes (first byte highest, zero-padded), then input
+// id -- close to the alphabetical order Alg. 1 visits in, so that strings
+// with long common prefixes are neighbours.  Strings of one length l occupy the contiguous sid
 // range [bbeg[l], bbeg[l+1]), which is the paper's group S_l (Sec. 3.2), and
 // "visited before" in the self join (Alg. 1: by length, then a fixed order)
 // becomes plain sid order.

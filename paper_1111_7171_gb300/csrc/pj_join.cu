@@ -691,34 +691,154 @@ __device__ __forceinline__ void append_match(Counters* ctr, const AccOut& out, u
   }
 }
 
-// One thread per distinct pair.
+// Shared prefixes (Sec. 5.3).  Distinct pairs are sorted by (probe, indexed
+// sid), and sids order each length's strings by their first eight bytes, so
+// consecutive pairs of one probe whose indexed strings have the same length
+// often share a prefix.  A verifier (thread or warp) then takes a run of
+// consecutive pairs and keeps one band state across them: with the rows over
+// the indexed string r, rows 1..c of two r's sharing their first c
+// characters are identical.  Before each pair it computes c against the
+// string whose band it holds; if that string was stopped by Lemma 4 at a row
+// e <= c, this pair stops there too (same rows, same lengths); if the band
+// was kept at a row <= c, the scan resumes after it.  The row kept is the
+// common prefix with the next pair of the group.  Verifiers take the groups
+// round robin, and most groups are single pairs, so the load stays spread.
+// Enabled by PJ_SHARE_PREFIX=1 (off by default: on the synthetic workloads
+// consecutive pairs of a probe rarely share a prefix of the same length).
+constexpr int PAIR_RUN = 64;  // longest group of consecutive pairs one verifier takes
+
+// The band state a verifier keeps between consecutive pairs.
+struct KeptBand {
+  uint32_t x = UINT32_MAX;    // probe of the pair that owns it
+  int len = -1;               // length of its indexed string
+  const uint8_t* r = nullptr; // its indexed string
+  int row = 0;                // row after which the band was kept (0: none)
+  int dead = 0;               // row at which Lemma 4 stopped it (0: ran to the end)
+};
+
+// A distinct pair with its strings (x: probe side, y: index side).
+struct PairView {
+  uint32_t x, y;
+  const uint8_t *sx, *sy;
+  int lx, ly;
+};
+
+__device__ __forceinline__ bool pair_view(const ProbeView& v, bool self, const unsigned long long* ukeys,
+                                          unsigned long long n, unsigned long long u, int pshift, PairView& p) {
+  if (u >= n) return false;
+  const unsigned long long key = ukeys[u];
+  if (key == NO_PAIR) return false;
+  pair_strings(v, self, key, pshift, p.x, p.y, p.sx, p.lx, p.sy, p.ly);
+  return true;
+}
+
+// Consecutive pairs whose rows can be shared: the same probe, indexed
+// strings of the same length, no longer than the probe (the rows run over
+// the shorter string).
+__device__ __forceinline__ bool same_group(const PairView& a, const PairView& b) {
+  return a.x == b.x && a.ly == b.ly && a.ly <= a.lx;
+}
+
+// One thread per distinct pair, or (v.share_prefix) one thread per group of
+// consecutive pairs that can share rows (same probe, indexed strings of one
+// length; at most PAIR_RUN, groups split at multiples of PAIR_RUN), the
+// band kept across them.
 template <int MAXW, bool SELF>
 __global__ void __launch_bounds__(BLOCK) k_verify_pairs(const ProbeView v, const unsigned long long* __restrict__ ukeys,
                                                         unsigned long long n, int pshift, AccOut out, Counters* ctr,
                                                         const unsigned long long* __restrict__ n_dev) {
   n = dev_count(n, n_dev);
   unsigned long long cells = 0, filtered = 0;
-  for (unsigned long long u = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; u < n;
-       u += (unsigned long long)gridDim.x * blockDim.x) {
-    const unsigned long long key = ukeys[u];
-    if (key == NO_PAIR) continue;
-    uint32_t x, y;
-    const uint8_t *sx, *sy;
-    int lx, ly;
-    pair_strings(v, SELF, key, pshift, x, y, sx, lx, sy, ly);
-    if (v.pbm && signature_bound(v.pbm[x], v.ibm[y]) > v.tau) {
-      ++filtered;
-      continue;
+  if (!v.share_prefix) {
+    for (unsigned long long u = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; u < n;
+         u += (unsigned long long)gridDim.x * blockDim.x) {
+      const unsigned long long key = ukeys[u];
+      if (key == NO_PAIR) continue;
+      uint32_t x, y;
+      const uint8_t *sx, *sy;
+      int lx, ly;
+      pair_strings(v, SELF, key, pshift, x, y, sx, lx, sy, ly);
+      if (v.pbm && signature_bound(v.pbm[x], v.ibm[y]) > v.tau) {
+        ++filtered;
+        continue;
+      }
+      const int d = vsp<MAXW>(sx, lx, sy, ly, v.tau, cells);
+      if (d <= v.tau) append_match(ctr, out, pair_out_key(v, SELF, x, y), d);
     }
-    const int d = vsp<MAXW>(sx, lx, sy, ly, v.tau, cells);
-    if (d <= v.tau) append_match(ctr, out, pair_out_key(v, SELF, x, y), d);
+  } else {
+    for (unsigned long long u = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; u < n;
+         u += (unsigned long long)gridDim.x * blockDim.x) {
+      PairView cur;
+      if (!pair_view(v, SELF, ukeys, n, u, pshift, cur)) continue;
+      if (u % PAIR_RUN != 0) {  // inside a group that an earlier position starts
+        PairView prev;
+        if (pair_view(v, SELF, ukeys, n, u - 1, pshift, prev) && same_group(prev, cur)) continue;
+      }
+      KeptBand kb;
+      int V[MAXW], snap[MAXW];
+      for (unsigned long long w = u;;) {
+        PairView nxt;
+        const bool more = w + 1 < n && (w + 1) % PAIR_RUN != 0 && pair_view(v, SELF, ukeys, n, w + 1, pshift, nxt) &&
+                          same_group(cur, nxt);
+        if (v.pbm && signature_bound(v.pbm[cur.x], v.ibm[cur.y]) > v.tau) {
+          ++filtered;
+        } else if (cur.ly > cur.lx) {  // rows over the shorter string: nothing to share
+          const int d = vsp<MAXW>(cur.sx, cur.lx, cur.sy, cur.ly, v.tau, cells);
+          if (d <= v.tau) append_match(ctr, out, pair_out_key(v, SELF, cur.x, cur.y), d);
+        } else if (cur.lx - cur.ly <= v.tau) {
+          const int keep = more ? common_prefix(cur.sy, nxt.sy, cur.ly) : 0;
+          int start = 0, d = v.tau + 1, dead = 0;
+          bool skip = false;
+          if (kb.x == cur.x && kb.len == cur.ly) {
+            const int c = common_prefix(cur.sy, kb.r, cur.ly);
+            if (kb.dead && c >= kb.dead) {
+              skip = true;  // the same rows stop the scan at the same row
+            } else if (kb.row && c >= kb.row) {
+              start = kb.row;
+#pragma unroll
+              for (int k = 0; k < MAXW; ++k) V[k] = snap[k];
+            }
+          }
+          if (!skip) {
+            d = vsp_rows<MAXW>(cur.sy, cur.ly, cur.sx, cur.lx, v.tau, start, V, keep, snap, dead, cells);
+            kb.x = cur.x;
+            kb.len = cur.ly;
+            kb.r = cur.sy;
+            kb.row = keep > start ? (!dead || dead >= keep ? keep : 0) : (keep == start ? start : 0);
+            kb.dead = dead;
+          }
+          if (d <= v.tau) append_match(ctr, out, pair_out_key(v, SELF, cur.x, cur.y), d);
+        }
+        if (!more) break;
+        ++w;
+        cur = nxt;
+      }
+    }
   }
   add_counter(&ctr->cells, cells);
   add_counter(&ctr->filtered, filtered);
 }
 
+// Length of the common prefix of a and b (n bytes at most), by the whole
+// warp; every lane must call it with the same arguments.
+__device__ __forceinline__ int warp_common_prefix(const uint8_t* a, const uint8_t* b, int n) {
+  const int lane = threadIdx.x & 31;
+  int res = n;
+  for (int k = 0; k < n; k += 32) {
+    const int j = k + lane;
+    const unsigned m = __ballot_sync(FULL, j < n && a[j] != b[j]);
+    if (m) {
+      res = k + __ffs((int)m) - 1;
+      break;
+    }
+  }
+  return res;
+}
+
 // One warp per distinct pair (long strings): the shuffle-scan band of
-// vsp_warp; every lane runs the same code on the same pair.
+// vsp_warp; every lane runs the same code on the same pair.  With
+// v.share_prefix, one warp per group of pairs that can share rows (as
+// k_verify_pairs), the band kept across them (vsp_warp_rows).
 template <bool SELF>
 __global__ void __launch_bounds__(BLOCK) k_verify_pairs_warp(const ProbeView v,
                                                              const unsigned long long* __restrict__ ukeys,
@@ -730,17 +850,68 @@ __global__ void __launch_bounds__(BLOCK) k_verify_pairs_warp(const ProbeView v,
   const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const unsigned long long n_warps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
   unsigned long long cells = 0;
-  for (unsigned long long u = warp; u < n; u += n_warps) {
-    __syncwarp();
-    const unsigned long long key = ukeys[u];
-    if (key == NO_PAIR) continue;  // uniform across the warp
-    uint32_t x, y;
-    const uint8_t *sx, *sy;
-    int lx, ly;
-    pair_strings(v, SELF, key, pshift, x, y, sx, lx, sy, ly);
-    if (v.pbm && signature_bound(v.pbm[x], v.ibm[y]) > v.tau) continue;  // uniform across the warp
-    const int d = vsp_warp(sx, lx, sy, ly, v.tau, cells);
-    if (d <= v.tau && lane == 0) append_match(ctr, out, pair_out_key(v, SELF, x, y), d);
+  if (!v.share_prefix) {
+    for (unsigned long long u = warp; u < n; u += n_warps) {
+      __syncwarp();
+      const unsigned long long key = ukeys[u];
+      if (key == NO_PAIR) continue;  // uniform across the warp
+      uint32_t x, y;
+      const uint8_t *sx, *sy;
+      int lx, ly;
+      pair_strings(v, SELF, key, pshift, x, y, sx, lx, sy, ly);
+      if (v.pbm && signature_bound(v.pbm[x], v.ibm[y]) > v.tau) continue;  // uniform across the warp
+      const int d = vsp_warp(sx, lx, sy, ly, v.tau, cells);
+      if (d <= v.tau && lane == 0) append_match(ctr, out, pair_out_key(v, SELF, x, y), d);
+    }
+  } else {
+    for (unsigned long long u = warp; u < n; u += n_warps) {
+      __syncwarp();
+      PairView cur;
+      if (!pair_view(v, SELF, ukeys, n, u, pshift, cur)) continue;  // uniform across the warp
+      if (u % PAIR_RUN != 0) {
+        PairView prev;
+        if (pair_view(v, SELF, ukeys, n, u - 1, pshift, prev) && same_group(prev, cur)) continue;  // uniform
+      }
+      KeptBand kb;
+      int V0 = 0, V1 = 0, S0 = 0, S1 = 0;
+      for (unsigned long long w = u;;) {
+        PairView nxt;
+        const bool more = w + 1 < n && (w + 1) % PAIR_RUN != 0 && pair_view(v, SELF, ukeys, n, w + 1, pshift, nxt) &&
+                          same_group(cur, nxt);
+        if (v.pbm && signature_bound(v.pbm[cur.x], v.ibm[cur.y]) > v.tau) {
+          // screened out (uniform across the warp)
+        } else if (cur.ly > cur.lx) {
+          const int d = vsp_warp(cur.sx, cur.lx, cur.sy, cur.ly, v.tau, cells);
+          if (d <= v.tau && lane == 0) append_match(ctr, out, pair_out_key(v, SELF, cur.x, cur.y), d);
+        } else if (cur.lx - cur.ly <= v.tau) {
+          const int keep = more ? warp_common_prefix(cur.sy, nxt.sy, cur.ly) : 0;
+          int start = 0, d = v.tau + 1, dead = 0;
+          bool skip = false;
+          if (kb.x == cur.x && kb.len == cur.ly) {
+            const int c = warp_common_prefix(cur.sy, kb.r, cur.ly);
+            if (kb.dead && c >= kb.dead) {
+              skip = true;
+            } else if (kb.row && c >= kb.row) {
+              start = kb.row;
+              V0 = S0;
+              V1 = S1;
+            }
+          }
+          if (!skip) {
+            d = vsp_warp_rows(cur.sy, cur.ly, cur.sx, cur.lx, v.tau, start, V0, V1, keep, S0, S1, dead, cells);
+            kb.x = cur.x;
+            kb.len = cur.ly;
+            kb.r = cur.sy;
+            kb.row = keep > start ? (!dead || dead >= keep ? keep : 0) : (keep == start ? start : 0);
+            kb.dead = dead;
+          }
+          if (d <= v.tau && lane == 0) append_match(ctr, out, pair_out_key(v, SELF, cur.x, cur.y), d);
+        }
+        if (!more) break;
+        ++w;
+        cur = nxt;
+      }
+    }
   }
   __syncwarp();
   if (lane == 0) add_counter(&ctr->cells, cells);
@@ -1619,6 +1790,10 @@ static ProbeView index_side(const pj_index& idx, const Partition& part) {
   const char* vq = getenv("PJ_VERIFY_QUEUE");
   v.queued = vq && vq[0] ? atoi(vq) : 1;
   v.hit_sides = v.queued && part.sides;  // off for mode L, which verifies whole strings
+  // shared prefixes in mode L: off unless PJ_SHARE_PREFIX=1 (on the
+  // synthetic workloads it saves under 2% of the DP cells and costs time)
+  const char* sp = getenv("PJ_SHARE_PREFIX");
+  v.share_prefix = sp && sp[0] ? atoi(sp) : 0;
   v.ibytes = idx.sbytes.p;
   v.ioff = idx.soff.p;
   v.ilen = idx.slen.p;

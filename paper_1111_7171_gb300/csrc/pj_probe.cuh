@@ -88,6 +88,7 @@ struct ProbeView {
   int hit_sides;  // hits carry the probe's side signatures (Hit::sl, sr) and the queued screen tests them
   int pair_mode;  // 1: mode L (distinct candidate pairs verified once over the whole strings)
   int pair_warp;  // mode L: one warp per pair instead of one thread
+  int share_prefix;  // mode L: consecutive pairs of a probe share the DP rows of common prefixes (Sec. 5.3)
   int block_warp;    // block size of the warp-per-candidate verification
 };
 

@@ -2,7 +2,7 @@
 // shard, and a set too large for the device joined window by window.
 //
 // Every similar pair of the self join is found by exactly one probe: the
-// later of its two strings in (length, id) order (Alg. 1 probes each string
+// later of its two strings in the store's sid order (Alg. 1 probes each string
 // against the strings visited before it).  Joins over disjoint ranges of
 // probing strings therefore return disjoint pair sets whose union is the
 // whole join.
@@ -33,7 +33,7 @@ namespace pj {
 namespace {
 
 struct Window {
-  uint32_t p0, p1;  // probing strings: positions p0 .. p1 - 1 of the (length, id) order
+  uint32_t p0, p1;  // probing strings: positions p0 .. p1 - 1 of the store order
 };
 
 // Device bytes a window's store, segment index and join scratch are expected
@@ -53,7 +53,8 @@ void self_join_stream(const pj_strings& S, int tau, const pj_options* opt, pj_re
   if (S.on_device) fail(PJ_EINVAL, "pj_self_join_stream: the strings must be in host memory");
   const uint32_t n = S.n;
   if (!S.offsets || (!S.bytes && n > 0)) fail(PJ_EINVAL, "pj_strings: NULL bytes or offsets");
-  // (length, id) order on the host: a stable counting sort by length
+  // (length, first eight bytes, id) order on the host, as the store orders
+  // strings: a stable counting sort by length, then a sort within each length
   std::vector<uint32_t> len(n);
   int lmax = 0;
   for (uint32_t k = 0; k < n; ++k) {
@@ -69,6 +70,27 @@ void self_join_stream(const pj_strings& S, int tau, const pj_options* opt, pj_re
   {
     std::vector<uint32_t> next(lbeg.begin(), lbeg.end() - 1);
     for (uint32_t k = 0; k < n; ++k) order[next[len[k]]++] = k;
+  }
+  // within each length, the store's order: by the first eight bytes (first
+  // byte highest, zero-padded), then by id -- so that every window's own
+  // store keeps the window's strings in this order and its probe range
+  // stays a range of its sids
+  {
+    auto prefix_key = [&](uint32_t id) {
+      unsigned long long key = 0;
+      const uint8_t* p = S.bytes + S.offsets[id];
+      for (uint32_t j = 0; j < 8; ++j) key = (key << 8) | (j < len[id] ? p[j] : 0u);
+      return key;
+    };
+    std::vector<std::pair<unsigned long long, uint32_t>> tmp;
+    for (int l = 0; l <= lmax; ++l) {
+      const uint32_t b = lbeg[l], e = lbeg[l + 1];
+      if (e - b < 2) continue;
+      tmp.clear();
+      for (uint32_t j = b; j < e; ++j) tmp.emplace_back(prefix_key(order[j]), order[j]);
+      std::sort(tmp.begin(), tmp.end());  // ties: ascending id
+      for (uint32_t j = b; j < e; ++j) order[j] = tmp[j - b].second;
+    }
   }
   std::vector<uint64_t> cum_bytes((size_t)n + 1, 0);
   for (uint32_t p = 0; p < n; ++p) {
@@ -114,7 +136,7 @@ void self_join_stream(const pj_strings& S, int tau, const pj_options* opt, pj_re
     todo.pop_front();
     const int l0 = (int)len_of[w.p0];
     const uint32_t d0 = lbeg[std::max(0, l0 - tau)];
-    // the window's strings in (length, id) order, as one host string set
+    // the window's strings in the store order, as one host string set
     const uint32_t nd = w.p1 - d0;
     hbytes.resize(std::max<uint64_t>(1, cum_bytes[w.p1] - cum_bytes[d0]));
     hoff.assign((size_t)nd + 1, 0);

@@ -289,6 +289,86 @@ __host__ __device__ __forceinline__ int vsp(const uint8_t* x, int nx, const uint
   return vsp_run<MAXW>(vsp_plan(nx, ny, t, MAXW), x, y, cells);
 }
 
+// Shared-prefix form of VERIFYSTRINGPAIR (Sec. 5.3), for verifying one
+// probing string s against a sequence of indexed strings r in (nearly)
+// alphabetical order: the rows run over r and the columns over s, so rows
+// 1..c of two r's that share their first c characters (and their length,
+// hence the band) are identical, and the second can start from the band
+// values after row c of the first.
+//
+// Band: diagonals d = j - i from dlo = -floor((t - D)/2), D = |s| - |r| (any
+// sign, |D| <= t), W registers; cells left of column 0 start at t + 1, and
+// Lemma 4 tests E(i, j) = M(i, j) + |D - (j - i)| over the row (as vsp_band).
+// V holds the band after row `start` (start = 0: it is set here to row 0);
+// rows start + 1 .. |r| are computed, a copy of the band after row snap_row
+// is left in snap when that row is computed, and dead receives the row at
+// which Lemma 4 stopped the scan (0 when it ran to the end).  Returns
+// min(t + 1, ED(r, s)).  Requires |r| >= 1 and |D| <= t.
+template <int W>
+__host__ __device__ __forceinline__ int vsp_rows(const uint8_t* r, int nr, const uint8_t* s, int ns, int t, int start,
+                                                 int (&V)[W], int snap_row, int (&snap)[W], int& dead,
+                                                 unsigned long long& cells) {
+  const int D = ns - nr;
+  const int cap = t + 1;
+  const int dlo = -((t - D) >> 1);
+  const int w = ((t + D) >> 1) - dlo + 1;
+  const int slast = ns - 1;
+  int eoff[W];
+  uint8_t B[W];  // B[k] = s[i + dlo + k - 1] for the row i being computed (index clamped)
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    const int j = dlo + k;
+    if (start == 0) V[k] = j < 0 ? cap : j;  // row 0: M(0, j) = j
+    eoff[k] = abs(D - dlo - k);
+    B[k] = ns > 0 ? s[min(max(start + j, 0), slast)] : (uint8_t)0;
+  }
+  dead = 0;
+  int rows = 0;
+  for (int i = start + 1; i <= nr; ++i) {
+    const uint8_t ca = r[i - 1];
+    int left = cap;
+    int emin = cap;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      const int up = (k + 1 < W) ? V[k + 1] : cap;
+      const int diag = V[k] + (ca != B[k] ? 1 : 0);
+      const int val = min(diag, min(up, left) + 1);
+      V[k] = val;
+      left = val;
+      emin = min(emin, val + eoff[k]);
+    }
+    ++rows;
+    if (i == snap_row) {
+#pragma unroll
+      for (int k = 0; k < W; ++k) snap[k] = V[k];
+    }
+    if (emin > t) {  // Lemma 4
+      dead = i;
+      break;
+    }
+    const int jn = i + dlo + W - 1;
+#pragma unroll
+    for (int k = 0; k + 1 < W; ++k) B[k] = B[k + 1];
+    B[W - 1] = ns > 0 ? s[min(max(jn, 0), slast)] : (uint8_t)0;
+  }
+  cells += (unsigned long long)(rows * w);
+  int res = cap;
+  if (!dead) {
+    const int kres = D - dlo;
+#pragma unroll
+    for (int k = 0; k < W; ++k)
+      if (k == kres) res = min(V[k], cap);
+  }
+  return res;
+}
+
+// Length of the common prefix of a and b (n bytes at most).
+__host__ __device__ __forceinline__ int common_prefix(const uint8_t* a, const uint8_t* b, int n) {
+  int k = 0;
+  while (k < n && a[k] == b[k]) ++k;
+  return k;
+}
+
 #ifdef __CUDACC__
 // Warp-cooperative VERIFYSTRINGPAIR for long strings: all 32 lanes of a warp
 // work on ONE pair, lane l holding band diagonals k = 2l and 2l+1 (up to 64
@@ -351,6 +431,64 @@ __device__ __forceinline__ int vsp_warp(const uint8_t* x, int nx, const uint8_t*
     if (alive) res = v;
   }
   return res;
+}
+
+// vsp_warp with the rows over r and the columns over s whatever their
+// lengths (D = |s| - |r| of either sign, |D| <= t), resumable like vsp_rows:
+// V0, V1 hold each lane's two band values after row `start` (set here when
+// start = 0), rows start + 1 .. |r| are computed, the values after row
+// snap_row are copied to S0, S1 when that row is computed, and dead receives
+// the row at which Lemma 4 stopped the scan (0: ran to the end).  Every lane
+// must call it with the same arguments, the warp converged.
+__device__ __forceinline__ int vsp_warp_rows(const uint8_t* r, int nr, const uint8_t* s, int ns, int t, int start,
+                                             int& V0, int& V1, int snap_row, int& S0, int& S1, int& dead,
+                                             unsigned long long& cells) {
+  const unsigned FULLM = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int D = ns - nr;
+  const int cap = t + 1;
+  const int dlo = -((t - D) >> 1);
+  const int w = ((t + D) >> 1) - dlo + 1;
+  const int k0 = 2 * lane, k1 = 2 * lane + 1;
+  if (start == 0) {
+    V0 = dlo + k0 < 0 ? cap : min(dlo + k0, cap);
+    V1 = dlo + k1 < 0 ? cap : min(dlo + k1, cap);
+  }
+  const int e0 = abs(D - dlo - k0), e1 = abs(D - dlo - k1);
+  dead = 0;
+  for (int i = start + 1; i <= nr; ++i) {
+    const uint8_t ca = r[i - 1];
+    const int jb0 = i + dlo + k0 - 1, jb1 = jb0 + 1;
+    const int c0 = (jb0 >= 0 && jb0 < ns) ? (int)s[jb0] : -1;
+    const int c1 = (jb1 >= 0 && jb1 < ns) ? (int)s[jb1] : -1;
+    const int upn = __shfl_down_sync(FULLM, V0, 1);
+    const int up1 = lane == 31 ? cap : upn;
+    const int x0 = min(V0 + ((int)ca != c0 ? 1 : 0), V1 + 1);
+    const int x1 = min(V1 + ((int)ca != c1 ? 1 : 0), up1 + 1);
+    int S = min(x1, x0 + 1);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int T = __shfl_up_sync(FULLM, S, o);
+      if (lane >= o) S = min(S, T + 2 * o);
+    }
+    const int Sl = __shfl_up_sync(FULLM, S, 1);
+    const int L = lane == 0 ? cap : Sl;
+    V0 = min(min(x0, L + 1), cap);
+    V1 = min(min(x1, V0 + 1), cap);
+    cells += (unsigned long long)w;
+    if (i == snap_row) {
+      S0 = V0;
+      S1 = V1;
+    }
+    if (!__any_sync(FULLM, (V0 + e0 <= t) || (V1 + e1 <= t))) {  // Lemma 4
+      dead = i;
+      break;
+    }
+  }
+  const int kres = D - dlo;
+  const int mine = (kres & 1) ? V1 : V0;
+  const int v = __shfl_sync(FULLM, mine, (kres >> 1) & 31);
+  return dead ? cap : v;
 }
 
 // extension-based verification with the warp-cooperative VERIFYSTRINGPAIR

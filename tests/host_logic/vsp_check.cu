@@ -59,7 +59,76 @@ template <int W> int run(int tmax) {
   printf("W=%d bad=%d near=%d\n", W, bad, near);
   return bad;
 }
+// Shared-prefix form (vsp_rows): a run of strings r that share prefixes,
+// each verified against s with the band kept across them exactly as the
+// mode-L kernel does (resume after the kept row when the common prefix
+// reaches it, stop at the kept dead row when the prefix reaches that);
+// every result must equal min(t + 1, ED) and the rows saved are counted.
+template <int W> int run_shared(int tmax) {
+  std::mt19937 g(11);
+  int bad = 0;
+  long saved = 0, resumed = 0, skipped = 0;
+  for (int it = 0; it < 20000; ++it) {
+    const int t = 1 + (int)(g() % tmax);
+    std::string s;
+    const int ls = 20 + (int)(g() % 30);
+    for (int k = 0; k < ls; ++k) s += char('a' + g() % 3);
+    // a run of 6 strings of one length, each derived from the previous by an
+    // edit at a random position (so consecutive ones share a prefix)
+    std::vector<std::string> rs;
+    std::string r = edited(g, s, (int)(g() % (t + 2)));
+    const int L = (int)r.size();
+    for (int k = 0; k < 6; ++k) {
+      rs.push_back(r);
+      r[g() % L] = char('a' + g() % 3);
+    }
+    int V[W], snap[W];
+    int krow = 0, kdead = 0, klen = -1;
+    std::string kr;
+    for (size_t k = 0; k < rs.size(); ++k) {
+      const std::string& y = rs[k];
+      if (std::abs((int)y.size() - (int)s.size()) > t || y.empty()) continue;
+      int keep = 0;
+      if (k + 1 < rs.size() && rs[k + 1].size() == y.size())
+        keep = pj::common_prefix((const uint8_t*)y.data(), (const uint8_t*)rs[k + 1].data(), (int)y.size());
+      int start = 0, d = t + 1, dead = 0;
+      bool skip = false;
+      if ((int)y.size() == klen) {
+        const int c = pj::common_prefix((const uint8_t*)y.data(), (const uint8_t*)kr.data(), (int)y.size());
+        if (kdead && c >= kdead) {
+          skip = true;
+          ++skipped;
+        } else if (krow && c >= krow) {
+          start = krow;
+          for (int j = 0; j < W; ++j) V[j] = snap[j];
+          saved += start;
+          ++resumed;
+        }
+      }
+      unsigned long long cells = 0;
+      if (!skip) {
+        d = pj::vsp_rows<W>((const uint8_t*)y.data(), (int)y.size(), (const uint8_t*)s.data(), (int)s.size(), t,
+                            start, V, keep, snap, dead, cells);
+        klen = (int)y.size();
+        kr = y;
+        krow = keep > start ? (!dead || dead >= keep ? keep : 0) : (keep == start ? start : 0);
+        kdead = dead;
+      }
+      const int want = std::min(t + 1, ed(y, s));
+      if (d != want) {
+        if (bad < 5) printf("shared W=%d t=%d k=%zu got %d want %d\n", W, t, k, d, want);
+        ++bad;
+      }
+    }
+  }
+  printf("shared W=%d bad=%d resumed=%ld skipped=%ld rows_saved=%ld\n", W, bad, resumed, skipped, saved);
+  return bad;
+}
+
 int main() {
+  run_shared<5>(4);
+  run_shared<9>(8);
+  run_shared<17>(16);
   run<2>(1);
   run<3>(2);
   run<5>(4);

@@ -87,11 +87,13 @@ def test_index_reuse_across_tau():
 
 def test_candidate_and_accept_counts_match_algorithm():
     """The kernels examine exactly the (s, r, i, p) matches of Alg. 1 with
-    multi-match selection (visiting by length, then id) and accept exactly
-    the ones extension verification accepts."""
+    multi-match selection (visiting by length, then by the first eight
+    bytes, then id: the store's order) and accept exactly the ones extension
+    verification accepts."""
     strings = synth.generate("short", 3, n=700)
+    strings += [strings[5][:6] + b"zz" + strings[5][8:], strings[5][:9] + b"q"]  # shared first 8 bytes
     st = {}
-    M.pass_join_self(strings, 3, order="id", stats=st)
+    M.pass_join_self(strings, 3, order="prefix8", stats=st)
     res = gpu_self(strings, 3)
     assert res.stats["candidates"] == st["tuples"]
     assert res.stats["accepted"] == st["accepted"]
@@ -496,3 +498,38 @@ def test_device_budget_refuses_instead_of_allocating():
         big.free()
     assert 0 < r.stats["device_peak"] <= 2 << 30
     assert_same(r.pairs, cpu_self(strings, 4), "budgeted self join")
+
+
+def _prefix_families(strings, n_fam, size, seed):
+    """Families of same-length strings that share long prefixes: a string of
+    the set and copies of it with one substitution in their last quarter."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in rng.choice(len(strings), size=n_fam, replace=False).tolist():
+        base = bytearray(strings[k])
+        for _ in range(size):
+            s = bytearray(base)
+            pos = len(s) - 1 - int(rng.integers(0, max(1, len(s) // 4)))
+            s[pos] = ord("a") + int(rng.integers(0, 26))
+            out.append(bytes(s))
+    return strings + out
+
+
+@pytest.mark.parametrize("mode", ["1", "2"])
+def test_shared_prefix_verification(monkeypatch, mode):
+    """Sec. 5.3 on the GPU: distinct pairs verified with the DP rows of
+    common prefixes shared between consecutive pairs of a probe (thread per
+    run of pairs 1, warp per run 2).  Same exact result as without sharing
+    and as the oracle, and fewer DP cells."""
+    monkeypatch.setenv("PJ_VERIFY_PAIRS", mode)
+    for name, tau, n in [("medium", 8, 2500), ("long", 16, 500), ("short", 4, 3000)]:
+        strings = _prefix_families(synth.generate(name, tau, n=n), 40, 6, seed=tau)
+        want = cpu_self(strings, tau, banded=True)
+        monkeypatch.setenv("PJ_SHARE_PREFIX", "1")
+        r1 = gpu_self(strings, tau)
+        monkeypatch.setenv("PJ_SHARE_PREFIX", "0")
+        r0 = gpu_self(strings, tau)
+        assert_same(r1.pairs, want, f"{name} tau={tau} shared")
+        assert_same(r0.pairs, want, f"{name} tau={tau} not shared")
+        assert r1.stats["verify_mode"] == 2
+        assert r1.stats["dp_cells"] < r0.stats["dp_cells"], (name, r1.stats["dp_cells"], r0.stats["dp_cells"])

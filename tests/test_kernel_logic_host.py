@@ -121,14 +121,23 @@ def test_rs_join_logic(emu, tmp_path):
 
 def test_vsp_widths_match_plain_dp(tmp_path):
     """VERIFYSTRINGPAIR (Sec. 5.1, Alg. 3) at every compiled band width, 2 to
-    33 diagonals, equals min(t + 1, ED) of the plain DP."""
+    33 diagonals, equals min(t + 1, ED) of the plain DP; so does its
+    shared-prefix form (Sec. 5.3) over runs of strings with common prefixes,
+    resuming from kept rows as the mode-L kernel does."""
     nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
     if not os.path.exists(nvcc):
         pytest.skip("nvcc not available")
     exe = tmp_path / "vsp_check"
     subprocess.run([nvcc, "-std=c++17", "-O2", "-I", CSRC, "-o", str(exe),
                     os.path.join(ROOT, "tests", "host_logic", "vsp_check.cu")], check=True)
-    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    lines = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines()
+    shared = [ln.split() for ln in lines if ln.startswith("shared")]
+    assert len(shared) == 3
+    for toks in shared:  # the shared-prefix form (Sec. 5.3): exact, and it does share rows
+        vals = dict(tok.split("=") for tok in toks[1:])
+        assert vals["bad"] == "0", toks
+        assert int(vals["resumed"]) > 1000 and int(vals["rows_saved"]) > 10000 and int(vals["skipped"]) > 100
+    out = " ".join(ln for ln in lines if not ln.startswith("shared")).split()
     widths = [tok.split("=")[1] for tok in out if tok.startswith("W=")]
     assert widths == ["2", "3", "5", "9", "17", "33"]
     assert all(tok == "bad=0" for tok in out if tok.startswith("bad="))
