@@ -65,6 +65,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--partition", choices=["even", "center"], default="even",
+                    help="partition scheme of the segment index (pj_options.partition)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="library default verification instead of the autotuned one (profiling)")
     return ap.parse_args()
 
 
@@ -385,7 +389,8 @@ def run_reference(args):
 
 def workload_config(args, n):
     return {"workload": f"{args.workload}: {n} strings, tau={args.tau} (self join)", "n_strings": n,
-            "tau": args.tau, "l2": "flushed between timed steps (256 MB write)",
+            "tau": args.tau, "partition": getattr(args, "partition", "even"),
+            "l2": "flushed between timed steps (256 MB write)",
             "parallelism": f"replicas x{args.gpus}" if args.gpus > 1 else "1 GPU"}
 
 
@@ -421,7 +426,7 @@ def run_native(args):
 
     def device_step():
         idx = pj.pj_build_index((d_bytes, d_off), args.tau, results_on_device=True, lazy_partitions=True,
-                                autotune=True)
+                                autotune=not args.no_autotune, partition=args.partition)
         r = pj.pj_self_join(idx, args.tau)
         out = (r.count, r.stats, idx.build_ms)
         r.free()
@@ -429,7 +434,8 @@ def run_native(args):
         return out
 
     def host_step():
-        idx = pj.pj_build_index((buf, off), args.tau, lazy_partitions=True, autotune=True)
+        idx = pj.pj_build_index((buf, off), args.tau, lazy_partitions=True, autotune=not args.no_autotune,
+                                partition=args.partition)
         r = pj.pj_self_join(idx, args.tau)
         idx.free()
         return len(r.pairs), r.stats
@@ -438,7 +444,7 @@ def run_native(args):
         device_step()
     barrier()
     cal = pj.pj_calibrate()  # the rooflines' ceilings, measured on this GPU (outside the timed region)
-    sel_idx = pj.pj_build_index((d_bytes, d_off), args.tau, lazy_partitions=True)
+    sel_idx = pj.pj_build_index((d_bytes, d_off), args.tau, lazy_partitions=True, partition=args.partition)
     selection = dict(pj.pj_count_selection(sel_idx, args.tau),
                      note="substrings each selection method of Sec. 4 would look up in this self join")
     sel_idx.free()
@@ -483,8 +489,8 @@ def run_native(args):
     # one recorded CUDA graph (graph_joins); store build not included
     resident = {}
     for mode, graph in (("eager", False), ("graph", True)):
-        idx = pj.pj_build_index((d_bytes, d_off), args.tau, results_on_device=True, autotune=True,
-                                graph_joins=graph)
+        idx = pj.pj_build_index((d_bytes, d_off), args.tau, results_on_device=True,
+                                autotune=not args.no_autotune, graph_joins=graph, partition=args.partition)
         for _ in range(2):  # tuning, then (graph) the recorded join
             pj.pj_self_join(idx, args.tau).free()
         ms, replayed = [], 0

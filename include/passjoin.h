@@ -68,6 +68,17 @@ enum {
                                the length-aware method (Sec. 5.1); same results */
 };
 
+/* partition values (pj_options.partition): where the longer segments go when
+ * a string's length is not a multiple of tau + 1.  Every segment has
+ * floor(|s| / (tau + 1)) or that plus one characters in both. */
+enum {
+  PJ_PARTITION_EVEN = 0,    /* the last segments are the longer ones (Sec. 3.1, even partition) */
+  PJ_PARTITION_CENTER = 1   /* the segments nearest the middle are the longer ones, where the
+                               multi-match windows (Sec. 4.2) are widest; same results, fewer
+                               candidates on short strings (a scheme of this library; the paper
+                               leaves other partition schemes to future work, Sec. 3.1) */
+};
+
 /* A set of n strings; see the conventions above. */
 typedef struct {
   const uint8_t* bytes;
@@ -166,6 +177,8 @@ typedef struct {
   const char* autotune_cache; /* file that keeps autotuning decisions across processes (read,
                                  then appended; copied at pj_build_index).  NULL = the file
                                  named by the environment variable PJ_AUTOTUNE_CACHE, if any */
+  int partition;          /* PJ_PARTITION_*: partition scheme of the segment indexes
+                             (pj_build_index, pj_join, pj_self_join_stream); default EVEN */
 } pj_options;
 
 typedef struct pj_index pj_index; /* opaque, library-owned */

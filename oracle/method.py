@@ -7,7 +7,10 @@ Every function follows one passage of the paper, in the paper's order and
 notation.  Positions are 0-based here: the paper's start position p (1-based)
 is ``p - 1`` in this module, and its segment start p_i is ``P[i-1]``.
 
-* ``even_partition``       -- Sec. 3.1 (even-partition scheme).
+* ``even_partition``       -- Sec. 3.1 (even-partition scheme);
+  ``center_partition``     -- a second scheme (Sec. 3.1 leaves other schemes
+                              to future work): the same lengths, the longer
+                              segments in the middle.
 * ``select_windows``       -- Sec. 4 (length- and shift-based), Sec. 4.1
                               (position-aware, W_p), Sec. 4.2 (multi-match-aware,
                               W_m) and Alg. 2.
@@ -59,14 +62,47 @@ def even_partition(length: int, tau: int) -> list[tuple[int, int]]:
     return segs
 
 
-def segments(s: bytes, tau: int) -> list[bytes]:
-    return [s[p:p + n] for p, n in even_partition(len(s), tau)]
+def center_partition(length: int, tau: int) -> list[tuple[int, int]]:
+    """A second partition scheme (the paper leaves other schemes to future
+    work, Sec. 3.1, and notes that its techniques extend to them): the same
+    segment lengths as the even partition -- floor(|s|/(tau+1)), and k of
+    them one longer -- but the k longer segments are the k closest to the
+    middle (segments ordered by |2i - (tau + 2)|, ties to the left), where
+    the multi-match windows of Sec. 4.2 are widest, so that the more
+    selective segments are looked up at the most positions.  Returns
+    [(start, length)] for i = 1..tau+1 (0-based starts)."""
+    if length < tau + 1:
+        raise ValueError("a partition needs |s| >= tau + 1")
+    m = tau + 1
+    base = length // m
+    k = length - base * m
+    by_centrality = sorted(range(1, m + 1), key=lambda i: (abs(2 * i - (m + 1)), i))
+    longer = set(by_centrality[:k])
+    segs, start = [], 0
+    for i in range(1, m + 1):
+        li = base + 1 if i in longer else base
+        segs.append((start, li))
+        start += li
+    assert start == length
+    return segs
+
+
+PARTITIONS = {"even": even_partition, "center": center_partition}
+
+
+def partition(length: int, tau: int, scheme: str = "even") -> list[tuple[int, int]]:
+    """The segments of a length-|s| string under a partition scheme."""
+    return PARTITIONS[scheme](length, tau)
+
+
+def segments(s: bytes, tau: int, scheme: str = "even") -> list[bytes]:
+    return [s[p:p + n] for p, n in partition(len(s), tau, scheme)]
 
 
 # ---------------------------------------------------------- Sec. 4 / 4.x ---
 
 def select_windows(s_len: int, l: int, tau: int, method: str = "multi",
-                   clip: bool = True) -> list[tuple[int, int, int, int]]:
+                   clip: bool = True, scheme: str = "even") -> list[tuple[int, int, int, int]]:
     """Start-position windows of the selected substrings of s for L_l^i.
 
     Returns [(i, lo, hi, l_i)] for i = 1..tau+1; positions p in [lo, hi]
@@ -87,7 +123,7 @@ def select_windows(s_len: int, l: int, tau: int, method: str = "multi",
     """
     D = s_len - l
     out = []
-    for i, (P, li) in enumerate(even_partition(l, tau), start=1):
+    for i, (P, li) in enumerate(partition(l, tau, scheme), start=1):
         last = s_len - li  # last start position at which s[p:p+l_i] exists
         if method == "length":
             lo, hi = 0, last
@@ -200,7 +236,7 @@ def verify_naive(s: bytes, r: bytes, tau: int, return_rows: bool = False):
 
 # -------------------------------------------------------------- Sec. 5.2 ---
 
-def extension_verify(r: bytes, s: bytes, i: int, p: int, tau: int):
+def extension_verify(r: bytes, s: bytes, i: int, p: int, tau: int, scheme: str = "even"):
     """Extension-based verification of one match (Sec. 5.2, Alg. 3).
 
     r is the indexed string (its i-th even segment w = r[P_i : P_i + l_i]);
@@ -211,7 +247,7 @@ def extension_verify(r: bytes, s: bytes, i: int, p: int, tau: int):
     Returns (accepted, d_l + d_r).  A segment that does not equal s[p : p+l_i]
     is not a match and is rejected.
     """
-    P, li = even_partition(len(r), tau)[i - 1]
+    P, li = partition(len(r), tau, scheme)[i - 1]
     if s[p:p + li] != r[P:P + li] or p < 0:
         return False, None
     tau_l, tau_r = i - 1, tau + 1 - i
@@ -240,19 +276,22 @@ def _direct_ed(a: bytes, b: bytes) -> int:
 
 
 def pass_join_self(strings: list[bytes], tau: int, order: str = "alphabetical",
-                   method: str = "multi", stats: dict | None = None):
+                   method: str = "multi", stats: dict | None = None, scheme: str = "even"):
     """Alg. 1 PASS-JOIN(S, tau) with multi-match selection and extension
     verification.  Returns {(a, b): ed} over input ids with a < b.
 
     order: "alphabetical" visits by (length, string), the order Alg. 1 sorts into;
-    "id" visits by (length, input id).  The result set is the same; the
-    visiting order only decides which string of a pair probes the other.
+    "id" visits by (length, input id); "prefix8" by (length, first eight
+    bytes, input id).  The result set is the same; the visiting order only
+    decides which string of a pair probes the other.
     stats (optional dict) receives "tuples" (candidate (s, r, i, p) matches
     after the visited-before rule), "lookups" and "accepted".
     """
     n = len(strings)
     if order == "alphabetical":
         visit = sorted(range(n), key=lambda k: (len(strings[k]), strings[k], k))
+    elif order == "prefix8":
+        visit = sorted(range(n), key=lambda k: (len(strings[k]), strings[k][:8], k))
     else:
         visit = sorted(range(n), key=lambda k: (len(strings[k]), k))
     index = defaultdict(lambda: defaultdict(list))  # (l, i) -> segment -> ids
@@ -264,7 +303,7 @@ def pass_join_self(strings: list[bytes], tau: int, order: str = "alphabetical",
         ls = len(s)
         # Alg. 1, probing step: L_l^i for |s| - tau <= l <= |s|
         for l in range(max(tau + 1, ls - tau), ls + 1):
-            for i, lo, hi, li in select_windows(ls, l, tau, method, clip=True):
+            for i, lo, hi, li in select_windows(ls, l, tau, method, clip=True, scheme=scheme):
                 lists = index.get((l, i))
                 for p in range(lo, hi + 1):
                     lookups += 1
@@ -272,7 +311,7 @@ def pass_join_self(strings: list[bytes], tau: int, order: str = "alphabetical",
                         continue
                     for rid in lists.get(s[p:p + li], ()):
                         tuples += 1
-                        ok, d = extension_verify(strings[rid], s, i, p, tau)
+                        ok, d = extension_verify(strings[rid], s, i, p, tau, scheme)
                         if ok:
                             accepted += 1
                             key = (min(rid, sid), max(rid, sid))
@@ -288,16 +327,18 @@ def pass_join_self(strings: list[bytes], tau: int, order: str = "alphabetical",
         visited.append(sid)
         # Alg. 1, indexing step: insert s's segments into L_{|s|}^i
         if ls >= tau + 1:
-            for i, seg in enumerate(segments(s, tau), start=1):
+            for i, seg in enumerate(segments(s, tau, scheme), start=1):
                 index[(ls, i)][seg].append(sid)
     if stats is not None:
         stats.update(tuples=tuples, lookups=lookups, accepted=accepted)
     return best
 
 
-def selection_counts(strings: list[bytes], tau: int) -> dict:
+def selection_counts(strings: list[bytes], tau: int, scheme: str = "even") -> dict:
     """Substrings each selection method of Sec. 4 selects over Alg. 1's self
-    join (visiting by length, then input id): for every probing string s,
+    join (visiting by length; the order within a length does not change the
+    counts, since only the first string of a length has no string of its own
+    length before it): for every probing string s,
     every l in [max(tau + 1, |s| - tau), |s|] whose inverted lists are
     non-empty when s probes them (some string of length l visited before s),
     and every segment i, the number of existing substrings s[p, l_i] in the
@@ -314,13 +355,14 @@ def selection_counts(strings: list[bytes], tau: int) -> dict:
                 continue
             counts["groups"] += tau + 1
             for m in ("length", "shift", "position", "multi"):
-                counts[m] += sum(max(0, hi - lo + 1) for _, lo, hi, _ in select_windows(ls, l, tau, m, clip=True))
+                counts[m] += sum(max(0, hi - lo + 1)
+                                 for _, lo, hi, _ in select_windows(ls, l, tau, m, clip=True, scheme=scheme))
         if ls >= tau + 1:
             indexed_lengths.add(ls)
     return counts
 
 
-def pass_join_rs(R: list[bytes], S: list[bytes], tau: int, stats: dict | None = None):
+def pass_join_rs(R: list[bytes], S: list[bytes], tau: int, stats: dict | None = None, scheme: str = "even"):
     """R != S join (Sec. 3.2): index S, probe each r in R against the lengths
     [|r| - tau, |r| + tau] with the Sec. 4.2 windows at signed D = |r| - l.
     Returns {(a in R, b in S): ed}."""
@@ -328,7 +370,7 @@ def pass_join_rs(R: list[bytes], S: list[bytes], tau: int, stats: dict | None = 
     short = []
     for sid, s in enumerate(S):
         if len(s) >= tau + 1:
-            for i, seg in enumerate(segments(s, tau), start=1):
+            for i, seg in enumerate(segments(s, tau, scheme), start=1):
                 index[(len(s), i)][seg].append(sid)
         else:
             short.append(sid)
@@ -337,14 +379,14 @@ def pass_join_rs(R: list[bytes], S: list[bytes], tau: int, stats: dict | None = 
     for qid, q in enumerate(R):
         lq = len(q)
         for l in range(max(tau + 1, lq - tau), lq + tau + 1):
-            for i, lo, hi, li in select_windows(lq, l, tau, "multi", clip=True):
+            for i, lo, hi, li in select_windows(lq, l, tau, "multi", clip=True, scheme=scheme):
                 lists = index.get((l, i))
                 if lists is None:
                     continue
                 for p in range(lo, hi + 1):
                     for sid in lists.get(q[p:p + li], ()):
                         tuples += 1
-                        ok, d = extension_verify(S[sid], q, i, p, tau)
+                        ok, d = extension_verify(S[sid], q, i, p, tau, scheme)
                         if ok:
                             key = (qid, sid)
                             best[key] = min(best.get(key, d), d)

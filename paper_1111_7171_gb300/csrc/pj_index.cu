@@ -295,14 +295,14 @@ __global__ void k_buckets(const uint32_t* __restrict__ slen, uint32_t n, uint32_
 
 __global__ void k_seg_records(const uint8_t* __restrict__ sbytes, const uint64_t* __restrict__ soff,
                               const uint32_t* __restrict__ slen, uint32_t first, uint64_t n_records, int tau,
-                              unsigned long long* __restrict__ keys, uint32_t* __restrict__ vals) {
+                              int scheme, unsigned long long* __restrict__ keys, uint32_t* __restrict__ vals) {
   const uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n_records) return;
   const uint32_t sid = first + (uint32_t)(r / (tau + 1));
   const int i = (int)(r % (tau + 1)) + 1;
   const int l = (int)slen[sid];
   int P, li;
-  even_segment(l, tau, i, P, li);
+  segment_m(l, tau + 1, 0, scheme, i, P, li);
   keys[r] = seg_key(sbytes + soff[sid] + P, li, l, i);
   vals[r] = sid;
 }
@@ -315,7 +315,7 @@ __global__ void k_seg_records(const uint8_t* __restrict__ sbytes, const uint64_t
 // it).  One thread per string: the prefix codes come from one pass forward,
 // the suffix codes from one pass backward.
 __global__ void k_side_sigs(const uint8_t* __restrict__ sbytes, const uint64_t* __restrict__ soff,
-                            const uint32_t* __restrict__ slen, uint32_t first, uint32_t n, int tau,
+                            const uint32_t* __restrict__ slen, uint32_t first, uint32_t n, int tau, int scheme,
                             ulonglong2* __restrict__ sides) {
   for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; first + x < n; x += gridDim.x * blockDim.x) {
     const uint32_t sid = first + x;
@@ -326,7 +326,7 @@ __global__ void k_side_sigs(const uint8_t* __restrict__ sbytes, const uint64_t* 
     int k = 0;
     for (int i = 1; i <= tau + 1; ++i) {  // prefixes: bytes [0, P_i)
       int P, li;
-      even_segment(l, tau, i, P, li);
+      segment_m(l, tau + 1, 0, scheme, i, P, li);
       for (; k < P; ++k) {
         const int sh = 4 * (int)(s[k] % SIDE_BUCKETS);
         const unsigned long long field = (t >> sh) & 15ull;
@@ -338,7 +338,7 @@ __global__ void k_side_sigs(const uint8_t* __restrict__ sbytes, const uint64_t* 
     k = l;
     for (int i = tau + 1; i >= 1; --i) {  // suffixes: bytes [P_i + l_i, l)
       int P, li;
-      even_segment(l, tau, i, P, li);
+      segment_m(l, tau + 1, 0, scheme, i, P, li);
       for (; k > P + li; --k) {
         const int sh = 4 * (int)(s[k - 1] % SIDE_BUCKETS);
         const unsigned long long field = (t >> sh) & 15ull;
@@ -559,6 +559,7 @@ static std::vector<uint16_t> group_order(int tau, bool self) {
 void build_partition(pj_index& idx, int tau, Partition& part) {
   const Ctx& c = idx.ctx;
   part.tau = tau;
+  part.scheme = idx.scheme;
   for (int self = 0; self < 2; ++self) {
     const std::vector<uint16_t> order = group_order(tau, self != 0);
     part.gorder[self].reset(c, order.size());
@@ -587,7 +588,7 @@ void build_partition(pj_index& idx, int tau, Partition& part) {
   }
   DBuf<unsigned long long> keys(c, nrec);
   k_seg_records<<<ceil_div(nrec, 256), 256, 0, c.stream>>>(idx.sbytes.p, idx.soff.p, idx.slen.p, part.first, nrec,
-                                                           tau, keys.p, part.postings.p);
+                                                           tau, part.scheme, keys.p, part.postings.p);
   PJ_LAUNCHED("k_seg_records");
   trace_mark(c, "partition: records");
   radix_sort_pairs<unsigned long long>(c, keys.p, part.postings.p, nrec, 64);
@@ -634,7 +635,7 @@ void build_partition(pj_index& idx, int tau, Partition& part) {
     DBuf<ulonglong2> sides(c, nrec);
     const uint32_t np = idx.n - part.first;
     k_side_sigs<<<std::min<unsigned>(ceil_div(np, 128), sm_grid_cap(16)), 128, 0, c.stream>>>(
-        idx.sbytes.p, idx.soff.p, idx.slen.p, part.first, idx.n, tau, sides.p);
+        idx.sbytes.p, idx.soff.p, idx.slen.p, part.first, idx.n, tau, part.scheme, sides.p);
     PJ_LAUNCHED("k_side_sigs");
     k_post_records<<<std::min<unsigned>(ceil_div(nrec, 256), sm_grid_cap(16)), 256, 0, c.stream>>>(
         part.postings.p, keys.p, nrec, part.first, tau, sides.p, part.precs.p);
@@ -783,6 +784,9 @@ int pj_build_index(const pj_strings* S, int tau_max, const pj_options* opt, pj_i
     idx->results_on_device = opt ? opt->results_on_device != 0 : false;
     idx->lazy = opt ? opt->lazy_partitions != 0 : false;
     idx->autotune = opt ? opt->autotune != 0 : false;
+    idx->scheme = opt ? opt->partition : PJ_PARTITION_EVEN;
+    if (idx->scheme != PJ_PARTITION_EVEN && idx->scheme != PJ_PARTITION_CENTER)
+      pj::fail(PJ_EINVAL, "pj_build_index: unknown partition scheme");
     if (opt && opt->autotune_cache) idx->autotune_cache = opt->autotune_cache;
     idx->verify_mode = opt ? opt->verify_mode : PJ_VERIFY_AUTO;
     idx->graph_joins = opt ? opt->graph_joins != 0 : false;

@@ -17,6 +17,7 @@
 // byte-compared before verification, so results stay exact.
 #pragma once
 
+#include <algorithm>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -25,6 +26,11 @@
 #include "pj_common.cuh"
 
 namespace pj {
+
+#ifndef __CUDA_ARCH__
+using std::max;
+using std::min;
+#endif
 
 struct __align__(16) Slot {
   unsigned long long key;  // 0 = empty
@@ -63,6 +69,52 @@ __host__ __device__ __forceinline__ void even_segment(int l, int tau, int i, int
   const int first_long = parts - k + 1;  // segments i >= first_long are longer
   li = base + (i >= first_long ? 1 : 0);
   P = (i - 1) * base + (i > first_long ? i - first_long : 0);
+}
+
+// Partition schemes (pj_options.partition).  Both cut a length-l string into
+// parts = tau + 1 segments of floor(l / parts) characters, k = l - floor(l /
+// parts) * parts of them one longer; they differ in which segments are the
+// longer ones:
+//   PJ_PARTITION_EVEN   the last k (Sec. 3.1, the paper's even partition);
+//   PJ_PARTITION_CENTER the k segments nearest the middle (ordered by
+//                       |2i - (parts + 1)|, ties to the left), where the
+//                       multi-match windows (Sec. 4.2) are widest, so that
+//                       the more selective segments are looked up at the most
+//                       positions.
+// The longer segments form one run [lo, hi] in both: the last k for EVEN;
+// for CENTER, with c the middle segment (the left one of the two middles
+// when parts is even), lo = c - floor(k / 2), hi = c + floor((k - 1) / 2)
+// for odd parts and lo = c - floor((k - 1) / 2), hi = c + floor(k / 2) for
+// even parts.  Then l_i = base + [lo <= i <= hi] and P_i = (i - 1) * base +
+// min(max(i - lo, 0), k).  Multi-match selection, extension verification
+// and the completeness of Lemma 1 only need the segments to depend on the
+// length alone, which both schemes satisfy.
+__host__ __device__ __forceinline__ void scheme_segment(int l, int parts, int base, int scheme, int i, int& P,
+                                                        int& li) {
+  const int k = l - base * parts;
+  int lo;
+  if (scheme == PJ_PARTITION_CENTER) {
+    const int c = (parts + 1) >> 1;
+    lo = (parts & 1) ? c - (k >> 1) : c - ((k - 1) >> 1);  // k = 0: an empty run (lo > hi)
+  } else {
+    lo = parts - k + 1;
+  }
+  const int hi = lo + k - 1;
+  li = base + (i >= lo && i <= hi ? 1 : 0);
+  P = (i - 1) * base + min(max(i - lo, 0), k);
+}
+
+// The partition of the given scheme, floor(l / parts) by the multiply of
+// even_segment_m (m = seg_magic(parts), or 0 to compute it).
+__host__ __device__ __forceinline__ void segment_m(int l, int parts, unsigned long long m, int scheme, int i, int& P,
+                                                   int& li) {
+  if (scheme == PJ_PARTITION_EVEN) {
+    even_segment_m(l, parts, m, i, P, li);
+    return;
+  }
+  if (m == 0) m = seg_magic(parts);
+  const int base = (int)(((unsigned long long)(unsigned)l * m) >> 32);
+  scheme_segment(l, parts, base, scheme, i, P, li);
 }
 
 // Segment keys: key = V << 32 | l << 8 | i for segment i of a length-l
@@ -386,6 +438,7 @@ struct Partition {
   DBuf<Slot> table;          // power-of-two capacity
   DBuf<uint8_t> fp;          // key_fp of each used slot (0 for empty ones), then the presence bitmap
   unsigned presence_bytes = 1;  // bitmap bytes per slot (2 for indexes of long strings)
+  int scheme = PJ_PARTITION_EVEN;  // partition scheme (pj_options.partition)
   DBuf<uint32_t> postings;   // sids, runs in key order, ascending inside a run
   DBuf<PostRec> precs;       // one record per posting, same order
   bool sides = false;        // the records carry side signatures (else 0): indexes of strings that
@@ -405,6 +458,7 @@ struct pj_index {
   bool results_on_device = false;
   bool lazy = false;         // thresholds are built on first use
   bool autotune = false;     // tune the verification of each threshold's self join
+  int scheme = PJ_PARTITION_EVEN;  // partition scheme of every threshold's segment index
   std::string autotune_cache;  // file of tuning decisions (empty: PJ_AUTOTUNE_CACHE)
   int verify_mode = PJ_VERIFY_AUTO;
   bool graph_joins = false;  // self joins replay a recorded graph (see pj_options.graph_joins)

@@ -1780,6 +1780,7 @@ constexpr double INTERLEAVE_MAX_AVG_LEN = 256.0;
 static ProbeView index_side(const pj_index& idx, const Partition& part) {
   ProbeView v{};
   v.seg_magic = seg_magic(part.tau + 1);
+  v.scheme = part.scheme;
   const double avg = idx.n ? (double)idx.total_bytes / idx.n : 0.0;
   v.interleave = avg <= INTERLEAVE_MAX_AVG_LEN ? 1 : 0;
   const char* il = getenv("PJ_PROBE_INTERLEAVE");
@@ -2287,7 +2288,7 @@ void query_multi_impl(const Ctx& c, pj_index& idx, const ProbeSet& R, const uint
     if (present[t]) {
       const Partition& part = idx.parts[t];
       pv = PartView{part.table.p, part.fp.p, part.presence_bytes, part.precs.p, part.table.n - 1,
-                    part.postings.p, part.n_records, part.first, t, seg_magic(t + 1)};
+                    part.postings.p, part.n_records, part.first, t, seg_magic(t + 1), part.scheme};
       has_short |= part.first > 0;
     }
     hp[t] = pv;
@@ -2471,6 +2472,7 @@ int pj_count_selection(pj_index* idx, int tau, pj_selection* out) {
     v.ilmax = idx->lmax;
     v.tau = tau;
     v.seg_magic = pj::seg_magic(tau + 1);
+    v.scheme = idx->scheme;
     v.pbegin = tau + 1 <= idx->lmax ? idx->h_bbeg[tau + 1] : idx->n;  // shorter probes select nothing
     v.pcount = idx->n - v.pbegin;
     const unsigned long long n_groups = (unsigned long long)v.pcount * pj::groups_per_probe(tau, true);
@@ -2505,6 +2507,9 @@ int pj_join(const pj_strings* R, const pj_strings* S, int tau, const pj_options*
     tmp->ctx = pj::make_ctx(opt);
     tmp->results_on_device = opt ? opt->results_on_device != 0 : false;
     tmp->verify_mode = opt ? opt->verify_mode : PJ_VERIFY_AUTO;
+    tmp->scheme = opt ? opt->partition : PJ_PARTITION_EVEN;
+    if (tmp->scheme != PJ_PARTITION_EVEN && tmp->scheme != PJ_PARTITION_CENTER)
+      pj::fail(PJ_EINVAL, "pj_join: unknown partition scheme");
     PJ_CUDA(cudaGetDevice(&tmp->device));
     pj::build_store(*tmp, *S);
     tmp->parts.resize(tau + 1);

@@ -227,6 +227,7 @@ void query_noalloc(pj_index& idx, const pj_strings& batch, int tau, pj_pair* out
   v.n_postings = part.n_records;
   v.tau = tau;
   v.seg_magic = seg_magic(tau + 1);
+  v.scheme = part.scheme;
   v.pbytes = R.bytes;
   v.poff = R.off;
   v.plen = R.len.p;

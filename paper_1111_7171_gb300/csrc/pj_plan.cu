@@ -256,7 +256,7 @@ void create(pj_plan& P, pj_index& idx, const pj_plan_options& o) {
   for (int t = 0; t <= tau_max; ++t) {
     const Partition& part = idx.parts[t];
     hp[t] = PartView{part.table.p, part.fp.p, part.presence_bytes, part.precs.p, part.table.n - 1,
-                     part.postings.p, part.n_records, part.first, t, seg_magic(t + 1)};
+                     part.postings.p, part.n_records, part.first, t, seg_magic(t + 1), part.scheme};
   }
   P.parts.reset(P.ctx, hp.size());
   PJ_CUDA(cudaMemcpyAsync(P.parts.p, hp.data(), hp.size() * sizeof(PartView), cudaMemcpyHostToDevice, P.stream));

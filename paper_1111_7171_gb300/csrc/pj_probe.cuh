@@ -39,6 +39,7 @@ struct PartView {
   uint32_t first;  // first sid of length >= tau + 1
   int tau;
   unsigned long long seg_magic;  // seg_magic(tau + 1)
+  int scheme;                    // partition scheme (PJ_PARTITION_*)
 };
 
 struct ProbeView {
@@ -67,7 +68,8 @@ struct ProbeView {
   const PostRec* precs;  // postings' records (same order)
   unsigned long long n_postings;
   int tau;
-  unsigned long long seg_magic;  // seg_magic(tau + 1): even partitions without a division
+  unsigned long long seg_magic;  // seg_magic(tau + 1): partitions without a division
+  int scheme;                    // partition scheme of the indexed strings (PJ_PARTITION_*)
   int key_shift;  // pair key = a << key_shift | b
   // multi-threshold batches (R != S only): probe q has threshold ptau[q],
   // its groups are qgoff[q] .. qgoff[q+1]-1, parts[tau] is tau's index
@@ -105,6 +107,7 @@ __host__ __device__ __forceinline__ ProbeView view_for_tau(const ProbeView& v, i
   t.n_postings = pv.n_postings;
   t.tau = tau;
   t.seg_magic = pv.seg_magic;
+  t.scheme = pv.scheme;
   return t;
 }
 
@@ -128,7 +131,7 @@ __host__ __device__ __forceinline__ bool group_lists(const ProbeView& v, bool se
   uint32_t b1 = v.ibbeg[l + 1];
   if (self && l == ls && b1 > q) b1 = q;  // only strings visited before q
   if (b1 <= b0) return false;
-  even_segment_m(l, parts, v.seg_magic, i, P, li);
+  segment_m(l, parts, v.seg_magic, v.scheme, i, P, li);
   return true;
 }
 
@@ -254,7 +257,7 @@ __host__ __device__ __forceinline__ bool verify_screened(const ProbeView& v, boo
   }
   if (i >= 1 && i <= v.tau + 1 && lr >= v.tau + 1) {  // r is a partitioned string
     int P, li;
-    even_segment_m(lr, v.tau + 1, v.seg_magic, i, P, li);
+    segment_m(lr, v.tau + 1, v.seg_magic, v.scheme, i, P, li);
     // exact keys (segments of at most SEG_EXACT_MAX bytes) guarantee the
     // segment match; hashed ones are compared
     if (hc.p + li <= hc.ls && verify_ext<MAXW>(hc.s, hc.ls, rb, lr, i, hc.p, li, P, v.tau,
@@ -322,7 +325,7 @@ __device__ __forceinline__ bool verify_candidate_warp(const ProbeView& v, bool s
     const int lr = (int)v.ilen[r];
     if (i >= 1 && i <= v.tau + 1 && lr >= v.tau + 1) {
       int P, li;
-      even_segment_m(lr, v.tau + 1, v.seg_magic, i, P, li);
+      segment_m(lr, v.tau + 1, v.seg_magic, v.scheme, i, P, li);
       if (p + li <= ls &&
           verify_ext_warp(v.pbytes + v.poff[q], ls, v.ibytes + v.ioff[r], lr, i, p, li, P, v.tau, li > SEG_EXACT_MAX,
                           ed, cells)) {

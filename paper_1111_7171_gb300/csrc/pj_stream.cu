@@ -51,6 +51,8 @@ uint64_t window_estimate(const std::vector<uint64_t>& cum_bytes, const std::vect
 
 void self_join_stream(const pj_strings& S, int tau, const pj_options* opt, pj_result* out) {
   if (S.on_device) fail(PJ_EINVAL, "pj_self_join_stream: the strings must be in host memory");
+  if (opt && opt->partition != PJ_PARTITION_EVEN && opt->partition != PJ_PARTITION_CENTER)
+    fail(PJ_EINVAL, "pj_self_join_stream: unknown partition scheme");
   const uint32_t n = S.n;
   if (!S.offsets || (!S.bytes && n > 0)) fail(PJ_EINVAL, "pj_strings: NULL bytes or offsets");
   // (length, first eight bytes, id) order on the host, as the store orders
@@ -152,6 +154,7 @@ void self_join_stream(const pj_strings& S, int tau, const pj_options* opt, pj_re
     try {
       tmp->ctx = base;  // shares the call's budget
       tmp->verify_mode = opt ? opt->verify_mode : PJ_VERIFY_AUTO;
+      tmp->scheme = opt ? opt->partition : PJ_PARTITION_EVEN;
       tmp->autotune = opt ? opt->autotune != 0 : false;
       if (opt && opt->autotune_cache) tmp->autotune_cache = opt->autotune_cache;
       PJ_CUDA(cudaGetDevice(&tmp->device));

@@ -29,6 +29,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libpassjoin.so")
 PJ_OK, PJ_EINVAL, PJ_ENOMEM, PJ_ECUDA, PJ_ETIMEDOUT, PJ_ECANCELED = 0, -1, -2, -3, -4, -5
 PJ_TAU_LIMIT = 32
 PAIR_DTYPE = np.dtype([("a", np.uint32), ("b", np.uint32), ("ed", np.uint32)])
+PARTITIONS = {"even": 0, "center": 1}  # pj_options.partition (PJ_PARTITION_EVEN / PJ_PARTITION_CENTER)
 
 
 class PJError(RuntimeError):
@@ -66,7 +67,7 @@ class pj_options(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
                 ("verify_mode", ctypes.c_int), ("results_on_device", ctypes.c_int), ("lazy_partitions", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("graph_joins", ctypes.c_int), ("device_budget", ctypes.c_uint64),
-                ("autotune_cache", ctypes.c_char_p)]
+                ("autotune_cache", ctypes.c_char_p), ("partition", ctypes.c_int)]
 
 
 class pj_server_options(ctypes.Structure):
@@ -232,7 +233,8 @@ def _torch_free(ctx, ptr, stream):
 
 def make_options(stream=None, results_on_device: bool = False, torch_allocator: bool = True,
                  lazy_partitions: bool = False, autotune: bool = False, graph_joins: bool = False,
-                 device_budget: int = 0, autotune_cache: str | None = None) -> pj_options:
+                 device_budget: int = 0, autotune_cache: str | None = None,
+                 partition: str = "even") -> pj_options:
     torch = _torch()
     opt = pj_options()
     library().pj_options_init(ctypes.byref(opt))
@@ -250,6 +252,7 @@ def make_options(stream=None, results_on_device: bool = False, torch_allocator: 
     # the library copies the path at pj_build_index; the bytes object lives
     # as long as the options
     opt.autotune_cache = os.fsencode(autotune_cache) if autotune_cache else None
+    opt.partition = PARTITIONS[partition]
     return opt
 
 
@@ -444,7 +447,7 @@ def pj_kernel_launches() -> int:
 
 def pj_build_index(strings, tau_max: int, stream=None, results_on_device: bool = False,
                    lazy_partitions: bool = False, autotune: bool = False, graph_joins: bool = False,
-                   device_budget: int = 0, autotune_cache: str | None = None) -> Index:
+                   device_budget: int = 0, autotune_cache: str | None = None, partition: str = "even") -> Index:
     """pj_build_index: resident segment index for thresholds 0..tau_max.
 
     results_on_device: results stay in device memory (DeviceResult).
@@ -454,9 +457,12 @@ def pj_build_index(strings, tau_max: int, stream=None, results_on_device: bool =
     replay that join recorded as one CUDA graph (pj_options.graph_joins).
     device_budget: most device bytes the index and its calls may hold at once
     (0 = no limit; beyond it a call fails with PJ_ENOMEM).
-    autotune_cache: file keeping autotuning decisions across processes."""
+    autotune_cache: file keeping autotuning decisions across processes.
+    partition: "even" (the paper's even partition) or "center" (the longer
+    segments in the middle; same results)."""
     opt = make_options(stream, results_on_device, lazy_partitions=lazy_partitions, autotune=autotune,
-                       graph_joins=graph_joins, device_budget=device_budget, autotune_cache=autotune_cache)
+                       graph_joins=graph_joins, device_budget=device_budget, autotune_cache=autotune_cache,
+                       partition=partition)
     S = Strings(strings)
     h = ctypes.c_void_p()
     _check(library().pj_build_index(ctypes.byref(S.c), int(tau_max), ctypes.byref(opt), ctypes.byref(h)),
@@ -499,11 +505,12 @@ def pj_self_join_shard(index: Index, tau: int, shard: int, n_shards: int):
     return _take(res)
 
 
-def pj_self_join_stream(strings, tau: int, device_budget: int = 0, stream=None, autotune: bool = False):
+def pj_self_join_stream(strings, tau: int, device_budget: int = 0, stream=None, autotune: bool = False,
+                        partition: str = "even"):
     """pj_self_join_stream: the self join of host strings, window by window of
     lengths, holding at most `device_budget` device bytes at once (0 = three
     quarters of the free device memory).  Host result."""
-    opt = make_options(stream, autotune=autotune, device_budget=device_budget)
+    opt = make_options(stream, autotune=autotune, device_budget=device_budget, partition=partition)
     S = Strings(strings)
     res = pj_result()
     _check(library().pj_self_join_stream(ctypes.byref(S.c), int(tau), ctypes.byref(opt), ctypes.byref(res)),
@@ -511,9 +518,10 @@ def pj_self_join_stream(strings, tau: int, device_budget: int = 0, stream=None, 
     return _take(res)
 
 
-def pj_join(R, S, tau: int, stream=None, results_on_device: bool = False, device_budget: int = 0):
+def pj_join(R, S, tau: int, stream=None, results_on_device: bool = False, device_budget: int = 0,
+            partition: str = "even"):
     """pj_join: all (a in R, b in S) with ED <= tau."""
-    opt = make_options(stream, results_on_device, device_budget=device_budget)
+    opt = make_options(stream, results_on_device, device_budget=device_budget, partition=partition)
     r, s = Strings(R), Strings(S)
     res = pj_result()
     _check(library().pj_join(ctypes.byref(r.c), ctypes.byref(s.c), int(tau), ctypes.byref(opt), ctypes.byref(res)),

@@ -533,3 +533,48 @@ def test_shared_prefix_verification(monkeypatch, mode):
         assert_same(r0.pairs, want, f"{name} tau={tau} not shared")
         assert r1.stats["verify_mode"] == 2
         assert r1.stats["dp_cells"] < r0.stats["dp_cells"], (name, r1.stats["dp_cells"], r0.stats["dp_cells"])
+
+
+@pytest.mark.parametrize("name,tau,n,banded", [("short", 4, 4000, False), ("short", 2, 3000, False),
+                                               ("medium", 8, 2500, True), ("long", 16, 500, True)])
+def test_center_partition(name, tau, n, banded):
+    """The centred partition scheme (the longer segments in the middle):
+    self joins, R x S joins and queries equal the oracle, and the kernels
+    examine exactly the Alg. 1 matches the oracle enumerates with that
+    scheme."""
+    strings = _with_short_strings(synth.generate(name, tau, n=n), tau)
+    want = cpu_self(strings, tau, banded=banded)
+    idx = pj.pj_build_index(strings, tau, partition="center")
+    try:
+        assert_same(pj.pj_self_join(idx, tau).pairs, want, f"{name} tau={tau} center")
+        R = synth.generate(name, tau, n=200, seed=99) + strings[:100]
+        rb, ro = synth.pack(R)
+        sb, so = synth.pack(strings)
+        want_rs = oracle.join(rb, ro, sb, so, tau, banded=True)
+        assert_same(pj.pj_query(idx, R, tau).pairs, want_rs, f"{name} tau={tau} center query")
+    finally:
+        idx.free()
+    assert_same(pj.pj_join(R, strings, tau, partition="center").pairs, want_rs, f"{name} tau={tau} center join")
+
+
+def test_center_partition_candidates_match_algorithm():
+    """With the centred scheme the kernels examine exactly the (s, r, i, p)
+    matches of Alg. 1 under that scheme (store order), and accept exactly
+    those extension verification accepts; fewer than under the even
+    partition on short strings."""
+    strings = synth.generate("short", 4, n=900)
+    counts = {}
+    for scheme in ("even", "center"):
+        st = {}
+        M.pass_join_self(strings, 4, order="prefix8", stats=st, scheme=scheme)
+        idx = pj.pj_build_index(strings, 4, partition=scheme)
+        try:
+            r = pj.pj_self_join(idx, 4)
+            sel = pj.pj_count_selection(idx, 4)
+        finally:
+            idx.free()
+        assert r.stats["candidates"] == st["tuples"], scheme
+        assert r.stats["accepted"] == st["accepted"], scheme
+        assert sel["multi_match"] == M.selection_counts(strings, 4, scheme=scheme)["multi"]
+        counts[scheme] = st["tuples"]
+    assert counts["center"] < counts["even"]

@@ -173,3 +173,26 @@ def test_character_set_bound_never_exceeds_edit_distance(tmp_path):
     assert vals["bad"] == "0", out
     assert int(vals["tight"]) > 1000  # the bound is often exact, so it has teeth
     assert int(vals["side_tight"]) > 1000
+
+
+def test_partition_schemes_match_the_oracle(tmp_path):
+    """The kernels' closed form of both partition schemes (the paper's even
+    partition, Sec. 3.1, and the centred scheme) gives exactly the segments
+    of the oracle's definitions (oracle/method.py) for every length up to 160
+    and 1..33 segments."""
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    exe = tmp_path / "scheme_dump"
+    subprocess.run([nvcc, "-std=c++17", "-O2", "-I", CSRC, "-I", os.path.join(ROOT, "include"), "-o", str(exe),
+                    os.path.join(ROOT, "tests", "host_logic", "scheme_dump.cu")], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines()
+    schemes = {0: M.even_partition, 1: M.center_partition}
+    n = 0
+    for line in out:
+        f = [int(x) for x in line.split()]
+        scheme, parts, length = f[:3]
+        got = [(f[3 + 2 * k], f[4 + 2 * k]) for k in range(parts)]
+        assert got == schemes[scheme](length, parts - 1), (scheme, parts, length)
+        n += 1
+    assert n == 2 * sum(161 - p for p in range(1, 34))

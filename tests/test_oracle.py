@@ -284,16 +284,23 @@ def _tiny_pairs(alphabet, max_len, min_len):
 def test_multi_match_completeness_exhaustive(tau):
     """Theorem 2 (and the signed-length reading for R != S): for every pair
     with ED <= tau and an indexed string r of length >= tau + 1, some segment
-    i of r equals s[p : p + l_i] for a p in the multi-match window."""
+    i of r equals s[p : p + l_i] for a p in the multi-match window -- for the
+    even partition (Sec. 3.1) and for the centred scheme, whose segments also
+    depend on the length alone."""
     words = _tiny_pairs("ab", 7, 0)
+    for scheme in ("even", "center"):
+        _completeness(words, tau, scheme)
+
+
+def _completeness(words, tau, scheme):
     for r in words:
         if len(r) < tau + 1:
             continue
-        segs = M.even_partition(len(r), tau)
+        segs = M.partition(len(r), tau, scheme)
         for s in words:
             if abs(len(s) - len(r)) > tau or ed_alignments(r.decode(), s.decode()) > tau:
                 continue
-            wins = M.select_windows(len(s), len(r), tau, "multi")
+            wins = M.select_windows(len(s), len(r), tau, "multi", scheme=scheme)
             assert any(s[p:p + li] == r[P:P + li]
                        for (i, lo, hi, li), (P, _) in zip(wins, segs) for p in range(lo, hi + 1)), (r, s)
 
@@ -364,9 +371,9 @@ def test_extension_min_over_matches_is_ed():
             assert best is None
 
 
-@pytest.mark.parametrize("order", ["alphabetical", "id"])
+@pytest.mark.parametrize("order,scheme", [("alphabetical", "even"), ("id", "even"), ("prefix8", "center")])
 @pytest.mark.parametrize("tau", [0, 1, 2, 3])
-def test_pass_join_equals_definition(order, tau):
+def test_pass_join_equals_definition(order, scheme, tau):
     """Theorem 6: Alg. 1 with multi-match selection and extension verification
     returns exactly the pairs of Def. 1, with exact ED (short and empty
     strings included)."""
@@ -382,9 +389,33 @@ def test_pass_join_equals_definition(order, tau):
             else:
                 t.insert(rng.randint(0, len(t)), ord(rng.choice("abc")))
         strings.append(bytes(t))
-    got = M.pass_join_self(strings, tau, order=order)
+    got = M.pass_join_self(strings, tau, order=order, scheme=scheme)
     want = {(a, b): d for a, b, d in brute_pairs(strings, tau)}
     assert got == want
+
+
+def test_center_partition_shape():
+    """The centred scheme keeps the even partition's segment lengths (floor
+    or ceil of |s| / (tau + 1), Sec. 3.1) and puts the longer ones in one
+    run around the middle; with |s| a multiple of tau + 1 both schemes are
+    the same."""
+    assert M.center_partition(13, 3) == [(0, 3), (3, 4), (7, 3), (10, 3)]   # k = 1, even parts: the left middle
+    assert M.center_partition(14, 3) == [(0, 3), (3, 4), (7, 4), (11, 3)]   # k = 2: both middles
+    assert M.center_partition(16, 4) == [(0, 3), (3, 3), (6, 4), (10, 3), (13, 3)]  # k = 1, odd parts: the middle
+    assert M.center_partition(18, 4) == [(0, 3), (3, 4), (7, 4), (11, 4), (15, 3)]  # k = 3
+    assert M.center_partition(19, 4) == [(0, 4), (4, 4), (8, 4), (12, 4), (16, 3)]  # k = 4: ties to the left
+    for L in range(1, 90):
+        for tau in range(0, min(L, 33)):
+            even, cen = M.even_partition(L, tau), M.center_partition(L, tau)
+            assert sorted(n for _, n in even) == sorted(n for _, n in cen)
+            assert all(cen[k][0] + cen[k][1] == cen[k + 1][0] for k in range(tau))
+            longer = [i for i, (_, n) in enumerate(cen) if n > L // (tau + 1)]
+            assert longer == list(range(longer[0], longer[0] + len(longer))) if longer else True
+            if longer:  # centred: equally many on each side, one more on the left at most
+                left, right = longer[0], tau - longer[-1]
+                assert 0 <= right - left <= 1 or 0 <= left - right <= 1
+            if L % (tau + 1) == 0:
+                assert even == cen
 
 
 def test_pass_join_table1():

@@ -117,6 +117,10 @@ PY_MUTANTS = {
     "expected_ed_transposed": ("expected = [cur[j] + abs((ns - j) - (nr - i)) for j in cur]", "expected = [cur[j] + abs((ns - i) - (nr - j)) for j in cur]"),
     "band_offsets_swapped": ("lo_off = (tau - D) // 2\n    hi_off = (tau + D) // 2", "lo_off = (tau + D) // 2\n    hi_off = (tau - D) // 2"),
     "segment_not_compared": ("if s[p:p + li] != r[P:P + li] or p < 0:", "if p < 0:"),
+    # centred partition scheme: longer segments off the middle, ties the other way, or swapped lengths
+    "center_off_by_one": ("key=lambda i: (abs(2 * i - (m + 1)), i))", "key=lambda i: (abs(2 * i - m), i))"),
+    "center_ties_right": ("key=lambda i: (abs(2 * i - (m + 1)), i))", "key=lambda i: (abs(2 * i - (m + 1)), -i))"),
+    "center_short_middle": ("li = base + 1 if i in longer else base\n", "li = base if i in longer else base + 1\n"),
 }
 
 
@@ -140,7 +144,9 @@ def _method_pins_pass(Mm) -> bool:
               T.test_verify_string_pair_is_capped_ed, T.test_extension_paper_example,
               T.test_extension_min_over_matches_is_ed, T.test_pass_join_table1,
               lambda: T.test_multi_match_completeness_exhaustive(2),
-              lambda: T.test_pass_join_equals_definition("id", 2)]
+              lambda: T.test_pass_join_equals_definition("id", "even", 2),
+              lambda: T.test_pass_join_equals_definition("prefix8", "center", 2),
+              T.test_center_partition_shape]
     saved = T.M
     T.M = Mm
     try:
