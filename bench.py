@@ -526,6 +526,8 @@ def run_native(args):
         # (mode L: the distinct pairs it keeps)
         dp_verified = (st["distinct_pairs"] if pair_mode else st["candidates"]) - st["filtered"]
         kernel = ("k_verify_pairs_warp" if st["pair_warp"] else "k_verify_pairs") if pair_mode else "k_verify_queued"
+        if st["fused"]:  # one kernel from selection to verification: its time is the verify phase
+            kernel = "k_fused_self"
         alu_peak_gcells = cal["dp_cells_per_s"] / 1e9
         sm_max = float(peaks.get("sm_max_mhz", 2070.0))
         derived_gcells = cal["sm_count"] * 128 * sm_max * 1e6 / OPS_PER_CELL / 1e9
@@ -574,6 +576,7 @@ def run_native(args):
                          "dedupe": statistics.mean(s["dedupe_ms"] for s in stats_all)},
             "tuning": {"verify_mode": "distinct pairs" if st["verify_mode"] == 2 else "extension",
                        "pair_per": "warp" if st["pair_warp"] else "thread",
+                       "fused": bool(st["fused"]),
                        "verify_block": int(st["verify_block"]), "warp_per_candidate_from_length": int(st["warp_min_len"]),
                        "note": "autotuned in the warm-up steps (cached per workload signature)"},
             "roofline": roofline,

@@ -126,6 +126,9 @@ typedef struct {
                            through the budgeted allocator (over the index's life so far, or over
                            the call for pj_join and pj_self_join_stream); 0 without a budget */
   uint32_t windows;     /* pj_self_join_stream: length windows joined; 0 for other calls */
+  int32_t fused;        /* self join in PJ_VERIFY_PAIRS: 1 when one persistent kernel ran selection,
+                           lookup, distinct-pair formation and verification together; pairs
+                           beyond its shared-memory lists went through the materialised path */
 } pj_stats;
 
 typedef struct {

@@ -29,12 +29,16 @@
 #include <cstring>
 #include <string>
 
+#include <cooperative_groups.h>
+
 #include "pj_internal.cuh"
 #include "pj_plan.cuh"
 #include "pj_prims.cuh"
 #include "pj_probe.cuh"
 
 namespace pj {
+
+namespace cg = cooperative_groups;
 
 struct Counters {
   unsigned long long accepted;
@@ -190,20 +194,11 @@ __device__ __forceinline__ void count_group(const ProbeView& vt, uint32_t q, int
   mask = 0;
   int l, i, P, li, lo, hi;
   if (group_window(vt, SELF, q, (int)vt.plen[q], g, l, i, P, li, lo, hi)) {
-    const int ls = (int)vt.plen[q];
-    const uint8_t* s = vt.pbytes + vt.poff[q];
-    const uint32_t pw = seg_pow(li);
-    uint32_t V = vt.phash && li > SEG_EXACT_MAX ? seg_value_from_prefix(vt.phash + vt.poff[q] + q, lo, li, pw)
-                                                : seg_value(s + lo, li);
-    for (int p = lo;; ++p) {
-      uint32_t b;
-      if (lookup_key(vt, SELF, q, ls, l, seg_key_of(V, l, i), b, err)) {
-        ++nh;
-        mask |= 1ull << (p - lo);
-      }
-      if (p == hi) break;
-      V = seg_roll(V, s[p], s[p + li], li, pw);  // p + li <= hi - 1 + li < ls
-    }
+    window_lookups(vt, SELF, q, (int)vt.plen[q], l, i, li, lo, hi, vt.pbytes + vt.poff[q], err,
+                   [&](int p, uint32_t, uint32_t) {
+                     ++nh;
+                     mask |= 1ull << (p - lo);
+                   });
     lookups += (unsigned long long)(hi - lo + 1);
   }
 }
@@ -917,6 +912,299 @@ __global__ void __launch_bounds__(BLOCK) k_verify_pairs_warp(const ProbeView v,
   if (lane == 0) add_counter(&ctr->cells, cells);
 }
 
+// ------------------------------------------------ fused self join (A9) ---
+//
+// One persistent kernel for the whole-pair (mode L) self join.  Each warp
+// takes work items -- `ppi` consecutive probing strings -- from a device
+// counter (work[0]), from the two ends of the length order in turn, and runs
+// the whole path for its item without leaving the SM:
+//   * multi-match-aware selection and the lookups of every (probe, length,
+//     segment) group, the window's keys rolled (Sec. 4.2, Alg. 2): for short
+//     and medium strings an item is 32 probes, a lane per probe, and the
+//     lanes take the same group number together (windows of about one size,
+//     as the interleaved probe pass does); for long strings the lanes share
+//     one probe's groups, widest windows first;
+//   * every posting of a non-empty run is a candidate pair (q, r) -- runs
+//     longer than FRUN_MIN are queued and expanded by the whole warp, a
+//     posting per lane, after the lookups; runs longer than FRUN_BIG (the
+//     short probes of a high threshold, whose segments are a few characters)
+//     leave the kernel as Hits (work[2] counts them) for the materialised
+//     mode-L pipeline, which spreads them over the whole GPU -- and a hash set
+//     in the warp's shared memory keeps the first occurrence of each pair, so
+//     the item's distinct pairs come out without a sort (a pair (q, r), r < q,
+//     is only found by probe q, hence only in q's item);
+//   * the whole-string character-count screen and one whole-pair banded
+//     verification per distinct pair (Sec. 5.1): 32 pairs at a time, a lane
+//     per pair, the last partial batch carried into the warp's next item so
+//     that lanes stay busy; or, for probes at least `warp_from` long, one pair
+//     at a time by the whole warp.
+// Warps never wait for one another, so one warp's lookups overlap another's
+// verification.  A pair that finds its item's list full goes to the global
+// overflow list as a pair key, verified afterwards by the materialised
+// mode-L pipeline (ovf: FOVF_LISTS counters, then as many lists of ovf_cap
+// keys); a pair verified twice is merged by the final dedupe (least ed per
+// pair).  work[1] counts the distinct pairs verified here.
+constexpr int FB = 256;          // 8 independent warps per block
+constexpr int FSET_BITS = 9;
+constexpr int FSET = 1 << FSET_BITS;  // pair slots of a warp's hash set
+constexpr int FLIST = 224;       // distinct pairs one item keeps (the set stays under half full)
+constexpr int FTASKS = 64;       // (probe, group) tasks per item at least
+constexpr int FRUNS = 32;        // posting runs a warp expands together, per item
+constexpr uint32_t FRUN_MIN = 8; // runs longer than this are expanded by the whole warp
+constexpr uint32_t FRUN_BIG = 16;   // runs longer than this leave the kernel as Hits
+constexpr unsigned long long FTAG_MAX = (1ull << 24) - 1;
+constexpr int FOVF_LISTS = 64;   // overflow sub-lists (the item at j from the long end appends to list j mod 64)
+
+// One warp's shared state.  A set slot holds tag << 40 | (q - first probe of
+// the item) << 32 | r; slots whose tag is not the current item's are free.
+struct FusedWarp {
+  unsigned long long set[FSET];
+  unsigned long long carry[32];  // (q << 32 | r) pairs waiting for a full batch
+  unsigned long long runs[FRUNS];  // long posting runs: (q - first probe) << 56 | count << 32 | begin
+  uint16_t list[FLIST];          // set slots of the item's distinct pairs, in insertion order
+  int nlist, nruns;
+};
+
+__device__ __forceinline__ unsigned long long fused_overflow_key(uint32_t q, uint32_t r, int pshift) {
+  return ((unsigned long long)min(q, r) << pshift) | max(q, r);
+}
+
+// Inserts candidate pair (q, r) of the current item; a new pair is listed,
+// or sent to the overflow list when the item's list is full.
+// ovf_n: the item's overflow sub-list counter; ovf_keys: its region of
+// ovf_cap entries.
+__device__ __forceinline__ void fused_insert(FusedWarp& w, unsigned long long tag, uint32_t qrel, uint32_t q,
+                                             uint32_t r, int pshift, unsigned long long* __restrict__ ovf_n,
+                                             unsigned long long* __restrict__ ovf_keys, unsigned long long ovf_cap) {
+  volatile unsigned long long* set = w.set;
+  if (*(volatile int*)&w.nlist < FLIST) {
+    const unsigned long long val = (tag << 40) | ((unsigned long long)qrel << 32) | r;
+    unsigned h = (r * 0x9E3779B1u + qrel * 0x85EBCA77u) >> (32 - FSET_BITS);
+    for (int n = 0; n < 2 * FSET; ++n) {
+      const unsigned long long cur = set[h];
+      if (cur == val) return;  // seen before in this item
+      if ((cur >> 40) != tag) {  // a free slot
+        const unsigned long long prev = atomicCAS(&w.set[h], cur, val);
+        if (prev == cur) {
+          const int pos = atomicAdd(&w.nlist, 1);
+          if (pos < FLIST) {
+            w.list[pos] = (uint16_t)h;
+            return;
+          }
+          break;  // listed nowhere: overflow (later copies are found in the set)
+        }
+        if (prev == val) return;
+        continue;  // taken meanwhile: look at the slot again
+      }
+      h = (h + 1) & (FSET - 1);
+    }
+  }
+  // one atomic per group of lanes that overflow together
+  const cg::coalesced_group lanes = cg::coalesced_threads();
+  unsigned long long o = 0;
+  if (lanes.thread_rank() == 0) o = atomicAdd(ovf_n, (unsigned long long)lanes.size());
+  o = lanes.shfl(o, 0) + lanes.thread_rank();
+  if (o < ovf_cap) ovf_keys[o] = fused_overflow_key(q, r, pshift);
+}
+
+template <int MAXW>
+__device__ __forceinline__ void fused_verify_thread(const ProbeView& v, uint32_t q, uint32_t r, const AccOut& out,
+                                                    Counters* ctr, unsigned long long& cells,
+                                                    unsigned long long& filtered) {
+  if (v.pbm && signature_bound(v.pbm[q], v.ibm[r]) > v.tau) {
+    ++filtered;
+    return;
+  }
+  const int d = vsp<MAXW>(v.pbytes + v.poff[q], (int)v.plen[q], v.ibytes + v.ioff[r], (int)v.ilen[r], v.tau, cells);
+  if (d <= v.tau) append_match(ctr, out, pair_out_key(v, true, q, r), d);
+}
+
+// FORM: FUSED_THREAD (every pair a lane), FUSED_WARP (every pair a warp) or
+// FUSED_CUT (a warp per pair for probes at least warp_from long); the single
+// forms leave the other verification out of the kernel and its registers.
+enum { FUSED_THREAD = 0, FUSED_WARP = 1, FUSED_CUT = 2 };
+
+template <int MAXW, int FORM>
+__global__ void __launch_bounds__(FB) k_fused_self(const ProbeView v, int ppi, int warp_from,
+                                                   unsigned long long* __restrict__ work,
+                                                   unsigned long long* __restrict__ ovf, unsigned long long ovf_cap,
+                                                   Hit* __restrict__ heavy, unsigned long long heavy_cap,
+                                                   int pshift, AccOut out, Counters* ctr) {
+  __shared__ FusedWarp fw[FB / 32];
+  const unsigned lane = threadIdx.x & 31u;
+  FusedWarp& w = fw[threadIdx.x >> 5];
+  for (int k = (int)lane; k < FSET; k += 32) w.set[k] = 0;  // tag 0 is no item's
+  const int G = groups_per_probe(v.tau, true);
+  const unsigned long long n_items = ((unsigned long long)v.pcount + ppi - 1) / ppi;
+  unsigned long long lookups = 0, cells = 0, wcells = 0, n_cand = 0, filtered = 0, pairs = 0;
+  int err = 0;
+  int ncarry = 0;                // the same in every lane
+  unsigned long long tag = 0;    // the current item's tag, 1..FTAG_MAX
+  for (;;) {
+    unsigned long long it = 0;
+    if (lane == 0) {
+      it = atomicAdd(&work[0], 1ull);
+      w.nlist = 0;
+      w.nruns = 0;
+    }
+    it = __shfl_sync(FULL, it, 0);
+    if (it >= n_items) break;
+    if (++tag > FTAG_MAX) {  // tags wrapped: free every slot
+      for (int k = (int)lane; k < FSET; k += 32) w.set[k] = 0;
+      tag = 1;
+    }
+    __syncwarp();
+    // items from both ends in turn: the longest probes (the costliest
+    // verifications) and the shortest (the longest posting runs) start first
+    const unsigned long long j = (it & 1) ? n_items - 1 - (it >> 1) : (it >> 1);
+    const unsigned sub = (unsigned)(j % FOVF_LISTS);  // neighbouring items (alike in cost) on different lists
+    unsigned long long* const ovf_n = ovf + sub;
+    unsigned long long* const ovf_keys = ovf + FOVF_LISTS + sub * ovf_cap;
+    const uint32_t q_end = (uint32_t)((unsigned long long)v.pbegin + v.pcount - j * (unsigned long long)ppi);
+    const uint32_t q_beg = q_end > v.pbegin + (uint32_t)ppi ? q_end - (uint32_t)ppi : v.pbegin;
+    const int nq = (int)(q_end - q_beg);
+    auto group = [&](uint32_t qrel, int g) {
+      const uint32_t q = q_beg + qrel;
+      const int ls = (int)v.plen[q];
+      int l, i, P, li, lo, hi;
+      if (!group_window(v, true, q, ls, g, l, i, P, li, lo, hi)) return;
+      window_lookups(v, true, q, ls, l, i, li, lo, hi, v.pbytes + v.poff[q], err, [&](int, uint32_t b, uint32_t cnt) {
+        if (cnt > FRUN_BIG) {  // a very long run: to the materialised pipeline
+          const cg::coalesced_group lanes = cg::coalesced_threads();
+          unsigned long long hv = 0;
+          if (lanes.thread_rank() == 0) hv = atomicAdd(&work[2], (unsigned long long)lanes.size());
+          hv = lanes.shfl(hv, 0) + lanes.thread_rank();
+          if (hv < heavy_cap) {
+            heavy[hv] = Hit{q, b, cnt, 0u, 0ull, 0ull};
+            n_cand += cnt;
+            return;
+          }
+        }
+        if (cnt > FRUN_MIN && cnt < (1u << 24)) {  // a long run: queued for the whole warp
+          const int slot = atomicAdd(&w.nruns, 1);
+          if (slot < FRUNS) {
+            w.runs[slot] = ((unsigned long long)qrel << 56) | ((unsigned long long)cnt << 32) | b;
+            n_cand += cnt;
+            return;
+          }
+        }
+        for (uint32_t k = 0; k < cnt; ++k) {
+          const uint32_t r = v.postings[b + k];
+          if (r >= v.n_index) {
+            err |= 1;
+            continue;
+          }
+          ++n_cand;
+          fused_insert(w, tag, qrel, q, r, pshift, ovf_n, ovf_keys, ovf_cap);
+        }
+      });
+      lookups += (unsigned long long)(hi - lo + 1);
+    };
+    if (v.interleave) {  // a lane per probe, the lanes on the same group g (windows of about one size)
+      if ((int)lane < nq)
+        for (int g = 0; g < G; ++g) group(lane, g);
+    } else {  // the lanes on consecutive groups of a probe, widest windows first
+      for (int t = (int)lane; t < nq * G; t += 32) {
+        const int g = t % G;
+        group((uint32_t)(t / G), v.gorder ? (int)v.gorder[g] : g);
+      }
+    }
+    __syncwarp();
+    const int nr = ::min(*(volatile int*)&w.nruns, FRUNS);
+    for (int k = 0; k < nr; ++k) {  // the long runs, a posting per lane
+      const unsigned long long run = w.runs[k];
+      const uint32_t qrel = (uint32_t)(run >> 56), cnt = (uint32_t)(run >> 32) & 0xFFFFFFu, b = (uint32_t)run;
+      for (uint32_t j = lane; j < cnt; j += 32) {
+        const uint32_t r = v.postings[b + j];
+        if (r >= v.n_index) {
+          err |= 1;
+          continue;
+        }
+        fused_insert(w, tag, qrel, q_beg + qrel, r, pshift, ovf_n, ovf_keys, ovf_cap);
+      }
+    }
+    __syncwarp();
+    const int nd = ::min(*(volatile int*)&w.nlist, FLIST);
+    // pair k of the item's list
+    auto listed = [&](int k, uint32_t& q, uint32_t& r) {
+      const unsigned long long val = w.set[w.list[k]];
+      q = q_beg + (uint32_t)((val >> 32) & 0xFFu);
+      r = (uint32_t)val;
+    };
+    const bool by_warp = FORM == FUSED_WARP || (FORM == FUSED_CUT && (int)v.plen[q_end - 1] >= warp_from);
+    if (by_warp) {  // a warp per pair
+      if constexpr (FORM != FUSED_WARP) {
+        if (ncarry) {  // pairs a lane per pair left from a shorter item
+          if ((int)lane < ncarry) {
+            ++pairs;
+            fused_verify_thread<MAXW>(v, (uint32_t)(w.carry[lane] >> 32), (uint32_t)w.carry[lane], out, ctr, cells,
+                                      filtered);
+          }
+          ncarry = 0;
+          __syncwarp();
+        }
+      }
+      for (int k = 0; k < nd; ++k) {
+        uint32_t q, r;
+        listed(k, q, r);
+        if (lane == 0) ++pairs;
+        if (v.pbm && signature_bound(v.pbm[q], v.ibm[r]) > v.tau) {  // the same in every lane
+          if (lane == 0) ++filtered;
+          continue;
+        }
+        const int d = vsp_warp(v.pbytes + v.poff[q], (int)v.plen[q], v.ibytes + v.ioff[r], (int)v.ilen[r], v.tau,
+                               wcells);
+        if (d <= v.tau && lane == 0) append_match(ctr, out, pair_out_key(v, true, q, r), d);
+      }
+    } else if constexpr (FORM != FUSED_WARP) {  // a lane per pair: carried pairs first, then the item's
+      const int total = ncarry + nd;
+      const int full = total & ~31;
+      for (int base = 0; base < full; base += 32) {
+        const int k = base + (int)lane;
+        uint32_t q, r;
+        if (k < ncarry) {
+          q = (uint32_t)(w.carry[k] >> 32);
+          r = (uint32_t)w.carry[k];
+        } else {
+          listed(k - ncarry, q, r);
+        }
+        ++pairs;
+        fused_verify_thread<MAXW>(v, q, r, out, ctr, cells, filtered);
+      }
+      const int rem = total - full;
+      unsigned long long cv = 0;
+      if ((int)lane < rem) {
+        const int k = full + (int)lane;
+        if (k < ncarry) {
+          cv = w.carry[k];
+        } else {
+          uint32_t q, r;
+          listed(k - ncarry, q, r);
+          cv = ((unsigned long long)q << 32) | r;
+        }
+      }
+      __syncwarp();
+      if ((int)lane < rem) w.carry[lane] = cv;
+      ncarry = rem;
+    }
+    __syncwarp();  // the list, the set and the carry are rewritten by the next item
+  }
+  if constexpr (FORM != FUSED_WARP) {
+    if ((int)lane < ncarry) {
+      ++pairs;
+      fused_verify_thread<MAXW>(v, (uint32_t)(w.carry[lane] >> 32), (uint32_t)w.carry[lane], out, ctr, cells,
+                                filtered);
+    }
+  }
+  add_counter(&ctr->lookups, lookups);
+  add_counter(&ctr->candidates, n_cand);
+  add_counter(&ctr->filtered, filtered);
+  add_counter(&work[1], pairs);
+  if (err) atomicOr(&ctr->err, (unsigned long long)err);
+  // the warp form counts each pair's cells in all 32 lanes: lane 0 reports them
+  add_counter(&ctr->cells, cells + (lane == 0 ? wcells : 0ull));
+}
+
 // ---------------------------------------------------------------- A8 ------
 
 // Pairs whose indexed string is too short to partition (length <= tau).
@@ -1270,24 +1558,21 @@ static unsigned long long first_candidate_of(const Ctx& c, const DBuf<Hit>& hits
   return c_cut;
 }
 
-// Mode L for one chunk's candidates [0, n_cand): pair keys, radix sort,
-// distinct pairs, one whole-string verification each.  Returns the number of
-// distinct pairs.
-constexpr unsigned long long PAIR_MODE_MAX_CANDS = 1ull << 27;  // 32 B of scratch per candidate
+// Largest number of candidates of one chunk verified in mode L (32 B of
+// scratch per candidate); bigger chunks use extension verification.
+constexpr unsigned long long PAIR_MODE_MAX_CANDS = 1ull << 27;
 
+// Mode L from a list of n_keys candidate pair keys (in k0, unsorted, k0 of
+// n_keys entries): radix sort, distinct pairs, one whole-string
+// verification each.  Returns the number of distinct pairs.
 template <bool SELF>
-static unsigned long long verify_pairs_chunk(const Ctx& c, const ProbeView& v, const Hit* hits,
-                                             const unsigned long long* off, unsigned long long n_hits,
-                                             unsigned long long n_cand, Counters* ctr, AccOut* scratch,
-                                             AcceptBuf* acc) {
+static unsigned long long verify_pair_keys(const Ctx& c, const ProbeView& v, DBuf<unsigned long long>& k0,
+                                           unsigned long long n_cand, Counters* ctr, AccOut* scratch,
+                                           AcceptBuf* acc) {
   const int pshift = bits_for(v.n_index);
   const int nbits = pshift + (SELF ? pshift : bits_for((unsigned long long)v.pbegin + v.pcount));
-  DBuf<unsigned long long> k0(c, n_cand), k1(c, n_cand);
+  DBuf<unsigned long long> k1(c, n_cand);
   DBuf<uint32_t> v0(c, n_cand), v1(c, n_cand);
-  const unsigned g = persistent_grid(k_pair_keys<SELF>, (n_cand + (unsigned long long)BLOCK * V_RUN - 1) /
-                                                            ((unsigned long long)BLOCK * V_RUN));
-  k_pair_keys<SELF><<<g, BLOCK, 0, c.stream>>>(v, hits, off, n_hits, 0, n_cand, pshift, k0.p, ctr, nullptr);
-  PJ_LAUNCHED("k_pair_keys");
   const bool second = radix_sort_pairs_dn<unsigned long long>(c, k0.p, v0.p, k1.p, v1.p, n_cand, nullptr, nbits);
   unsigned long long* sorted = second ? k1.p : k0.p;
   unsigned long long* ukeys = second ? k0.p : k1.p;
@@ -1322,6 +1607,166 @@ static unsigned long long verify_pairs_chunk(const Ctx& c, const ProbeView& v, c
   return U;
 }
 
+// Mode L for one chunk's candidates [0, n_cand): pair keys, then
+// verify_pair_keys.  Returns the number of distinct pairs.
+template <bool SELF>
+static unsigned long long verify_pairs_chunk(const Ctx& c, const ProbeView& v, const Hit* hits,
+                                             const unsigned long long* off, unsigned long long n_hits,
+                                             unsigned long long n_cand, Counters* ctr, AccOut* scratch,
+                                             AcceptBuf* acc) {
+  const int pshift = bits_for(v.n_index);
+  DBuf<unsigned long long> k0(c, n_cand);
+  const unsigned g = persistent_grid(k_pair_keys<SELF>, (n_cand + (unsigned long long)BLOCK * V_RUN - 1) /
+                                                            ((unsigned long long)BLOCK * V_RUN));
+  k_pair_keys<SELF><<<g, BLOCK, 0, c.stream>>>(v, hits, off, n_hits, 0, n_cand, pshift, k0.p, ctr, nullptr);
+  PJ_LAUNCHED("k_pair_keys");
+  return verify_pair_keys<SELF>(c, v, k0, n_cand, ctr, scratch, acc);
+}
+
+// Candidate pairs the fused kernel can send to one overflow sub-list; a join
+// with more falls back to the chunked pipeline.
+constexpr unsigned long long FUSED_OVF_CAP = 1ull << 20;
+
+// The overflow sub-lists, one after another: list k (n[k] keys at
+// src + k * cap) to dst + start[k], a block per list.
+__global__ void k_gather_lists(const unsigned long long* __restrict__ src, const unsigned long long* __restrict__ n,
+                               const unsigned long long* __restrict__ start, unsigned long long cap,
+                               unsigned long long* __restrict__ dst) {
+  const unsigned k = blockIdx.x;
+  const unsigned long long m = min(n[k], cap);
+  for (unsigned long long i = threadIdx.x; i < m; i += blockDim.x) dst[start[k] + i] = src[k * cap + i];
+}
+
+// Probes per work item of the fused kernel: a lane per probe when groups are
+// interleaved, else at least FTASKS groups for a warp.
+static int fused_ppi(const ProbeView& v) {
+  return v.interleave ? 32 : std::max(1, FTASKS / groups_per_probe(v.tau, true));
+}
+
+// The fused kernel's verification form for v's probes (the lengths of its
+// shortest and longest probe against fused_warp_from).
+static int fused_form_of(const Ctx& c, const ProbeView& v) {
+  uint32_t lens[2] = {0, 0};
+  PJ_CUDA(cudaMemcpyAsync(&lens[0], v.plen + v.pbegin, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.stream));
+  PJ_CUDA(cudaMemcpyAsync(&lens[1], v.plen + v.pbegin + v.pcount - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                          c.stream));
+  c.sync();
+  return v.fused_warp_from <= (int)lens[0] ? FUSED_WARP : v.fused_warp_from > (int)lens[1] ? FUSED_THREAD : FUSED_CUT;
+}
+
+// Capacities of the fused kernel's lists for v's probes: keys per overflow
+// sub-list, long runs.
+static unsigned long long fused_ovf_cap(const ProbeView& v) {
+  return std::min<unsigned long long>(FUSED_OVF_CAP,
+                                      std::max<unsigned long long>(1 << 12, 16ull * v.pcount / FOVF_LISTS));
+}
+static unsigned long long fused_heavy_cap(const ProbeView& v) {
+  return std::max<unsigned long long>(1 << 16, v.pcount);
+}
+
+// The fused self join (k_fused_self) over all of v's probes, then mode L over
+// the overflow list, appending to acc.  False (nothing appended) when the
+// overflow list would not hold the overflow: the caller runs the chunked
+// pipeline instead.
+static bool fused_self_join(const Ctx& c, const ProbeView& v, AcceptBuf& acc, Counters* ctr, Timings& tm) {
+  EventTimer tv(c.stream);
+  tv.start();
+  const int pshift = bits_for(v.n_index);
+  const int ppi = fused_ppi(v);
+  const int form = fused_form_of(c, v);
+  const unsigned long long n_items = ((unsigned long long)v.pcount + ppi - 1) / ppi;
+  const unsigned long long ovf_cap = fused_ovf_cap(v);
+  const unsigned long long heavy_cap = fused_heavy_cap(v);
+  DBuf<unsigned long long> work(c, 3), ovf(c, FOVF_LISTS + FOVF_LISTS * ovf_cap);
+  DBuf<Hit> heavy(c, heavy_cap);
+  Counters saved{};
+  PJ_CUDA(cudaMemcpyAsync(&saved, ctr, sizeof(saved), cudaMemcpyDeviceToHost, c.stream));
+  c.sync();
+  acc.run(
+      [&](AccOut o) {
+        PJ_CUDA(cudaMemsetAsync(work.p, 0, 3 * sizeof(unsigned long long), c.stream));
+        PJ_CUDA(cudaMemsetAsync(ovf.p, 0, FOVF_LISTS * sizeof(unsigned long long), c.stream));
+#define PJ_FORM(W, F)                                                                                          \
+  do {                                                                                                        \
+    const unsigned g = persistent_grid(k_fused_self<W, F>, n_items, FB);                                      \
+    k_fused_self<W, F><<<g, FB, 0, c.stream>>>(v, ppi, v.fused_warp_from, work.p, ovf.p, ovf_cap, heavy.p,      \
+                                               heavy_cap, pshift, o, ctr);                                    \
+    PJ_LAUNCHED("k_fused_self");                                                                              \
+  } while (0)
+#define PJ_CALL(W)                               \
+  do {                                           \
+    if (form == FUSED_THREAD) PJ_FORM(W, FUSED_THREAD); \
+    else if (form == FUSED_WARP) PJ_FORM(W, FUSED_WARP); \
+    else PJ_FORM(W, FUSED_CUT);                  \
+  } while (0)
+        PJ_BY_TAU(v.tau, PJ_CALL);
+#undef PJ_CALL
+#undef PJ_FORM
+      },
+      [&](unsigned long long after) { return 2 * after; });
+  unsigned long long n_work[3] = {0, 0, 0}, n_sub[FOVF_LISTS], start[FOVF_LISTS];
+  PJ_CUDA(cudaMemcpyAsync(n_sub, ovf.p, sizeof(n_sub), cudaMemcpyDeviceToHost, c.stream));
+  PJ_CUDA(cudaMemcpyAsync(n_work, work.p, sizeof(n_work), cudaMemcpyDeviceToHost, c.stream));
+  c.sync();
+  unsigned long long n_ovf = 0, sub_max = 0;
+  for (int k = 0; k < FOVF_LISTS; ++k) {
+    start[k] = n_ovf;
+    n_ovf += n_sub[k];
+    sub_max = std::max(sub_max, n_sub[k]);
+  }
+  const unsigned long long n_heavy = n_work[2];
+  // the long runs' candidates: offsets of the Hits' runs
+  DBuf<unsigned long long> cnt, off;
+  unsigned long long n_hcand = 0;
+  if (n_heavy && n_heavy <= heavy_cap) {
+    cnt.reset(c, n_heavy + 1);
+    off.reset(c, n_heavy + 1);
+    PJ_CUDA(cudaMemsetAsync(cnt.p + n_heavy, 0, sizeof(unsigned long long), c.stream));
+    k_hit_counts<<<ceil_div(n_heavy, 256), 256, 0, c.stream>>>(heavy.p, n_heavy, cnt.p, nullptr);
+    PJ_LAUNCHED("k_hit_counts");
+    exclusive_scan<unsigned long long>(c, cnt.p, off.p, n_heavy + 1);
+    PJ_CUDA(cudaMemcpyAsync(&n_hcand, off.p + n_heavy, sizeof(n_hcand), cudaMemcpyDeviceToHost, c.stream));
+    c.sync();
+  }
+  if (getenv("PJ_TRACE"))
+    fprintf(stderr,
+            "[pj] fused: %llu items of %d probes, %llu distinct pairs in-kernel, %llu to the overflow list, "
+            "%llu long runs (%llu candidates)\n",
+            n_items, ppi, n_work[1], n_ovf, n_heavy, n_hcand);
+  if (sub_max > ovf_cap || n_heavy > heavy_cap || n_ovf + n_hcand > PAIR_MODE_MAX_CANDS) {
+    // wind the counters back: the chunked pipeline redoes the join
+    PJ_CUDA(cudaMemcpyAsync(ctr, &saved, sizeof(saved), cudaMemcpyHostToDevice, c.stream));
+    c.sync();
+    return false;
+  }
+  tm.distinct += n_work[1];
+  if (n_ovf + n_hcand) {  // mode L over the long runs' candidates and the overflow list
+    DBuf<unsigned long long> keys(c, n_hcand + n_ovf);
+    if (n_hcand) {
+      const unsigned g = persistent_grid(k_pair_keys<true>, (n_hcand + (unsigned long long)BLOCK * V_RUN - 1) /
+                                                                ((unsigned long long)BLOCK * V_RUN));
+      k_pair_keys<true><<<g, BLOCK, 0, c.stream>>>(v, heavy.p, off.p, n_heavy, 0, n_hcand, pshift, keys.p, ctr,
+                                                   nullptr);
+      PJ_LAUNCHED("k_pair_keys");
+    }
+    if (n_ovf) {
+      DBuf<unsigned long long> dstart(c, FOVF_LISTS);
+      PJ_CUDA(cudaMemcpyAsync(dstart.p, start, sizeof(start), cudaMemcpyHostToDevice, c.stream));
+      k_gather_lists<<<FOVF_LISTS, 256, 0, c.stream>>>(ovf.p + FOVF_LISTS, ovf.p, dstart.p, ovf_cap,
+                                                       keys.p + n_hcand);
+      PJ_LAUNCHED("k_gather_lists");
+      c.sync();  // `start` lives on this stack frame
+    }
+    ProbeView vp = v;
+    vp.pair_warp = v.fused_warp_from == 0;
+    tm.distinct += verify_pair_keys<true>(c, vp, keys, n_hcand + n_ovf, ctr, nullptr, &acc);
+  }
+  tv.stop();
+  tm.verify += tv.ms();
+  trace_mark(c, "join: fused select + probe + verify");
+  return true;
+}
+
 template <bool SELF, bool MULTI>
 static void probe_and_verify(const Ctx& c, const ProbeView& v0, uint32_t fb_count, AcceptBuf& acc, Counters* ctr,
                              Counters& h, Timings& tm, const unsigned long long* h_qgoff) {
@@ -1334,15 +1779,26 @@ static void probe_and_verify(const Ctx& c, const ProbeView& v0, uint32_t fb_coun
   DBuf<uint32_t> gcount, goff;
   DBuf<unsigned long long> cnt, off;
   unsigned long long total_cand = 0, verified = 0;
-  for (uint32_t done = 0; done < v0.pcount;) {
-    ProbeView v = v0;
-    v.pbegin = v0.pbegin + done;
-    v.pcount = std::min(chunk_items, v0.pcount - done);
+  bool fused_done = false;
+  ProbeView vc = v0;  // the probes of the chunked pipeline
+  if (SELF && !MULTI && v0.fused && v0.pcount) {  // the fused persistent kernel over the probes from fused_q_cut
+    const uint32_t end = v0.pbegin + v0.pcount;
+    const uint32_t qf = std::min(end, std::max(v0.pbegin, v0.fused_q_cut));
+    ProbeView vf = v0;
+    vf.pbegin = qf;
+    vf.pcount = end - qf;
+    fused_done = vf.pcount > 0 && fused_self_join(c, vf, acc, ctr, tm);
+    if (fused_done) vc.pcount = qf - v0.pbegin;
+  }
+  for (uint32_t done = 0; done < vc.pcount;) {
+    ProbeView v = vc;
+    v.pbegin = vc.pbegin + done;
+    v.pcount = std::min(chunk_items, vc.pcount - done);
     unsigned long long n_groups =
         (MULTI || !v.interleave) ? (unsigned long long)v.pcount * G : interleaved_groups(v.pcount, G);
     if (MULTI) {  // probes whose groups fit the budget (at least one)
       uint32_t q1 = v.pbegin + 1;
-      while (q1 < v0.pbegin + v0.pcount && h_qgoff[q1 + 1] - h_qgoff[v.pbegin] <= group_budget) ++q1;
+      while (q1 < vc.pbegin + vc.pcount && h_qgoff[q1 + 1] - h_qgoff[v.pbegin] <= group_budget) ++q1;
       v.pcount = q1 - v.pbegin;
       n_groups = h_qgoff[q1] - h_qgoff[v.pbegin];
       if (n_groups == 0) {
@@ -1366,7 +1822,7 @@ static void probe_and_verify(const Ctx& c, const ProbeView& v0, uint32_t fb_coun
     h.candidates += n_cand;
     h.hits += n_hits;
     total_cand += n_cand;
-    const double remaining_groups = (double)(v0.pcount - done - v.pcount) / std::max(1u, v.pcount) + 1.0;  // chunks left
+    const double remaining_groups = (double)(vc.pcount - done - v.pcount) / std::max(1u, v.pcount) + 1.0;  // chunks left
     if (!MULTI && v.pair_mode && n_cand <= PAIR_MODE_MAX_CANDS) {  // mode L
       tv.start();
       tm.distinct += verify_pairs_chunk<SELF>(c, v, hits.p, off.p, n_hits, n_cand, ctr, nullptr, &acc);
@@ -1428,7 +1884,9 @@ static void probe_and_verify(const Ctx& c, const ProbeView& v0, uint32_t fb_coun
   const unsigned long long cand = h.candidates, nh = h.hits;
   PJ_CUDA(cudaMemcpyAsync(&h, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, c.stream));
   c.sync();
-  h.candidates = cand;
+  // the chunked pipeline counts candidates and hits on the host, the fused
+  // kernel its candidates on the device
+  h.candidates = cand + (fused_done ? h.candidates : 0ull);
   h.hits = nh;
   if (h.err)
     fail(PJ_ECUDA, std::string("segment index consistency check failed (") +
@@ -1559,13 +2017,16 @@ static void run_join(const Ctx& c, const ProbeView& v, bool self, uint32_t fb_co
 // (best of two runs, CUDA events) wins.  Decisions are cached per workload
 // signature for the process and, when the index names a cache file
 // (pj_options.autotune_cache, else the environment variable
-// PJ_AUTOTUNE_CACHE), in that file (one "signature|cut|block|mode" line each).
+// PJ_AUTOTUNE_CACHE), in that file (one "signature|cut|block|mode|from" line
+// each).
 
 struct TuneResult {
-  int warp_min_len = 65536;
+  int warp_min_len = 65536;  // with `fused`: the fused kernel's warp-per-pair cut
   int block_thread = 256;
   int pair_mode = 0;  // mode L
   int pair_warp = 0;
+  int fused = 0;  // mode L by the fused kernel (k_fused_self)
+  int fused_from_len = 0;  // with `fused`: shorter probes run in the chunked mode-L pipeline
 };
 
 static std::mutex g_tune_mu;
@@ -1597,14 +2058,20 @@ static bool tune_from_file(const char* path, const std::string& key, TuneResult&
   while (std::getline(f, line)) {
     const size_t a = line.find('|'), b = line.rfind('|');
     if (a == std::string::npos || a == b || line.substr(0, a) != key) continue;
-    // signature|cut|block|pairs (pairs: 0 extension, 1 thread per pair, 2 warp per pair)
+    // signature|cut|block|pairs|from (pairs: 0 extension, 1 thread per pair,
+    // 2 warp per pair, 3 the fused kernel with a warp per pair from length
+    // `cut` for the probes from length `from`)
     const size_t m = line.find('|', a + 1);
     if (m == std::string::npos || m == b) continue;
+    const size_t pm_at = line.find('|', m + 1);
+    if (pm_at == std::string::npos || pm_at == b) continue;
     r.warp_min_len = atoi(line.c_str() + a + 1);
     r.block_thread = atoi(line.c_str() + m + 1);
-    const int pm = atoi(line.c_str() + b + 1);
+    const int pm = atoi(line.c_str() + pm_at + 1);
     r.pair_mode = pm > 0;
     r.pair_warp = pm == 2;
+    r.fused = pm == 3;
+    r.fused_from_len = atoi(line.c_str() + b + 1);
     found = true;  // the last line for a key wins
   }
   return found;
@@ -1614,9 +2081,13 @@ static void tune_to_file(const char* path, const std::string& key, const TuneRes
   if (!path || !path[0]) return;
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%s|%d|%d|%d\n", key.c_str(), r.warp_min_len, r.block_thread, r.pair_mode ? 1 + r.pair_warp : 0);
+  fprintf(f, "%s|%d|%d|%d|%d\n", key.c_str(), r.warp_min_len, r.block_thread,
+          r.fused ? 3 : r.pair_mode ? 1 + r.pair_warp : 0, r.fused_from_len);
   fclose(f);
 }
+
+// Average string length from which the autotuner tries the fused kernel.
+constexpr double FUSED_MIN_AVG_LEN = 32.0;
 
 static TuneResult autotune_self(pj_index& idx, const ProbeView& v0) {
   const Ctx& c = idx.ctx;
@@ -1707,9 +2178,76 @@ static TuneResult autotune_self(pj_index& idx, const ProbeView& v0) {
       }
     }
   }
+  // the fused kernel does selection, probing and verification in one launch:
+  // whole joins of the sample with it (the probes shorter than `from` in the
+  // chunked mode-L pipeline), against a whole join with the best choice above,
+  // when that choice was timed over every candidate of the sample and the
+  // strings are not short (short strings have few-character segments and
+  // long posting runs, which the chunked pipeline spreads over the GPU)
+  const double avg_len = idx.n ? (double)idx.total_bytes / idx.n : 0.0;
+  if (S == n_cand && avg_len >= FUSED_MIN_AVG_LEN) {
+    gcount.release();
+    goff.release();
+    hits.release();
+    cnt.release();
+    off.release();
+    AcceptBuf facc(c, ctr.p, std::min<unsigned long long>(S, 1ull << 20));
+    auto whole_join_ms = [&](const ProbeView& vj) {
+      double ms = 1e30;
+      for (int rep = 0; rep < 2; ++rep) {
+        PJ_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(Counters), c.stream));
+        Counters hh{};
+        Timings ft;
+        tm.start();
+        probe_and_verify<true, false>(c, vj, 0, facc, ctr.p, hh, ft, nullptr);
+        tm.stop();
+        ms = std::min(ms, (double)tm.ms());
+      }
+      return ms;
+    };
+    {  // the chunked pipeline with the choice so far, as a whole join of the sample
+      ProbeView vb = v;
+      vb.pair_mode = best.pair_mode;
+      vb.pair_warp = best.pair_warp;
+      if (vb.pair_mode) vb.hit_sides = 0;
+      vb.block_thread = best.block_thread;
+      if (!best.pair_mode && best.warp_min_len <= idx.lmax) vb.warp_q_cut = idx.h_bbeg[std::max(0, best.warp_min_len)];
+      best_ms = whole_join_ms(vb);
+    }
+    const uint32_t q_last = v.pbegin + v.pcount - 1;
+    std::vector<int> froms{0};
+    for (int e : {16, 32, 64, 128, 256})
+      if (e <= idx.lmax && idx.h_bbeg[e] > v.pbegin && idx.h_bbeg[e] <= q_last) froms.push_back(e);
+    for (int from : froms) {
+      for (int cut : {65536, 0}) {
+        ProbeView vf = v;
+        vf.pair_mode = 1;
+        vf.pair_warp = cut == 0;
+        vf.hit_sides = 0;
+        vf.fused = 1;
+        vf.fused_warp_from = cut;
+        vf.fused_q_cut = from > 0 ? idx.h_bbeg[from] : 0;
+        const double ms = whole_join_ms(vf);
+        if (getenv("PJ_TRACE"))
+          fprintf(stderr, "[pj] autotune tau=%d fused from length %d, warp per pair %s: %.3f ms (best so far %.3f ms)\n",
+                  tau, from, cut == 0 ? "yes" : "no", ms, best_ms);
+        if (ms < best_ms) {
+          best_ms = ms;
+          best.pair_mode = 1;
+          best.pair_warp = cut == 0;
+          best.fused = 1;
+          best.warp_min_len = cut;
+          best.fused_from_len = from;
+        }
+      }
+    }
+  }
   if (getenv("PJ_TRACE"))
-    fprintf(stderr, "[pj] autotune tau=%d: warp from length %d, block %d, distinct pairs %d (warp %d)\n", tau,
-            best.warp_min_len, best.block_thread, best.pair_mode, best.pair_warp);
+    fprintf(stderr,
+            "[pj] autotune tau=%d: warp from length %d, block %d, distinct pairs %d (warp %d), fused %d from length "
+            "%d\n",
+            tau, best.warp_min_len, best.block_thread, best.pair_mode, best.pair_warp, best.fused,
+            best.fused_from_len);
   return best;
 }
 
@@ -1740,6 +2278,27 @@ static void force_mode(const pj_index& idx, TuneResult& r) {
     r.pair_mode = m > 0;
     r.pair_warp = m == 2;
   }
+  if (!r.pair_mode) r.fused = 0;
+}
+
+// PJ_FUSED=0|1|2 (chunked pipeline, the fused kernel with a thread per
+// pair, the fused kernel with a warp per pair) overrides a self join's
+// choice, PJ_FUSED_FROM=<length> the shortest probe length of the fused
+// kernel.
+static void force_fused(TuneResult& r) {
+  const char* fz = getenv("PJ_FUSED");
+  if (fz && fz[0]) {
+    const int m = atoi(fz);
+    r.fused = m > 0;
+    r.fused_from_len = 0;
+    if (r.fused) {
+      r.pair_mode = 1;
+      r.pair_warp = m == 2;
+      r.warp_min_len = m == 2 ? 0 : 65536;
+    }
+  }
+  const char* ff = getenv("PJ_FUSED_FROM");
+  if (r.fused && ff && ff[0]) r.fused_from_len = std::max(0, atoi(ff));
 }
 
 // The tuning of a self join: environment overrides, then the caches, then a
@@ -1765,6 +2324,7 @@ static TuneResult self_join_tuning(pj_index& idx, const ProbeView& v, float* tun
   }
   if (!idx.autotune) default_mode(idx, r);
   force_mode(idx, r);
+  force_fused(r);
   const char* e = getenv("PJ_WARP_MIN_LEN");
   if (e && e[0]) r.warp_min_len = atoi(e);
   const char* bk = getenv("PJ_VERIFY_BLOCK");
@@ -1829,12 +2389,17 @@ static ProbeView index_side(const pj_index& idx, const Partition& part) {
 // than PJ_GRAPH_MAX_GROUPS probe groups (2^28 by default; the graph probes
 // all groups in one pass, where the eager join takes chunks).
 
+// fz (the fused form, else NULL): fz[2] nonzero when one of its lists
+// outgrew its capacity; its candidates are then counted in ctr->candidates.
 __global__ void k_self_finish(const Counters* __restrict__ ctr, const PlanSizes* __restrict__ sizes,
-                              const unsigned long long* __restrict__ unique, PlanHeader* header) {
+                              const unsigned long long* __restrict__ unique, PlanHeader* header,
+                              const unsigned long long* __restrict__ fz) {
   PlanHeader h;
   h.groups = 0;
   h.hits = sizes->hits;
-  h.cands = sizes->cands;
+  h.cands = fz ? ctr->candidates : sizes->cands;
+  h.overflow = fz ? fz[2] : 0ull;
+  const unsigned long long in_kernel = fz ? fz[3] : 0ull;
   h.accepted = ctr->accepted;
   h.pairs = sizes->pairs;
   h.lookups = ctr->lookups;
@@ -1842,14 +2407,15 @@ __global__ void k_self_finish(const Counters* __restrict__ ctr, const PlanSizes*
   h.fallback = ctr->fallback;
   h.err = ctr->err;
   h.filtered = ctr->filtered;
-  h.unique = *unique;
+  h.unique = *unique + in_kernel;
   *header = h;
 }
 
 struct SelfPlan {
   Ctx ctx;  // the index's allocator on the plan's own stream
   cudaStream_t stream = nullptr;
-  int warp_min_len = 0, block_thread = 0, pair_mode = 0, pair_warp = 0;  // the tuning it was recorded with
+  int warp_min_len = 0, block_thread = 0, pair_mode = 0, pair_warp = 0, fused = 0,
+      fused_from_len = 0;  // the tuning it was recorded with
   uint32_t fb_count = 0;
   int a_bits = 0;
   unsigned long long n_groups = 0, cap_hits = 0, cap_cands = 0, cap_acc = 0, cap_pairs = 0;
@@ -1859,6 +2425,13 @@ struct SelfPlan {
   DBuf<uint32_t> gcounts, goff, pv0, pv1, pflags, ppos, ae0, ae1, flags, pos;
   DBuf<Hit> hits;
   DBuf<pj_pair> out;
+  // the fused form: k_fused_self over probes [q_cut, end), the chunked
+  // mode-L pipeline over the shorter ones
+  uint32_t q_cut = 0;
+  int fused_form = 0, ppi = 1;
+  unsigned long long ovf_cap = 0, heavy_cap = 0;
+  DBuf<unsigned long long> fwork, fovf, fhcnt, fhoff, fhk, fz, fstart;
+  DBuf<Hit> fheavy;
   HostBuf header;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -1868,8 +2441,10 @@ struct SelfPlan {
     if (stream) cudaStreamSynchronize(stream);
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
-    DBuf<unsigned long long>* b64[] = {&nuniq, &gmask, &hcnt, &hoff, &pk0, &pk1, &ukeys, &ak0, &ak1};
+    DBuf<unsigned long long>* b64[] = {&nuniq, &gmask, &hcnt, &hoff, &pk0, &pk1, &ukeys, &ak0, &ak1,
+                                       &fwork, &fovf, &fhcnt, &fhoff, &fhk, &fz, &fstart};
     for (auto* b : b64) b->release();
+    fheavy.release();
     DBuf<uint32_t>* b32[] = {&gcounts, &goff, &pv0, &pv1, &pflags, &ppos, &ae0, &ae1, &flags, &pos};
     for (auto* b : b32) b->release();
     counters.release();
@@ -1884,22 +2459,116 @@ struct SelfPlan {
   }
 };
 
+// The recorded fused join's bookkeeping: fz[0] = long runs kept (at most
+// heavy_cap), fz[3] = distinct pairs verified in the kernel, and, in
+// k_fused_tail_starts, the place of every list of pair
+// keys after the chunked pipeline's sz->cands: the 64 overflow sub-lists,
+// then the long runs' keys (fz[1] of them); sz->cands becomes the total, the
+// chunked pipeline's candidates join ctr->candidates, and fz[2] flags a list
+// that outgrew its capacity (the replay is then discarded).
+__global__ void k_fused_heavy_n(const unsigned long long* __restrict__ work, unsigned long long heavy_cap,
+                                unsigned long long* __restrict__ fz) {
+  fz[0] = min(work[2], heavy_cap);
+  fz[2] = work[2] > heavy_cap ? 1ull : 0ull;
+  fz[3] = work[1];  // distinct pairs verified in the kernel
+}
+
+__global__ void k_fused_tail_starts(const unsigned long long* __restrict__ ovf_n, unsigned long long ovf_cap,
+                                    unsigned long long* __restrict__ fz, unsigned long long* __restrict__ start,
+                                    PlanSizes* sz, Counters* ctr, unsigned long long cap_keys) {
+  unsigned long long at = sz->cands, flag = fz[2];
+  ctr->candidates += sz->cands;
+  for (int k = 0; k < FOVF_LISTS; ++k) {
+    start[k] = at;
+    at += min(ovf_n[k], ovf_cap);
+    if (ovf_n[k] > ovf_cap) flag = 1;
+  }
+  start[FOVF_LISTS] = at;
+  at += fz[1];
+  if (at > cap_keys) flag = 1;
+  sz->cands = min(at, cap_keys);
+  fz[2] = flag;
+}
+
+// Lists k < 64: overflow sub-list k; list 64: the long runs' keys.  Block k
+// copies list k to dst + start[k] (clamped to cap).
+__global__ void k_fused_gather(const unsigned long long* __restrict__ ovf, unsigned long long ovf_cap,
+                               const unsigned long long* __restrict__ hk, const unsigned long long* __restrict__ fz,
+                               const unsigned long long* __restrict__ start, unsigned long long* __restrict__ dst,
+                               unsigned long long cap) {
+  const unsigned k = blockIdx.x;
+  const unsigned long long* src = k < FOVF_LISTS ? ovf + FOVF_LISTS + k * ovf_cap : hk;
+  const unsigned long long m = k < FOVF_LISTS ? min(ovf[k], ovf_cap) : fz[1];
+  const unsigned long long s = start[k];
+  for (unsigned long long i = threadIdx.x; i < m && s + i < cap; i += blockDim.x) dst[s + i] = src[i];
+}
+
+static void record_fused_tail(const Ctx& c, const ProbeView& v, SelfPlan& P, Counters* ctr, PlanSizes* sz,
+                              const AccOut& acc) {
+  ProbeView vf = v;
+  vf.pbegin = P.q_cut;
+  vf.pcount = v.pbegin + v.pcount - P.q_cut;
+  const int pshift = bits_for(v.n_index);
+  const unsigned long long n_items = ((unsigned long long)vf.pcount + P.ppi - 1) / P.ppi;
+  PJ_CUDA(cudaMemsetAsync(P.fwork.p, 0, 3 * sizeof(unsigned long long), c.stream));
+  PJ_CUDA(cudaMemsetAsync(P.fovf.p, 0, FOVF_LISTS * sizeof(unsigned long long), c.stream));
+  PJ_CUDA(cudaMemsetAsync(P.fz.p, 0, 4 * sizeof(unsigned long long), c.stream));
+#define PJ_FORM(W, F)                                                                                          \
+  do {                                                                                                        \
+    const unsigned g = persistent_grid(k_fused_self<W, F>, n_items, FB);                                      \
+    k_fused_self<W, F><<<g, FB, 0, c.stream>>>(vf, P.ppi, vf.fused_warp_from, P.fwork.p, P.fovf.p, P.ovf_cap,   \
+                                               P.fheavy.p, P.heavy_cap, pshift, acc, ctr);                    \
+    PJ_LAUNCHED("k_fused_self");                                                                              \
+  } while (0)
+#define PJ_CALL(W)                                             \
+  do {                                                         \
+    if (P.fused_form == FUSED_THREAD) PJ_FORM(W, FUSED_THREAD); \
+    else if (P.fused_form == FUSED_WARP) PJ_FORM(W, FUSED_WARP); \
+    else PJ_FORM(W, FUSED_CUT);                                \
+  } while (0)
+  PJ_BY_TAU(v.tau, PJ_CALL);
+#undef PJ_CALL
+#undef PJ_FORM
+  // the long runs' pair keys
+  k_fused_heavy_n<<<1, 1, 0, c.stream>>>(P.fwork.p, P.heavy_cap, P.fz.p);
+  PJ_LAUNCHED("k_fused_heavy_n");
+  k_hit_counts<<<stride_grid(P.heavy_cap), 256, 0, c.stream>>>(P.fheavy.p, P.heavy_cap, P.fhcnt.p, P.fz.p);
+  PJ_LAUNCHED("k_hit_counts");
+  exclusive_scan_dn<unsigned long long>(c, P.fhcnt.p, P.fhoff.p, P.heavy_cap, P.fz.p, P.fz.p + 1);
+  const unsigned gk = persistent_grid(k_pair_keys<true>, ~0ull >> 8);
+  k_pair_keys<true><<<gk, BLOCK, 0, c.stream>>>(vf, P.fheavy.p, P.fhoff.p, P.heavy_cap, 0, P.cap_cands, pshift,
+                                                P.fhk.p, ctr, P.fz.p);
+  PJ_LAUNCHED("k_pair_keys");
+  // every list after the chunked pipeline's keys
+  k_fused_tail_starts<<<1, 1, 0, c.stream>>>(P.fovf.p, P.ovf_cap, P.fz.p, P.fstart.p, sz, ctr, P.cap_cands);
+  PJ_LAUNCHED("k_fused_tail_starts");
+  k_fused_gather<<<FOVF_LISTS + 1, 256, 0, c.stream>>>(P.fovf.p, P.ovf_cap, P.fhk.p, P.fz.p, P.fstart.p, P.pk0.p,
+                                                        P.cap_cands);
+  PJ_LAUNCHED("k_fused_gather");
+}
+
 static void record_self_plan(const Ctx& c, const ProbeView& v, SelfPlan& P) {
   Counters* ctr = reinterpret_cast<Counters*>(P.counters.p);
   PlanSizes* sz = P.sizes.p;
   PJ_CUDA(cudaMemsetAsync(ctr, 0, sizeof(Counters), c.stream));
+  ProbeView vc = v;  // the probes of the chunked pipeline
+  if (P.fused) vc.pcount = P.q_cut - v.pbegin;
   // A4
-  const unsigned g1 = persistent_grid(k_group_counts<true, false>, (P.n_groups + BLOCK - 1) / BLOCK);
-  k_group_counts<true, false><<<g1, BLOCK, 0, c.stream>>>(v, P.n_groups, P.gcounts.p, P.gmask.p, ctr, nullptr);
-  PJ_LAUNCHED("k_group_counts");
-  exclusive_scan_dn<uint32_t>(c, P.gcounts.p, P.goff.p, P.n_groups, nullptr, &sz->hits);
-  const unsigned g2 = persistent_grid(k_group_hits<true, false>, (P.n_groups + BLOCK - 1) / BLOCK);
-  k_group_hits<true, false><<<g2, BLOCK, 0, c.stream>>>(v, P.n_groups, P.gcounts.p, P.gmask.p, P.goff.p, P.hits.p,
-                                                        nullptr, P.cap_hits);
-  PJ_LAUNCHED("k_group_hits");
-  k_hit_counts<<<stride_grid(P.cap_hits), 256, 0, c.stream>>>(P.hits.p, P.cap_hits, P.hcnt.p, &sz->hits);
-  PJ_LAUNCHED("k_hit_counts");
-  exclusive_scan_dn<unsigned long long>(c, P.hcnt.p, P.hoff.p, P.cap_hits, &sz->hits, &sz->cands);
+  if (P.n_groups) {
+    const unsigned g1 = persistent_grid(k_group_counts<true, false>, (P.n_groups + BLOCK - 1) / BLOCK);
+    k_group_counts<true, false><<<g1, BLOCK, 0, c.stream>>>(vc, P.n_groups, P.gcounts.p, P.gmask.p, ctr, nullptr);
+    PJ_LAUNCHED("k_group_counts");
+    exclusive_scan_dn<uint32_t>(c, P.gcounts.p, P.goff.p, P.n_groups, nullptr, &sz->hits);
+    const unsigned g2 = persistent_grid(k_group_hits<true, false>, (P.n_groups + BLOCK - 1) / BLOCK);
+    k_group_hits<true, false><<<g2, BLOCK, 0, c.stream>>>(vc, P.n_groups, P.gcounts.p, P.gmask.p, P.goff.p,
+                                                          P.hits.p, nullptr, P.cap_hits);
+    PJ_LAUNCHED("k_group_hits");
+    k_hit_counts<<<stride_grid(P.cap_hits), 256, 0, c.stream>>>(P.hits.p, P.cap_hits, P.hcnt.p, &sz->hits);
+    PJ_LAUNCHED("k_hit_counts");
+    exclusive_scan_dn<unsigned long long>(c, P.hcnt.p, P.hoff.p, P.cap_hits, &sz->hits, &sz->cands);
+  } else {  // every probe in the fused kernel
+    PJ_CUDA(cudaMemsetAsync(sz, 0, sizeof(PlanSizes), c.stream));
+  }
   // A5 (mode L) + A6 + A8
   const AccOut acc{P.ak0.p, P.ae0.p, P.cap_acc};
   if (!P.pair_mode) {
@@ -1915,10 +2584,13 @@ static void record_self_plan(const Ctx& c, const ProbeView& v, SelfPlan& P) {
 #undef PJ_CALL
   } else {
     const int pshift = bits_for(v.n_index);
-    const unsigned gk = persistent_grid(k_pair_keys<true>, ~0ull >> 8);
-    k_pair_keys<true><<<gk, BLOCK, 0, c.stream>>>(v, P.hits.p, P.hoff.p, P.cap_hits, 0, P.cap_cands, pshift, P.pk0.p, ctr,
-                                                  &sz->hits);
-    PJ_LAUNCHED("k_pair_keys");
+    if (P.n_groups) {
+      const unsigned gk = persistent_grid(k_pair_keys<true>, ~0ull >> 8);
+      k_pair_keys<true><<<gk, BLOCK, 0, c.stream>>>(vc, P.hits.p, P.hoff.p, P.cap_hits, 0, P.cap_cands, pshift,
+                                                    P.pk0.p, ctr, &sz->hits);
+      PJ_LAUNCHED("k_pair_keys");
+    }
+    if (P.fused) record_fused_tail(c, v, P, ctr, sz, acc);  // its pair keys after the chunked ones
     const bool second = radix_sort_pairs_dn<unsigned long long>(c, P.pk0.p, P.pv0.p, P.pk1.p, P.pv1.p, P.cap_cands,
                                                                 &sz->cands, 2 * pshift);
     const unsigned long long* sorted = second ? P.pk1.p : P.pk0.p;
@@ -1964,7 +2636,8 @@ static void record_self_plan(const Ctx& c, const ProbeView& v, SelfPlan& P) {
   k_emit_pairs<<<stride_grid(P.cap_acc), 256, 0, c.stream>>>(keys, eds, P.flags.p, P.pos.p, P.cap_acc, v.key_shift,
                                                              P.out.p, &ctr->accepted, P.cap_pairs);
   PJ_LAUNCHED("k_emit_pairs");
-  k_self_finish<<<1, 1, 0, c.stream>>>(ctr, sz, P.nuniq.p, static_cast<PlanHeader*>(P.header.dev));
+  k_self_finish<<<1, 1, 0, c.stream>>>(ctr, sz, P.nuniq.p, static_cast<PlanHeader*>(P.header.dev),
+                                       P.fused ? P.fz.p : nullptr);
   PJ_LAUNCHED("k_self_finish");
 }
 
@@ -1980,9 +2653,13 @@ static unsigned long long with_slack(unsigned long long n) {
 static std::shared_ptr<SelfPlan> make_self_plan(pj_index& idx, const ProbeView& v, const TuneResult& tr,
                                                 uint32_t fb_count, const pj_stats& st, uint64_t pairs) {
   const int G = groups_per_probe(v.tau, true);
+  const uint32_t end = v.pbegin + v.pcount;
+  // the fused form: the chunked pipeline over probes [pbegin, q_cut)
+  const uint32_t q_cut = tr.fused ? std::min(end, std::max(v.pbegin, v.fused_q_cut)) : end;
+  const uint32_t n_chunked = q_cut - v.pbegin;
   const unsigned long long n_groups =
-      v.interleave ? interleaved_groups(v.pcount, G) : (unsigned long long)v.pcount * G;
-  if (n_groups == 0) return nullptr;  // nothing to probe
+      v.interleave ? interleaved_groups(n_chunked, G) : (unsigned long long)n_chunked * G;
+  if (n_groups == 0 && !tr.fused) return nullptr;  // nothing to probe
   // one probe pass over all groups (16 B each), however the eager join chunked them
   if (n_groups > std::min(env_knob("PJ_GRAPH_MAX_GROUPS", 1ull << 28), 1ull << 31)) return nullptr;
   if (!tr.pair_mode && aligned_cut(v, v.warp_q_cut) < v.pbegin + v.pcount) return nullptr;  // a warp range
@@ -1995,6 +2672,8 @@ static std::shared_ptr<SelfPlan> make_self_plan(pj_index& idx, const ProbeView& 
   P->block_thread = tr.block_thread;
   P->pair_mode = tr.pair_mode;
   P->pair_warp = tr.pair_warp;
+  P->fused = tr.fused;
+  P->fused_from_len = tr.fused_from_len;
   P->fb_count = fb_count;
   P->a_bits = bits_for(idx.n);
   P->n_groups = n_groups;
@@ -2027,9 +2706,28 @@ static std::shared_ptr<SelfPlan> make_self_plan(pj_index& idx, const ProbeView& 
   P->pos.reset(c, P->cap_acc);
   P->out.reset(c, P->cap_pairs);
   P->header.reset(sizeof(PlanHeader), true);
+  if (tr.fused) {
+    ProbeView vf = v;
+    vf.pbegin = q_cut;
+    vf.pcount = end - q_cut;
+    P->q_cut = q_cut;
+    P->ppi = fused_ppi(vf);
+    P->fused_form = fused_form_of(c, vf);
+    P->ovf_cap = fused_ovf_cap(vf);
+    P->heavy_cap = fused_heavy_cap(vf);
+    P->fwork.reset(c, 3);
+    P->fovf.reset(c, FOVF_LISTS + FOVF_LISTS * P->ovf_cap);
+    P->fheavy.reset(c, P->heavy_cap);
+    P->fhcnt.reset(c, P->heavy_cap + 1);
+    P->fhoff.reset(c, P->heavy_cap + 1);
+    P->fhk.reset(c, P->cap_cands);
+    P->fz.reset(c, 4);
+    P->fstart.reset(c, FOVF_LISTS + 1);
+  }
   size_t arena_bytes = scan_temp_bytes(n_groups, 4) + scan_temp_bytes(P->cap_hits, 8) +
                        2 * scan_temp_bytes(P->cap_cands, 4) + sort_temp_bytes(P->cap_cands) +
-                       scan_temp_bytes(P->cap_acc, 4) + sort_temp_bytes(P->cap_acc) + (1u << 16);
+                       scan_temp_bytes(P->cap_acc, 4) + sort_temp_bytes(P->cap_acc) +
+                       scan_temp_bytes(P->heavy_cap, 8) + (1u << 16);
   for (int attempt = 0;; ++attempt) {
     P->arena.reset(c, arena_bytes);
     c.sync();
@@ -2097,8 +2795,8 @@ static bool replay_self_plan(SelfPlan& P, const Ctx& rc, bool on_device, pj_resu
   if (h.err)
     fail(PJ_ECUDA, std::string("segment index consistency check failed (") +
                        ((h.err & 1) ? "posting outside the index" : "probe limit reached") + ")");
-  if (h.hits > P.cap_hits || (P.pair_mode && h.cands > P.cap_cands) || h.accepted > P.cap_acc ||
-      h.pairs > P.cap_pairs)
+  if (h.hits > P.cap_hits || (P.pair_mode && !P.fused && h.cands > P.cap_cands) || h.accepted > P.cap_acc ||
+      h.pairs > P.cap_pairs || h.overflow)
     return false;
   const uint64_t count = h.pairs;
   out->count = count;
@@ -2187,16 +2885,22 @@ static void self_join_impl(pj_index& idx, int tau, pj_result* out, bool on_devic
   } else {  // nothing to probe: only the fallback (if any) runs
     default_mode(idx, tr);
   }
-  if (tr.warp_min_len <= idx.lmax) v.warp_q_cut = idx.h_bbeg[std::max(0, tr.warp_min_len)];
+  if (tr.warp_min_len <= idx.lmax && !tr.fused) v.warp_q_cut = idx.h_bbeg[std::max(0, tr.warp_min_len)];
   v.block_thread = tr.block_thread;
   v.pair_mode = tr.pair_mode;
   v.pair_warp = tr.pair_warp;
+  v.fused = tr.fused;
+  v.fused_warp_from = tr.warp_min_len;
+  v.fused_q_cut = tr.fused_from_len <= 0 ? 0u
+                  : tr.fused_from_len > idx.lmax ? UINT32_MAX
+                                                 : idx.h_bbeg[tr.fused_from_len];
   if (v.pair_mode) v.hit_sides = 0;
   if (idx.graph_joins && whole) {
     if (idx.self_plans.size() < idx.parts.size()) idx.self_plans.resize(idx.parts.size());
     SelfPlan* sp = static_cast<SelfPlan*>(idx.self_plans[tau].get());
     if (sp && (sp->warp_min_len != tr.warp_min_len || sp->block_thread != tr.block_thread ||
-               sp->pair_mode != tr.pair_mode || sp->pair_warp != tr.pair_warp)) {
+               sp->pair_mode != tr.pair_mode || sp->pair_warp != tr.pair_warp || sp->fused != tr.fused ||
+               sp->fused_from_len != tr.fused_from_len)) {
       idx.self_plans[tau].reset();  // recorded with another tuning
       sp = nullptr;
     }
@@ -2207,6 +2911,7 @@ static void self_join_impl(pj_index& idx, int tau, pj_result* out, bool on_devic
         out->stats.warp_min_len = tr.warp_min_len;
         out->stats.verify_mode = tr.pair_mode ? PJ_VERIFY_PAIRS : PJ_VERIFY_EXTENSION;
         out->stats.pair_warp = tr.pair_mode ? tr.pair_warp : 0;
+        out->stats.fused = tr.fused;
         return;
       }
       pj_result_free(out);  // counts above the recorded capacities: run eagerly, record again
@@ -2228,6 +2933,7 @@ static void self_join_impl(pj_index& idx, int tau, pj_result* out, bool on_devic
   out->stats.tune_ms = tune_ms;
   out->stats.verify_mode = tr.pair_mode ? PJ_VERIFY_PAIRS : PJ_VERIFY_EXTENSION;
   out->stats.pair_warp = tr.pair_mode ? tr.pair_warp : 0;
+  out->stats.fused = tr.fused;
 }
 
 void self_join_range(pj_index& idx, int tau, uint32_t q_lo, uint32_t q_hi, bool fallback, pj_result* out,

@@ -26,6 +26,7 @@ struct PlanHeader {
   unsigned long long groups, hits, cands, accepted, pairs;
   unsigned long long lookups, cells, fallback, err;
   unsigned long long filtered, unique;  // screened-out candidates; distinct pairs (mode L)
+  unsigned long long overflow;          // nonzero: a list of the fused self join outgrew its capacity
 };
 
 struct PlanDev {

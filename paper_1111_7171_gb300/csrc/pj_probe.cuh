@@ -91,6 +91,10 @@ struct ProbeView {
   int pair_mode;  // 1: mode L (distinct candidate pairs verified once over the whole strings)
   int pair_warp;  // mode L: one warp per pair instead of one thread
   int share_prefix;  // mode L: consecutive pairs of a probe share the DP rows of common prefixes (Sec. 5.3)
+  int fused;         // self join, mode L: one persistent select/probe/verify kernel (k_fused_self)
+  int fused_warp_from;  // fused form: probes at least this long verify their pairs one warp per pair
+  uint32_t fused_q_cut;  // fused form: probes q >= fused_q_cut run in the fused kernel, the shorter ones
+                         // (the longest posting runs) in the chunked mode-L pipeline
   int block_warp;    // block size of the warp-per-candidate verification
 };
 
@@ -205,6 +209,27 @@ __host__ __device__ __forceinline__ uint32_t lookup_key(const ProbeView& v, bool
     cnt = x0;
   }
   return cnt;
+}
+
+// The lookups of a group's window: substrings s[p, li], p = lo .. hi, in
+// L_l^i, their keys rolled from one position to the next.  f(p, begin,
+// count) is called, in order of p, for every lookup that found postings to
+// verify.  (Loading the presence words of 8 positions back to back, so that
+// their latencies overlap, measured slower: the loop is bound by its integer
+// instructions, and the batch's extra registers cost occupancy.)
+template <class F>
+__device__ __forceinline__ void window_lookups(const ProbeView& v, bool self, uint32_t q, int ls, int l, int i, int li,
+                                               int lo, int hi, const uint8_t* s, int& err, F f) {
+  const uint32_t pw = seg_pow(li);
+  uint32_t V = v.phash && li > SEG_EXACT_MAX ? seg_value_from_prefix(v.phash + v.poff[q] + q, lo, li, pw)
+                                             : seg_value(s + lo, li);
+  for (int p = lo;; ++p) {
+    uint32_t b;
+    const uint32_t cnt = lookup_key(v, self, q, ls, l, seg_key_of(V, l, i), b, err);
+    if (cnt) f(p, b, cnt);
+    if (p == hi) break;
+    V = seg_roll(V, s[p], s[p + li], li, pw);  // p + li <= hi - 1 + li < ls
+  }
 }
 
 // Lookup of s[p, li] in L_l^i (lookup_key with the key computed here).

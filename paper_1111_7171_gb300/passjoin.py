@@ -51,7 +51,8 @@ class pj_stats(ctypes.Structure):
                 ("warp_min_len", ctypes.c_int32), ("tune_ms", ctypes.c_float), ("verify_mode", ctypes.c_int32),
                 ("pair_warp", ctypes.c_int32), ("filtered", ctypes.c_uint64),
                 ("distinct_pairs", ctypes.c_uint64), ("graph_replay", ctypes.c_int32), ("graph_ms", ctypes.c_float),
-                ("device_peak", ctypes.c_uint64), ("windows", ctypes.c_uint32)]
+                ("device_peak", ctypes.c_uint64), ("windows", ctypes.c_uint32),
+                ("fused", ctypes.c_int32)]
 
 
 class pj_result(ctypes.Structure):
@@ -362,7 +363,8 @@ def _stats(st: pj_stats) -> dict:
                 verify_block=int(st.verify_block), warp_min_len=int(st.warp_min_len), tune_ms=float(st.tune_ms),
                 verify_mode=int(st.verify_mode), pair_warp=int(st.pair_warp), filtered=int(st.filtered),
                 distinct_pairs=int(st.distinct_pairs), graph_replay=int(st.graph_replay),
-                graph_ms=float(st.graph_ms), device_peak=int(st.device_peak), windows=int(st.windows))
+                graph_ms=float(st.graph_ms), device_peak=int(st.device_peak), windows=int(st.windows),
+                fused=int(st.fused))
 
 
 class _HostPairs:

@@ -188,3 +188,34 @@ def test_graph_replay_launch_accounting():
         assert pj.pj_kernel_launches() - before == k
     finally:
         idx.free()
+
+
+@pytest.mark.parametrize("mode", ["1", "2"])
+def test_graph_replay_fused(monkeypatch, mode):
+    """The fused self join recorded into the graph: k_fused_self over the
+    probes from PJ_FUSED_FROM, the chunked mode-L pipeline over the shorter
+    ones, the overflow and long-run lists gathered and verified on the device.
+    Replays equal the oracle; the probe counts repeat (which pairs leave the
+    kernel through the overflow lists depends on timing, so the verification
+    counts may differ); replays whose lists or buffers outgrow the recorded
+    capacities are discarded."""
+    monkeypatch.setenv("PJ_FUSED", mode)
+    probe_counts = ("lookups", "candidates", "hits", "fallback_pairs")
+    cases = [("medium", 8, 2500, True, "0"), ("medium", 8, 2500, True, "80"), ("long", 32, 600, True, "0"),
+             ("short", 4, 3000, False, "16")]
+    for name, tau, n, banded, frm in cases:
+        monkeypatch.setenv("PJ_FUSED_FROM", frm)
+        strings = synth.generate(name, tau, n=n) + [b"", b"xy"]
+        rs = joins(strings, tau)
+        check_replays(rs, cpu_self(strings, tau, banded=banded), f"{name} tau={tau} fused={mode} from {frm}",
+                      probe_counts)
+        assert all(r.stats["fused"] == 1 for r in rs)
+    monkeypatch.setenv("PJ_FUSED_FROM", "0")
+    base = synth.generate("medium", 8, n=1500)
+    strings = base + [base[7]] * 300 + [base[11]] * 40  # long runs and full lists
+    check_replays(joins(strings, 8), cpu_self(strings, 8, banded=True), f"copies fused={mode}", probe_counts)
+    monkeypatch.setenv("PJ_GRAPH_TIGHT", "1")
+    rs = joins(strings, 8, runs=3)
+    assert all(r.stats["graph_replay"] == 0 for r in rs)
+    want = cpu_self(strings, 8, banded=True)
+    assert all(np.array_equal(np.asarray(r.pairs), want) for r in rs)

@@ -391,7 +391,7 @@ def test_autotuned_self_join(monkeypatch, tmp_path):
         assert r2.stats["tune_ms"] == 0.0  # decision cached
         assert (r1.stats["warp_min_len"], r1.stats["verify_block"]) == (r2.stats["warp_min_len"], r2.stats["verify_block"])
     lines = cache.read_text().strip().splitlines()
-    assert len(lines) == 2 and all(line.count("|") == 3 for line in lines)
+    assert len(lines) == 2 and all(line.count("|") == 4 for line in lines)
 
 
 @pytest.mark.parametrize("queued", ["0", "1"])
@@ -578,3 +578,45 @@ def test_center_partition_candidates_match_algorithm():
         assert sel["multi_match"] == M.selection_counts(strings, 4, scheme=scheme)["multi"]
         counts[scheme] = st["tuples"]
     assert counts["center"] < counts["even"]
+
+
+def _copies(strings, n_fam, size, seed):
+    """`size` exact copies of `n_fam` strings of the set, appended."""
+    rng = np.random.default_rng(seed)
+    picks = rng.choice(len(strings), size=n_fam, replace=False).tolist()
+    return strings + [strings[k] for k in picks for _ in range(size)]
+
+
+@pytest.mark.parametrize("mode", ["1", "2"])
+def test_fused_self_join(monkeypatch, mode):
+    """Mode L by the fused persistent kernel (selection, lookups, distinct
+    pairs and verification of a work item in shared memory; thread per pair
+    1, warp per pair 2): the same exact result as the oracle, with items
+    whose distinct pairs overflow the warp's list and posting runs long
+    enough to leave the kernel (copies of a string), with the short probes
+    in the chunked pipeline (PJ_FUSED_FROM), and with an accepted-match
+    buffer that has to grow."""
+    monkeypatch.setenv("PJ_FUSED", mode)
+    cases = [("short2k", 2, 2000, False), ("short", 4, 3000, False), ("medium", 8, 2500, True),
+             ("long", 32, 600, True), ("long", 8, 600, True)]
+    for name, tau, n, banded in cases:
+        strings = synth.generate(name, tau, n=n)
+        r = gpu_self(strings, tau)
+        assert_same(r.pairs, cpu_self(strings, tau, banded=banded), f"{name} tau={tau} fused={mode}")
+        assert r.stats["fused"] == 1 and r.stats["verify_mode"] == 2
+        assert r.stats["distinct_pairs"] > 0 and r.stats["candidates"] >= r.stats["distinct_pairs"]
+    for size in (50, 700):
+        strings = _copies(synth.generate("medium", 8, n=1500), 2, size, seed=size)
+        r = gpu_self(strings, 8)
+        assert_same(r.pairs, cpu_self(strings, 8, banded=True), f"copies {size} fused={mode}")
+    # probes shorter than PJ_FUSED_FROM in the chunked mode-L pipeline, the rest fused
+    for name, tau, n, banded, cut in [("medium", 8, 2500, True, "80"), ("short", 4, 3000, False, "16"),
+                                      ("long", 16, 600, True, "1000")]:
+        monkeypatch.setenv("PJ_FUSED_FROM", cut)
+        strings = synth.generate(name, tau, n=n)
+        assert_same(gpu_self(strings, tau).pairs, cpu_self(strings, tau, banded=banded),
+                    f"{name} tau={tau} fused={mode} from {cut}")
+    monkeypatch.delenv("PJ_FUSED_FROM")
+    monkeypatch.setenv("PJ_ACCEPT_INITIAL", "5")  # the fused launch re-runs into a grown buffer
+    strings = synth.generate("short", 3, n=3000)
+    assert_same(gpu_self(strings, 3).pairs, cpu_self(strings, 3), f"grown buffer fused={mode}")
