@@ -487,28 +487,48 @@ def run_native(args):
 
     # ---- the same join repeated on a resident index: eager, and replayed as
     # one recorded CUDA graph (graph_joins); store build not included
+    def resident_ms(graph, fused=None):
+        """Mean time of the join alone on a resident index (PJ_FUSED=fused
+        overrides the tuned choice of the fused kernel)."""
+        saved = os.environ.get("PJ_FUSED")
+        if fused is not None:
+            os.environ["PJ_FUSED"] = fused
+        try:
+            idx = pj.pj_build_index((d_bytes, d_off), args.tau, results_on_device=True,
+                                    autotune=not args.no_autotune, graph_joins=graph, partition=args.partition)
+            for _ in range(2):  # tuning, then (graph) the recorded join
+                pj.pj_self_join(idx, args.tau).free()
+            ms, replayed, used = [], 0, 0
+            for _ in range(args.steps):
+                flush.zero_()
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+                r = pj.pj_self_join(idx, args.tau)
+                ev1.record(stream)
+                ev1.synchronize()
+                ms.append(ev0.elapsed_time(ev1))
+                replayed += r.stats["graph_replay"]
+                used = r.stats["fused"]
+                r.free()
+            idx.free()
+            return statistics.mean(ms), replayed, used
+        finally:
+            if saved is None:
+                os.environ.pop("PJ_FUSED", None)
+            else:
+                os.environ["PJ_FUSED"] = saved
+
     resident = {}
-    for mode, graph in (("eager", False), ("graph", True)):
-        idx = pj.pj_build_index((d_bytes, d_off), args.tau, results_on_device=True,
-                                autotune=not args.no_autotune, graph_joins=graph, partition=args.partition)
-        for _ in range(2):  # tuning, then (graph) the recorded join
-            pj.pj_self_join(idx, args.tau).free()
-        ms, replayed = [], 0
-        for _ in range(args.steps):
-            flush.zero_()
-            ev0 = torch.cuda.Event(enable_timing=True)
-            ev1 = torch.cuda.Event(enable_timing=True)
-            ev0.record(stream)
-            r = pj.pj_self_join(idx, args.tau)
-            ev1.record(stream)
-            ev1.synchronize()
-            ms.append(ev0.elapsed_time(ev1))
-            replayed += r.stats["graph_replay"]
-            r.free()
-        idx.free()
-        resident[f"{mode}_ms"] = statistics.mean(ms)
-        if graph:
-            resident["graph_replays"] = replayed
+    resident["eager_ms"], _, tuned_fused = resident_ms(False)
+    resident["graph_ms"], resident["graph_replays"], _ = resident_ms(True)
+    resident["choice"] = "fused kernel" if tuned_fused else "chunked pipeline"
+    if len(buf) / max(1, n) >= 32:  # medium and long strings: both forms, side by side
+        if tuned_fused:
+            resident["chunked_eager_ms"] = resident_ms(False, "0")[0]
+            resident["chunked_graph_ms"] = resident_ms(True, "0")[0]
+        resident["fused_thread_graph_ms"] = resident_ms(True, "1")[0]
+        resident["fused_warp_graph_ms"] = resident_ms(True, "2")[0]
     barrier()
 
     found = sum(int(c) for c in counts)
@@ -587,7 +607,9 @@ def run_native(args):
                     "h2d_bytes_per_step": int(buf.nbytes + off.nbytes),
                     "d2h_bytes_per_step": int(e2e_pairs * 12)},
             "resident_join": dict(resident, note="join alone on a resident index, mean over the timed steps; "
-                                                 "graph = one recorded CUDA graph replayed per join"),
+                                                 "graph = one recorded CUDA graph replayed per join; eager/graph "
+                                                 "use the tuned form (choice), chunked_* the chunked pipeline, "
+                                                 "fused_* the fused kernel with a thread / a warp per pair"),
             "gpu_launches": int(launches),
             "clocks": clk,
             "serving": serving,

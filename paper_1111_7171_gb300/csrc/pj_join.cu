@@ -17,6 +17,10 @@
 //   A5/A7  accepted matches (pair key, d_l + d_r) are radix-sorted by key,
 //       each run of equal keys keeps its least ed (the exact ED of the pair),
 //       and runs are compacted by prefix sum into sorted (a, b, ed) records.
+//   A9  k_fused_self runs selection, lookups, distinct-pair formation and
+//       whole-pair verification of the self join in one persistent kernel
+//       (warps pull probes from a device counter); the chunked form above
+//       stays for what it does not keep in shared memory.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>

@@ -216,7 +216,9 @@ __host__ __device__ __forceinline__ uint32_t lookup_key(const ProbeView& v, bool
 // count) is called, in order of p, for every lookup that found postings to
 // verify.  (Loading the presence words of 8 positions back to back, so that
 // their latencies overlap, measured slower: the loop is bound by its integer
-// instructions, and the batch's extra registers cost occupancy.)
+// instructions, and the batch's extra registers cost occupancy.  Testing the
+// whole window's presence bits first and looking up the passing positions
+// after measured 5% faster on long strings at tau 32 and slower elsewhere.)
 template <class F>
 __device__ __forceinline__ void window_lookups(const ProbeView& v, bool self, uint32_t q, int ls, int l, int i, int li,
                                                int lo, int hi, const uint8_t* s, int& err, F f) {
