@@ -50,6 +50,15 @@ UNIT = "pairs/s"
 L2_FLUSH_BYTES = 256 << 20
 OPS_PER_CELL = 6            # integer ops of one DP cell: delta compare, diagonal add, up/left +1, two mins
 SCREEN_BYTES = 16           # one posting record (sid + character signature) read per candidate
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of
+# k_verify_queued on the short workload at 1,000,000 strings and tau 4, where
+# a launch verifies 2^30 candidates: mean of three launches of a one-pass ncu
+# capture of the current kernel (reads 51.1 / 47.9 / 56.9 MB, writes 749.0 /
+# 177.9 / 66.8 MB: the accepted matches and the write-back of lines dirtied
+# before the launch).  The 16-byte posting records (17.2 GB per launch) are
+# read from L2.
+VERIFY_TRAFFIC_SHORT1M_TAU4 = (51.1 + 47.9 + 56.9 + 749.0 + 177.9 + 66.8) / 3 * 1e6
+VERIFY_LAUNCH_CANDIDATES = 1 << 30
 
 
 def parse():
@@ -552,8 +561,14 @@ def run_native(args):
         sm_max = float(peaks.get("sm_max_mhz", 2070.0))
         derived_gcells = cal["sm_count"] * 128 * sm_max * 1e6 / OPS_PER_CELL / 1e9
         achieved = cells / (verify_ms / 1e3) / 1e9
+        headline = (args.workload == "short" and n == 1_000_000 and args.tau == 4 and kernel == "k_verify_queued")
+        traffic = VERIFY_TRAFFIC_SHORT1M_TAU4 if headline else None
         roofline = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": alu_peak_gcells,
-                    "unit": "Gcell/s", "frac": achieved / alu_peak_gcells, "traffic": None,
+                    "unit": "Gcell/s", "frac": achieved / alu_peak_gcells, "traffic": traffic,
+                    "traffic_unit": ("DRAM bytes per launch of 2^30 candidates (ncu dram__bytes_read.sum + "
+                                     "dram__bytes_write.sum, mean of 3 launches); the launch's algorithmic "
+                                     f"record stream is {VERIFY_LAUNCH_CANDIDATES * SCREEN_BYTES / 1e9:.1f} GB, "
+                                     "read from L2") if headline else None,
                     "work": "DP cells evaluated by the verification (counted exactly), per second of verification",
                     "peak_source": f"measured (pj_calibrate): the verification's banded cell recurrence with "
                                    f"operands in registers, {alu_peak_gcells:.0f} Gcell/s at {cal['sm_mhz']:.0f} MHz "
