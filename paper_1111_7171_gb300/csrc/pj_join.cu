@@ -1686,8 +1686,10 @@ static bool fused_self_join(const Ctx& c, const ProbeView& v, AcceptBuf& acc, Co
   Counters saved{};
   PJ_CUDA(cudaMemcpyAsync(&saved, ctr, sizeof(saved), cudaMemcpyDeviceToHost, c.stream));
   c.sync();
+  EventTimer tk(c.stream);  // the kernel alone (PJ_TRACE)
   acc.run(
       [&](AccOut o) {
+        tk.start();
         PJ_CUDA(cudaMemsetAsync(work.p, 0, 3 * sizeof(unsigned long long), c.stream));
         PJ_CUDA(cudaMemsetAsync(ovf.p, 0, FOVF_LISTS * sizeof(unsigned long long), c.stream));
 #define PJ_FORM(W, F)                                                                                          \
@@ -1706,6 +1708,7 @@ static bool fused_self_join(const Ctx& c, const ProbeView& v, AcceptBuf& acc, Co
         PJ_BY_TAU(v.tau, PJ_CALL);
 #undef PJ_CALL
 #undef PJ_FORM
+        tk.stop();
       },
       [&](unsigned long long after) { return 2 * after; });
   unsigned long long n_work[3] = {0, 0, 0}, n_sub[FOVF_LISTS], start[FOVF_LISTS];
@@ -1734,9 +1737,9 @@ static bool fused_self_join(const Ctx& c, const ProbeView& v, AcceptBuf& acc, Co
   }
   if (getenv("PJ_TRACE"))
     fprintf(stderr,
-            "[pj] fused: %llu items of %d probes, %llu distinct pairs in-kernel, %llu to the overflow list, "
-            "%llu long runs (%llu candidates)\n",
-            n_items, ppi, n_work[1], n_ovf, n_heavy, n_hcand);
+            "[pj] fused: probes from %u, %llu items of %d probes, kernel %.3f ms, %llu distinct pairs in-kernel, "
+            "%llu to the overflow list, %llu long runs (%llu candidates)\n",
+            v.pbegin, n_items, ppi, tk.ms(), n_work[1], n_ovf, n_heavy, n_hcand);
   if (sub_max > ovf_cap || n_heavy > heavy_cap || n_ovf + n_hcand > PAIR_MODE_MAX_CANDS) {
     // wind the counters back: the chunked pipeline redoes the join
     PJ_CUDA(cudaMemcpyAsync(ctr, &saved, sizeof(saved), cudaMemcpyHostToDevice, c.stream));
