@@ -1060,12 +1060,11 @@ __global__ void __launch_bounds__(FB) k_fused_self(const ProbeView v, int ppi, i
     __syncwarp();
     // items from both ends in turn: the longest probes (the costliest
     // verifications) and the shortest (the longest posting runs) start first
-    const unsigned long long j = (it & 1) ? n_items - 1 - (it >> 1) : (it >> 1);
+    uint32_t q_beg, q_end;
+    const unsigned long long j = fused_item(it, n_items, v.pbegin, v.pcount, ppi, q_beg, q_end);
     const unsigned sub = (unsigned)(j % FOVF_LISTS);  // neighbouring items (alike in cost) on different lists
     unsigned long long* const ovf_n = ovf + sub;
     unsigned long long* const ovf_keys = ovf + FOVF_LISTS + sub * ovf_cap;
-    const uint32_t q_end = (uint32_t)((unsigned long long)v.pbegin + v.pcount - j * (unsigned long long)ppi);
-    const uint32_t q_beg = q_end > v.pbegin + (uint32_t)ppi ? q_end - (uint32_t)ppi : v.pbegin;
     const int nq = (int)(q_end - q_beg);
     auto group = [&](uint32_t qrel, int g) {
       const uint32_t q = q_beg + qrel;

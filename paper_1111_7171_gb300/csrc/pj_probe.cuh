@@ -211,6 +211,20 @@ __host__ __device__ __forceinline__ uint32_t lookup_key(const ProbeView& v, bool
   return cnt;
 }
 
+// Work item `it` (0 <= it < n_items, n_items = ceil(pcount / ppi)) of the
+// fused self join: the items are handed out from the two ends of the probes'
+// length order in turn (longest, shortest, second longest, ...), so item
+// `it` is position j from the long end (returned) and covers probes
+// [q_beg, q_end), ppi of them except the shortest item.
+__host__ __device__ __forceinline__ unsigned long long fused_item(unsigned long long it, unsigned long long n_items,
+                                                                  uint32_t pbegin, uint32_t pcount, int ppi,
+                                                                  uint32_t& q_beg, uint32_t& q_end) {
+  const unsigned long long j = (it & 1) ? n_items - 1 - (it >> 1) : (it >> 1);
+  q_end = (uint32_t)((unsigned long long)pbegin + pcount - j * (unsigned long long)ppi);
+  q_beg = q_end > pbegin + (uint32_t)ppi ? q_end - (uint32_t)ppi : pbegin;
+  return j;
+}
+
 // The lookups of a group's window: substrings s[p, li], p = lo .. hi, in
 // L_l^i, their keys rolled from one position to the next.  f(p, begin,
 // count) is called, in order of p, for every lookup that found postings to

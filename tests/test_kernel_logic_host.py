@@ -196,3 +196,19 @@ def test_partition_schemes_match_the_oracle(tmp_path):
         assert got == schemes[scheme](length, parts - 1), (scheme, parts, length)
         n += 1
     assert n == 2 * sum(161 - p for p in range(1, 34))
+
+
+def test_fused_work_items_cover_every_probe_once(tmp_path):
+    """The fused self join's work items (fused_item: items from the two ends
+    of the length order in turn) cover every probe of the range exactly once,
+    for probe ranges of 1..300 probes at several starts and 1..40 probes per
+    item."""
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    exe = tmp_path / "fused_items"
+    subprocess.run([nvcc, "-std=c++17", "-O2", "-I", CSRC, "-I", os.path.join(ROOT, "include"), "-o", str(exe),
+                    os.path.join(ROOT, "tests", "host_logic", "fused_items.cu")], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True).stdout.strip()
+    assert out == f"ok {4 * 300 * 40}", out
+
