@@ -122,6 +122,43 @@ def test_full_size_complete_long_tau8():
     assert np.array_equal(pairs, want)
 
 
+@pytest.mark.parametrize("name,tau", [("medium", 4), ("long", 32), ("medium", 8)])
+def test_full_size_graph_replay_and_forms_agree(name, tau, monkeypatch):
+    """At full size, the tuned self join replayed from its recorded CUDA graph
+    (graph_joins; the fused kernel where the tuner picks it), the chunked
+    pipeline (PJ_FUSED=0) and the fused kernel on every probe (PJ_FUSED=1)
+    return the same pair set; that set is checked against the oracle by
+    test_full_size_sampled."""
+    strings = synth.generate(name, tau)
+    buf, off = synth.pack(strings)
+    db = torch.from_numpy(buf).cuda()
+    do = torch.from_numpy(off.astype(np.int64)).cuda()
+
+    def join(graph, fused):
+        if fused is None:
+            monkeypatch.delenv("PJ_FUSED", raising=False)
+        else:
+            monkeypatch.setenv("PJ_FUSED", fused)
+        idx = pj.pj_build_index((db, do), tau, results_on_device=True, autotune=True, graph_joins=graph)
+        try:
+            out = []
+            for _ in range(2 if graph else 1):
+                r = pj.pj_self_join(idx, tau)
+                out.append((r.to_host(), r.stats["graph_replay"]))
+                r.free()
+            return out[-1]
+        finally:
+            idx.free()
+
+    replayed, was_replay = join(True, None)
+    assert was_replay == 1
+    chunked, _ = join(False, "0")
+    fused, _ = join(False, "1")
+    assert len(chunked) > 0
+    assert np.array_equal(replayed, chunked), (name, tau, "graph replay")
+    assert np.array_equal(fused, chunked), (name, tau, "fused kernel")
+
+
 def test_serving_full_size_mixed_tau():
     """The serving workload: 1M short strings resident (tau_max = 4), a stream
     of requests of 1..4096 queries with tau uniform in 1..4, run through the
