@@ -1454,6 +1454,7 @@ struct AcceptBuf {
   DBuf<unsigned long long> key;
   DBuf<uint32_t> ed;
   unsigned long long cap = 0;
+  unsigned long long last = 0;  // accepted count after the last run()
   AcceptBuf(const Ctx& ctx, Counters* counters, unsigned long long initial) : c(ctx), ctr(counters) {
     key.reset(c, initial);
     ed.reset(c, initial);
@@ -1476,12 +1477,19 @@ struct AcceptBuf {
     const unsigned long long before = saved.accepted;
     launch(out());
     const unsigned long long after = read_count();
+    last = after;
     if (after <= cap) return;
     grow(std::max<unsigned long long>(after, want(after)), before);
     PJ_CUDA(cudaMemcpyAsync(ctr, &saved, sizeof(saved), cudaMemcpyHostToDevice, c.stream));
     c.sync();  // `saved` lives on this stack frame
     launch(out());
-    if (read_count() > cap) fail(PJ_ECUDA, "accepted-match buffer overflowed after growing");
+    last = read_count();
+    if (last > cap) fail(PJ_ECUDA, "accepted-match buffer overflowed after growing");
+  }
+  // Grows (keeping the entries so far) to hold `need` entries, before a
+  // launch that would otherwise overflow and run twice.
+  void reserve(unsigned long long need) {
+    if (need > cap) grow(need, std::min(last, cap));
   }
   void grow(unsigned long long new_cap, unsigned long long keep) {
     DBuf<unsigned long long> k2(c, new_cap);
@@ -1779,7 +1787,10 @@ static void probe_and_verify(const Ctx& c, const ProbeView& v0, uint32_t fb_coun
   EventTimer tp(c.stream), tv(c.stream), tf(c.stream);
   const int G = MULTI ? 1 : groups_per_probe(v0.tau, SELF);
   const unsigned long long group_budget = std::min(env_knob("PJ_GROUP_BUDGET", 64ull << 20), 1ull << 31);
-  const unsigned long long launch_cands = env_knob("PJ_LAUNCH_CANDS", 1ull << 30);
+  // candidates per verification launch after the first: one launch unless
+  // PJ_LAUNCH_CANDS asks for more (the accepted-match buffer is sized before
+  // each launch from the rate so far, so launches rarely run twice)
+  const unsigned long long launch_cands = env_knob("PJ_LAUNCH_CANDS", 1ull << 40);
   const uint32_t chunk_items = (uint32_t)std::max<unsigned long long>(1, group_budget / G);
   DBuf<Hit> hits;
   DBuf<uint32_t> gcount, goff;
@@ -1850,6 +1861,11 @@ static void probe_and_verify(const Ctx& c, const ProbeView& v0, uint32_t fb_coun
       const unsigned long long step =
           verified == 0 ? std::min(launch_cands, std::max(1ull << 22, n_cand / 64)) : launch_cands;
       const unsigned long long ce = std::min(warp_range ? n_cand : c_cut, cb + step);
+      if (verified > 0) {  // room for this launch at the rate so far (+25%), for the join's rest if bigger
+        const double rate = (double)acc.last / (double)verified;
+        const double left = (double)(n_cand - cb) + (remaining_groups - 1.0) * (double)n_cand;
+        acc.reserve((unsigned long long)(acc.last + 1.25 * rate * std::max((double)(ce - cb), left)) + (1ull << 20));
+      }
       tv.start();
       acc.run(
           [&](AccOut o) {
