@@ -378,7 +378,9 @@ __global__ void __launch_bounds__(512) k_verify_hits(const ProbeView v, const Hi
 }
 
 // The same verification with a screen and a per-warp queue.  The candidates
-// are dealt to the warps round robin in chunks of Q_CHUNK; a warp walks a
+// are dealt to the warps round robin in chunks of `chunk` (Q_CHUNK, or up to
+// 4 Q_CHUNK for launches long enough that every warp gets thousands of
+// chunks: fewer searches of the candidate offsets); a warp walks a
 // chunk in steps of 32 * S_RUN: in a step, lane l screens candidates base +
 // l + 32 k (k < S_RUN) -- valid sid, not the probe itself, the side bounds
 // of the extension screen -- so that every load of a posting record is one
@@ -397,7 +399,16 @@ constexpr int Q_BLOCK = 256;
 constexpr int Q_WARPS = Q_BLOCK / 32;
 constexpr int S_RUN = 8;                 // candidates one lane screens per step
 constexpr int Q_CAP = 32 * S_RUN + 32;   // < 32 left + up to 32 * S_RUN new
-constexpr unsigned long long Q_CHUNK = 8ull * 32 * S_RUN;  // candidates a warp takes at a time
+constexpr unsigned long long Q_CHUNK = 8ull * 32 * S_RUN;  // candidates a warp takes at a time (at least)
+
+// Chunk of a queued verification launch over n candidates on `grid` blocks:
+// Q_CHUNK, times up to 4 when every warp gets at least 512 chunks of that
+// size (measured on 2.2e10 candidates: 3% less time with 4; on 3e8, where a
+// warp gets 30 chunks, larger chunks unbalance the warps).
+static unsigned long long queued_chunk(unsigned long long n, unsigned grid) {
+  const unsigned long long per_warp = n / ((unsigned long long)grid * Q_WARPS * Q_CHUNK);
+  return Q_CHUNK * std::min<unsigned long long>(4, std::max<unsigned long long>(1, per_warp / 512));
+}
 
 // One lane's hit: index h, its posting for candidate c is rec_base + c
 // (mod 2^32: posting indices are 32-bit), and what the screen needs of it.
@@ -454,7 +465,8 @@ __global__ void __launch_bounds__(Q_BLOCK) k_verify_queued(const ProbeView v, co
                                                             const unsigned long long* __restrict__ cand_off,
                                                             unsigned long long n_hits, unsigned long long c_begin,
                                                             unsigned long long n_cand, AccOut out, Counters* ctr,
-                                                            const unsigned long long* __restrict__ dn) {
+                                                            const unsigned long long* __restrict__ dn,
+                                                            unsigned long long chunk) {
   __shared__ uint32_t q_q[Q_WARPS][Q_CAP];
   __shared__ uint32_t q_sid[Q_WARPS][Q_CAP];
   __shared__ uint32_t q_pi[Q_WARPS][Q_CAP];
@@ -471,9 +483,9 @@ __global__ void __launch_bounds__(Q_BLOCK) k_verify_queued(const ProbeView v, co
   int qn = 0;  // the same in every lane
   LaneHit lh;
   lh.h = UINT32_MAX;
-  // chunks of Q_CHUNK candidates, dealt to the warps round robin
-  for (unsigned long long r0 = c_begin + warp * Q_CHUNK; r0 < n_cand; r0 += n_warps * Q_CHUNK) {
-    const unsigned long long r1 = min(n_cand, r0 + Q_CHUNK);
+  // chunks of `chunk` candidates, dealt to the warps round robin
+  for (unsigned long long r0 = c_begin + warp * chunk; r0 < n_cand; r0 += n_warps * chunk) {
+    const unsigned long long r1 = min(n_cand, r0 + chunk);
     // each lane's hit: its first candidate's, found by a warp search; then
     // every lane walks forward on its own as its candidates advance
     unsigned long long l_hi;  // first candidate after the lane's hit
@@ -1310,7 +1322,7 @@ static void launch_verify(const Ctx& c, const ProbeView& v, const Hit* hits, con
                                         (c_end - c_begin + (unsigned long long)Q_BLOCK * S_RUN - 1) /
                                             ((unsigned long long)Q_BLOCK * S_RUN), Q_BLOCK);
     k_verify_queued<MAXW, SELF, MULTI><<<gq, Q_BLOCK, 0, c.stream>>>(v, hits, off, n_hits, c_begin, c_end, out, ctr,
-                                                                    nullptr);
+                                                                    nullptr, queued_chunk(c_end - c_begin, gq));
     PJ_LAUNCHED("k_verify_queued");
     return;
   }
@@ -1850,6 +1862,18 @@ static void probe_and_verify(const Ctx& c, const ProbeView& v0, uint32_t fb_coun
       done += v.pcount;
       continue;
     }
+    if (verified == 0) {
+      // room for 1/64 of the candidates before the first launch: growing the
+      // buffer between launches measured slower than the same allocation
+      // made here (a few milliseconds at a billion candidates)
+      unsigned long long room = std::min(n_cand / 64, 1ull << 30);
+      if (c.budget) {
+        std::lock_guard<std::mutex> g(c.budget->mu);
+        const size_t left = c.budget->limit > c.budget->cur ? c.budget->limit - c.budget->cur : 0;
+        room = std::min<unsigned long long>(room, left / 8 / 12);
+      }
+      acc.reserve(room);
+    }
     // candidates [c_cut, n_cand) belong to long probes: one warp per candidate
     unsigned long long c_cut = n_cand;
     const uint32_t q_cut = aligned_cut(v, v.warp_q_cut);
@@ -1946,10 +1970,16 @@ static void run_join(const Ctx& c, const ProbeView& v, bool self, uint32_t fb_co
   void* host_block = nullptr;  // host results written by the emit kernel (mapped pool block)
   size_t host_got = 0;
   if (nacc > 0) {
-    radix_sort_pairs<unsigned long long>(c, acc_key.p, acc_ed.p, nacc, v.key_shift + a_bits);
+    // sorted into whichever buffer pair the last pass wrote (no copy back)
+    DBuf<unsigned long long> key2(c, nacc);
+    DBuf<uint32_t> ed2(c, nacc);
+    const bool second = radix_sort_pairs_dn<unsigned long long>(c, acc_key.p, acc_ed.p, key2.p, ed2.p, nacc,
+                                                                nullptr, v.key_shift + a_bits);
+    const unsigned long long* skeys = second ? key2.p : acc_key.p;
+    const uint32_t* seds = second ? ed2.p : acc_ed.p;
     trace_mark(c, "join: sort accepted");
     DBuf<uint32_t> flags(c, nacc), pos(c, nacc);
-    k_run_heads<<<ceil_div(nacc, 256), 256, 0, c.stream>>>(acc_key.p, nacc, flags.p, nullptr);
+    k_run_heads<<<ceil_div(nacc, 256), 256, 0, c.stream>>>(skeys, nacc, flags.p, nullptr);
     PJ_LAUNCHED("k_run_heads");
     exclusive_scan<uint32_t>(c, flags.p, pos.p, nacc);
     uint32_t last[2] = {0, 0};
@@ -1973,8 +2003,8 @@ static void run_join(const Ctx& c, const ProbeView& v, bool self, uint32_t fb_co
       pairs.reset(c, count);
       dst = pairs.p;
     }
-    k_emit_pairs<<<ceil_div(nacc, 256), 256, 0, c.stream>>>(acc_key.p, acc_ed.p, flags.p, pos.p, nacc, v.key_shift,
-                                                             dst, nullptr, count);
+    k_emit_pairs<<<ceil_div(nacc, 256), 256, 0, c.stream>>>(skeys, seds, flags.p, pos.p, nacc, v.key_shift, dst,
+                                                             nullptr, count);
     PJ_LAUNCHED("k_emit_pairs");
   }
   td.stop();
@@ -2441,6 +2471,7 @@ struct SelfPlan {
   uint32_t fb_count = 0;
   int a_bits = 0;
   unsigned long long n_groups = 0, cap_hits = 0, cap_cands = 0, cap_acc = 0, cap_pairs = 0;
+  unsigned long long n_cand = 0;  // the eager run's candidates (sets the verification chunk)
   DBuf<unsigned char> counters, arena;
   DBuf<PlanSizes> sizes;
   DBuf<unsigned long long> nuniq, gmask, hcnt, hoff, pk0, pk1, ukeys, ak0, ak1;
@@ -2599,7 +2630,7 @@ static void record_self_plan(const Ctx& c, const ProbeView& v, SelfPlan& P) {
   do {                                                                                                         \
     const unsigned gv = persistent_grid(k_verify_queued<W, true, false>, ~0ull >> 8, Q_BLOCK);                  \
     k_verify_queued<W, true, false><<<gv, Q_BLOCK, 0, c.stream>>>(v, P.hits.p, P.hoff.p, P.cap_hits, 0, 0, acc,  \
-                                                                  ctr, &sz->hits);                             \
+                                                                  ctr, &sz->hits, queued_chunk(P.n_cand, gv));  \
     PJ_LAUNCHED("k_verify_queued");                                                                            \
   } while (0)
     PJ_BY_TAU(v.tau, PJ_CALL);
@@ -2701,6 +2732,7 @@ static std::shared_ptr<SelfPlan> make_self_plan(pj_index& idx, const ProbeView& 
   P->n_groups = n_groups;
   P->cap_hits = with_slack(st.hits);
   P->cap_cands = tr.pair_mode ? with_slack(st.candidates) : 1;
+  P->n_cand = st.candidates;
   P->cap_acc = std::min<unsigned long long>(0xFFFFFFFFull, with_slack(st.accepted));
   P->cap_pairs = with_slack(pairs);
   const Ctx& c = P->ctx;
@@ -3130,7 +3162,7 @@ void record_query_plan(const Ctx& c, const pj_index& idx, const PlanDev& d) {
   do {                                                                                                         \
     const unsigned gv = persistent_grid(k_verify_queued<W, false, true>, ~0ull >> 8, Q_BLOCK);                  \
     k_verify_queued<W, false, true><<<gv, Q_BLOCK, 0, c.stream>>>(v, d.hits, d.hoff, d.cap_hits, 0, 0, acc, ctr, \
-                                                                  &sz->hits);                                  \
+                                                                  &sz->hits, Q_CHUNK);                         \
     PJ_LAUNCHED("k_verify_queued");                                                                            \
     if (has_short) {                                                                                           \
       const unsigned gf = persistent_grid(k_fallback<W, false, true>, (d.cap_q + BLOCK - 1) / BLOCK);           \
