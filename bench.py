@@ -50,15 +50,13 @@ UNIT = "pairs/s"
 L2_FLUSH_BYTES = 256 << 20
 OPS_PER_CELL = 6            # integer ops of one DP cell: delta compare, diagonal add, up/left +1, two mins
 SCREEN_BYTES = 16           # one posting record (sid + character signature) read per candidate
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of
-# k_verify_queued on the short workload at 1,000,000 strings and tau 4, where
-# a launch verifies 2^30 candidates: mean of three launches of a one-pass ncu
-# capture of the current kernel (reads 51.1 / 47.9 / 56.9 MB, writes 749.0 /
-# 177.9 / 66.8 MB: the accepted matches and the write-back of lines dirtied
-# before the launch).  The 16-byte posting records (17.2 GB per launch) are
-# read from L2.
-VERIFY_TRAFFIC_SHORT1M_TAU4 = (51.1 + 47.9 + 56.9 + 749.0 + 177.9 + 66.8) / 3 * 1e6
-VERIFY_LAUNCH_CANDIDATES = 1 << 30
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of k_verify_queued
+# over one self join of the short workload at 1,000,000 strings and tau 4, from
+# a one-pass ncu capture of the current kernel: the join's short first launch
+# (0.022 GB read, 1.244 GB written: mostly the write-back of the hits written
+# just before it) and its one long launch (4.343 GB read, 1.310 GB written).
+# The 16-byte posting records the join screens (356 GB) are read from L2.
+VERIFY_TRAFFIC_SHORT1M_TAU4 = (0.022 + 1.244 + 4.343 + 1.310) * 1e9
 
 
 def parse():
@@ -565,10 +563,10 @@ def run_native(args):
         traffic = VERIFY_TRAFFIC_SHORT1M_TAU4 if headline else None
         roofline = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": alu_peak_gcells,
                     "unit": "Gcell/s", "frac": achieved / alu_peak_gcells, "traffic": traffic,
-                    "traffic_unit": ("DRAM bytes per launch of 2^30 candidates (ncu dram__bytes_read.sum + "
-                                     "dram__bytes_write.sum, mean of 3 launches); the launch's algorithmic "
-                                     f"record stream is {VERIFY_LAUNCH_CANDIDATES * SCREEN_BYTES / 1e9:.1f} GB, "
-                                     "read from L2") if headline else None,
+                    "traffic_unit": ("DRAM bytes of the verification kernel per join, both launches (ncu "
+                                     "dram__bytes_read.sum + dram__bytes_write.sum), like `achieved`, which is per "
+                                     "second of the join's verification; its algorithmic record stream is "
+                                     f"{cands * SCREEN_BYTES / 1e9:.0f} GB, read from L2") if headline else None,
                     "work": "DP cells evaluated by the verification (counted exactly), per second of verification",
                     "peak_source": f"measured (pj_calibrate): the verification's banded cell recurrence with "
                                    f"operands in registers, {alu_peak_gcells:.0f} Gcell/s at {cal['sm_mhz']:.0f} MHz "
