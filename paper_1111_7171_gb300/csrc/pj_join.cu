@@ -1700,8 +1700,16 @@ static bool fused_self_join(const Ctx& c, const ProbeView& v, AcceptBuf& acc, Co
   const unsigned long long n_items = ((unsigned long long)v.pcount + ppi - 1) / ppi;
   const unsigned long long ovf_cap = fused_ovf_cap(v);
   const unsigned long long heavy_cap = fused_heavy_cap(v);
-  DBuf<unsigned long long> work(c, 3), ovf(c, FOVF_LISTS + FOVF_LISTS * ovf_cap);
-  DBuf<Hit> heavy(c, heavy_cap);
+  DBuf<unsigned long long> work, ovf;
+  DBuf<Hit> heavy;
+  try {  // lists the device (or its budget) cannot hold: the chunked pipeline instead
+    work.reset(c, 3);
+    ovf.reset(c, FOVF_LISTS + FOVF_LISTS * ovf_cap);
+    heavy.reset(c, heavy_cap);
+  } catch (const Error& e) {
+    if (e.code != PJ_ENOMEM) throw;
+    return false;
+  }
   Counters saved{};
   PJ_CUDA(cudaMemcpyAsync(&saved, ctr, sizeof(saved), cudaMemcpyDeviceToHost, c.stream));
   c.sync();
