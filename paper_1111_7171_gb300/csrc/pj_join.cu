@@ -1297,6 +1297,45 @@ __global__ void k_emit_pairs(const unsigned long long* __restrict__ keys, const 
   }
 }
 
+// The packed form of the accepted matches for the final sort: the pair key
+// with ed in its top 6 bits (pair keys of at most PACKED_KEY_BITS bits,
+// ed <= tau <= 32).  Runs are then told apart by the low bits, and each
+// run's least ed is the least top field.
+constexpr int PACKED_KEY_BITS = 58;
+
+__global__ void k_pack_ed(unsigned long long* __restrict__ keys, const uint32_t* __restrict__ eds,
+                          unsigned long long n) {
+  for (unsigned long long k = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (unsigned long long)gridDim.x * blockDim.x)
+    keys[k] |= (unsigned long long)eds[k] << PACKED_KEY_BITS;
+}
+
+__global__ void k_run_heads_masked(const unsigned long long* __restrict__ keys, unsigned long long n,
+                                   unsigned long long mask, uint32_t* __restrict__ flags) {
+  for (unsigned long long k = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (unsigned long long)gridDim.x * blockDim.x)
+    flags[k] = (k == 0 || ((keys[k] ^ keys[k - 1]) & mask) != 0) ? 1u : 0u;
+}
+
+__global__ void k_emit_packed(const unsigned long long* __restrict__ keys, const uint32_t* __restrict__ flags,
+                              const uint32_t* __restrict__ pos, unsigned long long n, int key_shift,
+                              pj_pair* __restrict__ out, unsigned long long out_cap) {
+  constexpr unsigned long long M = (1ull << PACKED_KEY_BITS) - 1;
+  for (unsigned long long k = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (unsigned long long)gridDim.x * blockDim.x) {
+    if (!flags[k] || pos[k] >= out_cap) continue;
+    const unsigned long long key = keys[k] & M;
+    uint32_t ed = (uint32_t)(keys[k] >> PACKED_KEY_BITS);
+    for (unsigned long long j = k + 1; j < n && (keys[j] & M) == key; ++j)
+      ed = min(ed, (uint32_t)(keys[j] >> PACKED_KEY_BITS));
+    pj_pair pr;
+    pr.a = (uint32_t)(key >> key_shift);
+    pr.b = (uint32_t)(key & ((1ull << key_shift) - 1));
+    pr.ed = ed;
+    out[pos[k]] = pr;
+  }
+}
+
 // ------------------------------------------------------------- launch -----
 
 // Grid for grid-stride loops over `cap` items, 256 threads a block: one wave
@@ -1978,17 +2017,28 @@ static void run_join(const Ctx& c, const ProbeView& v, bool self, uint32_t fb_co
   void* host_block = nullptr;  // host results written by the emit kernel (mapped pool block)
   size_t host_got = 0;
   if (nacc > 0) {
-    // sorted into whichever buffer pair the last pass wrote (no copy back)
+    const int kbits = v.key_shift + a_bits;
+    // ed rides in the key's top bits when the pair key leaves room: the sort
+    // then moves 8 bytes per match instead of 12
+    const bool packed = kbits <= PACKED_KEY_BITS;
     DBuf<unsigned long long> key2(c, nacc);
-    DBuf<uint32_t> ed2(c, nacc);
-    const bool second = radix_sort_pairs_dn<unsigned long long>(c, acc_key.p, acc_ed.p, key2.p, ed2.p, nacc,
-                                                                nullptr, v.key_shift + a_bits);
+    DBuf<uint32_t> ed2;
+    if (packed) {
+      k_pack_ed<<<ceil_div(nacc, 256), 256, 0, c.stream>>>(acc_key.p, acc_ed.p, nacc);
+      PJ_LAUNCHED("k_pack_ed");
+    } else {
+      ed2.reset(c, nacc);
+    }
+    // sorted into whichever buffer (pair) the last pass wrote (no copy back)
+    const bool second = radix_sort_pairs_dn<unsigned long long>(c, acc_key.p, packed ? nullptr : acc_ed.p, key2.p,
+                                                                packed ? nullptr : ed2.p, nacc, nullptr, kbits);
     const unsigned long long* skeys = second ? key2.p : acc_key.p;
-    const uint32_t* seds = second ? ed2.p : acc_ed.p;
+    const uint32_t* seds = packed ? nullptr : second ? ed2.p : acc_ed.p;
+    const unsigned long long kmask = packed ? (1ull << PACKED_KEY_BITS) - 1 : ~0ull;
     trace_mark(c, "join: sort accepted");
     DBuf<uint32_t> flags(c, nacc), pos(c, nacc);
-    k_run_heads<<<ceil_div(nacc, 256), 256, 0, c.stream>>>(skeys, nacc, flags.p, nullptr);
-    PJ_LAUNCHED("k_run_heads");
+    k_run_heads_masked<<<ceil_div(nacc, 256), 256, 0, c.stream>>>(skeys, nacc, kmask, flags.p);
+    PJ_LAUNCHED("k_run_heads_masked");
     exclusive_scan<uint32_t>(c, flags.p, pos.p, nacc);
     uint32_t last[2] = {0, 0};
     PJ_CUDA(cudaMemcpyAsync(&last[0], pos.p + nacc - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.stream));
@@ -2011,9 +2061,14 @@ static void run_join(const Ctx& c, const ProbeView& v, bool self, uint32_t fb_co
       pairs.reset(c, count);
       dst = pairs.p;
     }
-    k_emit_pairs<<<ceil_div(nacc, 256), 256, 0, c.stream>>>(skeys, seds, flags.p, pos.p, nacc, v.key_shift, dst,
-                                                             nullptr, count);
-    PJ_LAUNCHED("k_emit_pairs");
+    if (packed) {
+      k_emit_packed<<<ceil_div(nacc, 256), 256, 0, c.stream>>>(skeys, flags.p, pos.p, nacc, v.key_shift, dst, count);
+      PJ_LAUNCHED("k_emit_packed");
+    } else {
+      k_emit_pairs<<<ceil_div(nacc, 256), 256, 0, c.stream>>>(skeys, seds, flags.p, pos.p, nacc, v.key_shift, dst,
+                                                               nullptr, count);
+      PJ_LAUNCHED("k_emit_pairs");
+    }
   }
   td.stop();
   tm.dedupe = td.ms();

@@ -123,7 +123,8 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const K* __restrict__ ke
   hist[(size_t)tid * ntiles + blockIdx.x] = h[tid];
 }
 
-template <class K>
+// VALS false: keys only (vin, vout unused).
+template <class K, bool VALS>
 __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
                                                            K* __restrict__ kout, uint32_t* __restrict__ vout,
                                                            size_t n, int shift, const uint32_t* __restrict__ offs,
@@ -135,7 +136,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const K* __restrict__
   __shared__ uint32_t wcnt[RS_WARPS][256];
   __shared__ uint32_t local_start[256], global_start[256];
   __shared__ K skey[RS_TILE];
-  __shared__ uint32_t sval[RS_TILE];
+  __shared__ uint32_t sval[VALS ? RS_TILE : 1];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   n = dev_count(n, n_dev);
   if ((size_t)blockIdx.x * RS_TILE >= n) return;
@@ -152,7 +153,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const K* __restrict__
     const size_t i = wbase + (size_t)r * 32 + lane;
     const bool valid = i < n;
     key[r] = valid ? kin[i] : K(0);
-    val[r] = valid ? vin[i] : 0u;
+    val[r] = (VALS && valid) ? vin[i] : 0u;
     const unsigned d = valid ? ((unsigned)(key[r] >> shift) & 0xFFu) : 256u + lane;
     const unsigned peers = __match_any_sync(FULL, d);
     const int leader = __ffs(peers) - 1;
@@ -194,7 +195,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const K* __restrict__
       const unsigned d = (unsigned)(key[r] >> shift) & 0xFFu;
       const uint32_t lp = local_start[d] + wcnt[warp][d] + rank[r];
       skey[lp] = key[r];
-      sval[lp] = val[r];
+      if (VALS) sval[lp] = val[r];
     }
   }
   __syncthreads();
@@ -204,7 +205,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const K* __restrict__
     const unsigned d = (unsigned)(k >> shift) & 0xFFu;
     const uint32_t pos = global_start[d] + (uint32_t)(j - (int)local_start[d]);
     kout[pos] = k;
-    vout[pos] = sval[j];
+    if (VALS) vout[pos] = sval[j];
   }
 }
 
@@ -261,7 +262,11 @@ bool radix_sort_pairs_dn(const Ctx& c, K* keys, uint32_t* vals, K* keys2, uint32
     k_rs_hist<K><<<ntiles, RS_THREADS, 0, c.stream>>>(ka, cap, shift, hist.p, ntiles, n_dev);
     PJ_LAUNCHED("k_rs_hist");
     exclusive_scan<uint32_t>(c, hist.p, offs.p, (size_t)256 * ntiles);
-    k_rs_scatter<K><<<ntiles, RS_THREADS, 0, c.stream>>>(ka, va, kb, vb, cap, shift, offs.p, ntiles, n_dev);
+    if (vals)
+      k_rs_scatter<K, true><<<ntiles, RS_THREADS, 0, c.stream>>>(ka, va, kb, vb, cap, shift, offs.p, ntiles, n_dev);
+    else
+      k_rs_scatter<K, false><<<ntiles, RS_THREADS, 0, c.stream>>>(ka, nullptr, kb, nullptr, cap, shift, offs.p, ntiles,
+                                                                 n_dev);
     PJ_LAUNCHED("k_rs_scatter");
     K* tk = ka; ka = kb; kb = tk;
     uint32_t* tv = va; va = vb; vb = tv;

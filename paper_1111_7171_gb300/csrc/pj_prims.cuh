@@ -20,7 +20,8 @@ void radix_sort_pairs(const Ctx& c, K* keys, uint32_t* vals, size_t n, int nbits
 // (n_dev NULL: all cap).  exclusive_scan_dn also writes the sum of those
 // items to *total when total is not NULL.  radix_sort_pairs_dn ping-pongs
 // between (keys, vals) and (keys2, vals2) and returns true when the sorted
-// pairs end up in the second pair of arrays.
+// pairs end up in the second pair of arrays; with vals NULL it sorts the
+// keys alone (vals2 unused).
 template <class T>
 void exclusive_scan_dn(const Ctx& c, const T* in, T* out, size_t cap, const unsigned long long* n_dev,
                        unsigned long long* total);
