@@ -275,7 +275,9 @@ def test_stats_timings_and_launch_counter():
 
 def test_chunked_probe_multi_launch_and_buffer_growth(monkeypatch):
     """Small probe chunks, small verification launches and a tiny initial
-    accepted-match buffer must give the same exact result."""
+    accepted-match buffer (with and without the room reserved before the
+    first launch: launches that overflow it run again into a grown buffer)
+    must give the same exact result."""
     strings = synth.generate("short", 3, n=5000)
     want = cpu_self(strings, 3)
     monkeypatch.setenv("PJ_GROUP_BUDGET", "3000")
@@ -283,6 +285,12 @@ def test_chunked_probe_multi_launch_and_buffer_growth(monkeypatch):
     monkeypatch.setenv("PJ_ACCEPT_INITIAL", "7")
     r = gpu_self(strings, 3)
     assert_same(r.pairs, want, "chunked")
+    monkeypatch.setenv("PJ_ACCEPT_RESERVE", "0")
+    assert_same(gpu_self(strings, 3).pairs, want, "chunked, buffer grown on overflow")
+    monkeypatch.delenv("PJ_GROUP_BUDGET")
+    monkeypatch.delenv("PJ_LAUNCH_CANDS")
+    assert_same(gpu_self(strings, 3).pairs, want, "one launch, buffer grown on overflow")
+    monkeypatch.delenv("PJ_ACCEPT_RESERVE")
     R, S = _rs_sets(5, 2)
     rb, ro = synth.pack(R)
     sb, so = synth.pack(S)
