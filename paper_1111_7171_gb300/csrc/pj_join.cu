@@ -1939,8 +1939,8 @@ static void probe_and_verify(const Ctx& c, const ProbeView& v0, uint32_t fb_coun
     if (SELF && !MULTI && q_cut < v.pbegin + v.pcount) c_cut = first_candidate_of(c, hits, off, n_hits, n_cand, q_cut);
     for (unsigned long long cb = 0; cb < n_cand;) {
       const bool warp_range = cb >= c_cut;
-      // the join's first launch is short, so that the accepted-match buffer is
-      // sized from its acceptance rate before the long launches run
+      // a big join's first launch is short, so that the accepted-match buffer
+      // is sized from its acceptance rate before the long launch runs
       const unsigned long long step =
           verified == 0 && sizing ? std::min(launch_cands, std::max(1ull << 22, n_cand / 64)) : launch_cands;
       const unsigned long long ce = std::min(warp_range ? n_cand : c_cut, cb + step);
